@@ -1,0 +1,234 @@
+"""TEST INFRASTRUCTURE ONLY: the FP64 CPU oracle for the KBE hot path.
+
+A ctypes wrapper around ``kbe_oracle.cpp``, a plain, slow, obviously correct
+C++ restatement of the paper's definitions (arXiv 2405.08737): the
+interpolatory quadrature weights (Sec. 3.2, Eq. weights), the second-Born
+self-energy (Sec. 2, Eq. SE), the history integrals of Eq. (KBE2) and
+Eq. (KBE1), and an integral-form Adams stepper built on them.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this module.  The
+product package never imports it and shares no code with it.
+
+Array conventions (input format only): two-time arrays are complex128
+``[tri(N), M, M]`` holding the lower triangle ``r >= c`` at block
+``r*(r+1)/2 + c``; ``L = G^<``, ``R = G^R`` with ``R(r,r) = -i*1``.
+Self-energy rows are ``[n+1, M, M]``; history slices ``[2, n+1, M, M]``
+with ``s = 0`` for ``<`` and ``s = 1`` for ``>``.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kbe_oracle.cpp")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile the oracle with g++ (portable flags, OpenMP)."""
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-fopenmp", "-fPIC",
+                           "-shared", "-o", tmp, _SRC])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_SO)
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError("oracle %s rejected its arguments (rc=%d)" % (what, rc))
+
+
+def threads_available():
+    return int(lib().orc_threads_available())
+
+
+def gauss_legendre(q):
+    x = np.zeros(q)
+    w = np.zeros(q)
+    _check(lib().orc_gauss_legendre(ctypes.c_int(q), _p(x), _p(w)), "gauss_legendre")
+    return x, w
+
+
+def lagrange_weights(tau, lo, hi):
+    """Weights of the interpolatory rule on nodes ``tau`` over [lo, hi]."""
+    tau = _f64(tau)
+    w = np.zeros(len(tau))
+    _check(lib().orc_lagrange_weights(_p(tau), ctypes.c_int(len(tau) - 1),
+                                      ctypes.c_double(lo), ctypes.c_double(hi), _p(w)),
+           "lagrange_weights")
+    return w
+
+
+def composite_row(t, order, n):
+    """w_{n,m}, m = 0..n (Sec. 3.2), as a direct sum over intervals."""
+    t, order = _f64(t), _i32(order)
+    row = np.zeros(n + 1)
+    _check(lib().orc_composite_row(_p(t), _p(order), ctypes.c_int(n), _p(row)), "composite_row")
+    return row
+
+
+def local_U4(U):
+    """Four-index tensor U_abcd = U_a delta_abcd of a local interaction."""
+    U = np.asarray(U, dtype=np.float64)
+    M = len(U)
+    U4 = np.zeros((M, M, M, M))
+    for a in range(M):
+        U4[a, a, a, a] = U[a]
+    return U4
+
+
+def sigma_row(U4, n, L, R):
+    """Row n of Eq. (SE) for a general real four-index tensor."""
+    U4 = _f64(U4)
+    M = U4.shape[0]
+    L, R = _c128(L), _c128(R)
+    Sl = np.zeros((n + 1, M, M), np.complex128)
+    Sg = np.zeros((n + 1, M, M), np.complex128)
+    _check(lib().orc_sigma_row(ctypes.c_int(M), ctypes.c_int(n), _p(U4), _p(L), _p(R),
+                               _p(Sl), _p(Sg)), "sigma_row")
+    return Sl, Sg
+
+
+def history_slice(t, order, n, L, R, Sl, Sg, nthreads=1):
+    """I^s(n,c) of Eq. (KBE2) for s in {<,>}, c = 0..n; [2, n+1, M, M]."""
+    t, order = _f64(t), _i32(order)
+    L, R, Sl, Sg = _c128(L), _c128(R), _c128(Sl), _c128(Sg)
+    M = L.shape[-1]
+    out = np.zeros((2, n + 1, M, M), np.complex128)
+    _check(lib().orc_history_slice(ctypes.c_int(M), ctypes.c_int(n), _p(t), _p(order), _p(L), _p(R),
+                                   _p(Sl), _p(Sg), _p(out), ctypes.c_int(nthreads)), "history_slice")
+    return out
+
+
+def history_columns(t, order, n, L, R, Sl, Sg, cols, nthreads=1):
+    """The history slice at the listed output columns only; [2, len(cols), M, M]."""
+    t, order = _f64(t), _i32(order)
+    L, R, Sl, Sg = _c128(L), _c128(R), _c128(Sl), _c128(Sg)
+    cols = _i32(cols)
+    M = L.shape[-1]
+    out = np.zeros((2, len(cols), M, M), np.complex128)
+    _check(lib().orc_history_columns(ctypes.c_int(M), ctypes.c_int(n), _p(t), _p(order), _p(L), _p(R),
+                                     _p(Sl), _p(Sg), _p(cols), ctypes.c_int(len(cols)), _p(out),
+                                     ctypes.c_int(nthreads)), "history_columns")
+    return out
+
+
+def kbe1_slice(t, order, n, L, R, Sl, Sg, nthreads=1):
+    """Lesser Eq. (KBE1) history integrals at (t_c, t_n), c = 0..n; [n+1, M, M]."""
+    t, order = _f64(t), _i32(order)
+    L, R, Sl, Sg = _c128(L), _c128(R), _c128(Sl), _c128(Sg)
+    M = L.shape[-1]
+    out = np.zeros((n + 1, M, M), np.complex128)
+    _check(lib().orc_kbe1_slice(ctypes.c_int(M), ctypes.c_int(n), _p(t), _p(order), _p(L), _p(R),
+                                _p(Sl), _p(Sg), _p(out), ctypes.c_int(nthreads)), "kbe1_slice")
+    return out
+
+
+def _pulse4(pulse):
+    if pulse is None:  # no field: E0 = 0 (sigma = 1 keeps the envelope finite)
+        return _f64([0.0, 0.0, 1.0, 0.0])
+    return _f64([pulse["E0"], pulse["t0"], pulse["sigma"], pulse["omega"]])
+
+
+def rhs_row(j, t, order, h0, U, v, pulse, L, R, nthreads=1):
+    """F^s(j,c) = -i(eps(t_j) G^s(j,c) + I^s(j,c)), c = 0..j; [2, j+1, M, M]."""
+    t, order = _f64(t), _i32(order)
+    h0, L, R = _c128(h0), _c128(L), _c128(R)
+    U, v = _f64(U), _f64(v)
+    M = h0.shape[0]
+    F = np.zeros((2, j + 1, M, M), np.complex128)
+    _check(lib().orc_rhs_row(ctypes.c_int(M), ctypes.c_int(j), _p(t), _p(order), _p(h0), _p(U), _p(v),
+                             _p(_pulse4(pulse)), _p(L), _p(R), _p(F), ctypes.c_int(nthreads)), "rhs_row")
+    return F
+
+
+def max_order(order, n_end):
+    return max(1, int(np.max(order[1:n_end]))) if n_end > 1 else 1
+
+
+def f_rows_needed(order, n_start, n_end):
+    """Right-hand-side rows that the stepper needs on entry at n_start."""
+    K = max_order(order, n_end)
+    return list(range(max(0, n_start - K), n_start))
+
+
+def run(t, order, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1):
+    """KBE steps n_start..n_end-1.  ``L``/``R`` are triangles of n_end rows,
+    filled for rows < n_start; ``F_rows`` maps each row j of
+    ``f_rows_needed`` to its [2, j+1, M, M] right-hand side.  Returns
+    (L, R, I_last) with the history slice of the last row."""
+    t, order = _f64(t), _i32(order)
+    h0 = _c128(h0)
+    U, v = _f64(U), _f64(v)
+    M = h0.shape[0]
+    L = np.array(L, dtype=np.complex128, copy=True)
+    R = np.array(R, dtype=np.complex128, copy=True)
+    need = f_rows_needed(order, n_start, n_end)
+    Fin = np.concatenate([_c128(F_rows[j]).ravel() for j in need]) if need else np.zeros(1, np.complex128)
+    I_last = np.zeros((2, n_end, M, M), np.complex128)
+    _check(lib().orc_run(ctypes.c_int(M), ctypes.c_int(n_start), ctypes.c_int(n_end), _p(t), _p(order),
+                         _p(h0), _p(U), _p(v), _p(_pulse4(pulse)), ctypes.c_int(P), _p(L), _p(R),
+                         _p(Fin), _p(I_last), ctypes.c_int(nthreads)), "run")
+    return L, R, I_last
+
+
+def run_tangent(t, order, h0, U, dU, v, pulse, dE0, P, L, R, F_rows, n_start, n_end, nthreads=1):
+    """Forward-mode derivative of ``run`` along (dU, dE0).  Returns the value
+    and derivative of the final diagonal block L(n_end-1, n_end-1)."""
+    t, order = _f64(t), _i32(order)
+    h0 = _c128(h0)
+    U, dU, v = _f64(U), _f64(dU), _f64(v)
+    M = h0.shape[0]
+    L, R = _c128(L), _c128(R)
+    need = f_rows_needed(order, n_start, n_end)
+    Fin = np.concatenate([_c128(F_rows[j]).ravel() for j in need]) if need else np.zeros(1, np.complex128)
+    Lv = np.zeros((M, M), np.complex128)
+    Ld = np.zeros((M, M), np.complex128)
+    _check(lib().orc_run_tangent(ctypes.c_int(M), ctypes.c_int(n_start), ctypes.c_int(n_end), _p(t),
+                                 _p(order), _p(h0), _p(U), _p(dU), _p(v), _p(_pulse4(pulse)),
+                                 ctypes.c_double(dE0), ctypes.c_int(P), _p(L), _p(R), _p(Fin), _p(Lv),
+                                 _p(Ld), ctypes.c_int(nthreads)), "run_tangent")
+    return Lv, Ld
+
+
+def initial_rhs(t, order, h0, U, v, pulse, rho0):
+    """Row 0 of a run from an uncorrelated state: L(0,0) = i rho0,
+    R(0,0) = -i, and its right-hand side (the history integral over a
+    zero-length interval vanishes)."""
+    h0 = _c128(h0)
+    M = h0.shape[0]
+    L0 = (1j * _c128(rho0)).reshape(1, M, M)
+    R0 = (-1j * np.eye(M)).reshape(1, M, M).astype(np.complex128)
+    F0 = rhs_row(0, t, order, h0, U, v, pulse, L0, R0)
+    return L0, R0, F0

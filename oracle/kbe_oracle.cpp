@@ -1,0 +1,641 @@
+// kbe_oracle.cpp -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, FP64 CPU reference for the hot path of the adaptive
+// Kadanoff-Baym solver of Blommel, Gardner, Woodward and Gull
+// (arXiv 2405.08737).  Only the tests, the smoke check and the CPU-baseline
+// leg of the benchmark may load this library.  The product path never calls
+// it and shares no code with it.
+//
+// Every routine follows the paper's definitions literally:
+//   * quadrature weights -- Sec. 3.2, Eq. (weights): integrate the degree-k
+//     interpolant through t_{l-k..l} over [t_{l-1}, t_l].  The Lagrange basis
+//     polynomials are integrated by Gauss-Legendre, a route independent of the
+//     paper's Vandermonde solve; both give the same numbers.
+//   * composite weights -- Sec. 3.2: w_{n,m} = sum over intervals l <= n of
+//     the local weights, summed directly (the recursion is not used here).
+//   * self-energy -- Sec. 2, Eq. (SE), summed over the non-zero entries of
+//     the four-index Coulomb tensor.
+//   * history integrals -- Sec. 2, Eq. (KBE2), and Eq. (KBE1) for the adjoint
+//     identity, with theta(0) = 1 and G(t,t') = -G(t',t)^+.
+//   * stepper -- integral-form Adams-Moulton on the same kind of weights with
+//     P fixed-point sweeps (Sec. 3.1 solves each step by fixed-point
+//     iteration; Sec. 5.3 reports about two sweeps per step).
+//
+// Storage convention (input format, not arithmetic): two-time arrays hold
+// the lower triangle r >= c; block p(r,c) = r(r+1)/2 + c is an MxM row-major
+// complex128 matrix.  L(r,c) = G^<(t_r,t_c), R(r,c) = G^R(t_r,t_c), and
+// R(r,r) = -i*1 (Eq. BC with theta(0) = 1).
+//
+// History sums are Neumaier-compensated.  The arithmetic type is a template
+// parameter so that the stepper also runs on forward-mode dual numbers,
+// which gives exact directional derivatives of the discrete map.
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------- scalars --
+struct Dual {  // value and directional derivative
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double a) : v(a), d(0) {}
+  Dual(double a, double b) : v(a), d(b) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline bool is_zero(double x) { return x == 0.0; }
+inline bool is_zero(Dual x) { return x.v == 0.0 && x.d == 0.0; }
+
+template <class T> struct Cx {
+  T re, im;
+  Cx() : re(0.0), im(0.0) {}
+  Cx(T a) : re(a), im(0.0) {}
+  Cx(T a, T b) : re(a), im(b) {}
+};
+template <class T> inline Cx<T> operator+(Cx<T> a, Cx<T> b) { return Cx<T>(a.re + b.re, a.im + b.im); }
+template <class T> inline Cx<T> operator-(Cx<T> a, Cx<T> b) { return Cx<T>(a.re - b.re, a.im - b.im); }
+template <class T> inline Cx<T> operator-(Cx<T> a) { return Cx<T>(-a.re, -a.im); }
+template <class T> inline Cx<T> operator*(Cx<T> a, Cx<T> b) {
+  return Cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class T> inline Cx<T> scale(T s, Cx<T> a) { return Cx<T>(s * a.re, s * a.im); }
+template <class T> inline Cx<T> conj(Cx<T> a) { return Cx<T>(a.re, -a.im); }
+template <class T> inline Cx<T> mul_mi(Cx<T> a) { return Cx<T>(a.im, -a.re); }  // -i * a
+
+using C64 = Cx<double>;
+
+// Neumaier compensated accumulation, per real component.
+inline void nadd(double& s, double& c, double x) {
+  double t = s + x;
+  if (std::fabs(s) >= std::fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+  s = t;
+}
+template <class T> struct Acc;
+template <> struct Acc<double> {
+  double sr = 0, cr = 0, si = 0, ci = 0;
+  void add(C64 x) { nadd(sr, cr, x.re); nadd(si, ci, x.im); }
+  C64 get() const { return C64(sr + cr, si + ci); }
+};
+template <> struct Acc<Dual> {
+  double sr = 0, cr = 0, si = 0, ci = 0, dsr = 0, dcr = 0, dsi = 0, dci = 0;
+  void add(Cx<Dual> x) {
+    nadd(sr, cr, x.re.v); nadd(si, ci, x.im.v);
+    nadd(dsr, dcr, x.re.d); nadd(dsi, dci, x.im.d);
+  }
+  Cx<Dual> get() const { return Cx<Dual>(Dual(sr + cr, dsr + dcr), Dual(si + ci, dsi + dci)); }
+};
+
+inline int64_t tri(int64_t r, int64_t c) { return r * (r + 1) / 2 + c; }
+
+// ----------------------------------------------------- quadrature weights --
+// Gauss-Legendre nodes and weights on [-1,1]: Newton iteration on P_q, with
+// P_q from the recurrence k P_k = (2k-1) x P_{k-1} - (k-1) P_{k-2}.
+void legendre_eval(int q, double z, double* pq, double* dpq) {
+  double p0 = 1.0, p1 = z;
+  for (int k = 2; k <= q; ++k) {
+    double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+    p0 = p1; p1 = pk;
+  }
+  *pq = p1;
+  *dpq = (q == 1) ? 1.0 : q * (z * p1 - p0) / (z * z - 1.0);
+}
+void gauss_legendre(int q, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < q; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (q + 0.5)), p, dp;
+    for (int it = 0; it < 100; ++it) {
+      legendre_eval(q, z, &p, &dp);
+      double dz = p / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    legendre_eval(q, z, &p, &dp);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// w[j] = integral over [lo,hi] of the Lagrange basis polynomial l_j on the
+// nodes tau[0..k] -- the weights of the degree-k interpolatory rule of
+// Eq. (weights).  12 Gauss-Legendre points are exact up to degree 23.
+void lagrange_weights(const double* tau, int k, double lo, double hi, double* w) {
+  const int q = 12;
+  double gx[q], gw[q];
+  gauss_legendre(q, gx, gw);
+  const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+  for (int j = 0; j <= k; ++j) {
+    double s = 0.0;
+    for (int g = 0; g < q; ++g) {
+      double x = mid + half * gx[g], lj = 1.0;
+      for (int i = 0; i <= k; ++i)
+        if (i != j) lj *= (x - tau[i]) / (tau[j] - tau[i]);
+      s += gw[g] * lj;
+    }
+    w[j] = half * s;
+  }
+}
+
+inline int eff_order(const int* order, int l) { return order[l] < l ? order[l] : l; }
+
+// Composite row w_{n,m}, m = 0..n: direct sum over the intervals l = 1..n of
+// the local weights of order kappa_l = min(order[l], l).
+void composite_row(const double* t, const int* order, int n, double* row) {
+  for (int m = 0; m <= n; ++m) row[m] = 0.0;
+  double w[64];
+  for (int l = 1; l <= n; ++l) {
+    const int kap = eff_order(order, l);
+    lagrange_weights(t + (l - kap), kap, t[l - 1], t[l], w);
+    for (int j = 0; j <= kap; ++j) row[l - kap + j] += w[j];
+  }
+}
+
+// -------------------------------------------------- two-time plane access --
+// Values anywhere in the (t,t') plane from the stored lower triangles:
+// G^<> (t,t') = -G^<>(t',t)^+ (Sec. 2), G^> = G^R + G^< on and below the
+// diagonal (definition of G^R with theta(0) = 1), G^A(t,t') = G^R(t',t)^+.
+template <class T> struct Plane {
+  int M;
+  const Cx<T>* L;
+  const Cx<T>* R;
+  Cx<T> l_at(int r, int c, int a, int b) const { return L[tri(r, c) * M * M + a * M + b]; }
+  Cx<T> r_at(int r, int c, int a, int b) const { return R[tri(r, c) * M * M + a * M + b]; }
+  Cx<T> less(int r, int c, int a, int b) const {
+    if (r >= c) return l_at(r, c, a, b);
+    return -conj(l_at(c, r, b, a));
+  }
+  Cx<T> great(int r, int c, int a, int b) const {
+    if (r >= c) return r_at(r, c, a, b) + l_at(r, c, a, b);
+    return -conj(r_at(c, r, b, a) + l_at(c, r, b, a));
+  }
+  Cx<T> ret(int r, int c, int a, int b) const {
+    if (r >= c) return r_at(r, c, a, b);
+    return Cx<T>();
+  }
+  Cx<T> adv(int r, int c, int a, int b) const {
+    if (r <= c) return conj(r_at(c, r, b, a));
+    return Cx<T>();
+  }
+  Cx<T> get(int s, int r, int c, int a, int b) const { return s == 0 ? less(r, c, a, b) : great(r, c, a, b); }
+};
+
+// ------------------------------------------------------------ self-energy --
+// Row n of Eq. (SE):  S^<>(n,c)_ij for c = 0..n,
+//   S^<>_ij(t,t') = U_ifde UEx_jabc G^<>_fb(t,t') G^<>_ea(t,t') G^><_cd(t',t),
+//   UEx_jabc = 2 U_jbac - U_jabc,
+// summed over the entries where U and UEx are non-zero.
+template <class T>
+void sigma_row(const Plane<T>& G, const T* U4, int n, Cx<T>* Sl, Cx<T>* Sg) {
+  const int M = G.M;
+  auto at = [M](int a, int b, int c, int d) { return ((a * M + b) * M + c) * M + d; };
+  struct E { int i, f, d, e; T u; };
+  std::vector<E> nzU, nzX;  // nzX holds (j,a,b,c) in (i,f,d,e)
+  for (int i = 0; i < M; ++i)
+    for (int f = 0; f < M; ++f)
+      for (int d = 0; d < M; ++d)
+        for (int e = 0; e < M; ++e) {
+          T u = U4[at(i, f, d, e)];
+          T ux = T(2.0) * U4[at(i, d, f, e)] - U4[at(i, f, d, e)];  // UEx_{j a b c}: U_{j b a c}
+          if (!is_zero(u)) nzU.push_back({i, f, d, e, u});
+          if (!is_zero(ux)) nzX.push_back({i, f, d, e, ux});
+        }
+  for (int c = 0; c <= n; ++c) {
+    Cx<T>* sl = Sl + (int64_t)c * M * M;
+    Cx<T>* sg = Sg + (int64_t)c * M * M;
+    for (int k = 0; k < M * M; ++k) { sl[k] = Cx<T>(); sg[k] = Cx<T>(); }
+    for (const E& p : nzU) {       // p = (i, f, d, e)
+      for (const E& q : nzX) {     // q = (j, a, b, c')
+        const int i = p.i, f = p.f, d = p.d, e = p.e;
+        const int j = q.i, a = q.f, b = q.d, cc = q.e;
+        const T uu = p.u * q.u;
+        // S^>: G^>_fb(t,t') G^>_ea(t,t') G^<_cd(t',t);  S^<: the same with < and > swapped
+        Cx<T> g = G.great(n, c, f, b) * G.great(n, c, e, a) * G.less(c, n, cc, d);
+        Cx<T> l = G.less(n, c, f, b) * G.less(n, c, e, a) * G.great(c, n, cc, d);
+        sg[i * M + j] = sg[i * M + j] + scale(uu, g);
+        sl[i * M + j] = sl[i * M + j] + scale(uu, l);
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------- history slices --
+// Plane access to the self-energy of row n: S^s(n,c) stored for c <= n;
+// S^s(c,n) = -S^s(n,c)^+ for c < n; Sigma^R(n,m) = S^>(n,m) - S^<(n,m) for
+// m <= n (theta(0) = 1); Sigma^A(m,n) = Sigma^R(n,m)^+.
+template <class T> struct SigmaRow {
+  int M;
+  const Cx<T>* Sl;
+  const Cx<T>* Sg;
+  Cx<T> s_nm(int s, int m, int a, int b) const {
+    return (s == 0 ? Sl : Sg)[(int64_t)m * M * M + a * M + b];
+  }
+  Cx<T> ret_nm(int m, int a, int b) const { return s_nm(1, m, a, b) - s_nm(0, m, a, b); }
+  Cx<T> s_mn(int s, int m, int n, int a, int b) const {  // Sigma^s(t_m, t_n), m <= n
+    if (m == n) return s_nm(s, m, a, b);
+    return -conj(s_nm(s, m, b, a));
+  }
+  Cx<T> adv_mn(int m, int a, int b) const { return conj(ret_nm(m, b, a)); }
+};
+
+// Eq. (KBE2) history integrals for row n, both s in {<, >} and c = 0..n:
+//   I^s(n,c) = sum_{m=0..n} w_{n,m} Sigma^R(n,m) G^s(m,c)
+//            + sum_{m=0..c} w_{c,m} Sigma^s(n,m) G^A(m,c).
+// out layout [s][c][a][b].  Threads split the output columns c.
+template <class T>
+void history_slice(const Plane<T>& G, const SigmaRow<T>& S, const double* t, const int* order,
+                   int n, Cx<T>* out, int nthreads) {
+  const int M = G.M;
+  std::vector<std::vector<double>> w(n + 1);
+  for (int c = 0; c <= n; ++c) { w[c].resize(c + 1); composite_row(t, order, c, w[c].data()); }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) collapse(2)
+  for (int s = 0; s < 2; ++s)
+    for (int c = 0; c <= n; ++c) {
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+          Acc<T> acc;
+          for (int m = 0; m <= n; ++m)
+            for (int x = 0; x < M; ++x)
+              acc.add(scale(T(w[n][m]), S.ret_nm(m, a, x) * G.get(s, m, c, x, b)));
+          for (int m = 0; m <= c; ++m)
+            for (int x = 0; x < M; ++x)
+              acc.add(scale(T(w[c][m]), S.s_nm(s, m, a, x) * G.adv(m, c, x, b)));
+          out[(((int64_t)s * (n + 1) + c) * M + a) * M + b] = acc.get();
+        }
+    }
+}
+
+// Eq. (KBE1), lesser form, at (t_c, t_n) for c = 0..n:
+//   J(c) = sum_{m=0..c} w_{c,m} G^R(c,m) Sigma^<(m,n)
+//        + sum_{m=0..n} w_{n,m} G^<(c,m) Sigma^A(m,n).
+template <class T>
+void kbe1_slice(const Plane<T>& G, const SigmaRow<T>& S, const double* t, const int* order,
+                int n, Cx<T>* out, int nthreads) {
+  const int M = G.M;
+  std::vector<std::vector<double>> w(n + 1);
+  for (int c = 0; c <= n; ++c) { w[c].resize(c + 1); composite_row(t, order, c, w[c].data()); }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  for (int c = 0; c <= n; ++c)
+    for (int a = 0; a < M; ++a)
+      for (int b = 0; b < M; ++b) {
+        Acc<T> acc;
+        for (int m = 0; m <= c; ++m)
+          for (int x = 0; x < M; ++x)
+            acc.add(scale(T(w[c][m]), G.ret(c, m, a, x) * S.s_mn(0, m, n, x, b)));
+        for (int m = 0; m <= n; ++m)
+          for (int x = 0; x < M; ++x)
+            acc.add(scale(T(w[n][m]), G.less(c, m, a, x) * S.adv_mn(m, x, b)));
+        out[((int64_t)c * M + a) * M + b] = acc.get();
+      }
+}
+
+// ---------------------------------------------------------------- stepper --
+// Model: h(t) = h0 + E(t) diag(v), E(t) = E0 exp(-(t-t0)^2/(2 sigma^2)) cos(omega t);
+// local interaction U_a (Coulomb tensor U_abcd = U_a delta_abcd).
+// Fock matrix (Eq. eps) for that tensor: eps = h(t) + diag(U_a n_a),
+// n_a = Im L(t,t)_aa (the real part of -i G^<_aa(t,t)).
+template <class T> struct Model {
+  int M;
+  const C64* h0;
+  const T* U;
+  const double* v;
+  T E0;
+  double t0, sig, om;
+};
+
+template <class T> T pulse(const Model<T>& md, double t) {
+  const double g = std::exp(-(t - md.t0) * (t - md.t0) / (2.0 * md.sig * md.sig)) * std::cos(md.om * t);
+  return md.E0 * T(g);
+}
+
+template <class T> void fock(const Model<T>& md, double t, const Cx<T>* Lnn, Cx<T>* eps) {
+  const int M = md.M;
+  const T e = pulse(md, t);
+  for (int a = 0; a < M; ++a)
+    for (int b = 0; b < M; ++b) eps[a * M + b] = Cx<T>(T(md.h0[a * M + b].re), T(md.h0[a * M + b].im));
+  for (int a = 0; a < M; ++a) {
+    eps[a * M + a].re = eps[a * M + a].re + e * T(md.v[a]) + md.U[a] * Lnn[a * M + a].im;
+  }
+}
+
+// Row of right-hand sides F^s(j,c) = -i ( eps(t_j) G^s(j,c) + I^s(j,c) ), c = 0..j
+// (the t-derivative from Eq. (KBE2)); layout [s][c][a][b].
+template <class T>
+void rhs_row(const Model<T>& md, const Plane<T>& G, const double* t, const Cx<T>* I, int j, Cx<T>* F) {
+  const int M = md.M;
+  std::vector<Cx<T>> eps(M * M);
+  fock(md, t[j], G.L + tri(j, j) * M * M, eps.data());
+  for (int s = 0; s < 2; ++s)
+    for (int c = 0; c <= j; ++c)
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+          Cx<T> acc = I[(((int64_t)s * (j + 1) + c) * M + a) * M + b];
+          for (int x = 0; x < M; ++x) acc = acc + eps[a * M + x] * G.get(s, j, c, x, b);
+          F[(((int64_t)s * (j + 1) + c) * M + a) * M + b] = mul_mi(acc);
+        }
+}
+
+// Weights of the rule that integrates, over [t_{n-1}, t_n], the interpolant
+// through the points t_first .. t_last.
+void span_weights(const double* t, int first, int last, int n, double* w) {
+  lagrange_weights(t + first, last - first, t[n - 1], t[n], w);
+}
+
+// Unrolled access to the stored right-hand sides: ring of K+1 rows.
+template <class T> struct Ring {
+  int M, N, K;
+  std::vector<Cx<T>> F;  // [K+1][2][N][M][M]
+  Cx<T>* row(int j) { return F.data() + (int64_t)(j % (K + 1)) * 2 * N * M * M; }
+  Cx<T> at(int j, int s, int c, int a, int b) {  // row j holds j+1 columns per s
+    return row(j)[(((int64_t)s * (j + 1) + c) * M + a) * M + b];
+  }
+};
+
+// One KBE step for row n (Sec. 3.1 structure, integral form):
+//  predictor   G^s(n,c) = G^s(n-1,c) + sum_p wp_p F^s(n-q+p, c),   q = min(k_n, n-c) points
+//              t_{n-q..n-1} (Adams-Bashforth type); diagonal with D(j) = F^<(j,j) - F^<(j,j)^+
+//              and q = min(k_n, n).
+//  P sweeps:   Sigma row n, history row n, F row n, then the corrector
+//              G^s(n,c) = G^s(n-1,c) + sum_p w_p F^s(n-kap+p, c),  kap = min(k_n, n-c)
+//              (Adams-Moulton type, points t_{n-kap..n}), diagonal kap = min(k_n, n).
+//  G^>(n,c) for c < n comes from the stepped G^> and G^<:  R(n,c) = G^>(n,c) - L(n,c);
+//  R(n,n) = -i*1.  F row n keeps the value of the last evaluation.
+template <class T>
+void kbe_step(const Model<T>& md, const double* t, const int* order, int n, int P,
+              const T* U4, Cx<T>* L, Cx<T>* R, Ring<T>& ring, Cx<T>* I_last, int nthreads) {
+  const int M = md.M;
+  const int MM = M * M;
+  const int kn = order[n];
+  Plane<T> G{M, L, R};
+  std::vector<Cx<T>> Gl((n + 1) * MM), Gg((n + 1) * MM);  // stepped G^< and G^> of row n
+  double w[64];
+  auto old_less = [&](int c, int k) { return L[tri(n - 1, c) * MM + k]; };
+  auto old_great = [&](int c, int k) { return R[tri(n - 1, c) * MM + k] + L[tri(n - 1, c) * MM + k]; };
+  auto diag_D = [&](int j, int a, int b) {  // total derivative of G^<(t,t) at t_j
+    return ring.at(j, 0, j, a, b) - conj(ring.at(j, 0, j, b, a));
+  };
+  // predictor
+  for (int c = 0; c < n; ++c) {
+    const int q = (kn < n - c) ? kn : (n - c);
+    span_weights(t, n - q, n - 1, n, w);
+    for (int k = 0; k < MM; ++k) {
+      Cx<T> al = old_less(c, k), ag = old_great(c, k);
+      for (int p = 0; p < q; ++p) {
+        const int j = n - q + p;
+        al = al + scale(T(w[p]), ring.at(j, 0, c, k / M, k % M));
+        ag = ag + scale(T(w[p]), ring.at(j, 1, c, k / M, k % M));
+      }
+      Gl[c * MM + k] = al; Gg[c * MM + k] = ag;
+    }
+  }
+  {
+    const int q = (kn < n) ? kn : n;
+    span_weights(t, n - q, n - 1, n, w);
+    for (int k = 0; k < MM; ++k) {
+      Cx<T> al = L[tri(n - 1, n - 1) * MM + k];
+      for (int p = 0; p < q; ++p) al = al + scale(T(w[p]), diag_D(n - q + p, k / M, k % M));
+      Gl[n * MM + k] = al;
+    }
+  }
+  auto commit = [&]() {
+    for (int c = 0; c < n; ++c)
+      for (int k = 0; k < MM; ++k) {
+        L[tri(n, c) * MM + k] = Gl[c * MM + k];
+        R[tri(n, c) * MM + k] = Gg[c * MM + k] - Gl[c * MM + k];
+      }
+    for (int k = 0; k < MM; ++k) {
+      L[tri(n, n) * MM + k] = Gl[n * MM + k];
+      R[tri(n, n) * MM + k] = (k / M == k % M) ? Cx<T>(T(0.0), T(-1.0)) : Cx<T>();
+    }
+  };
+  commit();
+  std::vector<Cx<T>> Sl((n + 1) * MM), Sg((n + 1) * MM), I(2 * (n + 1) * MM);
+  for (int sweep = 0; sweep < P; ++sweep) {
+    sigma_row(G, U4, n, Sl.data(), Sg.data());
+    SigmaRow<T> S{M, Sl.data(), Sg.data()};
+    history_slice(G, S, t, order, n, I.data(), nthreads);
+    rhs_row(md, G, t, I.data(), n, ring.row(n));
+    // corrector
+    for (int c = 0; c < n; ++c) {
+      const int kap = (kn < n - c) ? kn : (n - c);
+      span_weights(t, n - kap, n, n, w);
+      for (int k = 0; k < MM; ++k) {
+        Cx<T> al = old_less(c, k), ag = old_great(c, k);
+        for (int p = 0; p <= kap; ++p) {
+          const int j = n - kap + p;
+          al = al + scale(T(w[p]), ring.at(j, 0, c, k / M, k % M));
+          ag = ag + scale(T(w[p]), ring.at(j, 1, c, k / M, k % M));
+        }
+        Gl[c * MM + k] = al; Gg[c * MM + k] = ag;
+      }
+    }
+    {
+      const int kap = (kn < n) ? kn : n;
+      span_weights(t, n - kap, n, n, w);
+      for (int k = 0; k < MM; ++k) {
+        Cx<T> al = L[tri(n - 1, n - 1) * MM + k];
+        for (int p = 0; p <= kap; ++p) al = al + scale(T(w[p]), diag_D(n - kap + p, k / M, k % M));
+        Gl[n * MM + k] = al;
+      }
+    }
+    commit();
+  }
+  if (I_last) for (size_t k = 0; k < I.size(); ++k) I_last[k] = I[k];
+}
+
+template <class T>
+std::vector<T> local_U4(int M, const T* U) {
+  std::vector<T> U4((size_t)M * M * M * M, T(0.0));
+  for (int a = 0; a < M; ++a) U4[((a * M + a) * M + a) * M + a] = U[a];
+  return U4;
+}
+
+}  // namespace
+
+// =================================================================== C ABI ==
+extern "C" {
+
+int orc_version() { return 1; }
+
+int orc_threads_available() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// Gauss-Legendre rule on [-1,1].
+int orc_gauss_legendre(int q, double* x, double* w) {
+  if (q < 1 || q > 64) return 1;
+  gauss_legendre(q, x, w);
+  return 0;
+}
+
+// Weights of the interpolatory rule on nodes tau[0..k] over [lo, hi].
+int orc_lagrange_weights(const double* tau, int k, double lo, double hi, double* w) {
+  if (k < 0 || k > 40) return 1;
+  lagrange_weights(tau, k, lo, hi, w);
+  return 0;
+}
+
+// Composite weight row w_{n,0..n}.
+int orc_composite_row(const double* t, const int* order, int n, double* row) {
+  if (n < 0) return 1;
+  composite_row(t, order, n, row);
+  return 0;
+}
+
+// Self-energy row n of Eq. (SE) for a general four-index tensor U4[M^4].
+int orc_sigma_row(int M, int n, const double* U4, const void* L, const void* R, void* Sl, void* Sg) {
+  if (M < 1 || n < 0) return 1;
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  sigma_row(G, U4, n, (C64*)Sl, (C64*)Sg);
+  return 0;
+}
+
+// History slice of Eq. (KBE2) for row n; out [2][n+1][M][M].
+int orc_history_slice(int M, int n, const double* t, const int* order, const void* L, const void* R,
+                      const void* Sl, const void* Sg, void* out, int nthreads) {
+  if (M < 1 || n < 0 || nthreads < 1) return 1;
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  SigmaRow<double> S{M, (const C64*)Sl, (const C64*)Sg};
+  history_slice(G, S, t, order, n, (C64*)out, nthreads);
+  return 0;
+}
+
+// History slice restricted to the output columns listed in cols (both s);
+// out [2][ncols][M][M].  Used to time bounded samples of a slice.
+int orc_history_columns(int M, int n, const double* t, const int* order, const void* L, const void* R,
+                        const void* Sl, const void* Sg, const int* cols, int ncols, void* out, int nthreads) {
+  if (M < 1 || n < 0 || nthreads < 1 || ncols < 0) return 1;
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  SigmaRow<double> S{M, (const C64*)Sl, (const C64*)Sg};
+  std::vector<double> wn(n + 1);
+  composite_row(t, order, n, wn.data());
+  C64* o = (C64*)out;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) collapse(2)
+  for (int s = 0; s < 2; ++s)
+    for (int ic = 0; ic < ncols; ++ic) {
+      const int c = cols[ic];
+      std::vector<double> wc(c + 1);
+      composite_row(t, order, c, wc.data());
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+          Acc<double> acc;
+          for (int m = 0; m <= n; ++m)
+            for (int x = 0; x < M; ++x) acc.add(scale(wn[m], S.ret_nm(m, a, x) * G.get(s, m, c, x, b)));
+          for (int m = 0; m <= c; ++m)
+            for (int x = 0; x < M; ++x) acc.add(scale(wc[m], S.s_nm(s, m, a, x) * G.adv(m, c, x, b)));
+          o[(((int64_t)s * ncols + ic) * M + a) * M + b] = acc.get();
+        }
+    }
+  return 0;
+}
+
+// Eq. (KBE1) lesser history integrals at (t_c, t_n), c = 0..n; out [n+1][M][M].
+int orc_kbe1_slice(int M, int n, const double* t, const int* order, const void* L, const void* R,
+                   const void* Sl, const void* Sg, void* out, int nthreads) {
+  if (M < 1 || n < 0 || nthreads < 1) return 1;
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  SigmaRow<double> S{M, (const C64*)Sl, (const C64*)Sg};
+  kbe1_slice(G, S, t, order, n, (C64*)out, nthreads);
+  return 0;
+}
+
+// Right-hand-side row j (history reconstruction): needs rows 0..j stored and
+// the self-energy from them.  F out [2][j+1][M][M].
+int orc_rhs_row(int M, int j, const double* t, const int* order, const double* h0, const double* U,
+                const double* v, const double* pulse4, const void* L, const void* R, void* F, int nthreads) {
+  if (M < 1 || j < 0 || nthreads < 1) return 1;
+  Model<double> md{M, (const C64*)h0, U, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  std::vector<double> U4 = local_U4(M, U);
+  std::vector<C64> Sl((j + 1) * M * M), Sg((j + 1) * M * M), I(2 * (j + 1) * M * M);
+  sigma_row(G, U4.data(), j, Sl.data(), Sg.data());
+  SigmaRow<double> S{M, Sl.data(), Sg.data()};
+  history_slice(G, S, t, order, j, I.data(), nthreads);
+  rhs_row(md, G, t, I.data(), j, (C64*)F);
+  return 0;
+}
+
+// Run KBE steps n = n_start .. n_end-1 (n_start >= 1).  L, R hold rows
+// 0..n_start-1 on entry and rows up to n_end-1 on exit (triangles of n_end
+// rows).  F_in holds the right-hand-side rows j = max(0, n_start-K)
+// .. n_start-1, packed one after the other, each [2][j+1][M][M]; K is the
+// largest order on the grid orders[1..n_end-1].  I_last (optional) receives the last history
+// row [2][n_end][M][M].
+int orc_run(int M, int n_start, int n_end, const double* t, const int* order, const double* h0,
+            const double* U, const double* v, const double* pulse4, int P, void* L, void* R,
+            const void* F_in, void* I_last, int nthreads) {
+  if (M < 1 || n_start < 1 || n_end < n_start || P < 1 || nthreads < 1) return 1;
+  int K = 1;
+  for (int l = 1; l < n_end; ++l) if (order[l] > K) K = order[l];
+  Model<double> md{M, (const C64*)h0, U, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  std::vector<double> U4 = local_U4(M, U);
+  Ring<double> ring{M, n_end, K, std::vector<C64>((size_t)(K + 1) * 2 * n_end * M * M)};
+  const C64* f = (const C64*)F_in;
+  for (int j = (n_start - K > 0 ? n_start - K : 0); j <= n_start - 1; ++j) {
+    const size_t cnt = (size_t)2 * (j + 1) * M * M;
+    std::memcpy((void*)ring.row(j), f, cnt * sizeof(C64));
+    f += cnt;
+  }
+  for (int n = n_start; n < n_end; ++n)
+    kbe_step(md, t, order, n, P, U4.data(), (C64*)L, (C64*)R, ring,
+             (n == n_end - 1) ? (C64*)I_last : nullptr, nthreads);
+  return 0;
+}
+
+// Forward-mode derivative of the same run: U_a -> U_a + eps*dU_a,
+// E0 -> E0 + eps*dE0.  Rows below n_start and the given F rows are held
+// fixed.  On exit Lv/Ld hold the value/derivative of the final diagonal
+// block L(n_end-1, n_end-1) [M][M]; L, R receive the value triangles.
+int orc_run_tangent(int M, int n_start, int n_end, const double* t, const int* order, const double* h0,
+                    const double* U, const double* dU, const double* v, const double* pulse4, double dE0,
+                    int P, const void* L_in, const void* R_in, const void* F_in, void* Lv, void* Ld,
+                    int nthreads) {
+  if (M < 1 || n_start < 1 || n_end < n_start || P < 1 || nthreads < 1) return 1;
+  using D = Dual;
+  int K = 1;
+  for (int l = 1; l < n_end; ++l) if (order[l] > K) K = order[l];
+  std::vector<D> Ud(M);
+  for (int a = 0; a < M; ++a) Ud[a] = D(U[a], dU[a]);
+  Model<D> md{M, (const C64*)h0, Ud.data(), v, D(pulse4[0], dE0), pulse4[1], pulse4[2], pulse4[3]};
+  std::vector<D> U4 = local_U4(M, Ud.data());
+  const size_t ntri = (size_t)n_end * (n_end + 1) / 2 * M * M;
+  const size_t nin = (size_t)n_start * (n_start + 1) / 2 * M * M;
+  std::vector<Cx<D>> L(ntri), R(ntri);
+  const C64* li = (const C64*)L_in;
+  const C64* ri = (const C64*)R_in;
+  for (size_t k = 0; k < nin; ++k) {
+    L[k] = Cx<D>(D(li[k].re), D(li[k].im));
+    R[k] = Cx<D>(D(ri[k].re), D(ri[k].im));
+  }
+  Ring<D> ring{M, n_end, K, std::vector<Cx<D>>((size_t)(K + 1) * 2 * n_end * M * M)};
+  const C64* f = (const C64*)F_in;
+  for (int j = (n_start - K > 0 ? n_start - K : 0); j <= n_start - 1; ++j) {
+    const size_t cnt = (size_t)2 * (j + 1) * M * M;
+    Cx<D>* dst = ring.row(j);
+    for (size_t k = 0; k < cnt; ++k) dst[k] = Cx<D>(D(f[k].re), D(f[k].im));
+    f += cnt;
+  }
+  for (int n = n_start; n < n_end; ++n)
+    kbe_step(md, t, order, n, P, U4.data(), L.data(), R.data(), ring, static_cast<Cx<D>*>(nullptr), nthreads);
+  const Cx<D>* last = L.data() + tri(n_end - 1, n_end - 1) * M * M;
+  C64* ov = (C64*)Lv;
+  C64* od = (C64*)Ld;
+  for (int k = 0; k < M * M; ++k) {
+    ov[k] = C64(last[k].re.v, last[k].im.v);
+    od[k] = C64(last[k].re.d, last[k].im.d);
+  }
+  return 0;
+}
+
+}  // extern "C"

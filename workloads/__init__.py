@@ -1,0 +1,199 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module only generates inputs: time grids with per-interval orders,
+one-body Hamiltonians, interaction strengths, pulse parameters, initial
+density matrices and two-time histories of the non-interacting (U = 0)
+problem or seeded random stress data.  It holds none of the method's
+arithmetic: no quadrature weights, self-energies, history integrals or time
+stepping.  Both the oracle and the CUDA path read what it produces.
+
+Two-time arrays use the triangle-packed layout ``[tri(N), M, M]`` with block
+``r*(r+1)/2 + c`` for ``r >= c``; ``L = G^<`` and ``R = G^R``.
+
+Workload recipes (the shapes of the paper's model systems, Sec. 5-6; the
+paper's own inputs are not available):
+  * time grid: ``dt_l = dt0 * exp(sig * z_l)``, ``z ~ N(0,1)`` from numpy's
+    PCG64 with the given seed, then per-interval orders ``k_l`` uniform in
+    ``{kmin..kmax}`` from the same generator (z first, then k);
+  * Hubbard chain: ``h_{i,i+1} = h_{i+1,i} = -J`` (open chain);
+  * GOE one-body matrix: ``A_ij ~ N(0, 1/M)``, ``h = (A + A^T)/2``;
+  * half filling: the lowest ``M//2`` eigenvectors of h occupied, per spin;
+  * pulse: ``E(t) = E0 exp(-(t-t0)^2/(2 sigma^2)) cos(omega t)`` entering as
+    the site potential ``E(t) * (i - (M-1)/2)``.
+"""
+import numpy as np
+
+try:  # torch is only needed for the large, device-side histories
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+
+def tri_size(n):
+    return n * (n + 1) // 2
+
+
+def tri_index(r, c):
+    return r * (r + 1) // 2 + c
+
+
+def grid(n_t, dt0, sig, seed, kmin=1, kmax=5):
+    """Nonuniform grid t[0..n_t-1] (t[0] = 0) and orders order[1..n_t-1]
+    (order[0] = 0 is unused)."""
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal(n_t - 1)
+    k = rng.integers(kmin, kmax + 1, size=n_t - 1)
+    t = np.zeros(n_t)
+    t[1:] = np.cumsum(dt0 * np.exp(sig * z))
+    order = np.zeros(n_t, dtype=np.int32)
+    order[1:] = k
+    return t, order
+
+
+def uniform_grid(n_t, h, k):
+    t = h * np.arange(n_t, dtype=np.float64)
+    order = np.full(n_t, k, dtype=np.int32)
+    order[0] = 0
+    return t, order
+
+
+def chain_h(M, J=1.0):
+    h = np.zeros((M, M), np.complex128)
+    for i in range(M - 1):
+        h[i, i + 1] = -J
+        h[i + 1, i] = -J
+    return h
+
+
+def goe_h(M, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0.0, 1.0 / np.sqrt(M), size=(M, M))
+    return ((A + A.T) / 2).astype(np.complex128)
+
+
+def site_potential(M):
+    return np.arange(M, dtype=np.float64) - (M - 1) / 2.0
+
+
+def half_filled_rho(h):
+    M = h.shape[0]
+    _, V = np.linalg.eigh(h)
+    occ = V[:, : M // 2]
+    return (occ @ occ.conj().T).astype(np.complex128)
+
+
+def propagators(h, t):
+    """e^{-i h t_r} for every grid time (the free evolution)."""
+    e, V = np.linalg.eigh(h)
+    ph = np.exp(-1j * np.outer(t, e))                 # [N, M]
+    return np.einsum("ak,rk,bk->rab", V, ph, V.conj())  # [N, M, M]
+
+
+def free_triangles(h, rho0, t, n_rows=None):
+    """Non-interacting history: G^<(t,t') = i A(t) rho0 A(t')^+,
+    G^R(t,t') = -i A(t) A(t')^+ with A(t) = e^{-iht}; rows 0..n_rows-1."""
+    n_rows = len(t) if n_rows is None else n_rows
+    A = propagators(h, t[:n_rows])
+    M = h.shape[0]
+    L = np.zeros((tri_size(n_rows), M, M), np.complex128)
+    R = np.zeros_like(L)
+    Ar = np.einsum("rab,bc->rac", A, rho0)
+    for r in range(n_rows):
+        p = tri_index(r, 0)
+        L[p:p + r + 1] = 1j * np.einsum("ab,cdb->cad", Ar[r], A[: r + 1].conj())
+        R[p:p + r + 1] = -1j * np.einsum("ab,cdb->cad", A[r], A[: r + 1].conj())
+        R[p + r] = -1j * np.eye(M)
+    return L, R
+
+
+def free_triangles_torch(h, rho0, t, n_rows, device):
+    """``free_triangles`` built with torch on ``device`` (large histories)."""
+    A = torch.from_numpy(propagators(h, t[:n_rows])).to(device)
+    rho = torch.from_numpy(rho0).to(device)
+    M = h.shape[0]
+    ntri = tri_size(n_rows)
+    L = torch.empty((ntri, M, M), dtype=torch.complex128, device=device)
+    R = torch.empty_like(L)
+    Ar = A @ rho
+    Ah = A.conj().transpose(1, 2)
+    eye = torch.eye(M, dtype=torch.complex128, device=device)
+    for r in range(n_rows):
+        p = tri_index(r, 0)
+        L[p:p + r + 1] = 1j * (Ar[r].unsqueeze(0) @ Ah[: r + 1])
+        R[p:p + r + 1] = -1j * (A[r].unsqueeze(0) @ Ah[: r + 1])
+        R[p + r] = -1j * eye
+    return L, R
+
+
+def free_rhs_rows(h, L, R, rows):
+    """Exact t-derivatives of the non-interacting history, used as frozen
+    right-hand-side rows at a restart: d/dt G^s(t_j, t_c) = -i h G^s(t_j, t_c)
+    for s = <, > (G^> = G^R + G^<), as [2, j+1, M, M] per row j."""
+    out = {}
+    for j in rows:
+        p = tri_index(j, 0)
+        Gl = L[p:p + j + 1]
+        Gg = R[p:p + j + 1] + Gl
+        out[j] = np.stack([-1j * np.einsum("ab,cbd->cad", h, Gl),
+                           -1j * np.einsum("ab,cbd->cad", h, Gg)])
+    return out
+
+
+def random_triangles(M, n_rows, seed, scale=1.0):
+    """Seeded random complex histories (stress data) with R(r,r) = -i*1."""
+    rng = np.random.default_rng(seed)
+    ntri = tri_size(n_rows)
+    L = scale * (rng.standard_normal((ntri, M, M)) + 1j * rng.standard_normal((ntri, M, M)))
+    R = scale * (rng.standard_normal((ntri, M, M)) + 1j * rng.standard_normal((ntri, M, M)))
+    for r in range(n_rows):
+        R[tri_index(r, r)] = -1j * np.eye(M)
+    return L.astype(np.complex128), R.astype(np.complex128)
+
+
+def random_rows(M, n, seed, scale=1.0):
+    """Seeded random self-energy rows S^<, S^> of row n: two [n+1, M, M]."""
+    rng = np.random.default_rng(seed)
+    shp = (n + 1, M, M)
+    Sl = scale * (rng.standard_normal(shp) + 1j * rng.standard_normal(shp))
+    Sg = scale * (rng.standard_normal(shp) + 1j * rng.standard_normal(shp))
+    return Sl.astype(np.complex128), Sg.astype(np.complex128)
+
+
+# ---------------------------------------------------------------- configs --
+PULSE_CHAIN = {"E0": 0.5, "t0": 5.0, "sigma": 1.0, "omega": 2.0}
+
+CONFIGS = {
+    # Hubbard dimer, quench of U at t = 0 (Sec. 6 model family, M = 2 as the
+    # H2/sto-6g system of Sec. 5).
+    "dimer_m2_n64": dict(M=2, J=1.0, U=1.0, n_t=64, dt0=0.05, sig=0.3, h="chain", pulse=None),
+    # open Hubbard chain with a Gaussian pulse (plain FP64 GPU workload)
+    "chain_m8_n1024": dict(M=8, J=1.0, U=2.0, n_t=1024, dt0=0.02, sig=0.4, h="chain", pulse=PULSE_CHAIN),
+    # GOE one-body matrix, precision-form workload
+    "goe_m32_n1024": dict(M=32, J=None, U=1.5, n_t=1024, dt0=0.02, sig=0.4, h="goe", pulse=None),
+    # differentiation workload: last 32 steps of a 512-point chain run
+    "chain_m16_n512_w32": dict(M=16, J=1.0, U=2.0, n_t=512, dt0=0.02, sig=0.4, h="chain",
+                               pulse=PULSE_CHAIN, window=32),
+}
+
+
+def build_model(cfg, seed):
+    """(h0, U vector, site potential, pulse) of a config."""
+    M = cfg["M"]
+    h = chain_h(M, cfg["J"]) if cfg["h"] == "chain" else goe_h(M, 1000 + seed)
+    U = np.full(M, cfg["U"], dtype=np.float64)
+    return h, U, site_potential(M), cfg["pulse"]
+
+
+def batch_systems(n_sys, seed):
+    """Batched workload: n_sys independent Hubbard-type chains with M in
+    {4,8,12,16,24}, history length N_t uniform in [256,1536], U uniform in
+    [0.5,3], J = 1, each on its own seeded grid."""
+    rng = np.random.default_rng(seed)
+    Ms = rng.choice(np.array([4, 8, 12, 16, 24]), size=n_sys)
+    Ns = rng.integers(256, 1537, size=n_sys)
+    Us = rng.uniform(0.5, 3.0, size=n_sys)
+    out = []
+    for i in range(n_sys):
+        out.append(dict(M=int(Ms[i]), n_t=int(Ns[i]), U=float(Us[i]), J=1.0,
+                        grid_seed=int(seed * 1000 + i)))
+    return out
