@@ -1,0 +1,344 @@
+"""Benchmark of the KBE hot path on GB300.
+
+One step = one KBE step of the last row n = N_t - 1 of the 8-orbital
+Hubbard-chain workload (N_t = 1024 nonuniform points, orders 1..5, Gaussian
+pulse): predictor, then P = 2 fixed-point sweeps of self-energy row,
+history slice (Eq. KBE2), right-hand side and corrector, all on the GPU
+(host FP64 weights are computed once per grid).  The history of rows
+0..n-1 is the non-interacting propagator of the chain; the stored
+right-hand-side rows n-K..n-1 are rebuilt by the library from that history
+before timing (the restart reconstruction).
+
+Metric: history-slice TFLOP/s = P * 8 M^3 (n+1)(3n+2) / step time, and ms
+per KBE step.  Inputs (1.07 GB of history) are larger than L2.
+
+--impl reference times the CPU oracle (test infrastructure) on bounded
+samples of the same slice instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "chain_m8_n1024"
+FP64_PEAK_TFLOPS = 1.199  # DFMA throughput measured on this GB300 pool
+METRIC = "history-slice TFLOP/s and ms per KBE step vs plain FP64 GPU path at stated error"
+
+
+def slice_flops(M, n):
+    """Algorithmic flops of one history slice of row n: complex multiply-adds
+    (8 flops each) of the 2n+1 required output blocks."""
+    return 8.0 * M ** 3 * (n + 1) * (3 * n + 2)
+
+
+def column_units(n, cols):
+    """Block multiply-adds of the listed output columns (both s)."""
+    return sum(2 * (n + 1) + 2 * (c + 1) for c in cols)
+
+
+def slice_units(n):
+    return (n + 1) * (3 * n + 4)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--P", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    rank, world = 0, 1
+    if args.gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if world > 1:
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend)
+    return rank, world
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, idx):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(idx),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_workload(kbe, seed):
+    import torch
+    import workloads as W
+    cfg = W.CONFIGS[WORKLOAD]
+    M, n_t = cfg["M"], cfg["n_t"]
+    t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], seed)
+    h, U, v, pulse = W.build_model(cfg, seed)
+    rho0 = W.half_filled_rho(h)
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, U, v, pulse)
+    run = kbe.Run(ctx)
+    L, R = W.free_triangles_torch(h, rho0, t, n_t, "cuda")
+    run.L.copy_(L)
+    run.R.copy_(R)
+    del L, R
+    n = n_t - 1
+    K = int(order[1:].max())
+    for j in range(max(0, n - K), n):  # restart: rebuild the stored right-hand sides
+        ctx.rhs_row(j, run.L, run.R, run.Sl, run.Sg, run.I, run.F)
+    ctx.sync_status()
+    torch.cuda.synchronize()
+    return cfg, t, order, h, U, v, pulse, ctx, run, n
+
+
+def time_steps(ctx, run, n, P, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        run.step(n, P=P, stream=stream)
+    torch.cuda.synchronize()
+    launches = 0
+    ctx.set_profiling(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        run.step(n, P=P, stream=stream)
+        launches += ctx.last_launch_count
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    k_count, k_ms = ctx.read_profiling()
+    ctx.set_profiling(False)
+    ctx.sync_status()
+    return ms, launches, k_count, k_ms
+
+
+def e2e_steps(ctx, run, n, P, steps, warmup, stream):
+    """The same step through the public API with host buffers: every step
+    copies the history and stored right-hand sides from pinned host memory,
+    runs the step and reads the new row back."""
+    import torch
+    L_h = run.L.cpu().pin_memory()
+    R_h = run.R.cpu().pin_memory()
+    F_h = run.F.cpu().pin_memory()
+    M = ctx.M
+    p0 = n * (n + 1) // 2
+    out_L = torch.empty((n + 1, M, M), dtype=torch.complex128).pin_memory()
+    out_R = torch.empty_like(out_L).pin_memory()
+    h2d = (L_h.numel() + R_h.numel() + F_h.numel()) * 16
+    d2h = 2 * (n + 1) * M * M * 16
+
+    def one():
+        with torch.cuda.stream(stream):
+            run.L.copy_(L_h, non_blocking=True)
+            run.R.copy_(R_h, non_blocking=True)
+            run.F.copy_(F_h, non_blocking=True)
+            run.step(n, P=P, stream=stream)
+            out_L.copy_(run.L[p0:p0 + n + 1], non_blocking=True)
+            out_R.copy_(run.R[p0:p0 + n + 1], non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, h2d, d2h
+
+
+def cpu_baseline(kbe_run, t, order, U, n, M, budget_s=15.0, gpu_slice=None):
+    """The oracle on a bounded sample of output columns of the same slice;
+    returns (TFLOP/s-equivalent, threads, sample text, max rel deviation from
+    the GPU slice on those columns)."""
+    import oracle
+    L = kbe_run.L.cpu().numpy()
+    R = kbe_run.R.cpu().numpy()
+    ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+    threads = oracle.threads_available()
+    rng = np.random.default_rng(1)
+    cols = [n, n - 1, 0]
+    t0 = time.perf_counter()
+    ref = oracle.history_columns(t, order, n, L, R, ol, og, cols, nthreads=threads)
+    dt = time.perf_counter() - t0
+    # grow the sample to about budget_s of CPU time
+    per_unit = dt / column_units(n, cols)
+    extra = int(max(0, budget_s / per_unit - column_units(n, cols)) / (3 * (n + 1)))
+    if extra > 0:
+        more = sorted(rng.choice(np.arange(1, n - 1), size=min(extra, n - 2), replace=False).tolist())
+        t0 = time.perf_counter()
+        ref2 = oracle.history_columns(t, order, n, L, R, ol, og, more, nthreads=threads)
+        dt = time.perf_counter() - t0
+        cols, ref = more, ref2
+    frac = column_units(n, cols) / slice_units(n)
+    tflops = slice_flops(M, n) * frac / dt / 1e12
+    err = None
+    if gpu_slice is not None:
+        g = gpu_slice[:, cols]
+        err = float(np.abs(g - ref).max() / np.abs(ref).max())
+    sample = "oracle history slice n=%d, %d of %d output columns (both s), %.1f s on %d threads" % (
+        n, len(cols), n + 1, dt, threads)
+    return tflops, threads, sample, err
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        return main_reference(args, rank, world)
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import paper_2405_08737_gb300 as kbe
+    kbe.lib()
+    cfg, t, order, h, U, v, pulse, ctx, run, n = setup_workload(kbe, args.seed + rank)
+    M = cfg["M"]
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ms, launches, k_count, k_ms = time_steps(ctx, run, n, args.P, args.steps, args.warmup, stream)
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    flops_step = args.P * slice_flops(M, n)
+    value = world * flops_step / (ms_step * 1e-3) / 1e12
+    k_avg = k_ms / max(k_count, 1)
+    achieved = slice_flops(M, n) / (k_avg * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+            "kernel": "history_partial (FP64 DFMA contraction)", "launches_timed": k_count,
+            "avg_ms": round(k_avg, 4), "peak_source": "measured DFMA probe (FP64 not in MEASURED_PEAKS.json)"}
+    gpu_slice = run.I[:, : n + 1].cpu().numpy()
+    e2e_ms, h2d, d2h = e2e_steps(ctx, run, n, args.P, max(3, args.steps // 4), 1, stream)
+    e2e = {"value": round(world * flops_step / (e2e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+           "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s: Hubbard chain M=8, N_t=1024 nonuniform, orders 1..5, pulse; "
+                                   "KBE step of row n=1023 with P=%d (FP64 path)" % (WORKLOAD, args.P),
+                       "norb": M, "n_t": cfg["n_t"], "n": n, "P": args.P, "precision": "fp64",
+                       "l2": "inputs larger than L2 (history 1.07 GB per step)",
+                       "parallelism": "independent replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches}
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tf, threads, sample, err = cpu_baseline(run, t, order, U, n, M, gpu_slice=gpu_slice)
+        line["cpu_baseline"] = {"value": round(tf, 6), "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                                "sample": sample}
+        line["error_vs_oracle"] = {"max_rel": err, "where": "sampled columns of the timed slice"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main_reference(args, rank, world):
+    """The oracle (plain FP64 CPU C++) on the host cores, on bounded samples of
+    the same workload: each step evaluates a fixed sample of output columns
+    of the history slice of row n = N_t - 1."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    cfg = W.CONFIGS[WORKLOAD]
+    M, n_t = cfg["M"], cfg["n_t"]
+    t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], args.seed)
+    h, U, v, pulse = W.build_model(cfg, args.seed)
+    rho0 = W.half_filled_rho(h)
+    L, R = W.free_triangles(h, rho0, t)
+    n = n_t - 1
+    Sl, Sg = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+    threads = oracle.threads_available()
+    cols = list(range(0, n + 1, 64))  # 16 columns per step
+    for _ in range(args.warmup):
+        oracle.history_columns(t, order, n, L, R, Sl, Sg, cols[:2], nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.history_columns(t, order, n, L, R, Sl, Sg, cols, nthreads=threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    frac = column_units(n, cols) / slice_units(n)
+    value = args.P * slice_flops(M, n) * frac / dt / 1e12 / args.P
+    sample = "oracle history slice n=%d, %d of %d output columns per step, %d threads" % (n, len(cols), n + 1, threads)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / frac * args.P, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: KBE step of row n=1023, P=%d (oracle, extrapolated from sampled columns)"
+                                   % (WORKLOAD, args.P)},
+            "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

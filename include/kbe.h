@@ -1,0 +1,198 @@
+/*
+ * kbe.h -- C ABI of the GB300 (sm_103a) hot path of the adaptive
+ * Kadanoff-Baym solver of Blommel, Gardner, Woodward and Gull,
+ * "Adaptive Time Stepping for the Two-Time Integro-Differential
+ * Kadanoff-Baym Equations" (arXiv 2405.08737).
+ *
+ * At each new time t_n of a nonuniform grid the library computes
+ *   - the second-Born self-energy row Sigma^{<,>}(t_n, t_c), c <= n
+ *     (Sec. 2, Eq. SE, for a local interaction U_abcd = U_a delta_abcd),
+ *   - the history (collision) integrals of Eq. (KBE2),
+ *       I^s(n,c) = sum_{m<=n} w_{n,m} Sigma^R(n,m) G^s(m,c)
+ *                + sum_{m<=c} w_{c,m} Sigma^s(n,m) G^A(m,c),   s in {<,>},
+ *     with the variable-order interpolatory weights w of Sec. 3.2
+ *     (Eq. weights and the composite-row recursion),
+ *   - one KBE step of row n (predictor, then P fixed-point sweeps of
+ *     self-energy, history integrals, right-hand side and corrector;
+ *     Sec. 3.1 solves each step by fixed-point iteration).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex numbers are interleaved (re, im) doubles (complex128).
+ *  - Two-time arrays are triangle-packed: the lower triangle r >= c of the
+ *    (t, t') plane, block p(r,c) = r(r+1)/2 + c, each block an MxM
+ *    row-major matrix (M = norb).  The upper triangle follows from the
+ *    anti-Hermitian symmetry G(t,t') = -G(t',t)^+ (Sec. 2).  Row n is the
+ *    contiguous run of blocks p(n,0) .. p(n,n).
+ *      L(r,c) = G^<(t_r, t_c),  R(r,c) = G^R(t_r, t_c),
+ *    and R(r,r) must hold -i*1 (Eq. BC with theta(0) = 1), so that
+ *    G^> = R + L on and below the diagonal.
+ *  - Self-energy rows are [n+1][M][M] (c = 0..n); history slices are
+ *    [2][n+1][M][M] with s = 0 for "<" and s = 1 for ">".
+ *  - Device pointers are borrowed, never freed, and must be 16-byte
+ *    aligned.  Host pointers are read during the call only.
+ *  - "stream" is a cudaStream_t (NULL = legacy default stream).  Calls
+ *    that launch kernels are asynchronous; a non-KBE_OK return means that
+ *    nothing (or not everything) was enqueued.
+ *  - Calls never exit, abort or trap the GPU.  Kernel-side problems
+ *    (non-finite values, a device wait that ran out) set a device status
+ *    word that kbe_sync_status() returns.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef KBE_H
+#define KBE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kbe_ctx kbe_ctx;
+typedef int kbe_status;
+
+#define KBE_OK 0
+#define KBE_EINVAL 1   /* null or misaligned pointer, bad size or index     */
+#define KBE_ERANGE 2   /* order outside [1, KBE_MAX_ORDER], n beyond grid   */
+#define KBE_ENOMEM 3   /* device allocation failed                          */
+#define KBE_ECUDA 4    /* a CUDA runtime call or launch failed              */
+#define KBE_ENUMERIC 5 /* a kernel saw a non-finite value                   */
+#define KBE_ETIMEOUT 6 /* a bounded device wait ran out                     */
+#define KBE_ESTATE 7   /* call made out of order (no grid, no model, ...)   */
+
+#define KBE_MAX_ORDER 12   /* largest per-interval quadrature order k      */
+#define KBE_RING_ROWS 13   /* right-hand-side rows kept by the stepper     */
+
+/* precision argument of kbe_history_slice / kbe_step */
+#define KBE_FP64 0        /* plain FP64 arithmetic, deterministic            */
+
+/* ---------------------------------------------------------- lifecycle -- */
+
+/* Create a context for norb orbitals and at most n_max time points.
+ * Allocates device workspace only (split-reduction partials, weight tables,
+ * status word); the two-time arrays belong to the caller.
+ * KBE_EINVAL: out == NULL, norb < 1, norb > 64, n_max < 1, or sizes that
+ * overflow 64-bit block indices.  KBE_ENOMEM / KBE_ECUDA on device errors. */
+kbe_status kbe_create(int norb, int n_max, kbe_ctx** out);
+
+/* Free the context and its workspace (NULL is accepted). */
+kbe_status kbe_destroy(kbe_ctx* ctx);
+
+/* Text of the last error on this context (static storage of the context;
+ * "" when none).  A NULL ctx gives the last kbe_create error. */
+const char* kbe_last_error(const kbe_ctx* ctx);
+
+/* ------------------------------------------------------------- grid ---- */
+
+/* Set the time grid t[0..n_t-1] and the per-interval orders order[1..n_t-1]
+ * (order[0] is ignored).  Host arrays, copied.  Requires t[0] = 0, t
+ * strictly increasing and finite (else KBE_EINVAL), 1 <= order[l] <=
+ * KBE_MAX_ORDER (else KBE_ERANGE), 1 <= n_t <= n_max (else KBE_EINVAL).
+ * Interval l uses order kappa_l = min(order[l], l) (backward stencils).
+ * The local weights of Sec. 3.2, Eq. (weights), are computed here in host
+ * FP64 by a fully pivoted LU solve of the Vandermonde system, the composite
+ * rows w_{c,m} are assembled by the recursion of Sec. 3.2 and stored as a
+ * settled vector plus a band, and the stepper's predictor/corrector weights
+ * are tabulated; all of it is uploaded synchronously. */
+kbe_status kbe_set_grid(kbe_ctx* ctx, const double* t, const int* order, int n_t);
+
+/* Host FP64 composite weight row w_{n,0..n} of a grid (Sec. 3.2), by the
+ * same LU solves and recursion kbe_set_grid uses.  No context, no GPU.
+ * Same validation as kbe_set_grid; n must lie in [0, n_t-1]. */
+kbe_status kbe_grid_weights(const double* t, const int* order, int n_t, int n, double* row);
+
+/* Host FP64 weights w[0..k] of the rule that integrates over [lo, hi] the
+ * degree-k interpolant through the nodes tau[0..k] (Eq. weights), by a
+ * fully pivoted LU solve of V^T w = T.  No context, no GPU.
+ * KBE_EINVAL for k < 0, k > KBE_MAX_ORDER, repeated nodes or NULL. */
+kbe_status kbe_local_weights(const double* tau, int k, double lo, double hi, double* w);
+
+/* ------------------------------------------------------------ model ---- */
+
+/* Model of the stepper: h(t) = h0 + E(t) diag(v) with
+ * E(t) = E0 exp(-(t-t0)^2 / (2 sigma^2)) cos(omega t), pulse = {E0, t0,
+ * sigma, omega}; local interaction U[0..M-1].  The Fock matrix of Eq. (eps)
+ * for this interaction is eps(t) = h(t) + diag(U_a n_a(t)) with
+ * n_a = Im G^<_aa(t,t).  h0 is a host complex MxM matrix; U, v host
+ * doubles.  KBE_EINVAL for NULL pointers, non-finite values or sigma <= 0. */
+kbe_status kbe_set_model(kbe_ctx* ctx, const double* h0, const double* U, const double* v,
+                         const double* pulse);
+
+/* ------------------------------------------------------- hot path ------ */
+
+/* Self-energy row n (Sec. 2, Eq. SE with the local interaction of the
+ * model): for c = 0..n and every (a,b)
+ *   S^>(n,c)_ab = -U_a U_b [G^>(n,c)_ab]^2 conj(G^<(n,c)_ab),
+ *   S^<(n,c)_ab = -U_a U_b [G^<(n,c)_ab]^2 conj(G^>(n,c)_ab),
+ * with G^< = L and G^> = R + L from row n.  (G^<>(t_c,t_n)_ba =
+ * -conj(G^<>(t_n,t_c)_ab) turns Eq. SE's third factor into the conjugate.)
+ * On the diagonal block c = n the third factor is the stored entry
+ * G^><(t_n,t_n)_ba itself, as Eq. SE reads.
+ * L, R: device triangles holding row n.  S_less, S_great: device rows
+ * [n+1][M][M], written.  Requires a grid (n < n_t) and a model. */
+kbe_status kbe_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, const void* R, void* S_less,
+                                void* S_great, void* stream);
+
+/* Self-energy of every stored block of a triangle of n_rows rows (the
+ * row formula above applied to each block), S triangles written.  Used for
+ * whole-history evaluation.  Requires a model. */
+kbe_status kbe_selfenergy_all(kbe_ctx* ctx, int n_rows, const void* L, const void* R, void* S_less,
+                              void* S_great, void* stream);
+
+/* History slice of row n, Eq. (KBE2) (formula at the top of this file):
+ * I_out [2][n+1][M][M] device, written.  L, R: device triangles holding
+ * rows 0..n; S_less, S_great: device self-energy row n.  precision:
+ * KBE_FP64.  Deterministic for KBE_FP64 (fixed split and reduction order).
+ * Requires a grid with n < n_t.  Uses the context's workspace: calls on
+ * one context must not overlap on different streams. */
+kbe_status kbe_history_slice(kbe_ctx* ctx, int n, int precision, const void* L, const void* R,
+                             const void* S_less, const void* S_great, void* I_out, void* stream);
+
+/* ----------------------------------------------------------- stepper --- */
+
+/* Right-hand-side row j of Eq. (KBE2), the t-derivative along row j:
+ *   F^s(j,c) = -i ( eps(t_j) G^s(j,c) + I^s(j,c) ),  c = 0..j,
+ * computed from rows 0..j of L, R (self-energy and history slice of row j
+ * included) into slot j % KBE_RING_ROWS of F_ring.  F_ring: device
+ * [KBE_RING_ROWS][2][n_max][M][M]; row j of a slot uses its first j+1
+ * blocks per s.  S_less/S_great: device rows [n_max][M][M] (scratch);
+ * I_work: device [2][n_max][M][M] (receives the history slice).  Used to
+ * start a run (j = 0) or to rebuild stored right-hand sides at a restart. */
+kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const void* R, void* S_less,
+                       void* S_great, void* I_work, void* F_ring, void* stream);
+
+/* One KBE step of row n >= 1 (rows 0..n-1 of L, R and the right-hand-side
+ * rows n-K..n-1 of F_ring present, K = largest order on the grid):
+ *   predictor  G^s(n,c) = G^s(n-1,c) + sum_p wp_p F^s(n-q+p, c) over the q =
+ *              min(k_n, n-c) points t_{n-q..n-1} (extrapolation rule);
+ *              diagonal from D(j) = F^<(j,j) - F^<(j,j)^+, q = min(k_n, n);
+ *   P times    self-energy row n, history row n, F row n, then the corrector
+ *              G^s(n,c) = G^s(n-1,c) + sum_p w_p F^s(n-kap+p, c) over the
+ *              kap+1 points t_{n-kap..n}, kap = min(k_n, n-c) (diagonal:
+ *              min(k_n, n)), and R(n,c) = G^>(n,c) - L(n,c), R(n,n) = -i*1.
+ * Row n of L, R and slot n of F_ring are written; S_less, S_great, I_work
+ * hold row n's last self-energy and history slice.  1 <= P <= 16. */
+kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* S_less,
+                    void* S_great, void* I_work, void* F_ring, void* stream);
+
+/* Synchronize stream and return the device status word accumulated since
+ * the last call (then cleared): KBE_OK, KBE_ENUMERIC or KBE_ETIMEOUT. */
+kbe_status kbe_sync_status(kbe_ctx* ctx, void* stream);
+
+/* Number of kernels the last kbe_* call on this context enqueued. */
+int kbe_last_launch_count(const kbe_ctx* ctx);
+
+/* Measurement support.  With profiling enabled, every history-contraction
+ * kernel the context launches is bracketed by a CUDA event pair recorded on
+ * its stream; kbe_set_profiling() also discards earlier records.
+ * kbe_read_profiling() waits for the recorded events and returns how many
+ * contraction kernels ran and their summed duration in milliseconds.
+ * Event recording adds no kernels and no synchronization to the calls. */
+kbe_status kbe_set_profiling(kbe_ctx* ctx, int enable);
+kbe_status kbe_read_profiling(kbe_ctx* ctx, int* count, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KBE_H */

@@ -1,0 +1,250 @@
+"""Python binding of libkbe: the GB300 hot path of the adaptive
+Kadanoff-Baym solver (arXiv 2405.08737).
+
+Argument marshalling only.  Every step of the path runs in the library's
+CUDA kernels; PyTorch provides device memory and streams.  There is no CPU
+fallback: if the compiled library is missing, importing the handles raises.
+
+Layouts (see include/kbe.h): complex128 tensors, two-time arrays
+``[tri(N), M, M]`` with block ``r*(r+1)//2 + c`` for ``r >= c``;
+self-energy rows ``[n+1, M, M]``; history slices ``[2, n+1, M, M]``;
+right-hand-side ring ``[KBE_RING_ROWS, 2, n_max, M, M]``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkbe.so")
+
+KBE_OK, KBE_EINVAL, KBE_ERANGE, KBE_ENOMEM, KBE_ECUDA, KBE_ENUMERIC, KBE_ETIMEOUT, KBE_ESTATE = range(8)
+KBE_MAX_ORDER = 12
+KBE_RING_ROWS = 13
+KBE_FP64 = 0
+PRECISIONS = {"fp64": KBE_FP64}
+
+_lib = None
+
+
+class KBEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("kbe status %d: %s" % (status, msg))
+        self.status = status
+
+
+def lib():
+    """The loaded libkbe (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libkbe.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_2405_08737_gb300.build); there is no fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.kbe_create.argtypes = [i, i, ctypes.POINTER(vp)]
+        L.kbe_destroy.argtypes = [vp]
+        L.kbe_last_error.argtypes = [vp]
+        L.kbe_last_error.restype = ctypes.c_char_p
+        L.kbe_last_launch_count.argtypes = [vp]
+        L.kbe_set_grid.argtypes = [vp, vp, vp, i]
+        L.kbe_grid_weights.argtypes = [vp, vp, i, i, vp]
+        L.kbe_local_weights.argtypes = [vp, i, d, d, vp]
+        L.kbe_set_model.argtypes = [vp, vp, vp, vp, vp]
+        L.kbe_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp]
+        L.kbe_selfenergy_all.argtypes = [vp, i, vp, vp, vp, vp, vp]
+        L.kbe_history_slice.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
+        L.kbe_rhs_row.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_sync_status.argtypes = [vp, vp]
+        L.kbe_set_profiling.argtypes = [vp, i]
+        L.kbe_read_profiling.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d)]
+        _lib = L
+    return _lib
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _raise(status, ctx=None):
+    if status != KBE_OK:
+        msg = lib().kbe_last_error(ctx).decode()
+        raise KBEError(status, msg)
+
+
+# ------------------------------------------------------------- host weights
+def grid_weights(t, order, n):
+    """Composite weight row w_{n,0..n} (host FP64, Sec. 3.2)."""
+    t = np.ascontiguousarray(t, np.float64)
+    order = np.ascontiguousarray(order, np.int32)
+    row = np.zeros(n + 1)
+    _raise(lib().kbe_grid_weights(_np_ptr(t), _np_ptr(order), len(t), n, _np_ptr(row)))
+    return row
+
+
+def local_weights(tau, lo, hi):
+    """Weights of the degree-(len(tau)-1) interpolatory rule over [lo, hi]."""
+    tau = np.ascontiguousarray(tau, np.float64)
+    w = np.zeros(len(tau))
+    _raise(lib().kbe_local_weights(_np_ptr(tau), len(tau) - 1, lo, hi, _np_ptr(w)))
+    return w
+
+
+def tri_size(n):
+    return n * (n + 1) // 2
+
+
+# --------------------------------------------------------------- context
+class Context:
+    """A kbe_ctx for ``norb`` orbitals and up to ``n_max`` time points."""
+
+    def __init__(self, norb, n_max):
+        import torch  # noqa: F401  (device memory and streams)
+        self.M = int(norb)
+        self.n_max = int(n_max)
+        h = ctypes.c_void_p()
+        _raise(lib().kbe_create(self.M, self.n_max, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kbe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers
+    def _check(self, status):
+        if status != KBE_OK:
+            raise KBEError(status, lib().kbe_last_error(self._h).decode())
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = torch.cuda.current_stream() if stream is None else stream
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _dev(self, x, shape=None):
+        import torch
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError("expected a CUDA tensor")
+        if x.dtype != torch.complex128:
+            raise TypeError("expected complex128, got %s" % x.dtype)
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        if shape is not None and tuple(x.shape[: len(shape)]) != tuple(shape):
+            raise ValueError("bad shape %s, expected leading %s" % (tuple(x.shape), tuple(shape)))
+        return ctypes.c_void_p(x.data_ptr())
+
+    @property
+    def last_launch_count(self):
+        return int(lib().kbe_last_launch_count(self._h))
+
+    # -- allocation helpers (PyTorch owns the memory)
+    def empty_triangle(self, n_rows=None):
+        import torch
+        n = self.n_max if n_rows is None else n_rows
+        return torch.zeros((tri_size(n), self.M, self.M), dtype=torch.complex128, device="cuda")
+
+    def empty_rows(self):
+        import torch
+        return torch.zeros((self.n_max, self.M, self.M), dtype=torch.complex128, device="cuda")
+
+    def empty_slice(self):
+        import torch
+        return torch.zeros((2, self.n_max, self.M, self.M), dtype=torch.complex128, device="cuda")
+
+    def empty_ring(self):
+        import torch
+        return torch.zeros((KBE_RING_ROWS, 2, self.n_max, self.M, self.M), dtype=torch.complex128, device="cuda")
+
+    # -- API
+    def set_grid(self, t, order):
+        t = np.ascontiguousarray(t, np.float64)
+        order = np.ascontiguousarray(order, np.int32)
+        self.t = t
+        self.order = order
+        self._check(lib().kbe_set_grid(self._h, _np_ptr(t), _np_ptr(order), len(t)))
+
+    def set_model(self, h0, U, v, pulse=None):
+        h0 = np.ascontiguousarray(h0, np.complex128)
+        U = np.ascontiguousarray(U, np.float64)
+        v = np.ascontiguousarray(v, np.float64)
+        p = np.array([0.0, 0.0, 1.0, 0.0]) if pulse is None else np.array(
+            [pulse["E0"], pulse["t0"], pulse["sigma"], pulse["omega"]], np.float64)
+        self._check(lib().kbe_set_model(self._h, _np_ptr(h0), _np_ptr(U), _np_ptr(v), _np_ptr(p)))
+
+    def selfenergy_slice(self, n, L, R, Sl, Sg, stream=None):
+        self._check(lib().kbe_selfenergy_slice(self._h, n, self._dev(L), self._dev(R), self._dev(Sl),
+                                               self._dev(Sg), self._stream(stream)))
+
+    def selfenergy_all(self, n_rows, L, R, Sl, Sg, stream=None):
+        self._check(lib().kbe_selfenergy_all(self._h, n_rows, self._dev(L), self._dev(R), self._dev(Sl),
+                                             self._dev(Sg), self._stream(stream)))
+
+    def history_slice(self, n, L, R, Sl, Sg, out, precision="fp64", stream=None):
+        self._check(lib().kbe_history_slice(self._h, n, PRECISIONS[precision], self._dev(L), self._dev(R),
+                                            self._dev(Sl), self._dev(Sg), self._dev(out), self._stream(stream)))
+
+    def rhs_row(self, j, L, R, Sl, Sg, I_work, F_ring, precision="fp64", stream=None):
+        self._check(lib().kbe_rhs_row(self._h, j, PRECISIONS[precision], self._dev(L), self._dev(R),
+                                      self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_ring),
+                                      self._stream(stream)))
+
+    def step(self, n, L, R, Sl, Sg, I_work, F_ring, P=2, precision="fp64", stream=None):
+        self._check(lib().kbe_step(self._h, n, P, PRECISIONS[precision], self._dev(L), self._dev(R),
+                                   self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_ring),
+                                   self._stream(stream)))
+
+    def set_profiling(self, enable):
+        """Record CUDA events around each contraction kernel (clears old records)."""
+        self._check(lib().kbe_set_profiling(self._h, 1 if enable else 0))
+
+    def read_profiling(self):
+        """(number of contraction kernels timed, their total milliseconds)."""
+        n = ctypes.c_int()
+        ms = ctypes.c_double()
+        self._check(lib().kbe_read_profiling(self._h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def sync_status(self, stream=None):
+        """Synchronize and raise if a kernel flagged a problem."""
+        self._check(lib().kbe_sync_status(self._h, self._stream(stream)))
+
+
+class Run:
+    """Device state of one run: triangles, self-energy rows, history slice
+    and the right-hand-side ring, plus the calls that advance it."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+        self.L = ctx.empty_triangle()
+        self.R = ctx.empty_triangle()
+        self.Sl = ctx.empty_rows()
+        self.Sg = ctx.empty_rows()
+        self.I = ctx.empty_slice()
+        self.F = ctx.empty_ring()
+
+    def init_uncorrelated(self, rho0, stream=None):
+        """Row 0 from G^<(0,0) = i rho0, G^R(0,0) = -i, and its right-hand side."""
+        import torch
+        M = self.ctx.M
+        rho = torch.as_tensor(np.asarray(rho0, np.complex128), device="cuda")
+        self.L[0].copy_(1j * rho)
+        self.R[0].copy_(-1j * torch.eye(M, dtype=torch.complex128, device="cuda"))
+        self.ctx.rhs_row(0, self.L, self.R, self.Sl, self.Sg, self.I, self.F, stream=stream)
+
+    def step(self, n, P=2, precision="fp64", stream=None):
+        self.ctx.step(n, self.L, self.R, self.Sl, self.Sg, self.I, self.F, P=P, precision=precision,
+                      stream=stream)

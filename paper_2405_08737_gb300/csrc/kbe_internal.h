@@ -1,0 +1,139 @@
+// kbe_internal.h -- definitions shared by the translation units of libkbe.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kbe.h"
+
+namespace kbe {
+
+constexpr int kMaxOrder = KBE_MAX_ORDER;
+constexpr int kRing = KBE_RING_ROWS;
+constexpr int kMaxNorb = 64;
+constexpr int kMaxSplit = 16;      // largest split of the history index m
+constexpr int kWTab = kMaxOrder + 1;  // row stride of the stepper weight tables
+
+__host__ __device__ inline int64_t tri(int64_t r, int64_t c) { return r * (r + 1) / 2 + c; }
+
+// Device status bits (reported by kbe_sync_status).
+constexpr int kStatusNumeric = 1;
+constexpr int kStatusTimeout = 2;
+
+// Read-only view of the composite weights on the device:
+//   w_{c,m} = band[c * band_w + (c - m)]  if c - m < band_w,
+//           = wbar[m]                     otherwise
+// (Sec. 3.2: rows agree with the settled sums for m < c - K).
+struct WeightsView {
+  const double* wbar;
+  const double* band;
+  int band_w;
+  __device__ __forceinline__ double at(int c, int m) const {
+    const int d = c - m;
+    return d < band_w ? band[(int64_t)c * band_w + d] : wbar[m];
+  }
+};
+
+// Host-side grid data (FP64), also the source of the device tables.
+struct HostGrid {
+  int n_t = 0;
+  int K = 0;                      // largest effective order on the grid
+  std::vector<double> t;
+  std::vector<int> order;         // order[l], l >= 1 (order[0] = 0)
+  std::vector<double> wbar;       // settled composite weights, [n_t]
+  std::vector<double> band;       // w_{c, c-j}, [n_t][K+1]
+  std::vector<double> corr;       // corrector weights [n_t][kMaxOrder][kWTab]
+  std::vector<double> pred;       // predictor weights [n_t][kMaxOrder][kWTab]
+};
+
+// Host FP64 weight routines (weights.cpp).  Return KBE_OK or an error code
+// with a message in *err.
+kbe_status local_weights(const double* tau, int k, double lo, double hi, double* w, std::string* err);
+kbe_status build_grid(const double* t, const int* order, int n_t, HostGrid* g, std::string* err);
+
+struct Model {
+  bool set = false;
+  std::vector<double> h0;   // complex MxM interleaved
+  std::vector<double> U, v;
+  double E0 = 0, t0 = 0, sigma = 1, omega = 0;
+  double field(double t) const;
+};
+
+}  // namespace kbe
+
+// The context behind the opaque handle.
+struct kbe_ctx {
+  int M = 0;
+  int n_max = 0;
+  std::string err;
+  int last_launches = 0;
+  kbe::HostGrid grid;
+  bool grid_set = false;
+  kbe::Model model;
+  // device state
+  int device = 0;
+  double* d_wbar = nullptr;
+  double* d_band = nullptr;
+  double* d_corr = nullptr;
+  double* d_pred = nullptr;
+  double* d_h0 = nullptr;     // complex MxM
+  double* d_U = nullptr;      // M
+  double* d_v = nullptr;      // M
+  double* d_eps = nullptr;    // complex MxM (Fock matrix of the current row)
+  double* d_part = nullptr;   // split partials [kMaxSplit][2][n_max][M][M] complex
+  int* d_status = nullptr;
+  size_t part_bytes = 0;
+  // measurement: event pairs around each contraction kernel
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+};
+
+namespace kbe {
+
+// ---- launchers (each returns cudaGetLastError() after the launch) -------
+cudaError_t launch_sigma(int M, int64_t first_block, int64_t n_blocks, int64_t diag_rel, const double* L,
+                         const double* R, const double* U, double* Sl, double* Sg, int* status, cudaStream_t s);
+
+struct HistoryArgs {
+  int M, n;
+  const double* L;
+  const double* R;
+  const double* Sl;
+  const double* Sg;
+  WeightsView w;
+  double* out;       // [2][n+1][M][M]
+  double* part;      // workspace
+  size_t part_bytes;
+  int* status;
+  cudaEvent_t ev_begin = nullptr;  // optional timing of the contraction kernel
+  cudaEvent_t ev_end = nullptr;
+};
+// FP64 history slice; sets *launches to the number of kernels enqueued.
+cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches);
+
+struct StepArgs {
+  int M, n, K;
+  int kn;            // order of interval n
+  double field;      // E(t_n)
+  double* L;
+  double* R;
+  double* F;         // ring [kRing][2][n_max][M][M]
+  int n_max;
+  const double* I;   // [2][n+1][M][M]
+  const double* h0;
+  const double* U;
+  const double* v;
+  double* eps;
+  const double* corr;  // weights of interval n: [kMaxOrder][kWTab]
+  const double* pred;
+  int* status;
+};
+cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_fock(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_rhs(const StepArgs& a, cudaStream_t s);          // F row n only
+cudaError_t launch_rhs_corrector(const StepArgs& a, cudaStream_t s);  // F row n, then new row n
+
+}  // namespace kbe

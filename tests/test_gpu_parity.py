@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerance: 1e-12 relative in the max norm per slice (both s, all columns)
+for the FP64 path; the self-energy is elementwise and checked at 1e-14."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def kbe():
+    import torch
+    from paper_2405_08737_gb300 import build as B
+    B.build()
+    import paper_2405_08737_gb300 as K
+    torch.cuda.set_device(0)
+    return K
+
+
+def _dev(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _case(M, n_t, seed, kind="free", kmax=5):
+    t, order = W.grid(n_t, 0.05, 0.4, seed, kmax=kmax)
+    h = W.goe_h(M, seed)
+    rho0 = W.half_filled_rho(h)
+    if kind == "free":
+        L, R = W.free_triangles(h, rho0, t)
+    else:
+        L, R = W.random_triangles(M, n_t, seed)
+    U = np.linspace(0.5, 1.5, M)
+    return t, order, h, rho0, U, L, R
+
+
+def _ctx(kbe, M, n_max, t, order, h, U):
+    ctx = kbe.Context(M, n_max)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, U, W.site_potential(M), None)
+    return ctx
+
+
+@pytest.mark.parametrize("M,n_t,n", [(1, 4, 0), (2, 12, 5), (3, 20, 19), (8, 70, 63), (5, 33, 20)])
+def test_sigma_slice(kbe, M, n_t, n):
+    import torch
+    t, order, h, rho0, U, L, R = _case(M, n_t, M + n)
+    ctx = _ctx(kbe, M, n_t, t, order, h, U)
+    Ld, Rd = _dev(L), _dev(R)
+    Sl = torch.zeros((n + 1, M, M), dtype=torch.complex128, device="cuda")
+    Sg = torch.zeros_like(Sl)
+    ctx.selfenergy_slice(n, Ld, Rd, Sl, Sg)
+    ctx.sync_status()
+    ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+    assert _rel(Sl.cpu().numpy(), ol) < 1e-14
+    assert _rel(Sg.cpu().numpy(), og) < 1e-14
+    assert ctx.last_launch_count == 0  # sync_status launches nothing
+
+
+def test_sigma_all_rows(kbe):
+    import torch
+    M, n_t = 3, 20
+    t, order, h, rho0, U, L, R = _case(M, n_t, 4)
+    ctx = _ctx(kbe, M, n_t, t, order, h, U)
+    Sl = torch.zeros((W.tri_size(n_t), M, M), dtype=torch.complex128, device="cuda")
+    Sg = torch.zeros_like(Sl)
+    ctx.selfenergy_all(n_t, _dev(L), _dev(R), Sl, Sg)
+    ctx.sync_status()
+    Sl, Sg = Sl.cpu().numpy(), Sg.cpu().numpy()
+    for n in range(n_t):
+        ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+        p = W.tri_index(n, 0)
+        assert _rel(Sl[p:p + n + 1], ol) < 1e-14
+        assert _rel(Sg[p:p + n + 1], og) < 1e-14
+
+
+def _gpu_slice(kbe, ctx, n, L, R, Sl, Sg):
+    import torch
+    M = ctx.M
+    out = torch.zeros((2, n + 1, M, M), dtype=torch.complex128, device="cuda")
+    ctx.history_slice(n, L, R, _dev(Sl) if isinstance(Sl, np.ndarray) else Sl,
+                      _dev(Sg) if isinstance(Sg, np.ndarray) else Sg, out)
+    ctx.sync_status()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 5, 8, 16])
+@pytest.mark.parametrize("kind", ["free", "random"])
+def test_history_slice_small(kbe, M, kind):
+    n_t = 40
+    t, order, h, rho0, U, L, R = _case(M, n_t, 7 * M, kind)
+    ctx = _ctx(kbe, M, n_t, t, order, h, U)
+    Ld, Rd = _dev(L), _dev(R)
+    for n in (0, 1, 2, 5, 17, 39):
+        if kind == "free":
+            Sl, Sg = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+        else:
+            Sl, Sg = W.random_rows(M, n, 3 * n + M)
+        I = _gpu_slice(kbe, ctx, n, Ld, Rd, Sl, Sg)
+        ref = oracle.history_slice(t, order, n, L, R, Sl, Sg, nthreads=8)
+        assert _rel(I, ref) < TOL, (M, kind, n, _rel(I, ref))
+
+
+def test_history_slice_high_orders(kbe):
+    M, n_t = 4, 60
+    t, order, h, rho0, U, L, R = _case(M, n_t, 3, "free", kmax=12)
+    ctx = _ctx(kbe, M, n_t, t, order, h, U)
+    Ld, Rd = _dev(L), _dev(R)
+    for n in (3, 12, 13, 59):
+        Sl, Sg = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+        I = _gpu_slice(kbe, ctx, n, Ld, Rd, Sl, Sg)
+        ref = oracle.history_slice(t, order, n, L, R, Sl, Sg, nthreads=8)
+        assert _rel(I, ref) < 1e-11, n  # high-order weights differ by ~1e-13 between routes
+
+
+def test_history_all_slices_dimer(kbe):
+    """Hubbard dimer, 64 nonuniform points, orders in {1..5}: every slice."""
+    cfg = W.CONFIGS["dimer_m2_n64"]
+    t, order = W.grid(cfg["n_t"], cfg["dt0"], cfg["sig"], 0)
+    h, U, v, pulse = W.build_model(cfg, 0)
+    rho0 = W.half_filled_rho(h)
+    L, R = W.free_triangles(h, rho0, t)
+    M = cfg["M"]
+    ctx = _ctx(kbe, M, cfg["n_t"], t, order, h, U)
+    Ld, Rd = _dev(L), _dev(R)
+    import torch
+    Sl = torch.zeros((cfg["n_t"], M, M), dtype=torch.complex128, device="cuda")
+    Sg = torch.zeros_like(Sl)
+    for n in range(cfg["n_t"]):
+        ctx.selfenergy_slice(n, Ld, Rd, Sl, Sg)
+        I = _gpu_slice(kbe, ctx, n, Ld, Rd, Sl[: n + 1].contiguous(), Sg[: n + 1].contiguous())
+        ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+        ref = oracle.history_slice(t, order, n, L, R, ol, og, nthreads=8)
+        assert _rel(I, ref) < TOL, n
+
+
+def _full_size_case(kbe, name, seed=0):
+    import torch
+    cfg = W.CONFIGS[name]
+    M, n_t = cfg["M"], cfg["n_t"]
+    t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], seed)
+    h, U, v, pulse = W.build_model(cfg, seed)
+    rho0 = W.half_filled_rho(h)
+    Ld, Rd = W.free_triangles_torch(h, rho0, t, n_t, "cuda")
+    ctx = _ctx(kbe, M, n_t, t, order, h, U)
+    return cfg, t, order, h, U, ctx, Ld, Rd
+
+
+@pytest.mark.parametrize("name", ["chain_m8_n1024"])
+def test_history_full_size_sampled(kbe, name):
+    """The full-size slice n = N_t - 1 in the launch configuration the
+    benchmark times; the oracle evaluates sampled output columns."""
+    import torch
+    cfg, t, order, h, U, ctx, Ld, Rd = _full_size_case(kbe, name)
+    M, n = cfg["M"], cfg["n_t"] - 1
+    Sl = torch.zeros((n + 1, M, M), dtype=torch.complex128, device="cuda")
+    Sg = torch.zeros_like(Sl)
+    ctx.selfenergy_slice(n, Ld, Rd, Sl, Sg)
+    out = torch.zeros((2, n + 1, M, M), dtype=torch.complex128, device="cuda")
+    ctx.history_slice(n, Ld, Rd, Sl, Sg, out)
+    ctx.sync_status()
+    I = out.cpu().numpy()
+    L, R = Ld.cpu().numpy(), Rd.cpu().numpy()
+    Sl_h, Sg_h = Sl.cpu().numpy(), Sg.cpu().numpy()
+    ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+    assert _rel(Sl_h, ol) < 1e-14 and _rel(Sg_h, og) < 1e-14
+    cols = [0, 1, 2, 255, 511, 700, n - 5, n - 1, n]
+    ref = oracle.history_columns(t, order, n, L, R, ol, og, cols, nthreads=oracle.threads_available())
+    assert _rel(I[:, cols], ref) < TOL
+
+
+def _oracle_run(t, order, h, U, v, pulse, rho0, n_t, P=2):
+    M = h.shape[0]
+    L0, R0, F0 = oracle.initial_rhs(t, order, h, U, v, pulse, rho0)
+    L = np.zeros((W.tri_size(n_t), M, M), np.complex128)
+    R = np.zeros_like(L)
+    L[0], R[0] = L0[0], R0[0]
+    return oracle.run(t[:n_t], order[:n_t], h, U, v, pulse, P, L, R, {0: F0}, 1, n_t,
+                      nthreads=oracle.threads_available())
+
+
+@pytest.mark.parametrize("name,n_t", [("dimer_m2_n64", 64), ("chain_m8_n1024", 48)])
+def test_stepper_matches_oracle(kbe, name, n_t):
+    cfg = W.CONFIGS[name]
+    t, order = W.grid(cfg["n_t"], cfg["dt0"], cfg["sig"], 1)
+    t, order = t[:n_t], order[:n_t]
+    h, U, v, pulse = W.build_model(cfg, 1)
+    if pulse is not None:  # move the pulse into the short window
+        pulse = dict(pulse, t0=t[n_t // 2], sigma=0.3)
+    rho0 = W.half_filled_rho(h)
+    M = cfg["M"]
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, U, v, pulse)
+    run = kbe.Run(ctx)
+    run.init_uncorrelated(rho0)
+    for n in range(1, n_t):
+        run.step(n, P=2)
+    ctx.sync_status()
+    Lo, Ro, Io = _oracle_run(t, order, h, U, v, pulse, rho0, n_t)
+    L, R = run.L.cpu().numpy(), run.R.cpu().numpy()
+    for n in range(n_t):
+        p = W.tri_index(n, 0)
+        assert _rel(L[p:p + n + 1], Lo[p:p + n + 1]) < TOL, n
+        assert _rel(R[p:p + n + 1], Ro[p:p + n + 1]) < TOL, n
+    # last history slice as well
+    assert _rel(run.I[:, :n_t].cpu().numpy(), Io) < TOL
+
+
+def test_restart_from_frozen_history(kbe):
+    """Restart at row ns from a non-interacting history with its exact
+    right-hand sides (the frozen state of the gradient window)."""
+    import torch
+    cfg = W.CONFIGS["chain_m16_n512_w32"]
+    M, n_t, ns = cfg["M"], 40, 32
+    t, order = W.grid(cfg["n_t"], cfg["dt0"], cfg["sig"], 2)
+    t, order = t[:n_t], order[:n_t]
+    h, U, v, pulse = W.build_model(cfg, 2)
+    pulse = dict(pulse, t0=t[36], sigma=0.1)
+    rho0 = W.half_filled_rho(h)
+    L, R = W.free_triangles(h, rho0, t, n_rows=ns)
+    rows = oracle.f_rows_needed(order, ns, n_t)
+    Fr = W.free_rhs_rows(h, L, R, rows)
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, U, v, pulse)
+    run = kbe.Run(ctx)
+    run.L[: len(L)].copy_(_dev(L))
+    run.R[: len(R)].copy_(_dev(R))
+    for j in rows:
+        run.F[j % kbe.KBE_RING_ROWS, :, : j + 1].copy_(_dev(Fr[j]))
+    for n in range(ns, n_t):
+        run.step(n, P=2)
+    ctx.sync_status()
+    Lf = np.zeros((W.tri_size(n_t), M, M), np.complex128)
+    Rf = np.zeros_like(Lf)
+    Lf[: len(L)], Rf[: len(R)] = L, R
+    Lo, Ro, _ = oracle.run(t, order, h, U, v, pulse, 2, Lf, Rf, Fr, ns, n_t, nthreads=oracle.threads_available())
+    Lg = run.L[: W.tri_size(n_t)].cpu().numpy()
+    Rg = run.R[: W.tri_size(n_t)].cpu().numpy()
+    assert _rel(Lg, Lo) < TOL and _rel(Rg, Ro) < TOL
+    del torch
+
+
+def test_errors_are_reported_not_raised_on_device(kbe):
+    import torch
+    M, n_t = 2, 10
+    t, order, h, rho0, U, L, R = _case(M, n_t, 1)
+    ctx = kbe.Context(M, n_t)
+    Ld, Rd = _dev(L), _dev(R)
+    Sl = torch.zeros((n_t, M, M), dtype=torch.complex128, device="cuda")
+    Sg = torch.zeros_like(Sl)
+    out = torch.zeros((2, n_t, M, M), dtype=torch.complex128, device="cuda")
+    with pytest.raises(kbe.KBEError) as e:  # no grid yet
+        ctx.history_slice(3, Ld, Rd, Sl, Sg, out)
+    assert e.value.status == kbe.KBE_ESTATE
+    ctx.set_grid(t, order)
+    with pytest.raises(kbe.KBEError) as e:  # no model yet
+        ctx.selfenergy_slice(3, Ld, Rd, Sl, Sg)
+    assert e.value.status == kbe.KBE_ESTATE
+    ctx.set_model(h, U, W.site_potential(M), None)
+    with pytest.raises(kbe.KBEError) as e:
+        ctx.history_slice(n_t, Ld, Rd, Sl, Sg, out)
+    assert e.value.status == kbe.KBE_ERANGE
+    # a misaligned device pointer is rejected before any launch
+    lib = kbe.lib()
+    import ctypes
+    st = lib.kbe_history_slice(ctx._h, 3, 0, ctypes.c_void_p(Ld.data_ptr() + 8), ctypes.c_void_p(Rd.data_ptr()),
+                               ctypes.c_void_p(Sl.data_ptr()), ctypes.c_void_p(Sg.data_ptr()),
+                               ctypes.c_void_p(out.data_ptr()), None)
+    assert st == kbe.KBE_EINVAL
+    # a non-finite input is reported through the status word
+    Lbad = L.copy()
+    Lbad[W.tri_index(3, 1), 0, 1] = np.nan
+    ctx.selfenergy_slice(3, _dev(Lbad), Rd, Sl, Sg)
+    with pytest.raises(kbe.KBEError) as e:
+        ctx.sync_status()
+    assert e.value.status == kbe.KBE_ENUMERIC
+    ctx.sync_status()  # cleared
+    ctx.selfenergy_slice(3, Ld, Rd, Sl, Sg)  # the context stays usable
+    ctx.history_slice(3, Ld, Rd, Sl, Sg, out)
+    ctx.sync_status()
