@@ -12,8 +12,8 @@ before timing (the restart reconstruction).
 Metric: history-slice TFLOP/s = P * 8 M^3 (n+1)(3n+2) / step time, and ms
 per KBE step.  Inputs (1.07 GB of history) are larger than L2.
 
---impl reference times the CPU oracle (test infrastructure) on bounded
-samples of the same slice instead.
+--impl reference times the CPU oracle (test infrastructure) on the host
+cores instead: one oracle KBE step of the same row per step.
 """
 import argparse
 import json
@@ -38,15 +38,6 @@ def slice_flops(M, n):
     return 8.0 * M ** 3 * (n + 1) * (3 * n + 2)
 
 
-def column_units(n, cols):
-    """Block multiply-adds of the listed output columns (both s)."""
-    return sum(2 * (n + 1) + 2 * (c + 1) for c in cols)
-
-
-def slice_units(n):
-    return (n + 1) * (3 * n + 4)
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -56,6 +47,9 @@ def parse():
     ap.add_argument("--P", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-t", type=int, default=None,
+                    help="truncate the grid to this many points (smaller profiling case)")
     return ap.parse_args()
 
 
@@ -119,12 +113,15 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def setup_workload(kbe, seed):
+def setup_workload(kbe, seed, n_t_override=None):
     import torch
     import workloads as W
     cfg = W.CONFIGS[WORKLOAD]
     M, n_t = cfg["M"], cfg["n_t"]
     t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], seed)
+    if n_t_override:
+        n_t = int(n_t_override)
+        t, order = t[:n_t], order[:n_t]
     h, U, v, pulse = W.build_model(cfg, seed)
     rho0 = W.half_filled_rho(h)
     ctx = kbe.Context(M, n_t)
@@ -203,38 +200,47 @@ def e2e_steps(ctx, run, n, P, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps, h2d, d2h
 
 
-def cpu_baseline(kbe_run, t, order, U, n, M, budget_s=15.0, gpu_slice=None):
-    """The oracle on a bounded sample of output columns of the same slice;
-    returns (TFLOP/s-equivalent, threads, sample text, max rel deviation from
-    the GPU slice on those columns)."""
+def oracle_step_inputs(t, order, h, U, v, pulse, L_rows, R_rows, n, threads):
+    """Inputs of one oracle KBE step of row n: the history rows 0..n-1 and the
+    right-hand-side rows n-K..n-1 rebuilt by the oracle itself from them."""
     import oracle
-    L = kbe_run.L.cpu().numpy()
-    R = kbe_run.R.cpu().numpy()
-    ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+    M = h.shape[0]
+    L = np.zeros((W_tri(n + 1), M, M), np.complex128)
+    R = np.zeros_like(L)
+    L[: W_tri(n)] = L_rows
+    R[: W_tri(n)] = R_rows
+    F = {}
+    for j in oracle.f_rows_needed(order, n, n + 1):
+        F[j] = oracle.rhs_row(j, t, order, h, U, v, pulse, L[: W_tri(j + 1)], R[: W_tri(j + 1)], nthreads=threads)
+    return L, R, F
+
+
+def W_tri(n):
+    return n * (n + 1) // 2
+
+
+def cpu_baseline(run, t, order, h, U, v, pulse, n, M, P):
+    """The oracle's own KBE step of row n (P sweeps) from the same history on
+    the host cores: its time, and its deviation from the GPU step."""
+    import oracle
     threads = oracle.threads_available()
-    rng = np.random.default_rng(1)
-    cols = [n, n - 1, 0]
+    L_rows = run.L[: W_tri(n)].cpu().numpy()
+    R_rows = run.R[: W_tri(n)].cpu().numpy()
+    L, R, F = oracle_step_inputs(t, order, h, U, v, pulse, L_rows, R_rows, n, threads)
     t0 = time.perf_counter()
-    ref = oracle.history_columns(t, order, n, L, R, ol, og, cols, nthreads=threads)
+    Lo, Ro, Io = oracle.run(t[: n + 1], order[: n + 1], h, U, v, pulse, P, L, R, F, n, n + 1, nthreads=threads)
     dt = time.perf_counter() - t0
-    # grow the sample to about budget_s of CPU time
-    per_unit = dt / column_units(n, cols)
-    extra = int(max(0, budget_s / per_unit - column_units(n, cols)) / (3 * (n + 1)))
-    if extra > 0:
-        more = sorted(rng.choice(np.arange(1, n - 1), size=min(extra, n - 2), replace=False).tolist())
-        t0 = time.perf_counter()
-        ref2 = oracle.history_columns(t, order, n, L, R, ol, og, more, nthreads=threads)
-        dt = time.perf_counter() - t0
-        cols, ref = more, ref2
-    frac = column_units(n, cols) / slice_units(n)
-    tflops = slice_flops(M, n) * frac / dt / 1e12
-    err = None
-    if gpu_slice is not None:
-        g = gpu_slice[:, cols]
-        err = float(np.abs(g - ref).max() / np.abs(ref).max())
-    sample = "oracle history slice n=%d, %d of %d output columns (both s), %.1f s on %d threads" % (
-        n, len(cols), n + 1, dt, threads)
-    return tflops, threads, sample, err
+    p = W_tri(n)
+    gl = run.L[p:p + n + 1].cpu().numpy()
+    gr = run.R[p:p + n + 1].cpu().numpy()
+    gi = run.I[:, : n + 1].cpu().numpy()
+    err = {"row_L": float(np.abs(gl - Lo[p:]).max() / np.abs(Lo[p:]).max()),
+           "row_R": float(np.abs(gr - Ro[p:]).max() / np.abs(Ro[p:]).max()),
+           "history_slice": float(np.abs(gi - Io).max() / np.abs(Io).max())}
+    tflops = P * slice_flops(M, n) / dt / 1e12
+    sample = ("one oracle KBE step of row n=%d (P=%d: self-energy, history slice, corrector), "
+              "%.2f s wall on %d threads" % (n, P, dt, threads))
+    return tflops, threads, sample, err, dt
 
 
 def main():
@@ -247,7 +253,7 @@ def main():
     torch.cuda.set_device(local)
     import paper_2405_08737_gb300 as kbe
     kbe.lib()
-    cfg, t, order, h, U, v, pulse, ctx, run, n = setup_workload(kbe, args.seed + rank)
+    cfg, t, order, h, U, v, pulse, ctx, run, n = setup_workload(kbe, args.seed + rank, args.n_t)
     M = cfg["M"]
     stream = torch.cuda.current_stream()
     if world > 1:
@@ -272,27 +278,29 @@ def main():
             "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
             "kernel": "history_partial (FP64 DFMA contraction)", "launches_timed": k_count,
             "avg_ms": round(k_avg, 4), "peak_source": "measured DFMA probe (FP64 not in MEASURED_PEAKS.json)"}
-    gpu_slice = run.I[:, : n + 1].cpu().numpy()
-    e2e_ms, h2d, d2h = e2e_steps(ctx, run, n, args.P, max(3, args.steps // 4), 1, stream)
-    e2e = {"value": round(world * flops_step / (e2e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
-           "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms, h2d, d2h = e2e_steps(ctx, run, n, args.P, max(3, args.steps // 4), 1, stream)
+        e2e = {"value": round(world * flops_step / (e2e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+               "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     line = {"metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "%s: Hubbard chain M=8, N_t=1024 nonuniform, orders 1..5, pulse; "
-                                   "KBE step of row n=1023 with P=%d (FP64 path)" % (WORKLOAD, args.P),
-                       "norb": M, "n_t": cfg["n_t"], "n": n, "P": args.P, "precision": "fp64",
-                       "l2": "inputs larger than L2 (history 1.07 GB per step)",
+            "config": {"workload": "%s: Hubbard chain M=8, N_t=%d nonuniform, orders 1..5, pulse; "
+                                   "KBE step of row n=%d with P=%d (FP64 path)" % (WORKLOAD, n + 1, n, args.P),
+                       "norb": M, "n_t": n + 1, "n": n, "P": args.P, "precision": "fp64",
+                       "l2": "inputs larger than L2 (history %.2f GB per step)" % (2 * (n + 1) * (n + 2) / 2 * M * M * 16 / 1e9),
                        "parallelism": "independent replicas" if world > 1 else "single GPU"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches}
     if clk:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        tf, threads, sample, err = cpu_baseline(run, t, order, U, n, M, gpu_slice=gpu_slice)
+        tf, threads, sample, err, _ = cpu_baseline(run, t, order, h, U, v, pulse, n, M, args.P)
         line["cpu_baseline"] = {"value": round(tf, 6), "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                                 "sample": sample}
-        line["error_vs_oracle"] = {"max_rel": err, "where": "sampled columns of the timed slice"}
+        line["error_vs_oracle"] = dict(err, where="new row n and last history slice of the timed KBE step, "
+                                                  "max-norm relative")
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -302,9 +310,9 @@ def main():
 
 
 def main_reference(args, rank, world):
-    """The oracle (plain FP64 CPU C++) on the host cores, on bounded samples of
-    the same workload: each step evaluates a fixed sample of output columns
-    of the history slice of row n = N_t - 1."""
+    """The oracle (plain FP64 CPU C++, test infrastructure) on the host cores:
+    each step is one full oracle KBE step of row n = N_t - 1 of the same
+    workload (P sweeps of self-energy row, history slice and corrector)."""
     if rank != 0:
         return
     import oracle
@@ -312,28 +320,28 @@ def main_reference(args, rank, world):
     cfg = W.CONFIGS[WORKLOAD]
     M, n_t = cfg["M"], cfg["n_t"]
     t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], args.seed)
+    if args.n_t:
+        n_t = int(args.n_t)
+        t, order = t[:n_t], order[:n_t]
     h, U, v, pulse = W.build_model(cfg, args.seed)
     rho0 = W.half_filled_rho(h)
-    L, R = W.free_triangles(h, rho0, t)
     n = n_t - 1
-    Sl, Sg = oracle.sigma_row(oracle.local_U4(U), n, L, R)
     threads = oracle.threads_available()
-    cols = list(range(0, n + 1, 64))  # 16 columns per step
+    Lh, Rh = W.free_triangles(h, rho0, t, n_rows=n)
+    L, R, F = oracle_step_inputs(t, order, h, U, v, pulse, Lh, Rh, n, threads)
     for _ in range(args.warmup):
-        oracle.history_columns(t, order, n, L, R, Sl, Sg, cols[:2], nthreads=threads)
+        oracle.run(t, order, h, U, v, pulse, args.P, L, R, F, n, n + 1, nthreads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.history_columns(t, order, n, L, R, Sl, Sg, cols, nthreads=threads)
+        oracle.run(t, order, h, U, v, pulse, args.P, L, R, F, n, n + 1, nthreads=threads)
     dt = (time.perf_counter() - t0) / args.steps
-    frac = column_units(n, cols) / slice_units(n)
-    value = args.P * slice_flops(M, n) * frac / dt / 1e12 / args.P
-    sample = "oracle history slice n=%d, %d of %d output columns per step, %d threads" % (n, len(cols), n + 1, threads)
+    value = args.P * slice_flops(M, n) / dt / 1e12
+    sample = "one full oracle KBE step of row n=%d per step (P=%d), %d threads" % (n, args.P, threads)
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(dt * 1e3 / frac * args.P, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "%s: KBE step of row n=1023, P=%d (oracle, extrapolated from sampled columns)"
-                                   % (WORKLOAD, args.P)},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: Hubbard chain M=8, N_t=%d; KBE step of row n=%d with P=%d (CPU oracle)"
+                                   % (WORKLOAD, n_t, n, args.P)},
             "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -106,8 +106,9 @@ def free_triangles(h, rho0, t, n_rows=None):
     return L, R
 
 
-def free_triangles_torch(h, rho0, t, n_rows, device):
-    """``free_triangles`` built with torch on ``device`` (large histories)."""
+def free_triangles_torch(h, rho0, t, n_rows, device, chunk_blocks=1 << 18):
+    """``free_triangles`` built with torch on ``device`` (large histories),
+    a few batched products per chunk of rows."""
     A = torch.from_numpy(propagators(h, t[:n_rows])).to(device)
     rho = torch.from_numpy(rho0).to(device)
     M = h.shape[0]
@@ -115,13 +116,23 @@ def free_triangles_torch(h, rho0, t, n_rows, device):
     L = torch.empty((ntri, M, M), dtype=torch.complex128, device=device)
     R = torch.empty_like(L)
     Ar = A @ rho
-    Ah = A.conj().transpose(1, 2)
-    eye = torch.eye(M, dtype=torch.complex128, device=device)
-    for r in range(n_rows):
-        p = tri_index(r, 0)
-        L[p:p + r + 1] = 1j * (Ar[r].unsqueeze(0) @ Ah[: r + 1])
-        R[p:p + r + 1] = -1j * (A[r].unsqueeze(0) @ Ah[: r + 1])
-        R[p + r] = -1j * eye
+    Ah = A.conj().transpose(1, 2).contiguous()
+    r0 = 0
+    while r0 < n_rows:
+        r1 = r0 + 1
+        while r1 < n_rows and tri_size(r1 + 1) - tri_size(r0) <= chunk_blocks:
+            r1 += 1
+        p0, p1 = tri_size(r0), tri_size(r1)
+        idx = torch.arange(p0, p1, device=device)
+        r = ((torch.sqrt(8.0 * idx.double() + 1.0) - 1.0) / 2.0).floor().long()
+        r = torch.where(r * (r + 1) // 2 > idx, r - 1, r)
+        r = torch.where((r + 1) * (r + 2) // 2 <= idx, r + 1, r)
+        c = idx - r * (r + 1) // 2
+        L[p0:p1] = 1j * torch.bmm(Ar[r], Ah[c])
+        R[p0:p1] = -1j * torch.bmm(A[r], Ah[c])
+        r0 = r1
+    diag = torch.tensor([tri_index(q, q) for q in range(n_rows)], device=device)
+    R[diag] = -1j * torch.eye(M, dtype=torch.complex128, device=device)
     return L, R
 
 
