@@ -191,6 +191,34 @@ int kbe_last_launch_count(const kbe_ctx* ctx);
 kbe_status kbe_set_profiling(kbe_ctx* ctx, int enable);
 kbe_status kbe_read_profiling(kbe_ctx* ctx, int* count, double* total_ms);
 
+/* ------------------------------------------------ allocation-free entry -- */
+
+/* History slice of row n (the same Eq. KBE2 contraction and kernels as
+ * kbe_history_slice, KBE_FP64) for callers that cannot allocate device
+ * memory: code that runs inside another framework's memory pool or
+ * allocator hooks, graph builders that may not allocate while recording,
+ * or hosts that only hand over fixed buffers.  The paper has no
+ * counterpart; this entry exists for those callers.
+ *
+ * No context: the grid t[0..n_t-1], order[1..n_t-1] is passed on the host
+ * (same validation as kbe_set_grid) and its weights are recomputed on each
+ * call.  L, R, S_less, S_great, I_out are the caller's device buffers with
+ * the layouts of kbe_history_slice.  All scratch lives in one static
+ * device array of 64 MiB that every GPU loading the library reserves until
+ * the process exits: n_t <= 8192 and (n+1)*norb^2 <= about 1.37e6 complex
+ * entries, else KBE_EINVAL with a message in kbe_last_error(NULL).  The
+ * call allocates no device memory (no cudaMalloc, cudaFree or allocating
+ * library routine).  Its first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  The weight tables are
+ * copied from pageable host memory, so the call waits for earlier work on
+ * `stream`.  Every call shares the array and leaves its contents behind;
+ * calls whose kernels overlap on the GPU race on it.  Non-finite values
+ * are not reported (there is no context to hold a status word). */
+kbe_status kbe_history_slice_noalloc(int norb, int n, const double* t, const int* order, int n_t,
+                                     const void* L, const void* R, const void* S_less,
+                                     const void* S_great, void* I_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,8 @@ StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F
 
 }  // namespace
 
+void kbe::set_global_error(const char* msg) { g_create_err = msg; }
+
 extern "C" {
 
 kbe_status kbe_create(int norb, int n_max, kbe_ctx** out) {

@@ -53,6 +53,9 @@ struct HostGrid {
 kbe_status local_weights(const double* tau, int k, double lo, double hi, double* w, std::string* err);
 kbe_status build_grid(const double* t, const int* order, int n_t, HostGrid* g, std::string* err);
 
+// Record a context-free error message (returned by kbe_last_error(NULL)).
+void set_global_error(const char* msg);
+
 struct Model {
   bool set = false;
   std::vector<double> h0;   // complex MxM interleaved
