@@ -65,6 +65,14 @@ typedef int kbe_status;
 
 /* precision argument of kbe_history_slice / kbe_step */
 #define KBE_FP64 0        /* plain FP64 arithmetic, deterministic            */
+#define KBE_SPLIT_BF16 1  /* the contraction on the bf16 tensor cores with   */
+                          /* error-free 4-digit fixed-point splitting: every  */
+                          /* value becomes round(v 2^(31-e)) in balanced      */
+                          /* base-256 digits (e: exponent of its 16-entry     */
+                          /* chunk), all 16 digit products are summed exactly */
+                          /* in FP32 and combined in double-float; about 1e-9 */
+                          /* relative to the slice maximum.  norb <= 32.      */
+                          /* Deterministic.  Requires R(r,r) = -i*1 exactly. */
 
 /* ---------------------------------------------------------- lifecycle -- */
 

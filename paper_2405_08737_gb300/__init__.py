@@ -22,7 +22,8 @@ KBE_OK, KBE_EINVAL, KBE_ERANGE, KBE_ENOMEM, KBE_ECUDA, KBE_ENUMERIC, KBE_ETIMEOU
 KBE_MAX_ORDER = 12
 KBE_RING_ROWS = 13
 KBE_FP64 = 0
-PRECISIONS = {"fp64": KBE_FP64}
+KBE_SPLIT_BF16 = 1
+PRECISIONS = {"fp64": KBE_FP64, "split": KBE_SPLIT_BF16}
 
 _lib = None
 

@@ -38,7 +38,8 @@ void release(kbe_ctx* ctx) {
   ctx->ev_pool.clear();
   cudaFree(ctx->d_wbar); cudaFree(ctx->d_band); cudaFree(ctx->d_corr); cudaFree(ctx->d_pred);
   cudaFree(ctx->d_h0); cudaFree(ctx->d_U); cudaFree(ctx->d_v); cudaFree(ctx->d_eps);
-  cudaFree(ctx->d_part); cudaFree(ctx->d_status);
+  cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split);
+  ctx->d_split = nullptr;
   ctx->d_wbar = ctx->d_band = ctx->d_corr = ctx->d_pred = nullptr;
   ctx->d_h0 = ctx->d_U = ctx->d_v = ctx->d_eps = ctx->d_part = nullptr;
   ctx->d_status = nullptr;
@@ -73,6 +74,14 @@ bool next_events(kbe_ctx* ctx, cudaEvent_t* b, cudaEvent_t* e) {
 
 kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void* R, const void* Sl,
                    const void* Sg, void* I_out, cudaStream_t s, int* launches) {
+  if (precision == KBE_SPLIT_BF16) {
+    if (!ctx->d_split) return fail(ctx, KBE_EINVAL, "split precision needs 1 <= norb <= 32");
+    SplitLaunch l{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
+                  weights_view(ctx), (double*)I_out, ctx->d_split, ctx->split_bytes, ctx->d_status};
+    if (!next_events(ctx, &l.ev_begin, &l.ev_end)) return fail(ctx, KBE_ECUDA, "profiling: cudaEventCreate");
+    cudaError_t e = launch_history_split(l, s, launches);
+    return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "split history slice launch");
+  }
   if (precision != KBE_FP64) return fail(ctx, KBE_EINVAL, "unknown precision");
   HistoryArgs a{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
                 weights_view(ctx), (double*)I_out, ctx->d_part, ctx->part_bytes, ctx->d_status};
@@ -139,6 +148,14 @@ kbe_status kbe_create(int norb, int n_max, kbe_ctx** out) {
     cudaGetLastError();
     return fail(nullptr, e == cudaErrorMemoryAllocation ? KBE_ENOMEM : KBE_ECUDA,
                 std::string("kbe_create: device allocation: ") + cudaGetErrorString(e));
+  }
+  ctx->split_bytes = split_workspace_bytes(norb, n_max);
+  if (ctx->split_bytes > 0 && (e = cudaMalloc(&ctx->d_split, ctx->split_bytes)) != cudaSuccess) {
+    release(ctx);
+    delete ctx;
+    cudaGetLastError();
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? KBE_ENOMEM : KBE_ECUDA,
+                std::string("kbe_create: split workspace: ") + cudaGetErrorString(e));
   }
   if ((e = cudaMemset(ctx->d_status, 0, sizeof(int))) != cudaSuccess) {
     release(ctx);
@@ -315,7 +332,7 @@ kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R,
   if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
   if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_work) || !aligned16(F_ring))
     return fail(ctx, KBE_EINVAL, "kbe_step: NULL or misaligned pointer");
-  if (precision != KBE_FP64) return fail(ctx, KBE_EINVAL, "kbe_step: unknown precision");
+  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16) return fail(ctx, KBE_EINVAL, "kbe_step: unknown precision");
   if ((st = use_device(ctx)) != KBE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   StepArgs a = step_args(ctx, n, L, R, I_work, F_ring);

@@ -86,6 +86,8 @@ struct kbe_ctx {
   double* d_v = nullptr;      // M
   double* d_eps = nullptr;    // complex MxM (Fock matrix of the current row)
   double* d_part = nullptr;   // split partials [kMaxSplit][2][n_max][M][M] complex
+  void* d_split = nullptr;    // split-precision workspace (digit planes of the small operands, partials)
+  size_t split_bytes = 0;
   int* d_status = nullptr;
   size_t part_bytes = 0;
   // measurement: event pairs around each contraction kernel
@@ -116,6 +118,30 @@ struct HistoryArgs {
 };
 // FP64 history slice; sets *launches to the number of kernels enqueued.
 cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches);
+
+// Split-precision history slice (history_split.cu).
+struct SplitGeomHost {
+  int M, n, CT, parts, cpt, tiles;
+  long long U;
+  int G, S;
+};
+struct SplitLaunch {
+  int M, n;
+  const double* L;
+  const double* R;
+  const double* Sl;
+  const double* Sg;
+  WeightsView w;
+  double* out;
+  void* work;
+  size_t work_bytes;
+  int* status;
+  cudaEvent_t ev_begin = nullptr;
+  cudaEvent_t ev_end = nullptr;
+};
+bool split_geometry(int M, int n, SplitGeomHost* h);
+size_t split_workspace_bytes(int M, int n_max);
+cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* launches);
 
 struct StepArgs {
   int M, n, K;

@@ -1,0 +1,226 @@
+// split_common.cuh -- fixed-point bf16 slicing and tcgen05 helpers of the
+// split-precision history slice.
+//
+// A double v with |v| < 2^e is represented as V = round(v * 2^(31-e)), an
+// integer with |V| < 2^31, written in balanced base-256 digits
+//   V = d0 2^24 + d1 2^16 + d2 2^8 + d3,   d0 in [-128, 128], d1..d3 in [-128, 127],
+// so v ~= 2^(e-7) (d0 + d1 2^-8 + d2 2^-16 + d3 2^-24).  Every digit is an
+// integer of at most 8 significant bits and is exact in bf16; a product of
+// two digits is at most 2^14 in magnitude and exact in FP32, and FP32 sums
+// of such products stay exact while they stay below 2^24.  The split path
+// keeps every tensor-core accumulation under that bound, forms the digit
+// products of levels d = i + j = 0..4 (the dropped levels 5 and 6 weigh
+// below 2^-40 of the product), and folds the per-chunk scales in afterwards
+// (Ozaki-style error-free splitting; Ozaki, Ogita, Oishi & Rump, Numer.
+// Algorithms 59 (2012)).
+//
+// Conversions use integer operations on the IEEE-754 bit pattern only (no
+// FP64 instructions, which are slow on this part).
+#pragma once
+
+#include <cstdint>
+
+namespace kbe {
+namespace split {
+
+constexpr int kSlices = 4;       // digits per value
+constexpr int kFrac = 31;        // fixed-point bits below the scale
+constexpr int kLevels = kSlices + 1;  // digit-product levels d = i + j kept: 0..4
+
+// Unbiased exponent e with |v| < 2^e for the largest magnitude among values
+// whose IEEE biased exponent fields have maximum ef (ef = 0 for zero/denormal).
+__host__ __device__ __forceinline__ int scale_from_field(int ef) { return ef == 0 ? -1022 : ef - 1022; }
+
+__device__ __forceinline__ int exp_field(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+}
+
+// round(v * 2^(31-e)) as an integer, |v| < 2^e (32-bit integer operations only).
+__device__ __forceinline__ int fixed31(double v, int e) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int ef = (hi >> 20) & 0x7FF;
+  const int s = 1044 + e - ef;  // right shift of the 53-bit significand, >= 22
+  if (ef == 0 || s > 53) return 0;
+  const unsigned mh = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+  unsigned V, rb;
+  if (s < 32) {
+    V = __funnelshift_r(lo, mh, s);
+    rb = (lo >> (s - 1)) & 1u;
+  } else {
+    V = mh >> (s - 32);
+    rb = s == 32 ? (lo >> 31) : ((mh >> (s - 33)) & 1u);
+  }
+  V += rb;
+  if (V > 0x7FFFFFFFu) V = 0x7FFFFFFFu;
+  return hi < 0 ? -(int)V : (int)V;
+}
+
+// The four balanced digits of V as bf16 bit patterns (low 16 bits).
+__device__ __forceinline__ void digits_bf16(int V, uint32_t out[kSlices]) {
+  const int d0 = (int)(((long long)V + 0x808080) >> 24);  // [-128, 128]
+  const unsigned w = (unsigned)V + 0x808080u;
+  out[0] = __float_as_uint(__int_as_float(0x4B400000 + d0) - 12582912.0f) >> 16;
+  out[1] = __float_as_uint(__int_as_float(0x4B000000 | ((w >> 16) & 0xFFu)) - 8388736.0f) >> 16;
+  out[2] = __float_as_uint(__int_as_float(0x4B000000 | ((w >> 8) & 0xFFu)) - 8388736.0f) >> 16;
+  out[3] = __float_as_uint(__int_as_float(0x4B000000 | (w & 0xFFu)) - 8388736.0f) >> 16;
+}
+
+// Digits as integers (used where the negated digits are needed too).
+__device__ __forceinline__ void digits(double v, int e, int d[kSlices]) {
+  const int V = fixed31(v, e);
+  const unsigned w = (unsigned)V + 0x808080u;
+  d[0] = (int)(((long long)V + 0x808080) >> 24);
+  d[1] = (int)((w >> 16) & 0xFFu) - 128;
+  d[2] = (int)((w >> 8) & 0xFFu) - 128;
+  d[3] = (int)(w & 0xFFu) - 128;
+}
+
+// bf16 bit pattern of a small integer (|d| <= 2^8, exactly representable).
+__device__ __forceinline__ uint32_t bf16_of_int(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;  // exact float(d)
+  return __float_as_uint(f) >> 16;
+}
+
+// Pack (lo, hi) bf16 patterns into one 32-bit word (lo at the lower address).
+__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return (hi << 16) | (lo & 0xFFFFu); }
+
+// ---------------------------------------------------------------- tcgen05 --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
+// 8 rows x 16 bytes; lbo = byte stride between core matrices along K,
+// sbo = byte stride between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor: bf16 x bf16 -> f32, K-major A and B, M = 128.
+__host__ __device__ __forceinline__ uint32_t umma_idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(void* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(void* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(void* mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(void* mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 4 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float v[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// kLevels groups of 4 columns at stride `stride` (the digit-product levels
+// of 4 output columns), one wait for all of them.
+__device__ __forceinline__ void tmem_ld4xL(uint32_t taddr, int stride, float v[kLevels][4]) {
+  uint32_t r[kLevels][4];
+#pragma unroll
+  for (int d = 0; d < kLevels; ++d)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
+                 : "r"(taddr + (uint32_t)(d * stride)));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int d = 0; d < kLevels; ++d)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[d][i] = __uint_as_float(r[d][i]);
+}
+
+// Zero 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// ----------------------------------------------------- double-float sums --
+// Error-free sum of two floats (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) += x exactly up to the final renormalisation.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  lo += e;
+  two_sum(s, lo, hi, lo);
+}
+
+// 2^k as a float for k in [-126, 127] (k clamped).
+__device__ __forceinline__ float pow2f(int k) {
+  k = k < -126 ? -126 : (k > 127 ? 127 : k);
+  return __int_as_float((k + 127) << 23);
+}
+
+}  // namespace split
+}  // namespace kbe
