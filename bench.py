@@ -141,10 +141,10 @@ def setup_workload(kbe, seed, n_t_override=None):
     return cfg, t, order, h, U, v, pulse, ctx, run, n
 
 
-def time_steps(ctx, run, n, P, steps, warmup, stream):
+def time_steps(ctx, run, n, P, steps, warmup, stream, precision="fp64"):
     import torch
     for _ in range(warmup):
-        run.step(n, P=P, stream=stream)
+        run.step(n, P=P, precision=precision, stream=stream)
     torch.cuda.synchronize()
     launches = 0
     ctx.set_profiling(True)
@@ -152,7 +152,7 @@ def time_steps(ctx, run, n, P, steps, warmup, stream):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        run.step(n, P=P, stream=stream)
+        run.step(n, P=P, precision=precision, stream=stream)
         launches += ctx.last_launch_count
     e1.record(stream)
     torch.cuda.synchronize()
@@ -219,9 +219,10 @@ def W_tri(n):
     return n * (n + 1) // 2
 
 
-def cpu_baseline(run, t, order, h, U, v, pulse, n, M, P):
+def cpu_baseline(run, t, order, h, U, v, pulse, n, M, P, gpu_rows):
     """The oracle's own KBE step of row n (P sweeps) from the same history on
-    the host cores: its time, and its deviation from the GPU step."""
+    the host cores: its time, and the deviation of each GPU step in
+    ``gpu_rows`` ({name: (row L, row R, history slice)}) from it."""
     import oracle
     threads = oracle.threads_available()
     L_rows = run.L[: W_tri(n)].cpu().numpy()
@@ -231,16 +232,21 @@ def cpu_baseline(run, t, order, h, U, v, pulse, n, M, P):
     Lo, Ro, Io = oracle.run(t[: n + 1], order[: n + 1], h, U, v, pulse, P, L, R, F, n, n + 1, nthreads=threads)
     dt = time.perf_counter() - t0
     p = W_tri(n)
-    gl = run.L[p:p + n + 1].cpu().numpy()
-    gr = run.R[p:p + n + 1].cpu().numpy()
-    gi = run.I[:, : n + 1].cpu().numpy()
-    err = {"row_L": float(np.abs(gl - Lo[p:]).max() / np.abs(Lo[p:]).max()),
-           "row_R": float(np.abs(gr - Ro[p:]).max() / np.abs(Ro[p:]).max()),
-           "history_slice": float(np.abs(gi - Io).max() / np.abs(Io).max())}
+    errs = {}
+    for name, (gl, gr, gi) in gpu_rows.items():
+        errs[name] = {"row_L": float(np.abs(gl - Lo[p:]).max() / np.abs(Lo[p:]).max()),
+                      "row_R": float(np.abs(gr - Ro[p:]).max() / np.abs(Ro[p:]).max()),
+                      "history_slice": float(np.abs(gi - Io).max() / np.abs(Io).max())}
     tflops = P * slice_flops(M, n) / dt / 1e12
     sample = ("one oracle KBE step of row n=%d (P=%d: self-energy, history slice, corrector), "
               "%.2f s wall on %d threads" % (n, P, dt, threads))
-    return tflops, threads, sample, err, dt
+    return tflops, threads, sample, errs, dt
+
+
+def step_rows(run, n):
+    p = W_tri(n)
+    return (run.L[p:p + n + 1].cpu().numpy(), run.R[p:p + n + 1].cpu().numpy(),
+            run.I[:, : n + 1].cpu().numpy())
 
 
 def main():
@@ -262,12 +268,16 @@ def main():
     torch.cuda.synchronize()
     clocks = Clocks(local)
     ms, launches, k_count, k_ms = time_steps(ctx, run, n, args.P, args.steps, args.warmup, stream)
+    rows = {"fp64": step_rows(run, n)}
+    # the precision form: the same step with the contraction on the tensor cores
+    ms_s, launches_s, kc_s, kms_s = time_steps(ctx, run, n, args.P, args.steps, args.warmup, stream, "split")
+    rows["split"] = step_rows(run, n)
     clk = clocks.stop()
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        tt = torch.tensor([ms, ms_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms, ms_s = float(tt[0].item()), float(tt[1].item())
         dist.barrier()
     ms_step = ms / args.steps
     flops_step = args.P * slice_flops(M, n)
@@ -278,6 +288,13 @@ def main():
             "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
             "kernel": "history_partial (FP64 DFMA contraction)", "launches_timed": k_count,
             "avg_ms": round(k_avg, 4), "peak_source": "measured DFMA probe (FP64 not in MEASURED_PEAKS.json)"}
+    ms_step_s = ms_s / args.steps
+    split = {"precision": "split: 4-digit bf16 fixed-point slices on tcgen05, exact FP32 chunk sums, "
+                          "double-float accumulation (KBE_SPLIT_BF16)",
+             "ms_per_step": round(ms_step_s, 4),
+             "value": round(world * flops_step / (ms_step_s * 1e-3) / 1e12, 4), "unit": "TFLOP/s (FP64-equivalent)",
+             "speedup_vs_fp64_step": round(ms_step / ms_step_s, 3), "stated_error_bound": 1e-8,
+             "contraction_kernel_ms": round(kms_s / max(kc_s, 1), 4), "gpu_launches": launches_s}
     e2e = None
     if not args.no_e2e:
         e2e_ms, h2d, d2h = e2e_steps(ctx, run, n, args.P, max(3, args.steps // 4), 1, stream)
@@ -292,15 +309,16 @@ def main():
                        "norb": M, "n_t": n + 1, "n": n, "P": args.P, "precision": "fp64",
                        "l2": "inputs larger than L2 (history %.2f GB per step)" % (2 * (n + 1) * (n + 2) / 2 * M * M * 16 / 1e9),
                        "parallelism": "independent replicas" if world > 1 else "single GPU"},
-            "roofline": roof, "e2e": e2e, "gpu_launches": launches}
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "precision_form": split}
     if clk:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        tf, threads, sample, err, _ = cpu_baseline(run, t, order, h, U, v, pulse, n, M, args.P)
+        tf, threads, sample, errs, _ = cpu_baseline(run, t, order, h, U, v, pulse, n, M, args.P, rows)
         line["cpu_baseline"] = {"value": round(tf, 6), "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                                 "sample": sample}
-        line["error_vs_oracle"] = dict(err, where="new row n and last history slice of the timed KBE step, "
-                                                  "max-norm relative")
+        line["error_vs_oracle"] = dict(errs["fp64"], where="new row n and last history slice of the timed KBE "
+                                                           "step, max-norm relative")
+        line["precision_form"]["error_vs_oracle"] = errs["split"]
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

@@ -145,3 +145,37 @@ def test_split_full_size_sampled(kbe, name):
     print(name, "split max rel err on sampled columns", err)
     assert err < TOL_SPLIT
     ctx.close()
+
+
+def test_split_stepper_tracks_oracle(kbe):
+    """KBE steps with the split-precision contraction (everything else FP64)
+    stay within the accumulated effect of the 1e-9 slice error of the FP64
+    oracle run: 63 steps of the dimer and 31 of the 8-orbital chain."""
+    for name, n_t in (("dimer_m2_n64", 64), ("chain_m8_n1024", 32)):
+        cfg = W.CONFIGS[name]
+        t, order = W.grid(cfg["n_t"], cfg["dt0"], cfg["sig"], 4)
+        t, order = t[:n_t], order[:n_t]
+        h, U, v, pulse = W.build_model(cfg, 4)
+        if pulse is not None:
+            pulse = dict(pulse, t0=t[n_t // 2], sigma=0.2)
+        rho0 = W.half_filled_rho(h)
+        M = cfg["M"]
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        run = kbe.Run(ctx)
+        run.init_uncorrelated(rho0)
+        for n in range(1, n_t):
+            run.step(n, P=2, precision="split")
+        ctx.sync_status()
+        L0, R0, F0 = oracle.initial_rhs(t, order, h, U, v, pulse, rho0)
+        Lo = np.zeros((W.tri_size(n_t), M, M), np.complex128)
+        Ro = np.zeros_like(Lo)
+        Lo[0], Ro[0] = L0[0], R0[0]
+        Lo, Ro, _ = oracle.run(t, order, h, U, v, pulse, 2, Lo, Ro, {0: F0}, 1, n_t,
+                               nthreads=oracle.threads_available())
+        Lg = run.L[: W.tri_size(n_t)].cpu().numpy()
+        err = _rel(Lg, Lo)
+        print(name, "split stepper max rel err over the run", err)
+        assert err < 1e-8, (name, err)
+        ctx.close()
