@@ -183,6 +183,72 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
 kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* S_less,
                     void* S_great, void* I_work, void* F_ring, void* stream);
 
+/* kbe_step with the right-hand-side rows in a row store instead of the
+ * ring: row j lives in slot j - j0 of F_rows, device
+ * [n_rows][2][n_max][M][M].  Step n reads rows n-k_n .. n-1 and writes row
+ * n, so n - k_n >= j0 and n - j0 < n_rows (else KBE_ERANGE).  Keeping every
+ * row of a window of steps is what the reverse sweep (kbe_step_adjoint)
+ * recomputes from. */
+kbe_status kbe_step_rows(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* S_less,
+                         void* S_great, void* I_work, void* F_rows, int j0, int n_rows, void* stream);
+
+/* --------------------------------------------------------- reverse mode -- */
+/* The paper computes no gradients; these calls give vector-Jacobian
+ * products of the calls above, for derivatives of observables with respect
+ * to the interaction U and the pulse amplitude E0 (E(t) = E0 g(t)).
+ * Cotangents use the convention of PyTorch for a real loss F of complex z:
+ * zbar = dF/d(Re z) + i dF/d(Im z).  All in FP64.  Cotangent triangles
+ * dL, dR cover rows row_lo.. only: block p(r,c) of rows r >= row_lo sits at
+ * p(r,c) - p(row_lo,0).  Rows below row_lo are treated as constants. */
+
+/* Vector-Jacobian product of the history slice of row n (Eq. KBE2), which
+ * is bilinear in the self-energy row and the rows 0..n of G.  dI: device
+ * [2][n+1][M][M], the cotangent of the slice.  dS_less, dS_great: device
+ * [n+1][M][M], OVERWRITTEN with the cotangent of the self-energy row:
+ *   dA1(m)  = sum_{s,c} dI^s(c) G^s(m,c)^+,  A1(m) = w_{n,m} (S^>(m) - S^<(m)),
+ *   dS^>(m) = w_{n,m} dA1(m) + sum_{c>=m} w_{c,m} dI^>(c) R(c,m),
+ *   dS^<(m) = -w_{n,m} dA1(m) + sum_{c>=m} w_{c,m} dI^<(c) R(c,m).
+ * dL, dR: cotangent triangles of rows row_lo..n (0 <= row_lo <= n),
+ * INCREMENTED by the slice's dependence on those rows (R(r,r) is fixed at
+ * -i*1 and gets none).  Deterministic.  Uses the context's workspace. */
+kbe_status kbe_adjoint_slice(kbe_ctx* ctx, int n, const void* L, const void* R, const void* S_less,
+                             const void* S_great, const void* dI, void* dS_less, void* dS_great, void* dL,
+                             void* dR, int row_lo, void* stream);
+
+/* Vector-Jacobian product of the self-energy row n (Eq. SE, with the
+ * diagonal block's third factor read from the stored block as in
+ * kbe_selfenergy_slice).  dS_less, dS_great: device [n+1][M][M]
+ * cotangents of the row.  dL_row, dR_row: device [n+1][M][M], INCREMENTED
+ * by the cotangent of row n of L and R (R(n,n) gets none).  dU: device
+ * double[M], INCREMENTED by dF/dU.  Uses the context's workspace. */
+kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, const void* R, const void* dS_less,
+                                        const void* dS_great, void* dL_row, void* dR_row, double* dU,
+                                        void* stream);
+
+/* Reverse sweep of one KBE step n taken by kbe_step_rows with precision
+ * KBE_FP64 (same P, same store F_rows, j0, n_rows).  On entry L, R hold rows
+ * 0..n and F_rows rows j0..n as the forward run left them (later steps do
+ * not touch them); the call recomputes step n from rows 0..n-1, keeping
+ * its P iterates on the device, then runs the adjoints of the corrector,
+ * right-hand side (Fock matrix with its Hartree term U_a Im L(n,n)_aa and
+ * the field E0 g(t_n) v_a), history slice and self-energy of each sweep in
+ * reverse, and finally of the predictor.
+ *   dL, dR: cotangent triangles of rows row_lo..n (1 <= n, row_lo <= n).
+ *           Row n holds the cotangent of the step's result on entry and is
+ *           read only; rows row_lo..n-1 are INCREMENTED.
+ *   dF_rows: cotangents of the stored right-hand-side rows, layout of
+ *           F_rows.  Slot n holds the cotangent of row n (from later steps)
+ *           on entry; slots of rows n-k_n..n-1 are INCREMENTED.
+ *   dU (device double[M]) and dE0 (device double[1]) are INCREMENTED.
+ * On return L, R and F_rows hold what they held on entry.  Sweeping n =
+ * n_end-1 down to n_start with the same dL, dR, dF_rows gives the gradient
+ * of any function of the rows through the window [n_start, n_end).  The
+ * first call allocates a reverse-mode workspace of (13 + 2 (P+1)) n_max M^2
+ * complex entries held by the context (KBE_ENOMEM if that fails). */
+kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* F_rows, int j0, int n_rows,
+                            void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0,
+                            void* stream);
+
 /* Synchronize stream and return the device status word accumulated since
  * the last call (then cleared): KBE_OK, KBE_ENUMERIC or KBE_ETIMEOUT. */
 kbe_status kbe_sync_status(kbe_ctx* ctx, void* stream);

@@ -57,6 +57,10 @@ def lib():
         L.kbe_history_slice.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
         L.kbe_rhs_row.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
+        L.kbe_adjoint_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, vp]
+        L.kbe_adjoint_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_step_adjoint.argtypes = [vp, i, i, vp, vp, vp, i, i, vp, vp, i, vp, vp, vp, vp]
         L.kbe_sync_status.argtypes = [vp, vp]
         L.kbe_set_profiling.argtypes = [vp, i]
         L.kbe_read_profiling.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d)]
@@ -166,6 +170,10 @@ class Context:
         import torch
         return torch.zeros((2, self.n_max, self.M, self.M), dtype=torch.complex128, device="cuda")
 
+    def empty_row_store(self, n_rows):
+        import torch
+        return torch.zeros((n_rows, 2, self.n_max, self.M, self.M), dtype=torch.complex128, device="cuda")
+
     def empty_ring(self):
         import torch
         return torch.zeros((KBE_RING_ROWS, 2, self.n_max, self.M, self.M), dtype=torch.complex128, device="cuda")
@@ -208,6 +216,41 @@ class Context:
                                    self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_ring),
                                    self._stream(stream)))
 
+    def step_rows(self, n, L, R, Sl, Sg, I_work, F_rows, j0, P=2, precision="fp64", stream=None):
+        """kbe_step with right-hand-side row j in slot j - j0 of the row store F_rows."""
+        self._check(lib().kbe_step_rows(self._h, n, P, PRECISIONS[precision], self._dev(L), self._dev(R),
+                                        self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_rows),
+                                        int(j0), int(F_rows.shape[0]), self._stream(stream)))
+
+    # -- reverse mode
+    def adjoint_slice(self, n, L, R, Sl, Sg, dI, dSl, dSg, dL, dR, row_lo, stream=None):
+        """Vector-Jacobian product of the history slice of row n: dSl, dSg
+        are overwritten, dL, dR (rows row_lo.. of a triangle) incremented."""
+        self._check(lib().kbe_adjoint_slice(self._h, n, self._dev(L), self._dev(R), self._dev(Sl), self._dev(Sg),
+                                            self._dev(dI), self._dev(dSl), self._dev(dSg), self._dev(dL),
+                                            self._dev(dR), int(row_lo), self._stream(stream)))
+
+    def adjoint_selfenergy_slice(self, n, L, R, dSl, dSg, dL_row, dR_row, dU, stream=None):
+        """Vector-Jacobian product of the self-energy row n: dL_row, dR_row
+        and dU (CUDA float64 [M]) incremented."""
+        self._check(lib().kbe_adjoint_selfenergy_slice(self._h, n, self._dev(L), self._dev(R), self._dev(dSl),
+                                                       self._dev(dSg), self._dev(dL_row), self._dev(dR_row),
+                                                       self._real_dev(dU), self._stream(stream)))
+
+    def step_adjoint(self, n, P, L, R, F_rows, j0, dL, dR, row_lo, dF_rows, dU, dE0, stream=None):
+        """Reverse sweep of the FP64 step n taken by step_rows (see kbe.h)."""
+        self._check(lib().kbe_step_adjoint(self._h, n, P, self._dev(L), self._dev(R), self._dev(F_rows), int(j0),
+                                           int(F_rows.shape[0]), self._dev(dL), self._dev(dR), int(row_lo),
+                                           self._dev(dF_rows), self._real_dev(dU), self._real_dev(dE0),
+                                           self._stream(stream)))
+
+    @staticmethod
+    def _real_dev(x):
+        import torch
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("expected a contiguous CUDA float64 tensor")
+        return ctypes.c_void_p(x.data_ptr())
+
     def set_profiling(self, enable):
         """Record CUDA events around each contraction kernel (clears old records)."""
         self._check(lib().kbe_set_profiling(self._h, 1 if enable else 0))
@@ -249,3 +292,102 @@ class Run:
     def step(self, n, P=2, precision="fp64", stream=None):
         self.ctx.step(n, self.L, self.R, self.Sl, self.Sg, self.I, self.F, P=P, precision=precision,
                       stream=stream)
+
+
+# ------------------------------------------------------------ reverse mode
+class Window:
+    """A window of KBE steps n_start..n_end-1 restarted from frozen rows,
+    as a function of the interaction U (per orbital) and the pulse
+    amplitude E0, with its reverse sweep.
+
+    Rows 0..n_start-1 of ``L``/``R`` (CUDA triangles of at least n_end
+    rows) and the right-hand-side rows j0..n_start-1 in ``F_frozen``
+    (mapping j -> [2, j+1, M, M]) are constants.  ``forward`` runs the
+    window through the library's FP64 stepper keeping every right-hand-side
+    row (the checkpoints), and returns the final diagonal block
+    L(n_end-1, n_end-1); ``backward`` sweeps kbe_step_adjoint from the last
+    step down and returns (dU, dE0) for a cotangent of that block.
+    """
+
+    def __init__(self, ctx, L, R, F_frozen, n_start, n_end, h0, v, pulse, P=2):
+        import torch
+        self.ctx, self.P = ctx, int(P)
+        self.n_start, self.n_end = int(n_start), int(n_end)
+        self.h0 = np.ascontiguousarray(h0, np.complex128)
+        self.v = np.ascontiguousarray(v, np.float64)
+        self.pulse = dict(pulse) if pulse is not None else dict(E0=0.0, t0=0.0, sigma=1.0, omega=0.0)
+        self.L, self.R = L, R
+        self.j0 = min(F_frozen) if F_frozen else self.n_start
+        self.F = ctx.empty_row_store(self.n_end - self.j0)
+        for j, f in F_frozen.items():
+            self.F[j - self.j0, :, : j + 1].copy_(torch.as_tensor(np.asarray(f), device="cuda"))
+        self.Sl, self.Sg, self.I = ctx.empty_rows(), ctx.empty_rows(), ctx.empty_slice()
+        self._state = None
+
+    def _set_params(self, U, E0):
+        p = dict(self.pulse, E0=float(E0))
+        self.ctx.set_model(self.h0, np.asarray(U, np.float64), self.v, p)
+
+    def forward(self, U, E0, stream=None):
+        U = np.array(U, np.float64)
+        self._set_params(U, E0)
+        for n in range(self.n_start, self.n_end):
+            self.ctx.step_rows(n, self.L, self.R, self.Sl, self.Sg, self.I, self.F, self.j0, P=self.P,
+                               stream=stream)
+        self._state = (U.tobytes(), float(E0))
+        p = tri_size(self.n_end) - 1
+        return self.L[p].clone()
+
+    def backward(self, grad_block, U, E0, stream=None):
+        import torch
+        U = np.array(U, np.float64)
+        if self._state != (U.tobytes(), float(E0)):
+            self.forward(U, E0, stream=stream)   # the rows must be those of (U, E0)
+        self._set_params(U, E0)
+        M, lo = self.ctx.M, self.n_start
+        base = tri_size(lo)
+        nblk = tri_size(self.n_end) - base
+        dL = torch.zeros((nblk, M, M), dtype=torch.complex128, device="cuda")
+        dR = torch.zeros_like(dL)
+        dL[tri_size(self.n_end) - 1 - base].copy_(torch.as_tensor(grad_block, dtype=torch.complex128))
+        dF = torch.zeros_like(self.F)
+        dU = torch.zeros(M, dtype=torch.float64, device="cuda")
+        dE0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for n in range(self.n_end - 1, self.n_start - 1, -1):
+            self.ctx.step_adjoint(n, self.P, self.L, self.R, self.F, self.j0, dL, dR, lo, dF, dU, dE0,
+                                  stream=stream)
+        return dU, dE0[0]
+
+
+def _window_function():
+    import torch
+
+    class WindowFunction(torch.autograd.Function):
+        """Final diagonal block of a Window as a differentiable function of
+        (U, E0); the backward pass runs the library's adjoint kernels."""
+
+        @staticmethod
+        def forward(fctx, U, E0, window):
+            fctx.window = window
+            fctx.save_for_backward(U, E0)
+            return window.forward(U.detach().cpu().numpy(), float(E0))
+
+        @staticmethod
+        def backward(fctx, grad):
+            U, E0 = fctx.saved_tensors
+            dU, dE0 = fctx.window.backward(grad.contiguous(), U.detach().cpu().numpy(), float(E0))
+            return dU.to(U.device, U.dtype), dE0.to(E0.device, E0.dtype).reshape(E0.shape), None
+
+    return WindowFunction
+
+
+def window_final_block(U, E0, window):
+    """Differentiable L(n_end-1, n_end-1) of ``window`` (a Window) for the
+    float64 tensors U [M] and E0 (scalar)."""
+    global _WF
+    if _WF is None:
+        _WF = _window_function()
+    return _WF.apply(U, E0, window)
+
+
+_WF = None

@@ -38,8 +38,10 @@ void release(kbe_ctx* ctx) {
   ctx->ev_pool.clear();
   cudaFree(ctx->d_wbar); cudaFree(ctx->d_band); cudaFree(ctx->d_corr); cudaFree(ctx->d_pred);
   cudaFree(ctx->d_h0); cudaFree(ctx->d_U); cudaFree(ctx->d_v); cudaFree(ctx->d_eps);
-  cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split);
+  cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split); cudaFree(ctx->d_adj);
   ctx->d_split = nullptr;
+  ctx->d_adj = nullptr;
+  ctx->adj_bytes = 0;
   ctx->d_wbar = ctx->d_band = ctx->d_corr = ctx->d_pred = nullptr;
   ctx->d_h0 = ctx->d_U = ctx->d_v = ctx->d_eps = ctx->d_part = nullptr;
   ctx->d_status = nullptr;
@@ -102,6 +104,8 @@ StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F
   a.R = (double*)R;
   a.F = (double*)F;
   a.n_max = ctx->n_max;
+  a.f_base = 0;
+  a.f_rows = kRing;
   a.I = (const double*)I;
   a.h0 = ctx->d_h0;
   a.U = ctx->d_U;
@@ -111,6 +115,92 @@ StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F
   a.pred = ctx->d_pred + (size_t)n * kMaxOrder * kWTab;
   a.status = ctx->d_status;
   return a;
+}
+
+// One KBE step (predictor, then P rounds of self-energy, history slice,
+// Fock matrix, right-hand side and corrector).  F rows are addressed as
+// slot (j - f_base) % f_rows.  With save != nullptr, row n of L and R is
+// copied to save[p] before round p and to save[P] at the end
+// (save[p] = [2][n+1][M][M]: L row, then R row).
+kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* Sl, void* Sg, void* I_work,
+                     void* F, int f_base, int f_rows, cudaStream_t s, double* save, int* count_out) {
+  StepArgs a = step_args(ctx, n, L, R, I_work, F);
+  a.f_base = f_base;
+  a.f_rows = f_rows;
+  const size_t MM = (size_t)ctx->M * ctx->M;
+  const size_t row_doubles = (size_t)(n + 1) * MM * 2;
+  double* Lrow = (double*)L + tri(n, 0) * MM * 2;
+  double* Rrow = (double*)R + tri(n, 0) * MM * 2;
+  auto keep = [&](int p) -> cudaError_t {
+    if (!save) return cudaSuccess;
+    double* dst = save + (size_t)p * 2 * row_doubles;
+    cudaError_t e = cudaMemcpyAsync(dst, Lrow, row_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst + row_doubles, Rrow, row_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return e;
+  };
+  int count = 0, nl = 0;
+  cudaError_t e = launch_predictor(a, s);
+  ++count;
+  *count_out = count;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: predictor");
+  for (int it = 0; it < P; ++it) {
+    if ((e = keep(it)) != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: iterate copy");
+    e = launch_sigma(ctx->M, tri(n, 0), n + 1, n, (const double*)L, (const double*)R, ctx->d_U, (double*)Sl,
+                     (double*)Sg, ctx->d_status, s);
+    *count_out = ++count;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: self-energy");
+    kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl);
+    *count_out = (count += nl);
+    if (st != KBE_OK) return st;
+    if ((e = launch_fock(a, s)) != cudaSuccess || (e = launch_rhs_corrector(a, s)) != cudaSuccess) {
+      *count_out = count + 3;
+      return cuda_fail(ctx, e, "kbe_step: corrector");
+    }
+    *count_out = (count += 3);
+  }
+  if ((e = keep(P)) != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: iterate copy");
+  return KBE_OK;
+}
+
+kbe_status check_step_call(kbe_ctx* ctx, int n, int P, int precision, const void* L, const void* R, const void* Sl,
+                           const void* Sg, const void* I_work, const void* F) {
+  kbe_status st = check_row_call(ctx, n);
+  if (st != KBE_OK) return st;
+  if (n < 1) return fail(ctx, KBE_ERANGE, "kbe_step: n must be >= 1 (row 0 is the initial state)");
+  if (P < 1 || P > 16) return fail(ctx, KBE_EINVAL, "kbe_step: P outside [1, 16]");
+  if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
+  if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_work) || !aligned16(F))
+    return fail(ctx, KBE_EINVAL, "kbe_step: NULL or misaligned pointer");
+  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16) return fail(ctx, KBE_EINVAL, "kbe_step: unknown precision");
+  return use_device(ctx);
+}
+
+// Rows of a right-hand-side row store needed by step n: n - k_n .. n.
+kbe_status check_row_store(kbe_ctx* ctx, int n, int j0, int n_rows) {
+  if (n_rows < 1 || j0 < 0) return fail(ctx, KBE_EINVAL, "row store: n_rows < 1 or j0 < 0");
+  if (n - ctx->grid.order[n] < j0) return fail(ctx, KBE_ERANGE, "row store: step n needs rows from n - k_n < j0");
+  if (n - j0 >= n_rows) return fail(ctx, KBE_ERANGE, "row store: row n is beyond the store (n - j0 >= n_rows)");
+  return KBE_OK;
+}
+
+// Reverse-mode workspace: 13 + 2 (P + 1) rows of n_max M^2 complex.
+constexpr int kAdjFixedRows = 13;
+kbe_status adjoint_workspace(kbe_ctx* ctx, int P) {
+  const size_t row = (size_t)ctx->n_max * ctx->M * ctx->M * 16;
+  const size_t need = (kAdjFixedRows + 2 * (size_t)(P + 1)) * row;
+  if (ctx->adj_bytes >= need) return KBE_OK;
+  cudaFree(ctx->d_adj);
+  ctx->d_adj = nullptr;
+  ctx->adj_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_adj, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? KBE_ENOMEM : KBE_ECUDA,
+                std::string("adjoint workspace: ") + cudaGetErrorString(e));
+  }
+  ctx->adj_bytes = need;
+  return KBE_OK;
 }
 
 }  // namespace
@@ -325,35 +415,186 @@ kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R,
                     void* F_ring, void* stream) {
   if (!ctx) return KBE_EINVAL;
   ctx->last_launches = 0;
+  kbe_status st = check_step_call(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_ring);
+  if (st != KBE_OK) return st;
+  int count = 0;
+  st = step_impl(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_ring, 0, kRing, (cudaStream_t)stream, nullptr, &count);
+  ctx->last_launches = count;
+  return st;
+}
+
+kbe_status kbe_step_rows(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* Sl, void* Sg,
+                         void* I_work, void* F_rows, int j0, int n_rows, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  kbe_status st = check_step_call(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_rows);
+  if (st != KBE_OK) return st;
+  if ((st = check_row_store(ctx, n, j0, n_rows)) != KBE_OK) return st;
+  int count = 0;
+  st = step_impl(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_rows, j0, n_rows, (cudaStream_t)stream, nullptr,
+                 &count);
+  ctx->last_launches = count;
+  return st;
+}
+
+kbe_status kbe_adjoint_slice(kbe_ctx* ctx, int n, const void* L, const void* R, const void* S_less,
+                             const void* S_great, const void* dI, void* dS_less, void* dS_great, void* dL, void* dR,
+                             int row_lo, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
   kbe_status st = check_row_call(ctx, n);
   if (st != KBE_OK) return st;
-  if (n < 1) return fail(ctx, KBE_ERANGE, "kbe_step: n must be >= 1 (row 0 is the initial state)");
-  if (P < 1 || P > 16) return fail(ctx, KBE_EINVAL, "kbe_step: P outside [1, 16]");
-  if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
-  if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_work) || !aligned16(F_ring))
-    return fail(ctx, KBE_EINVAL, "kbe_step: NULL or misaligned pointer");
-  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16) return fail(ctx, KBE_EINVAL, "kbe_step: unknown precision");
+  if (row_lo < 0 || row_lo > n) return fail(ctx, KBE_ERANGE, "kbe_adjoint_slice: row_lo outside [0, n]");
+  if (!aligned16(L) || !aligned16(R) || !aligned16(S_less) || !aligned16(S_great) || !aligned16(dI) ||
+      !aligned16(dS_less) || !aligned16(dS_great) || !aligned16(dL) || !aligned16(dR))
+    return fail(ctx, KBE_EINVAL, "kbe_adjoint_slice: NULL or misaligned pointer");
   if ((st = use_device(ctx)) != KBE_OK) return st;
+  const int64_t MM = (int64_t)ctx->M * ctx->M;
+  const int64_t row_n = (tri(n, 0) - tri(row_lo, 0)) * MM * 2;
+  AdjHistArgs h{ctx->M, n, row_lo, (const double*)L, (const double*)R, (const double*)S_less,
+                (const double*)S_great, (const double*)dI, weights_view(ctx), (double*)dS_less, (double*)dS_great,
+                (double*)dL, (double*)dR, (double*)dL + row_n, (double*)dR + row_n, ctx->d_part, ctx->part_bytes};
+  int nl = 0;
+  cudaError_t e = launch_adjoint_history(h, (cudaStream_t)stream, &nl);
+  ctx->last_launches = nl;
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_adjoint_slice");
+}
+
+kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, const void* R, const void* dS_less,
+                                        const void* dS_great, void* dL_row, void* dR_row, double* dU, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  kbe_status st = check_row_call(ctx, n);
+  if (st != KBE_OK) return st;
+  if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
+  if (!aligned16(L) || !aligned16(R) || !aligned16(dS_less) || !aligned16(dS_great) || !aligned16(dL_row) ||
+      !aligned16(dR_row) || !dU || (reinterpret_cast<uintptr_t>(dU) & 7u))
+    return fail(ctx, KBE_EINVAL, "kbe_adjoint_selfenergy_slice: NULL or misaligned pointer");
+  if ((st = use_device(ctx)) != KBE_OK) return st;
+  const int64_t MM = (int64_t)ctx->M * ctx->M;
+  AdjSigmaArgs a{ctx->M, n, (const double*)L + tri(n, 0) * MM * 2, (const double*)R + tri(n, 0) * MM * 2, ctx->d_U,
+                 (const double*)dS_less, (const double*)dS_great, (double*)dL_row, (double*)dR_row, ctx->d_part,
+                 dU};
+  int nl = 0;
+  cudaError_t e = launch_adjoint_sigma(a, (cudaStream_t)stream, &nl);
+  ctx->last_launches = nl;
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_adjoint_selfenergy_slice");
+}
+
+kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* F_rows, int j0, int n_rows,
+                            void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!aligned16(dL) || !aligned16(dR) || !aligned16(dF_rows) || !dU || !dE0 ||
+      (reinterpret_cast<uintptr_t>(dU) & 7u) || (reinterpret_cast<uintptr_t>(dE0) & 7u))
+    return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: NULL or misaligned pointer");
+  if (!ctx->grid_set) return fail(ctx, KBE_ESTATE, "no grid: call kbe_set_grid first");
+  if (n < 1 || n >= ctx->grid.n_t) return fail(ctx, KBE_ERANGE, "kbe_step_adjoint: n outside [1, n_t)");
+  if (row_lo < 0 || row_lo > n) return fail(ctx, KBE_ERANGE, "kbe_step_adjoint: row_lo outside [0, n]");
+  if (P < 1 || P > 16) return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: P outside [1, 16]");
+  if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
+  kbe_status st = adjoint_workspace(ctx, P);
+  if (st != KBE_OK) return st;
+  const int64_t MM = (int64_t)ctx->M * ctx->M;
+  const size_t rowd = (size_t)ctx->n_max * MM * 2;  // doubles of one workspace row
+  double* w = ctx->d_adj;
+  double* Sl = w;            double* Sg = w + rowd;
+  double* Iw = w + 2 * rowd;  // [2][n+1][M][M]
+  double* dSl = w + 4 * rowd; double* dSg = w + 5 * rowd;
+  double* gL = w + 6 * rowd;  double* gR = w + 7 * rowd;
+  double* Ib = w + 8 * rowd;  // [2][n+1][M][M]
+  double* Fs = w + 10 * rowd; // [2][n_max][M][M]
+  double* epsb = w + 12 * rowd;
+  double* save = w + kAdjFixedRows * rowd;
+  st = check_step_call(ctx, n, P, KBE_FP64, L, R, Sl, Sg, Iw, F_rows);
+  if (st != KBE_OK) return st;
+  if ((st = check_row_store(ctx, n, j0, n_rows)) != KBE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  StepArgs a = step_args(ctx, n, L, R, I_work, F_ring);
   int count = 0, nl = 0;
-  cudaError_t e = launch_predictor(a, s);
-  ++count;
-  if (e != cudaSuccess) { ctx->last_launches = count; return cuda_fail(ctx, e, "kbe_step: predictor"); }
-  for (int it = 0; it < P; ++it) {
-    e = launch_sigma(ctx->M, tri(n, 0), n + 1, n, (const double*)L, (const double*)R, ctx->d_U, (double*)Sl,
-                     (double*)Sg, ctx->d_status, s);
+  // forward again from the stored rows, keeping the iterates of row n
+  st = step_impl(ctx, n, P, KBE_FP64, L, R, Sl, Sg, Iw, F_rows, j0, n_rows, s, save, &count);
+  if (st != KBE_OK) { ctx->last_launches = count; return st; }
+  const size_t row_bytes = (size_t)(n + 1) * MM * 16;
+  const int64_t base = tri(row_lo, 0);
+  double* Lrow = (double*)L + tri(n, 0) * MM * 2;
+  double* Rrow = (double*)R + tri(n, 0) * MM * 2;
+  const double* dLn = (const double*)dL + (tri(n, 0) - base) * MM * 2;
+  const double* dRn = (const double*)dR + (tri(n, 0) - base) * MM * 2;
+  const int64_t fs = (int64_t)rowd;          // doubles between s = < and s = > in an F row
+  const int64_t fstride = 2 * fs;
+  double* Fn = (double*)dF_rows + (int64_t)(n - j0) * fstride;
+  const HostGrid& g = ctx->grid;
+  StepArgs a = step_args(ctx, n, L, R, Iw, F_rows);
+  a.f_base = j0;
+  a.f_rows = n_rows;
+  const double shape = ctx->model.shape(g.t[n]);
+  cudaError_t e = cudaSuccess;
+  auto check = [&](const char* where) -> kbe_status {
+    if (e != cudaSuccess) { ctx->last_launches = count; return cuda_fail(ctx, e, where); }
+    return KBE_OK;
+  };
+  // cotangent of the final row n
+  e = cudaMemcpyAsync(gL, dLn, row_bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gR, dRn, row_bytes, cudaMemcpyDeviceToDevice, s);
+  if ((st = check("kbe_step_adjoint: copy")) != KBE_OK) return st;
+  AdjLinArgs lin{ctx->M, n, a.kn, 1, a.corr, gL, gR, (double*)dL, (double*)dR, base, n - 1 >= row_lo ? 1 : 0,
+                 (double*)dF_rows, j0, fstride, fs, nullptr};
+  for (int p = P - 1; p >= 0; --p) {
+    // row n := iterate p, then its self-energy row and Fock matrix
+    const double* it = save + (size_t)p * 2 * (row_bytes / 8);
+    e = cudaMemcpyAsync(Lrow, it, row_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Rrow, it + row_bytes / 8, row_bytes, cudaMemcpyDeviceToDevice, s);
+    if ((st = check("kbe_step_adjoint: restore")) != KBE_OK) return st;
+    e = launch_sigma(ctx->M, tri(n, 0), n + 1, n, (const double*)L, (const double*)R, ctx->d_U, Sl, Sg,
+                     ctx->d_status, s);
     ++count;
-    if (e != cudaSuccess) { ctx->last_launches = count; return cuda_fail(ctx, e, "kbe_step: self-energy"); }
-    st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl);
-    count += nl;
-    if (st != KBE_OK) { ctx->last_launches = count; return st; }
-    if ((e = launch_fock(a, s)) != cudaSuccess || (e = launch_rhs_corrector(a, s)) != cudaSuccess) {
-      ctx->last_launches = count + 3;
-      return cuda_fail(ctx, e, "kbe_step: corrector");
+    if (e == cudaSuccess) e = launch_fock(a, s);
+    ++count;
+    if ((st = check("kbe_step_adjoint: self-energy")) != KBE_OK) return st;
+    // corrector: cotangent of iterate p+1 -> row n-1, stored F rows, F row n of round p
+    double* Fcur = Fn;
+    if (p != P - 1) {
+      Fcur = Fs;
+      e = cudaMemsetAsync(Fs, 0, (size_t)fstride * sizeof(double), s);
+      if ((st = check("kbe_step_adjoint: clear")) != KBE_OK) return st;
     }
-    count += 3;
+    lin.corrector = 1;
+    lin.wtab = a.corr;
+    lin.Fb_cur = Fcur;
+    e = launch_adjoint_lin(lin, s, &nl);
+    count += nl;
+    if (e == cudaSuccess) e = cudaMemsetAsync(gL, 0, row_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gR, 0, row_bytes, s);
+    if ((st = check("kbe_step_adjoint: corrector")) != KBE_OK) return st;
+    // right-hand side -> slice cotangent, row n, U, E0
+    AdjRhsArgs r{ctx->M, n, ctx->d_eps, Fcur, fs, Lrow, Rrow, ctx->d_U, ctx->d_v, shape, Ib, gL, gR, epsb, dU, dE0};
+    e = launch_adjoint_rhs(r, s, &nl);
+    count += nl;
+    if ((st = check("kbe_step_adjoint: right-hand side")) != KBE_OK) return st;
+    // history slice -> Sigma row, rows row_lo..n-1, row n
+    AdjHistArgs h{ctx->M, n, row_lo, (const double*)L, (const double*)R, Sl, Sg, Ib, weights_view(ctx), dSl, dSg,
+                  (double*)dL, (double*)dR, gL, gR, ctx->d_part, ctx->part_bytes};
+    e = launch_adjoint_history(h, s, &nl);
+    count += nl;
+    if ((st = check("kbe_step_adjoint: history slice")) != KBE_OK) return st;
+    // self-energy -> row n, U
+    AdjSigmaArgs sg{ctx->M, n, Lrow, Rrow, ctx->d_U, dSl, dSg, gL, gR, ctx->d_part, dU};
+    e = launch_adjoint_sigma(sg, s, &nl);
+    count += nl;
+    if ((st = check("kbe_step_adjoint: self-energy")) != KBE_OK) return st;
   }
+  // predictor: cotangent of iterate 0 -> row n-1 and stored F rows
+  lin.corrector = 0;
+  lin.wtab = a.pred;
+  lin.Fb_cur = nullptr;
+  e = launch_adjoint_lin(lin, s, &nl);
+  count += nl;
+  if ((st = check("kbe_step_adjoint: predictor")) != KBE_OK) return st;
+  // leave row n as the forward step left it
+  const double* fin = save + (size_t)P * 2 * (row_bytes / 8);
+  e = cudaMemcpyAsync(Lrow, fin, row_bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Rrow, fin + row_bytes / 8, row_bytes, cudaMemcpyDeviceToDevice, s);
+  if ((st = check("kbe_step_adjoint: restore")) != KBE_OK) return st;
   ctx->last_launches = count;
   return KBE_OK;
 }

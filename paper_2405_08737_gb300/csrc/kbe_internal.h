@@ -61,7 +61,8 @@ struct Model {
   std::vector<double> h0;   // complex MxM interleaved
   std::vector<double> U, v;
   double E0 = 0, t0 = 0, sigma = 1, omega = 0;
-  double field(double t) const;
+  double field(double t) const;   // E(t) = E0 * shape(t)
+  double shape(double t) const;   // Gaussian envelope times the carrier
 };
 
 }  // namespace kbe
@@ -90,6 +91,9 @@ struct kbe_ctx {
   size_t split_bytes = 0;
   int* d_status = nullptr;
   size_t part_bytes = 0;
+  // reverse-mode workspace, allocated by the first adjoint call that needs it
+  double* d_adj = nullptr;
+  size_t adj_bytes = 0;
   // measurement: event pairs around each contraction kernel
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -149,8 +153,10 @@ struct StepArgs {
   double field;      // E(t_n)
   double* L;
   double* R;
-  double* F;         // ring [kRing][2][n_max][M][M]
+  double* F;         // right-hand-side rows [f_rows][2][n_max][M][M]; row j in slot (j - f_base) % f_rows
   int n_max;
+  int f_base;        // 0 for the ring (f_rows = kRing); the first stored row for a row store
+  int f_rows;
   const double* I;   // [2][n+1][M][M]
   const double* h0;
   const double* U;
@@ -164,5 +170,75 @@ cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fock(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rhs(const StepArgs& a, cudaStream_t s);          // F row n only
 cudaError_t launch_rhs_corrector(const StepArgs& a, cudaStream_t s);  // F row n, then new row n
+
+// ---- reverse mode (adjoint.cu) ------------------------------------------
+// Cotangent convention: for a real loss, zbar = dF/dRe z + i dF/dIm z.
+struct AdjHistArgs {
+  int M, n, row_lo;
+  const double* L;      // triangles; row n holds the iterate the slice was taken at
+  const double* R;
+  const double* Sl;     // Sigma row n, [n+1][M][M]
+  const double* Sg;
+  const double* Ib;     // cotangent of the slice, [2][n+1][M][M]
+  WeightsView w;
+  double* dSl;          // cotangent of the Sigma row (overwritten)
+  double* dSg;
+  double* dL;           // rows row_lo..n-1 (incremented); block p at p - tri(row_lo, 0)
+  double* dR;
+  double* gL;           // row n (incremented), [n+1][M][M]
+  double* gR;
+  double* work;
+  size_t work_bytes;
+};
+cudaError_t launch_adjoint_history(const AdjHistArgs& a, cudaStream_t s, int* launches);
+
+struct AdjSigmaArgs {
+  int M, n;
+  const double* Lrow;   // row n of the triangles, [n+1][M][M]
+  const double* Rrow;
+  const double* U;
+  const double* dSl;
+  const double* dSg;
+  double* gL;           // incremented
+  double* gR;
+  double* dUp;          // scratch, 2 (n+1) M^2 doubles
+  double* dU;           // incremented
+};
+cudaError_t launch_adjoint_sigma(const AdjSigmaArgs& a, cudaStream_t s, int* launches);
+
+struct AdjRhsArgs {
+  int M, n;
+  const double* eps;    // Fock matrix of the iterate
+  const double* Fb;     // cotangent of F row n: entry (s, c, a, b) at Fb + s * fs + (c M^2 + a M + b) * 2
+  int64_t fs;
+  const double* Lrow;
+  const double* Rrow;
+  const double* U;
+  const double* v;
+  double shape;         // dE(t_n)/dE0
+  double* Ib;           // cotangent of the slice (overwritten), [2][n+1][M][M]
+  double* gL;           // incremented
+  double* gR;
+  double* epsb;         // scratch, M^2 complex
+  double* dU;
+  double* dE0;
+};
+cudaError_t launch_adjoint_rhs(const AdjRhsArgs& a, cudaStream_t s, int* launches);
+
+struct AdjLinArgs {
+  int M, n, kn, corrector;
+  const double* wtab;   // predictor or corrector weights of interval n, [kMaxOrder][kWTab]
+  const double* gL;     // cotangent of the new row n, [n+1][M][M]
+  const double* gR;
+  double* dL;           // triangles of cotangents, block p at p - tri_base
+  double* dR;
+  int64_t tri_base;
+  int write_prev;       // 0: row n-1 is frozen, its cotangent is not formed
+  double* Fb_rows;      // cotangents of F rows j < n: row j at (j - j0) * fstride, s at + s * fs
+  int j0;
+  int64_t fstride, fs;
+  double* Fb_cur;       // cotangent of F row n (corrector), same row layout
+};
+cudaError_t launch_adjoint_lin(const AdjLinArgs& a, cudaStream_t s, int* launches);
 
 }  // namespace kbe

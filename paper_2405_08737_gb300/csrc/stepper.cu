@@ -24,7 +24,8 @@ __device__ __forceinline__ void std2(double* p, double2 v) { *reinterpret_cast<d
 
 __device__ __forceinline__ const double* ring_at(const StepArgs& a, int j, int s, int c, int ab) {
   const int MM = a.M * a.M;
-  return a.F + ((((int64_t)(j % kRing) * 2 + s) * a.n_max + c) * MM + ab) * 2;
+  const int64_t slot = (j - a.f_base) % a.f_rows;
+  return a.F + (((slot * 2 + s) * a.n_max + c) * MM + ab) * 2;
 }
 
 // eps(t_n) = h0 + E(t_n) diag(v) + diag(U_a Im L(n,n)_aa)

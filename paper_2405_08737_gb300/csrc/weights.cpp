@@ -145,10 +145,14 @@ kbe_status build_grid(const double* t, const int* order, int n_t, HostGrid* g, s
   return KBE_OK;
 }
 
+double Model::shape(double t) const {
+  const double x = (t - t0) / sigma;
+  return std::exp(-0.5 * x * x) * std::cos(omega * t);
+}
+
 double Model::field(double t) const {
   if (E0 == 0.0) return 0.0;
-  const double x = (t - t0) / sigma;
-  return E0 * std::exp(-0.5 * x * x) * std::cos(omega * t);
+  return E0 * shape(t);
 }
 
 }  // namespace kbe

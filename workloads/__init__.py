@@ -208,3 +208,24 @@ def batch_systems(n_sys, seed):
         out.append(dict(M=int(Ms[i]), n_t=int(Ns[i]), U=float(Us[i]), J=1.0,
                         grid_seed=int(seed * 1000 + i)))
     return out
+
+
+def restart_state(h, rho0, t, order, n_start, n_rows, device=None):
+    """Frozen state of a restart at row n_start: the non-interacting
+    history (rows 0..n_rows-1; rows >= n_start are overwritten by the
+    steps) and the right-hand-side rows the stepper needs on entry,
+    j in [n_start - K, n_start) with K the largest order up to n_rows.
+    ``device`` None gives numpy triangles, else torch tensors there."""
+    K = max(1, int(np.max(order[1:n_rows]))) if n_rows > 1 else 1
+    rows = list(range(max(0, n_start - K), n_start))
+    if device is None:
+        L, R = free_triangles(h, rho0, t, n_rows)
+        Ln, Rn = L, R
+    else:
+        L, R = free_triangles_torch(h, rho0, t, n_rows, device)
+        lo, hi = tri_index(rows[0], 0) if rows else 0, tri_index(n_start, 0)
+        Ln = np.zeros((hi, h.shape[0], h.shape[0]), np.complex128)
+        Rn = np.zeros_like(Ln)
+        Ln[lo:hi] = L[lo:hi].cpu().numpy()
+        Rn[lo:hi] = R[lo:hi].cpu().numpy()
+    return L, R, free_rhs_rows(h, Ln, Rn, rows)
