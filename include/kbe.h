@@ -265,6 +265,59 @@ int kbe_last_launch_count(const kbe_ctx* ctx);
 kbe_status kbe_set_profiling(kbe_ctx* ctx, int enable);
 kbe_status kbe_read_profiling(kbe_ctx* ctx, int* count, double* total_ms);
 
+/* ------------------------------------------------------------ batching -- */
+/* Many independent systems (each a context with its own norb, grid and
+ * model) advanced together: one batched KBE step runs kbe_step's sequence
+ * for every active system as ONE CUDA graph launch (batched elementwise
+ * kernels, and for KBE_FP64 one persistent history kernel over a work list
+ * of (system, tile, history chunk) items).  The paper steps one system;
+ * this is a throughput form for ensembles of systems. */
+typedef struct kbe_batch kbe_batch;
+
+/* A batch over n_sys (1..1024) contexts on one device, each with its grid
+ * and model already set (later kbe_set_grid / kbe_set_model calls on them
+ * are not seen by the batch).  The contexts stay owned by the caller and
+ * must outlive the batch; their workspaces are used by the batched calls,
+ * so they must not run other calls concurrently. */
+kbe_status kbe_batch_create(kbe_ctx* const* ctxs, int n_sys, kbe_batch** out);
+kbe_status kbe_batch_destroy(kbe_batch* b);
+const char* kbe_batch_last_error(const kbe_batch* b);
+int kbe_batch_last_launch_count(const kbe_batch* b);  /* kernels of one batched step */
+
+/* State of system i, with the layouts of kbe_step (triangles of the
+ * context's n_max rows, self-energy rows, history slice, right-hand-side
+ * ring); device pointers, borrowed. */
+kbe_status kbe_batch_bind(kbe_batch* b, int i, void* L, void* R, void* S_less, void* S_great, void* I_work,
+                          void* F_ring);
+
+/* One batched step: system i advances row rows[i] (host int array of n_sys
+ * entries) exactly as kbe_step(ctx_i, rows[i], P, precision, ...) would;
+ * rows[i] < 1 leaves system i untouched, rows[i] >= n_t_i is KBE_ERANGE.
+ * The graph of the step is captured on the first call and reused while P,
+ * precision and the tile policy stay the same (KBE_SPLIT_BF16 graphs also
+ * depend on the rows and are re-captured when they change).  Results agree
+ * with kbe_step to rounding (the history sum is chunked differently). */
+kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, void* stream);
+
+/* Tile policy of the persistent FP64 history kernel: `block` output entries
+ * per work item (128 or 256) and a target of 2^item_work_log2 complex
+ * multiply-adds per item (10..40), which sets each system's history chunk
+ * length.  Default (256, 20). */
+kbe_status kbe_batch_set_policy(kbe_batch* b, int block, int item_work_log2);
+kbe_status kbe_batch_get_policy(const kbe_batch* b, int* block, int* item_work_log2);
+
+/* Autotuner: times the persistent history kernel of the batch at `rows`
+ * for each candidate policy (block 128 or 256, item_work_log2 = 14, 16, ..,
+ * 26; `reps` timed runs after one warm-up, CUDA events on `stream`), keeps
+ * the fastest (kbe_batch_set_policy) and returns it with its time in ms.
+ * Synchronous.  Overwrites the self-energy rows and history slices of the
+ * systems active at `rows`. */
+kbe_status kbe_batch_autotune(kbe_batch* b, const int* rows, int reps, void* stream, int* block_out,
+                              int* item_work_log2_out, double* best_ms);
+
+/* Synchronize stream and return (then clear) the batch's device status. */
+kbe_status kbe_batch_sync_status(kbe_batch* b, void* stream);
+
 /* ------------------------------------------------ allocation-free entry -- */
 
 /* History slice of row n (the same Eq. KBE2 contraction and kernels as

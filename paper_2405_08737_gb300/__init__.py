@@ -61,6 +61,18 @@ def lib():
         L.kbe_adjoint_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, vp]
         L.kbe_adjoint_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_adjoint.argtypes = [vp, i, i, vp, vp, vp, i, i, vp, vp, i, vp, vp, vp, vp]
+        L.kbe_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
+        L.kbe_batch_destroy.argtypes = [vp]
+        L.kbe_batch_last_error.argtypes = [vp]
+        L.kbe_batch_last_error.restype = ctypes.c_char_p
+        L.kbe_batch_last_launch_count.argtypes = [vp]
+        L.kbe_batch_bind.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+        L.kbe_batch_step.argtypes = [vp, vp, i, i, vp]
+        L.kbe_batch_set_policy.argtypes = [vp, i, i]
+        L.kbe_batch_get_policy.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.kbe_batch_autotune.argtypes = [vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i),
+                                         ctypes.POINTER(d)]
+        L.kbe_batch_sync_status.argtypes = [vp, vp]
         L.kbe_sync_status.argtypes = [vp, vp]
         L.kbe_set_profiling.argtypes = [vp, i]
         L.kbe_read_profiling.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d)]
@@ -292,6 +304,72 @@ class Run:
     def step(self, n, P=2, precision="fp64", stream=None):
         self.ctx.step(n, self.L, self.R, self.Sl, self.Sg, self.I, self.F, P=P, precision=precision,
                       stream=stream)
+
+
+# ---------------------------------------------------------------- batching
+class Batch:
+    """Independent systems advanced by one batched KBE step (kbe_batch_*).
+
+    ``runs`` is a list of Run objects (each on its own Context with grid and
+    model set); their device state is bound to the batch."""
+
+    def __init__(self, runs):
+        self.runs = list(runs)
+        arr = (ctypes.c_void_p * len(self.runs))(*[r.ctx._h.value for r in self.runs])
+        h = ctypes.c_void_p()
+        _raise(lib().kbe_batch_create(arr, len(self.runs), ctypes.byref(h)))
+        self._h = h
+        for i, r in enumerate(self.runs):
+            self._check(lib().kbe_batch_bind(self._h, i, r.ctx._dev(r.L), r.ctx._dev(r.R), r.ctx._dev(r.Sl),
+                                             r.ctx._dev(r.Sg), r.ctx._dev(r.I), r.ctx._dev(r.F)))
+
+    def _check(self, status):
+        if status != KBE_OK:
+            raise KBEError(status, lib().kbe_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kbe_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _rows(rows):
+        r = np.ascontiguousarray(rows, np.int32)
+        return r, _np_ptr(r)
+
+    def step(self, rows, P=2, precision="fp64", stream=None):
+        r, p = self._rows(rows)
+        self._check(lib().kbe_batch_step(self._h, p, P, PRECISIONS[precision], Context._stream(stream)))
+
+    @property
+    def last_launch_count(self):
+        return int(lib().kbe_batch_last_launch_count(self._h))
+
+    def set_policy(self, block, item_work_log2):
+        self._check(lib().kbe_batch_set_policy(self._h, block, item_work_log2))
+
+    def policy(self):
+        b, w = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().kbe_batch_get_policy(self._h, ctypes.byref(b), ctypes.byref(w)))
+        return b.value, w.value
+
+    def autotune(self, rows, reps=2, stream=None):
+        """Time the candidate tile policies at ``rows``; keep and return the
+        fastest as (block, item_work_log2, ms)."""
+        r, p = self._rows(rows)
+        b, w, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(lib().kbe_batch_autotune(self._h, p, reps, Context._stream(stream), ctypes.byref(b),
+                                             ctypes.byref(w), ctypes.byref(ms)))
+        return b.value, w.value, ms.value
+
+    def sync_status(self, stream=None):
+        self._check(lib().kbe_batch_sync_status(self._h, Context._stream(stream)))
 
 
 # ------------------------------------------------------------ reverse mode

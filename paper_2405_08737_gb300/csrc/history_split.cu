@@ -31,6 +31,7 @@
 // FP64 partial per (CTA, tile).  All mbarrier waits are bounded; a wait that
 // runs out sets the status word and every role leaves its loop.
 
+#include <atomic>
 #include <cstdio>
 
 #include "kbe_internal.h"
@@ -539,6 +540,21 @@ size_t split_workspace_bytes(int M, int n_max) {
   return small + part + 1024;
 }
 
+// The main kernel's dynamic shared memory exceeds the default limit; the
+// attribute is set once per device (outside any stream capture when the
+// first call is made before capturing).
+cudaError_t split_prepare() {
+  static std::atomic<unsigned long long> done_mask{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done_mask.load() & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(split_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e == cudaSuccess) done_mask.fetch_or(bit);
+  return e;
+}
+
 cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* launches) {
   SplitGeomHost h;
   *launches = 0;
@@ -552,13 +568,12 @@ cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* laun
   const size_t need = off + (size_t)h.G * h.S * 2 * 128 * kNA * 16;
   if (need > l.work_bytes) return cudaErrorInvalidValue;
 
+  cudaError_t e = split_prepare();
+  if (e != cudaSuccess) return e;
   split_prep<<<dim3(h.cpt, h.parts), 256, 0, s>>>(l.M, l.n, h.parts, l.Sl, l.Sg, l.w, small, e_small);
   ++*launches;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int smem = (int)sizeof(Smem);
-  e = cudaFuncSetAttribute(split_main, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   SplitArgs args{g, l.L, l.R, small, e_small, part, l.status};
   if (l.ev_begin) cudaEventRecord(l.ev_begin, s);
   split_main<<<h.G, kThreads, smem, s>>>(args);

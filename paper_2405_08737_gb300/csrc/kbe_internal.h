@@ -146,6 +146,7 @@ struct SplitLaunch {
 bool split_geometry(int M, int n, SplitGeomHost* h);
 size_t split_workspace_bytes(int M, int n_max);
 cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* launches);
+cudaError_t split_prepare();  // one-time kernel attributes of the current device
 
 struct StepArgs {
   int M, n, K;

@@ -1,0 +1,294 @@
+// row_kernels.cuh -- per-entry bodies of the row kernels (self-energy,
+// history slice, predictor, Fock matrix, right-hand side, corrector), shared
+// by the single-system launches and the batched persistent launches so that
+// both run the same arithmetic in the same order.
+#pragma once
+
+#include "kbe_internal.h"
+
+namespace kbe {
+namespace rk {
+
+struct Cd {
+  double re, im;
+};
+__device__ __forceinline__ Cd ld(const double* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return Cd{v.x, v.y};
+}
+// acc += a * b
+__device__ __forceinline__ void mac(Cd& acc, Cd a, Cd b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += a * conj(b)
+__device__ __forceinline__ void mac_cj(Cd& acc, Cd a, Cd b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// acc -= a * conj(b)
+__device__ __forceinline__ void msc_cj(Cd& acc, Cd a, Cd b) {
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+
+__device__ __forceinline__ double2 ldd(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ void std2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
+
+// ------------------------------------------------------------ self-energy --
+// Eq. (SE) with a local interaction, entry e of a run of blocks (see
+// sigma.cu); `diag` says whether the entry's block is a diagonal block, and
+// then the third factor is the stored transposed entry.  Returns false on a
+// non-finite result.
+__device__ __forceinline__ bool sigma_entry(int M, int MM, int64_t e, bool diag, const double2* __restrict__ L,
+                                            const double2* __restrict__ R, const double* __restrict__ U,
+                                            double2* __restrict__ Sl, double2* __restrict__ Sg) {
+  const int64_t blk = e / MM;
+  const int ab = (int)(e - blk * MM);
+  const int a = ab / M, b = ab - a * M;
+  const double2 l = L[e];
+  const double2 r = R[e];
+  const double uu = U[a] * U[b];
+  const double2 g = make_double2(r.x + l.x, r.y + l.y);
+  double2 tl, tg;
+  if (diag) {
+    const int64_t eb = e - ab + b * M + a;  // entry (b,a) of the same block
+    const double2 lt = L[eb], rt = R[eb];
+    tl = lt;
+    tg = make_double2(rt.x + lt.x, rt.y + lt.y);
+  } else {
+    tl = make_double2(-l.x, l.y);   // -conj(G^<_ab)
+    tg = make_double2(-g.x, g.y);   // -conj(G^>_ab)
+  }
+  const double g2r = g.x * g.x - g.y * g.y, g2i = 2.0 * g.x * g.y;
+  const double l2r = l.x * l.x - l.y * l.y, l2i = 2.0 * l.x * l.y;
+  double2 sg, sl;
+  sg.x = uu * (g2r * tl.x - g2i * tl.y);
+  sg.y = uu * (g2r * tl.y + g2i * tl.x);
+  sl.x = uu * (l2r * tg.x - l2i * tg.y);
+  sl.y = uu * (l2r * tg.y + l2i * tg.x);
+  Sg[e] = sg;
+  Sl[e] = sl;
+  return isfinite(sg.x) && isfinite(sg.y) && isfinite(sl.x) && isfinite(sl.y);
+}
+
+// ---------------------------------------------------------- history slice --
+// prep entry e of row n: A1 = w_{n,m} (Sg - Sl), Bl = wbar_m Sl, Bg = wbar_m Sg
+__device__ __forceinline__ void history_prep_entry(int MM, int n, int64_t e, const double* __restrict__ Sl,
+                                                   const double* __restrict__ Sg, const WeightsView& w,
+                                                   double* __restrict__ A1, double* __restrict__ Bl,
+                                                   double* __restrict__ Bg) {
+  const int m = (int)(e / MM);
+  const double wn = w.at(n, m), wb = w.wbar[m];
+  const double2 l = reinterpret_cast<const double2*>(Sl)[e];
+  const double2 g = reinterpret_cast<const double2*>(Sg)[e];
+  reinterpret_cast<double2*>(A1)[e] = make_double2(wn * (g.x - l.x), wn * (g.y - l.y));
+  reinterpret_cast<double2*>(Bl)[e] = make_double2(wb * l.x, wb * l.y);
+  reinterpret_cast<double2*>(Bg)[e] = make_double2(wb * g.x, wb * g.y);
+}
+
+struct PartialArgs {
+  int M, MM, n;
+  int chunk_len;
+  const double* L;
+  const double* R;
+  const double* Sl;   // raw row n (band points of term 2)
+  const double* Sg;
+  const double* A1;
+  const double* Bl;
+  const double* Bg;
+  WeightsView w;
+  double* dst;        // partials [chunk][2][n+1][MM] or the output when one chunk
+};
+
+// Output entry lin = (c, a, b) of the history slice over history points
+// m in chunk `chunk`; writes I^< and I^> partials of that chunk.
+__device__ __forceinline__ void history_partial_entry(const PartialArgs& p, int64_t lin, int chunk) {
+  const int M = p.M, MM = p.MM, n = p.n;
+  const int c = (int)(lin / MM);
+  const int ab = (int)(lin - (int64_t)c * MM);
+  const int a = ab / M, b = ab - a * M;
+  const int m0 = chunk * p.chunk_len;
+  const int m1 = min(n + 1, m0 + p.chunk_len);
+
+  Cd P{0, 0}, Q{0, 0}, Tl{0, 0}, Tg{0, 0};  // A1 G^<, A1 G^R, term-2 <, term-2 >
+  const int band_lo = c - p.w.band_w + 1;    // m >= band_lo: w_{c,m} from the band
+
+  // region m < c: stored block (c, m), read transposed
+  const int mA1 = min(m1, c);
+  for (int m = m0; m < mA1; ++m) {
+    const double* lc = p.L + (tri(c, m) * MM + b * M) * 2;
+    const double* rc = p.R + (tri(c, m) * MM + b * M) * 2;
+    const double* a1 = p.A1 + ((int64_t)m * MM + a * M) * 2;
+    if (m < band_lo) {
+      const double* bl = p.Bl + ((int64_t)m * MM + a * M) * 2;
+      const double* bg = p.Bg + ((int64_t)m * MM + a * M) * 2;
+#pragma unroll 4
+      for (int x = 0; x < M; ++x) {
+        const Cd l = ld(lc + 2 * x), r = ld(rc + 2 * x), s1 = ld(a1 + 2 * x);
+        // G^<(m,c)_xb = -conj(L(c,m)_bx);  G^R part: -conj(R(c,m)_bx)
+        msc_cj(P, s1, l);
+        msc_cj(Q, s1, r);
+        // G^A(m,c)_xb = conj(R(c,m)_bx)
+        mac_cj(Tl, ld(bl + 2 * x), r);
+        mac_cj(Tg, ld(bg + 2 * x), r);
+      }
+    } else {
+      const double wcm = p.w.at(c, m);
+      const double* sl = p.Sl + ((int64_t)m * MM + a * M) * 2;
+      const double* sg = p.Sg + ((int64_t)m * MM + a * M) * 2;
+      for (int x = 0; x < M; ++x) {
+        const Cd l = ld(lc + 2 * x), r = ld(rc + 2 * x), s1 = ld(a1 + 2 * x);
+        msc_cj(P, s1, l);
+        msc_cj(Q, s1, r);
+        Cd vl = ld(sl + 2 * x), vg = ld(sg + 2 * x);
+        vl.re *= wcm; vl.im *= wcm; vg.re *= wcm; vg.im *= wcm;
+        mac_cj(Tl, vl, r);
+        mac_cj(Tg, vg, r);
+      }
+    }
+  }
+  // diagonal m == c
+  if (c >= m0 && c < m1) {
+    const int m = c;
+    const double wcc = p.w.at(c, c);
+    const double* lb = p.L + tri(c, c) * MM * 2;
+    const double* rb = p.R + tri(c, c) * MM * 2;
+    const double* a1 = p.A1 + ((int64_t)m * MM + a * M) * 2;
+    const double* sl = p.Sl + ((int64_t)m * MM + a * M) * 2;
+    const double* sg = p.Sg + ((int64_t)m * MM + a * M) * 2;
+    for (int x = 0; x < M; ++x) {
+      const Cd s1 = ld(a1 + 2 * x);
+      mac(P, s1, ld(lb + 2 * (x * M + b)));
+      mac(Q, s1, ld(rb + 2 * (x * M + b)));
+      const Cd ra = ld(rb + 2 * (b * M + x));  // G^A(c,c)_xb = conj(R(c,c)_bx)
+      Cd vl = ld(sl + 2 * x), vg = ld(sg + 2 * x);
+      vl.re *= wcc; vl.im *= wcc; vg.re *= wcc; vg.im *= wcc;
+      mac_cj(Tl, vl, ra);
+      mac_cj(Tg, vg, ra);
+    }
+  }
+  // region m > c: stored block (m, c), read directly
+  for (int m = max(m0, c + 1); m < m1; ++m) {
+    const double* lm = p.L + (tri(m, c) * MM + b) * 2;
+    const double* rm = p.R + (tri(m, c) * MM + b) * 2;
+    const double* a1 = p.A1 + ((int64_t)m * MM + a * M) * 2;
+#pragma unroll 4
+    for (int x = 0; x < M; ++x) {
+      const Cd s1 = ld(a1 + 2 * x);
+      mac(P, s1, ld(lm + 2 * x * M));
+      mac(Q, s1, ld(rm + 2 * x * M));
+    }
+  }
+  // I^< = P + Tl,  I^> = P + Q + Tg
+  double2* d = reinterpret_cast<double2*>(p.dst);
+  const int64_t stride_s = (int64_t)(n + 1) * MM;
+  const int64_t base = (int64_t)chunk * 2 * stride_s + lin;
+  d[base] = make_double2(P.re + Tl.re, P.im + Tl.im);
+  d[base + stride_s] = make_double2(P.re + Q.re + Tg.re, P.im + Q.im + Tg.im);
+}
+
+// Ordered sum over the chunks of entry e; returns false if non-finite.
+__device__ __forceinline__ bool history_reduce_entry(int64_t per_chunk, int nchunk, int64_t e,
+                                                     const double2* __restrict__ part, double2* __restrict__ out) {
+  double2 s = part[e];
+  for (int k = 1; k < nchunk; ++k) {
+    const double2 v = part[(int64_t)k * per_chunk + e];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[e] = s;
+  return isfinite(s.x) && isfinite(s.y);
+}
+
+// ----------------------------------------------------------------- stepper --
+__device__ __forceinline__ const double* ring_at(const StepArgs& a, int j, int s, int c, int ab) {
+  const int MM = a.M * a.M;
+  const int64_t slot = (j - a.f_base) % a.f_rows;
+  return a.F + (((slot * 2 + s) * a.n_max + c) * MM + ab) * 2;
+}
+
+// eps(t_n) = h0 + E(t_n) diag(v) + diag(U_a Im L(n,n)_aa), entry ab
+__device__ __forceinline__ void fock_entry(const StepArgs& a, int ab) {
+  const int M = a.M, MM = M * M;
+  const double* Lnn = a.L + tri(a.n, a.n) * MM * 2;
+  const int i = ab / M, j = ab - i * M;
+  double2 e = ldd(a.h0 + 2 * ab);
+  if (i == j) e.x += a.field * a.v[i] + a.U[i] * Lnn[2 * ab + 1];
+  std2(a.eps + 2 * ab, e);
+}
+
+// predictor (corrector = false) or corrector (corrector = true) for entry
+// lin = (c, a, b) of row n.
+__device__ __forceinline__ void adams_entry(const StepArgs& a, int64_t lin, bool corrector) {
+  const int M = a.M, MM = M * M, n = a.n;
+  const int c = (int)(lin / MM), ab = (int)(lin - (int64_t)c * MM);
+  const int ia = ab / M, ib = ab - ia * M;
+  const double* wt = corrector ? a.corr : a.pred;
+  const int extra = corrector ? 1 : 0;  // the corrector also uses the node t_n
+  double* Ln = a.L + (tri(n, c) * MM + ab) * 2;
+  double* Rn = a.R + (tri(n, c) * MM + ab) * 2;
+  if (c < n) {
+    const int q = min(a.kn, n - c);
+    const double* w = wt + (q - 1) * kWTab;
+    const double2 l0 = ldd(a.L + (tri(n - 1, c) * MM + ab) * 2);
+    const double2 r0 = ldd(a.R + (tri(n - 1, c) * MM + ab) * 2);
+    double2 gl = l0, gg = make_double2(r0.x + l0.x, r0.y + l0.y);
+    for (int p = 0; p < q + extra; ++p) {
+      const int j = n - q + p;
+      const double2 fl = ldd(ring_at(a, j, 0, c, ab)), fg = ldd(ring_at(a, j, 1, c, ab));
+      gl.x = fma(w[p], fl.x, gl.x); gl.y = fma(w[p], fl.y, gl.y);
+      gg.x = fma(w[p], fg.x, gg.x); gg.y = fma(w[p], fg.y, gg.y);
+    }
+    std2(Ln, gl);
+    std2(Rn, make_double2(gg.x - gl.x, gg.y - gl.y));
+  } else {
+    const int q = min(a.kn, n);
+    const double* w = wt + (q - 1) * kWTab;
+    double2 gl = ldd(a.L + (tri(n - 1, n - 1) * MM + ab) * 2);
+    const int ba = ib * M + ia;
+    for (int p = 0; p < q + extra; ++p) {
+      const int j = n - q + p;
+      const double2 f = ldd(ring_at(a, j, 0, j, ab)), ft = ldd(ring_at(a, j, 0, j, ba));
+      // D(j)_ab = F^<(j,j)_ab - conj(F^<(j,j)_ba)
+      gl.x = fma(w[p], f.x - ft.x, gl.x);
+      gl.y = fma(w[p], f.y + ft.y, gl.y);
+    }
+    std2(Ln, gl);
+    std2(Rn, make_double2(0.0, ia == ib ? -1.0 : 0.0));
+  }
+}
+
+// F^s(n,c)_ab = -i ( sum_x eps_ax G^s(n,c)_xb + I^s(n,c)_ab ),  G^> = R + L;
+// returns false on a non-finite value.
+__device__ __forceinline__ bool rhs_entry(const StepArgs& a, int64_t lin) {
+  const int M = a.M, MM = M * M, n = a.n;
+  const int c = (int)(lin / MM), ab = (int)(lin - (int64_t)c * MM);
+  const int ia = ab / M, ib = ab - ia * M;
+  const double* Lb = a.L + tri(n, c) * MM * 2;
+  const double* Rb = a.R + tri(n, c) * MM * 2;
+  double2 sl = ldd(a.I + ((int64_t)c * MM + ab) * 2);
+  double2 sg = ldd(a.I + (((int64_t)(n + 1) + c) * MM + ab) * 2);
+  for (int x = 0; x < M; ++x) {
+    const double2 e = ldd(a.eps + 2 * (ia * M + x));
+    const double2 l = ldd(Lb + 2 * (x * M + ib));
+    const double2 r = ldd(Rb + 2 * (x * M + ib));
+    const double gr = r.x + l.x, gi = r.y + l.y;
+    sl.x += e.x * l.x - e.y * l.y; sl.y += e.x * l.y + e.y * l.x;
+    sg.x += e.x * gr - e.y * gi;   sg.y += e.x * gi + e.y * gr;
+  }
+  // -i (x + i y) = y - i x
+  const double2 fl = make_double2(sl.y, -sl.x), fg = make_double2(sg.y, -sg.x);
+  std2(const_cast<double*>(ring_at(a, n, 0, c, ab)), fl);
+  std2(const_cast<double*>(ring_at(a, n, 1, c, ab)), fg);
+  return isfinite(fl.x) && isfinite(fl.y) && isfinite(fg.x) && isfinite(fg.y);
+}
+
+}  // namespace rk
+}  // namespace kbe

@@ -13,7 +13,7 @@
 // 32 bytes written per entry.  One thread per entry per pass of a
 // grid-stride loop; 16-byte (double2) accesses, fully coalesced.
 
-#include "kbe_internal.h"
+#include "row_kernels.cuh"
 
 namespace kbe {
 namespace {
@@ -36,12 +36,10 @@ __global__ void __launch_bounds__(256) sigma_kernel(int MM, int M, int64_t n_ele
                                                     const double* __restrict__ U,
                                                     double2* __restrict__ Sl,
                                                     double2* __restrict__ Sg, int* status) {
-  bool bad = false;
+  bool ok = true;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t blk = e / MM;
-    const int ab = (int)(e - blk * MM);
-    const int a = ab / M, b = ab - a * M;
     bool diag;
     if (diag_block >= 0) {
       diag = blk == diag_block;
@@ -50,34 +48,9 @@ __global__ void __launch_bounds__(256) sigma_kernel(int MM, int M, int64_t n_ele
       const int64_t r = tri_row(p);
       diag = (p - r * (r + 1) / 2) == r;
     }
-    const double2 l = L[e];
-    const double2 r = R[e];
-    const double uu = U[a] * U[b];
-    const double2 g = make_double2(r.x + l.x, r.y + l.y);
-    // third factor of Eq. (SE): G^<_ba(t',t) for S^>, G^>_ba(t',t) for S^<
-    double2 tl, tg;
-    if (diag) {
-      const int64_t eb = e - ab + b * M + a;  // entry (b,a) of the same block
-      const double2 lt = L[eb], rt = R[eb];
-      tl = lt;
-      tg = make_double2(rt.x + lt.x, rt.y + lt.y);
-    } else {
-      tl = make_double2(-l.x, l.y);   // -conj(G^<_ab)
-      tg = make_double2(-g.x, g.y);   // -conj(G^>_ab)
-    }
-    const double g2r = g.x * g.x - g.y * g.y, g2i = 2.0 * g.x * g.y;
-    const double l2r = l.x * l.x - l.y * l.y, l2i = 2.0 * l.x * l.y;
-    // S^> = uu g^2 tl,  S^< = uu l^2 tg
-    double2 sg, sl;
-    sg.x = uu * (g2r * tl.x - g2i * tl.y);
-    sg.y = uu * (g2r * tl.y + g2i * tl.x);
-    sl.x = uu * (l2r * tg.x - l2i * tg.y);
-    sl.y = uu * (l2r * tg.y + l2i * tg.x);
-    bad |= !(isfinite(sg.x) && isfinite(sg.y) && isfinite(sl.x) && isfinite(sl.y));
-    Sg[e] = sg;
-    Sl[e] = sl;
+    ok &= rk::sigma_entry(M, MM, e, diag, L, R, U, Sl, Sg);
   }
-  if (bad) atomicOr(status, kStatusNumeric);
+  if (!ok) atomicOr(status, kStatusNumeric);
 }
 
 }  // namespace
