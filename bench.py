@@ -28,7 +28,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "chain_m8_n1024"
-FP64_PEAK_TFLOPS = 1.199  # DFMA throughput measured on this GB300 pool
+# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock x 2 flops
+# x 2.070 GHz (the nominal 1.25 TFLOP/s of the part); a DFMA probe kernel
+# reached 1.199 TFLOP/s (95%) and the persistent batched contraction 1.247.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes of one FP64 contraction launch of the bench slice (ncu capture,
+# profiles/history_partial_fp64_chain_m8_n1024.md)
+FP64_SLICE_TRAFFIC = 2.077e9
 METRIC = "history-slice TFLOP/s and ms per KBE step vs plain FP64 GPU path at stated error"
 
 
@@ -50,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-t", type=int, default=None,
                     help="truncate the grid to this many points (smaller profiling case)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batching form")
+    ap.add_argument("--no-window", action="store_true", help="skip the differentiation form")
     return ap.parse_args()
 
 
@@ -243,6 +251,145 @@ def cpu_baseline(run, t, order, h, U, v, pulse, n, M, P, gpu_rows):
     return tflops, threads, sample, errs, dt
 
 
+def batch_bench(kbe, seed, P, stream):
+    """The batching form on 64 independent chains (M in {4,8,12,16,24},
+    N_t in [256,1536], U in [0.5,3]): one batched KBE step advances every
+    system at its last row n_i = N_t,i - 1.  Times the plain FP64 path (one
+    kbe_step per system, in sequence), the batched graph in FP64 and with
+    the split-precision contraction, and reports the deviation of the new
+    rows from the plain path's.  Histories are the non-interacting
+    propagators; the stored right-hand sides are their exact t-derivatives."""
+    import torch
+    import workloads as W
+    systems = W.batch_systems(64, seed)
+    need = 0
+    for sy in systems:
+        M, nt = sy["M"], sy["n_t"]
+        need += (2 * W.tri_size(nt) + (2 * 13 + 2 + 2 + 35) * nt) * M * M * 16 + 200e6
+    free, _ = torch.cuda.mem_get_info()
+    if need > free - 16e9:
+        return {"skipped": "needs %.1f GB of device memory, %.1f GB free" % (need / 1e9, free / 1e9)}
+    t_setup = time.perf_counter()
+    runs, rows, flops = [], [], 0.0
+    for sy in systems:
+        t, order, h, U, v, pulse = W.batch_model(sy)
+        M, nt = sy["M"], sy["n_t"]
+        ctx = kbe.Context(M, nt)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        run = kbe.Run(ctx)
+        W.free_triangles_torch(h, W.half_filled_rho(h), t, nt, "cuda", out=(run.L, run.R))
+        n = nt - 1
+        hd = torch.as_tensor(h, device="cuda")
+        for j in range(max(0, n - int(order[1:].max())), n):
+            p = W.tri_size(j)
+            Lj, Rj = run.L[p:p + j + 1], run.R[p:p + j + 1]
+            run.F[j % 13, 0, : j + 1] = -1j * torch.matmul(hd, Lj)
+            run.F[j % 13, 1, : j + 1] = -1j * torch.matmul(hd, Rj + Lj)
+        runs.append(run)
+        rows.append(n)
+        flops += P * slice_flops(M, n)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    setup_s = time.perf_counter() - t_setup
+    batch = kbe.Batch(runs)
+    t0 = time.perf_counter()
+    tune_rows = [max(1, r // 4) for r in rows]
+    blk, work, tune_ms = batch.autotune(tune_rows, reps=1, stream=stream)
+    tune_s = time.perf_counter() - t0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def new_rows():
+        return [r.L[W.tri_size(n):W.tri_size(n) + n + 1].clone() for r, n in zip(runs, rows)]
+
+    # plain FP64 path: one kbe_step per system
+    plain_launches = 0
+    e0.record(stream)
+    for r, n in zip(runs, rows):
+        r.step(n, P=P, stream=stream)
+        plain_launches += r.ctx.last_launch_count
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    ref = new_rows()
+    out = {"workload": "64 chains, M in {4,8,12,16,24}, N_t in [256,1536], U in [0.5,3] (seed %d); "
+                       "one batched step = every system steps its last row, P=%d" % (seed, P),
+           "history_GB": round(sum(2 * W.tri_size(sy["n_t"]) * sy["M"] ** 2 * 16 for sy in systems) / 1e9, 1),
+           "setup_s": round(setup_s, 1), "plain_fp64_ms_per_step": round(plain_ms, 2),
+           "plain_fp64_launches": plain_launches,
+           "autotune": {"block": blk, "item_work_log2": work, "history_ms_at_quarter_rows": round(tune_ms, 3),
+                        "seconds": round(tune_s, 2)}}
+    for prec in ("fp64", "split"):
+        batch.step(rows, P=P, precision=prec, stream=stream)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.step(rows, P=P, precision=prec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batch.sync_status()
+        ms = e0.elapsed_time(e1)
+        got = new_rows()
+        err = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(got, ref))
+        out["batched_" + prec] = {"ms_per_step": round(ms, 2), "speedup_vs_plain_fp64": round(plain_ms / ms, 3),
+                                  "value": round(flops / (ms * 1e-3) / 1e12, 4),
+                                  "unit": "TFLOP/s (history slices, FP64-equivalent)",
+                                  "graph_launches_per_step": 1, "kernels_per_step": batch.last_launch_count,
+                                  "max_rel_dev_from_plain_fp64": err}
+    out["batched_fp64"]["roofline_frac_of_fp64_peak"] = round(out["batched_fp64"]["value"] / FP64_PEAK_TFLOPS, 4)
+    batch.close()
+    for r in runs:
+        r.ctx.close()
+    del runs, batch
+    torch.cuda.empty_cache()
+    return out
+
+
+def window_bench(kbe, seed, stream):
+    """The differentiation form: gradient of the final site-0 density
+    2 Im L(N-1,N-1)_00 with respect to U (uniform) and E0 through the last 32
+    steps of the 16-orbital, 512-point chain (pulse centred inside the
+    window), restarted from the non-interacting history.  Times the window
+    forward (FP64 steps keeping every right-hand-side row) and the reverse
+    sweep, and checks dF/dU and dF/dE0 against central differences (h=1e-5)."""
+    import torch
+    import workloads as W
+    cfg = W.CONFIGS["chain_m16_n512_w32"]
+    M, nt, Wn = cfg["M"], cfg["n_t"], cfg["window"]
+    n_start = nt - Wn
+    t, order = W.grid(nt, cfg["dt0"], cfg["sig"], seed)
+    h, U, v, pulse = W.build_model(cfg, seed)
+    pulse = dict(pulse, t0=float(t[-1] - 0.35))
+    L, R, F = W.restart_state(h, W.half_filled_rho(h), t, order, n_start, nt, device="cuda")
+    ctx = kbe.Context(M, nt)
+    ctx.set_grid(t, order)
+    win = kbe.Window(ctx, L, R, F, n_start, nt, h, v, pulse, P=2)
+    Ut = torch.tensor(U, dtype=torch.float64, requires_grad=True)
+    Et = torch.tensor(pulse["E0"], dtype=torch.float64, requires_grad=True)
+    kbe.window_final_block(Ut, Et, win)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    blk = kbe.window_final_block(Ut, Et, win)
+    e1.record(stream)
+    (2.0 * blk[0, 0].imag).backward()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    fwd, bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    gU, gE = float(Ut.grad.sum()), float(Et.grad)
+    hh = 1e-5
+    dens = lambda u, e: 2.0 * float(win.forward(u, e)[0, 0].imag.cpu())
+    fdU = (dens(U + hh, pulse["E0"]) - dens(U - hh, pulse["E0"])) / (2 * hh)
+    fdE = (dens(U, pulse["E0"] + hh) - dens(U, pulse["E0"] - hh)) / (2 * hh)
+    ctx.close()
+    return {"workload": "chain_m16_n512_w32: M=16, N_t=512, gradient through the last %d steps (P=2), "
+                        "pulse centred 0.35 before the final time" % Wn,
+            "forward_ms": round(fwd, 2), "backward_ms": round(bwd, 2),
+            "dF_dU": gU, "dF_dU_fd": fdU, "rel_err_U": abs(gU - fdU) / abs(fdU),
+            "dF_dE0": gE, "dF_dE0_fd": fdE, "rel_err_E0": abs(gE - fdE) / abs(fdE)}
+
+
 def step_rows(run, n):
     p = W_tri(n)
     return (run.L[p:p + n + 1].cpu().numpy(), run.R[p:p + n + 1].cpu().numpy(),
@@ -284,10 +431,13 @@ def main():
     value = world * flops_step / (ms_step * 1e-3) / 1e12
     k_avg = k_ms / max(k_count, 1)
     achieved = slice_flops(M, n) / (k_avg * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+            "traffic": FP64_SLICE_TRAFFIC if (M, n) == (8, 1023) else None,
+            "traffic_source": "ncu dram__bytes_read+write of the launch at n=1022, scaled to n=1023",
             "kernel": "history_partial (FP64 DFMA contraction)", "launches_timed": k_count,
-            "avg_ms": round(k_avg, 4), "peak_source": "measured DFMA probe (FP64 not in MEASURED_PEAKS.json)"}
+            "avg_ms": round(k_avg, 4), "peak_source": "unit counts x clock: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz "
+                              "(FP64 is not in MEASURED_PEAKS.json)"}
     ms_step_s = ms_s / args.steps
     split = {"precision": "split: 4-digit bf16 fixed-point slices on tcgen05, exact FP32 chunk sums, "
                           "double-float accumulation (KBE_SPLIT_BF16)",
@@ -319,9 +469,15 @@ def main():
         line["error_vs_oracle"] = dict(errs["fp64"], where="new row n and last history slice of the timed KBE "
                                                            "step, max-norm relative")
         line["precision_form"]["error_vs_oracle"] = errs["split"]
+    if rank == 0 and not args.no_window:
+        line["differentiation_form"] = window_bench(kbe, args.seed, stream)
+    ctx.close()
+    del run
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_batch:
+        line["batching_form"] = batch_bench(kbe, args.seed, args.P, stream)
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -27,12 +27,16 @@
 // Operands are read through the read-only path; a block of G is reused M
 // times from L1 (once per a), the self-energy row stays L2-resident.
 
+#include <algorithm>
+
 #include "row_kernels.cuh"
 
 namespace kbe {
 namespace {
 
 using rk::PartialArgs;
+
+constexpr int kHistBlock = 128;  // threads per block of the contraction
 
 __global__ void __launch_bounds__(256) history_prep(int MM, int n, const double* __restrict__ Sl,
                                                     const double* __restrict__ Sg, WeightsView w,
@@ -82,8 +86,13 @@ cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launch
   const int M = a.M, MM = M * M, n = a.n;
   const int64_t row = (int64_t)(n + 1) * MM;       // complex entries per s
   const int64_t outputs = row;                     // threads of one chunk
-  // Enough threads for full occupancy: 152 SMs x 2048 threads.
+  // Split of the history index m: at least enough threads for full
+  // occupancy (152 SMs x 2048 threads), and chunks short enough that one
+  // 128-thread block does about 2^16 complex multiply-adds (3M per point and
+  // output), which keeps the tail of the launch short.
   int64_t want = (152LL * 2048 + outputs - 1) / outputs;
+  const int64_t len_target = std::max<int64_t>(1, (1 << 16) / (kHistBlock * 3 * M));
+  want = std::max<int64_t>(want, (n + 1 + len_target - 1) / len_target);
   int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
   if (nchunk > n + 1) nchunk = n + 1;
   // the partials must fit the workspace
@@ -104,9 +113,9 @@ cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launch
   if (e != cudaSuccess) { *launches = nl; return e; }
   PartialArgs p{M, MM, n, chunk_len, a.L, a.R, a.Sl, a.Sg, A1, Bl, Bg, a.w,
                 nchunk == 1 ? a.out : partials};
-  dim3 grid((unsigned)((outputs + 255) / 256), (unsigned)nchunk);
+  dim3 grid((unsigned)((outputs + kHistBlock - 1) / kHistBlock), (unsigned)nchunk);
   if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
-  history_partial<<<grid, 256, 0, s>>>(p);
+  history_partial<<<grid, kHistBlock, 0, s>>>(p);
   if (a.ev_end) cudaEventRecord(a.ev_end, s);
   ++nl;
   e = cudaGetLastError();

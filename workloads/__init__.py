@@ -106,15 +106,21 @@ def free_triangles(h, rho0, t, n_rows=None):
     return L, R
 
 
-def free_triangles_torch(h, rho0, t, n_rows, device, chunk_blocks=1 << 18):
+def free_triangles_torch(h, rho0, t, n_rows, device, chunk_blocks=None, out=None):
     """``free_triangles`` built with torch on ``device`` (large histories),
-    a few batched products per chunk of rows."""
+    a few batched products per chunk of rows; ``out`` = (L, R) fills the
+    first tri(n_rows) blocks of existing tensors instead of new ones."""
     A = torch.from_numpy(propagators(h, t[:n_rows])).to(device)
     rho = torch.from_numpy(rho0).to(device)
     M = h.shape[0]
     ntri = tri_size(n_rows)
-    L = torch.empty((ntri, M, M), dtype=torch.complex128, device=device)
-    R = torch.empty_like(L)
+    if chunk_blocks is None:  # about 512 MB per temporary
+        chunk_blocks = max(4096, (1 << 29) // (M * M * 16))
+    if out is None:
+        L = torch.empty((ntri, M, M), dtype=torch.complex128, device=device)
+        R = torch.empty_like(L)
+    else:
+        L, R = out
     Ar = A @ rho
     Ah = A.conj().transpose(1, 2).contiguous()
     r0 = 0
@@ -193,6 +199,15 @@ def build_model(cfg, seed):
     h = chain_h(M, cfg["J"]) if cfg["h"] == "chain" else goe_h(M, 1000 + seed)
     U = np.full(M, cfg["U"], dtype=np.float64)
     return h, U, site_potential(M), cfg["pulse"]
+
+
+def batch_model(sys):
+    """Grid and model of one batched system: an open chain (J = 1) with
+    local U, the site potential, no pulse, on its own seeded grid
+    (dt_n = 0.02 exp(0.4 z_n), orders 1..5)."""
+    t, order = grid(sys["n_t"], 0.02, 0.4, sys["grid_seed"])
+    M = sys["M"]
+    return t, order, chain_h(M, sys["J"]), np.full(M, sys["U"]), site_potential(M), None
 
 
 def batch_systems(n_sys, seed):
