@@ -251,7 +251,7 @@ def cpu_baseline(run, t, order, h, U, v, pulse, n, M, P, gpu_rows):
     return tflops, threads, sample, errs, dt
 
 
-def batch_bench(kbe, seed, P, stream):
+def batch_bench(kbe, seed, P, stream, rank=0, world=1):
     """The batching form on 64 independent chains (M in {4,8,12,16,24},
     N_t in [256,1536], U in [0.5,3]): one batched KBE step advances every
     system at its last row n_i = N_t,i - 1.  Times the plain FP64 path (one
@@ -292,6 +292,7 @@ def batch_bench(kbe, seed, P, stream):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     setup_s = time.perf_counter() - t_setup
+    total_flops = sum(P * slice_flops(sy["M"], sy["n_t"] - 1) for sy in all_systems)
     batch = kbe.Batch(runs)
     t0 = time.perf_counter()
     tune_rows = [max(1, r // 4) for r in rows]
@@ -311,11 +312,12 @@ def batch_bench(kbe, seed, P, stream):
         plain_launches += r.ctx.last_launch_count
     e1.record(stream)
     torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
+    plain_ms = parallel.max_over_ranks(e0.elapsed_time(e1))
     ref = new_rows()
     out = {"workload": "64 chains, M in {4,8,12,16,24}, N_t in [256,1536], U in [0.5,3] (seed %d); "
                        "one batched step = every system steps its last row, P=%d" % (seed, P),
-           "history_GB": round(sum(2 * W.tri_size(sy["n_t"]) * sy["M"] ** 2 * 16 for sy in systems) / 1e9, 1),
+           "history_GB": round(sum(2 * W.tri_size(sy["n_t"]) * sy["M"] ** 2 * 16 for sy in all_systems) / 1e9, 1),
+           "ranks": world, "scaling": "strong (the 64 systems are split across ranks)" if world > 1 else None,
            "setup_s": round(setup_s, 1), "plain_fp64_ms_per_step": round(plain_ms, 2),
            "plain_fp64_launches": plain_launches,
            "autotune": {"block": blk, "item_work_log2": work, "history_ms_at_quarter_rows": round(tune_ms, 3),
@@ -328,11 +330,11 @@ def batch_bench(kbe, seed, P, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         batch.sync_status()
-        ms = e0.elapsed_time(e1)
+        ms = parallel.max_over_ranks(e0.elapsed_time(e1))
         got = new_rows()
-        err = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(got, ref))
+        err = parallel.max_over_ranks(max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(got, ref)))
         out["batched_" + prec] = {"ms_per_step": round(ms, 2), "speedup_vs_plain_fp64": round(plain_ms / ms, 3),
-                                  "value": round(flops / (ms * 1e-3) / 1e12, 4),
+                                  "value": round(total_flops / (ms * 1e-3) / 1e12, 4),
                                   "unit": "TFLOP/s (history slices, FP64-equivalent)",
                                   "graph_launches_per_step": 1, "kernels_per_step": batch.last_launch_count,
                                   "max_rel_dev_from_plain_fp64": err}
@@ -474,8 +476,8 @@ def main():
     ctx.close()
     del run
     torch.cuda.empty_cache()
-    if rank == 0 and not args.no_batch:
-        line["batching_form"] = batch_bench(kbe, args.seed, args.P, stream)
+    if not args.no_batch:
+        line["batching_form"] = batch_bench(kbe, args.seed, args.P, stream, rank, world)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
