@@ -258,19 +258,25 @@ def batch_bench(kbe, seed, P, stream, rank=0, world=1):
     kbe_step per system, in sequence), the batched graph in FP64 and with
     the split-precision contraction, and reports the deviation of the new
     rows from the plain path's.  Histories are the non-interacting
-    propagators; the stored right-hand sides are their exact t-derivatives."""
+    propagators; the stored right-hand sides are their exact t-derivatives.
+    With several ranks each takes a cost-balanced share of the 64 systems
+    (no communication on the data path) and times are the max over ranks."""
     import torch
     import workloads as W
-    systems = W.batch_systems(64, seed)
+    from paper_2405_08737_gb300 import parallel
+    all_systems = W.batch_systems(64, seed)
+    costs = [parallel.slice_cost(sy["M"], sy["n_t"] - 1) for sy in all_systems]
+    mine = parallel.shard_systems(costs, world)[rank]
+    systems = [all_systems[i] for i in mine]
     need = 0
     for sy in systems:
         M, nt = sy["M"], sy["n_t"]
         need += (2 * W.tri_size(nt) + (2 * 13 + 2 + 2 + 35) * nt) * M * M * 16 + 200e6
     free, _ = torch.cuda.mem_get_info()
-    if need > free - 16e9:
+    if parallel.max_over_ranks(1.0 if need > free - 16e9 else 0.0) > 0:
         return {"skipped": "needs %.1f GB of device memory, %.1f GB free" % (need / 1e9, free / 1e9)}
     t_setup = time.perf_counter()
-    runs, rows, flops = [], [], 0.0
+    runs, rows = [], []
     for sy in systems:
         t, order, h, U, v, pulse = W.batch_model(sy)
         M, nt = sy["M"], sy["n_t"]
@@ -288,7 +294,6 @@ def batch_bench(kbe, seed, P, stream, rank=0, world=1):
             run.F[j % 13, 1, : j + 1] = -1j * torch.matmul(hd, Rj + Lj)
         runs.append(run)
         rows.append(n)
-        flops += P * slice_flops(M, n)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     setup_s = time.perf_counter() - t_setup
@@ -345,6 +350,46 @@ def batch_bench(kbe, seed, P, stream, rank=0, world=1):
     del runs, batch
     torch.cuda.empty_cache()
     return out
+
+
+def sigma_bench(kbe, ctx, run, n_t, stream, reps=10):
+    """The self-energy kernel over the whole stored triangle (kbe_selfenergy_all):
+    32 B read and 32 B written per complex entry, 2.15 GB for the chain
+    workload (far above L2).  Returns GB/s against the measured HBM peak."""
+    import torch
+    Sl = torch.empty_like(run.L)
+    Sg = torch.empty_like(run.L)
+    for _ in range(3):
+        ctx.selfenergy_all(n_t, run.L, run.R, Sl, Sg, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.selfenergy_all(n_t, run.L, run.R, Sl, Sg, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = 64.0 * n_t * (n_t + 1) // 2 * ctx.M * ctx.M
+    peak = hbm_peak_gbs()
+    del Sl, Sg
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"kernel": "sigma_kernel over the whole triangle (kbe_selfenergy_all)", "bound": "hbm",
+            "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "avg_ms": round(ms, 4), "bytes_per_launch": nbytes,
+            "note": "algorithmic bytes: L, R read and S^<, S^> written once (64 B per complex entry)"}
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k])
+    except Exception:
+        pass
+    return 6800.0
 
 
 def window_bench(kbe, seed, stream):
@@ -471,6 +516,8 @@ def main():
         line["error_vs_oracle"] = dict(errs["fp64"], where="new row n and last history slice of the timed KBE "
                                                            "step, max-norm relative")
         line["precision_form"]["error_vs_oracle"] = errs["split"]
+    if rank == 0:
+        line["selfenergy"] = sigma_bench(kbe, ctx, run, n + 1, stream)
     if rank == 0 and not args.no_window:
         line["differentiation_form"] = window_bench(kbe, args.seed, stream)
     ctx.close()
