@@ -190,9 +190,11 @@ __global__ void __launch_bounds__(256) batch_rows(BatchDev b) {
       ok &= rk::rhs_entry(step_of(s, b.status), lin);
     } else if (OP == kOpSigma) {
       const int64_t off = tri(n, 0) * MM;
-      ok &= rk::sigma_entry(s.M, MM, lin, lin / MM == n, reinterpret_cast<const double2*>(s.L) + off,
-                            reinterpret_cast<const double2*>(s.R) + off, s.U, reinterpret_cast<double2*>(s.Sl),
-                            reinterpret_cast<double2*>(s.Sg));
+      const int64_t blk = lin / MM;
+      const int ab = (int)(lin - blk * MM);
+      ok &= rk::sigma_entry(s.M, lin, ab, blk == n, rk::sigma_uu(s.M, ab, s.U),
+                            reinterpret_cast<const double2*>(s.L) + off, reinterpret_cast<const double2*>(s.R) + off,
+                            reinterpret_cast<double2*>(s.Sl), reinterpret_cast<double2*>(s.Sg));
     } else if (OP == kOpPrep) {
       const int64_t row = (int64_t)(n + 1) * MM;
       const WeightsView w{s.wbar, s.band, s.band_w};

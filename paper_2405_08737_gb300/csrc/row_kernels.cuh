@@ -4,6 +4,7 @@
 // both run the same arithmetic in the same order.
 #pragma once
 
+#include "dfloat.cuh"
 #include "kbe_internal.h"
 
 namespace kbe {
@@ -42,40 +43,53 @@ __device__ __forceinline__ double2 ldd(const double* p) { return *reinterpret_ca
 __device__ __forceinline__ void std2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
 
 // ------------------------------------------------------------ self-energy --
-// Eq. (SE) with a local interaction, entry e of a run of blocks (see
-// sigma.cu); `diag` says whether the entry's block is a diagonal block, and
-// then the third factor is the stored transposed entry.  Returns false on a
-// non-finite result.
-__device__ __forceinline__ bool sigma_entry(int M, int MM, int64_t e, bool diag, const double2* __restrict__ L,
-                                            const double2* __restrict__ R, const double* __restrict__ U,
-                                            double2* __restrict__ Sl, double2* __restrict__ Sg) {
-  const int64_t blk = e / MM;
-  const int ab = (int)(e - blk * MM);
+// Eq. (SE) with a local interaction, entry e = (block, ab) of a run of
+// blocks (see sigma.cu); `diag` says whether the entry's block is a diagonal
+// block, and then the third factor is the stored transposed entry.  The
+// products run in double-float on the FP32 pipe (dfloat.cuh; about 2^-47
+// relative per operation), because ~40 FP64 instructions per 64-byte entry
+// would hold the kernel far below memory bandwidth on this part.  Only
+// G^> = R + L (where L and R may cancel), U_a U_b and the final hi + lo stay
+// in FP64: 7 FP64 instructions per entry.  Off the diagonal, with
+// q = -U_a U_b g conj(l):  S^> = g q,  S^< = l conj(q).
+// Returns false on a non-finite result.
+__device__ __forceinline__ df::C2 ld_c2(double2 v) {
+  return df::C2{df::from_double_fast(v.x), df::from_double_fast(v.y)};
+}
+__device__ __forceinline__ double2 to_d2(df::C2 a) { return make_double2(df::to_double(a.re), df::to_double(a.im)); }
+
+// uu = U_a U_b of entry ab = (a, b) in double-float (the caller may keep it
+// while ab stays the same).
+__device__ __forceinline__ df::F2 sigma_uu(int M, int ab, const double* __restrict__ U) {
   const int a = ab / M, b = ab - a * M;
-  const double2 l = L[e];
-  const double2 r = R[e];
-  const double uu = U[a] * U[b];
-  const double2 g = make_double2(r.x + l.x, r.y + l.y);
-  double2 tl, tg;
-  if (diag) {
-    const int64_t eb = e - ab + b * M + a;  // entry (b,a) of the same block
-    const double2 lt = L[eb], rt = R[eb];
-    tl = lt;
-    tg = make_double2(rt.x + lt.x, rt.y + lt.y);
+  return df::from_double_fast(U[a] * U[b]);
+}
+
+__device__ __forceinline__ bool sigma_entry(int M, int64_t e, int ab, bool diag, df::F2 uu,
+                                            const double2* __restrict__ L, const double2* __restrict__ R,
+                                            double2* __restrict__ Sl, double2* __restrict__ Sg) {
+  const double2 l64 = L[e], r64 = R[e];
+  const df::C2 l = ld_c2(l64);
+  const df::C2 g = ld_c2(make_double2(r64.x + l64.x, r64.y + l64.y));
+  df::C2 sg, sl;
+  if (!diag) {
+    const df::C2 q = df::cscale(df::neg(uu), df::cmul_cj(g, l));  // -uu g conj(l)
+    sg = df::cmul(g, q);
+    sl = df::cmul_cj(l, q);
   } else {
-    tl = make_double2(-l.x, l.y);   // -conj(G^<_ab)
-    tg = make_double2(-g.x, g.y);   // -conj(G^>_ab)
+    const int a = ab / M, b = ab - a * M;
+    const int64_t eb = e - ab + b * M + a;  // entry (b,a) of the same block
+    const double2 lt64 = L[eb], rt64 = R[eb];
+    const df::C2 lt = ld_c2(lt64);
+    const df::C2 gt = ld_c2(make_double2(rt64.x + lt64.x, rt64.y + lt64.y));
+    sg = df::cmul(df::cscale(uu, df::cmul(g, g)), lt);
+    sl = df::cmul(df::cscale(uu, df::cmul(l, l)), gt);
   }
-  const double g2r = g.x * g.x - g.y * g.y, g2i = 2.0 * g.x * g.y;
-  const double l2r = l.x * l.x - l.y * l.y, l2i = 2.0 * l.x * l.y;
-  double2 sg, sl;
-  sg.x = uu * (g2r * tl.x - g2i * tl.y);
-  sg.y = uu * (g2r * tl.y + g2i * tl.x);
-  sl.x = uu * (l2r * tg.x - l2i * tg.y);
-  sl.y = uu * (l2r * tg.y + l2i * tg.x);
-  Sg[e] = sg;
-  Sl[e] = sl;
-  return isfinite(sg.x) && isfinite(sg.y) && isfinite(sl.x) && isfinite(sl.y);
+  Sg[e] = to_d2(sg);
+  Sl[e] = to_d2(sl);
+  // hi + lo is finite exactly when hi is: x - x is 0 for finite x, nan otherwise
+  const float z = (sg.re.hi - sg.re.hi) + (sg.im.hi - sg.im.hi) + (sl.re.hi - sl.re.hi) + (sl.im.hi - sl.im.hi);
+  return z == 0.0f;
 }
 
 // ---------------------------------------------------------- history slice --

@@ -10,8 +10,8 @@
 // G^><_ba(t,t) itself, as Eq. (SE) reads; it equals -conj(G^><_ab) when the
 // block is exactly anti-Hermitian.
 // The kernel is a pure stream over complex128 entries: 32 bytes read and
-// 32 bytes written per entry.  One thread per entry per pass of a
-// grid-stride loop; 16-byte (double2) accesses, fully coalesced.
+// 32 bytes written per entry, 16-byte (double2) accesses, fully coalesced;
+// the products run in double-float on the FP32 pipe (row_kernels.cuh).
 
 #include "row_kernels.cuh"
 
@@ -29,26 +29,56 @@ __device__ __forceinline__ int64_t tri_row(int64_t p) {
 // first_block: triangle index of the first block of the launch; diag_block:
 // the one diagonal block of a row launch (relative index), or -1 when the
 // launch covers whole rows of a triangle (the diagonal blocks are found
-// from the triangle index).
+// from the triangle index).  Each CTA streams one contiguous range of
+// entries, blockDim at a time; a thread keeps (block, ab) and, for whole
+// triangles, the index of the next diagonal block by increments.
 __global__ void __launch_bounds__(256) sigma_kernel(int MM, int M, int64_t n_elem, int64_t first_block,
                                                     int64_t diag_block, const double2* __restrict__ L,
                                                     const double2* __restrict__ R,
                                                     const double* __restrict__ U,
                                                     double2* __restrict__ Sl,
                                                     double2* __restrict__ Sg, int* status) {
+  const int64_t per_cta = ((n_elem + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const int64_t e_end = min(n_elem, (int64_t)(blockIdx.x + 1) * per_cta);
+  int64_t e = (int64_t)blockIdx.x * per_cta + threadIdx.x;
+  if (e >= e_end) return;
+  int64_t blk = e / MM;
+  int ab = (int)(e - blk * MM);
+  const int sblk = (int)(blockDim.x / MM);
+  const int sab = (int)(blockDim.x - sblk * MM);
+  // whole triangles: next diagonal block index at or after the current block
+  int64_t r = 0, next_diag = 0;
+  if (diag_block < 0) {
+    const int64_t p = first_block + blk;
+    r = tri_row(p);
+    next_diag = r * (r + 1) / 2 + r;
+  }
   bool ok = true;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t blk = e / MM;
+  int uu_ab = ab;
+  df::F2 uu = rk::sigma_uu(M, ab, U);
+  for (; e < e_end; e += blockDim.x) {
+    if (ab != uu_ab) {  // never for M dividing 16: blockDim is a multiple of M^2
+      uu = rk::sigma_uu(M, ab, U);
+      uu_ab = ab;
+    }
     bool diag;
     if (diag_block >= 0) {
       diag = blk == diag_block;
     } else {
       const int64_t p = first_block + blk;
-      const int64_t r = tri_row(p);
-      diag = (p - r * (r + 1) / 2) == r;
+      while (p > next_diag) {  // rows advance by at most a few blocks per iteration
+        ++r;
+        next_diag += r + 1;
+      }
+      diag = p == next_diag;
     }
-    ok &= rk::sigma_entry(M, MM, e, diag, L, R, U, Sl, Sg);
+    ok &= rk::sigma_entry(M, e, ab, diag, uu, L, R, Sl, Sg);
+    blk += sblk;
+    ab += sab;
+    if (ab >= MM) {
+      ab -= MM;
+      ++blk;
+    }
   }
   if (!ok) atomicOr(status, kStatusNumeric);
 }

@@ -1,7 +1,9 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
 Tolerance: 1e-12 relative in the max norm per slice (both s, all columns)
-for the FP64 path; the self-energy is elementwise and checked at 1e-14."""
+for the FP64 path.  The self-energy kernel forms its products in
+double-float arithmetic (about 2^-47 per operation, a few 1e-14 per entry)
+and is checked at 1e-13."""
 import numpy as np
 import pytest
 
@@ -10,6 +12,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
+TOL_SIGMA = 1e-13
 
 
 @pytest.fixture(scope="module")
@@ -61,8 +64,8 @@ def test_sigma_slice(kbe, M, n_t, n):
     ctx.selfenergy_slice(n, Ld, Rd, Sl, Sg)
     ctx.sync_status()
     ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
-    assert _rel(Sl.cpu().numpy(), ol) < 1e-14
-    assert _rel(Sg.cpu().numpy(), og) < 1e-14
+    assert _rel(Sl.cpu().numpy(), ol) < TOL_SIGMA
+    assert _rel(Sg.cpu().numpy(), og) < TOL_SIGMA
     assert ctx.last_launch_count == 0  # sync_status launches nothing
 
 
@@ -79,8 +82,8 @@ def test_sigma_all_rows(kbe):
     for n in range(n_t):
         ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
         p = W.tri_index(n, 0)
-        assert _rel(Sl[p:p + n + 1], ol) < 1e-14
-        assert _rel(Sg[p:p + n + 1], og) < 1e-14
+        assert _rel(Sl[p:p + n + 1], ol) < TOL_SIGMA
+        assert _rel(Sg[p:p + n + 1], og) < TOL_SIGMA
 
 
 def _gpu_slice(kbe, ctx, n, L, R, Sl, Sg):
@@ -172,7 +175,7 @@ def test_history_full_size_sampled(kbe, name):
     L, R = Ld.cpu().numpy(), Rd.cpu().numpy()
     Sl_h, Sg_h = Sl.cpu().numpy(), Sg.cpu().numpy()
     ol, og = oracle.sigma_row(oracle.local_U4(U), n, L, R)
-    assert _rel(Sl_h, ol) < 1e-14 and _rel(Sg_h, og) < 1e-14
+    assert _rel(Sl_h, ol) < TOL_SIGMA and _rel(Sg_h, og) < TOL_SIGMA
     cols = [0, 1, 2, 255, 511, 700, n - 5, n - 1, n]
     ref = oracle.history_columns(t, order, n, L, R, ol, og, cols, nthreads=oracle.threads_available())
     assert _rel(I[:, cols], ref) < TOL
