@@ -39,6 +39,9 @@ void release(kbe_ctx* ctx) {
   cudaFree(ctx->d_wbar); cudaFree(ctx->d_band); cudaFree(ctx->d_corr); cudaFree(ctx->d_pred);
   cudaFree(ctx->d_h0); cudaFree(ctx->d_U); cudaFree(ctx->d_v); cudaFree(ctx->d_eps);
   cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split); cudaFree(ctx->d_adj);
+  cudaFree(ctx->d_planes);
+  ctx->d_planes = nullptr;
+  ctx->planes_bytes = 0;
   ctx->d_split = nullptr;
   ctx->d_adj = nullptr;
   ctx->adj_bytes = 0;
@@ -81,7 +84,18 @@ kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void
     SplitLaunch l{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
                   weights_view(ctx), (double*)I_out, ctx->d_split, ctx->split_bytes, ctx->d_status};
     if (!next_events(ctx, &l.ev_begin, &l.ev_end)) return fail(ctx, KBE_ECUDA, "profiling: cudaEventCreate");
-    cudaError_t e = launch_history_split(l, s, launches);
+    if (!ctx->d_planes && !ctx->planes_failed) {
+      const size_t bytes = split_planes_bytes(ctx->M, ctx->n_max);
+      if (bytes == 0 || cudaMalloc(&ctx->d_planes, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->d_planes = nullptr;
+        ctx->planes_failed = true;  // not enough memory: convert inside the contraction kernel instead
+      } else {
+        ctx->planes_bytes = bytes;
+      }
+    }
+    cudaError_t e = ctx->d_planes ? launch_history_split2(l, ctx->d_planes, ctx->planes_bytes, s, launches)
+                                  : launch_history_split(l, s, launches);
     return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "split history slice launch");
   }
   if (precision != KBE_FP64) return fail(ctx, KBE_EINVAL, "unknown precision");
@@ -639,6 +653,7 @@ kbe_status kbe_sync_status(kbe_ctx* ctx, void* stream) {
   if ((e = cudaMemset(ctx->d_status, 0, sizeof(int))) != cudaSuccess)
     return cuda_fail(ctx, e, "kbe_sync_status: clear");
   if (flag & kStatusTimeout) return fail(ctx, KBE_ETIMEOUT, "a device wait ran out");
+  if (flag & kStatusInternal) return fail(ctx, KBE_ECUDA, "a kernel found an inconsistent launch geometry");
   if (flag & kStatusNumeric) return fail(ctx, KBE_ENUMERIC, "a kernel produced a non-finite value");
   return KBE_OK;
 }

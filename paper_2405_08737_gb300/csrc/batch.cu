@@ -635,6 +635,7 @@ kbe_status kbe_batch_sync_status(kbe_batch* b, void* stream) {
       (e = cudaMemset(b->dev.status, 0, sizeof(int))) != cudaSuccess)
     return bcuda(b, e, "kbe_batch_sync_status: status word");
   if (flag & kStatusTimeout) return bfail(b, KBE_ETIMEOUT, "a device wait ran out");
+  if (flag & kStatusInternal) return bfail(b, KBE_ECUDA, "a kernel found an inconsistent launch geometry");
   if (flag & kStatusNumeric) return bfail(b, KBE_ENUMERIC, "a kernel produced a non-finite value");
   return KBE_OK;
 }

@@ -454,6 +454,338 @@ __global__ void __launch_bounds__(kThreads, 1) split_main(SplitArgs a) {
   }
 }
 
+// ============================================================ planes path ==
+// The same contraction with the conversion taken off the main kernel: an
+// encoder kernel at full occupancy writes, per (column tile, chunk), the
+// digit planes of PL and Q and the column exponents in exactly the
+// shared-memory image the MMAs read (and QU for the chunks straddling the
+// band), and the main kernel streams them in with bulk copies issued by one
+// producer thread.  Eight epilogue warps drain the accumulators, four per
+// accumulator group (I^< and I^>).
+
+constexpr int kUnitBytes = 2 * kBigTile + 1024;                 // PL | Q | column exponents (padded)
+constexpr int kStage2Bytes = kUnitBytes + kBigTile + kSmallBytes;  // + QU | small operand
+constexpr int kEpi2 = 8;
+constexpr int kThreads2 = (kEpi2 + 2) * 32;                     // + MMA warp + producer warp
+
+// Slot of a straddling chunk kc in the QU buffer of the tile starting at
+// column c0 (the first straddling chunk is the first whose last point
+// m_hi exceeds c0 - band_w).
+__host__ __device__ __forceinline__ int qu_slot(int kc, int c0, int M, int band_w) {
+  const int t = (c0 - band_w + 1) * M - 15;
+  const int first = t <= 0 ? 0 : (t + 15) / 16;
+  return kc - first;
+}
+
+struct EncodeArgs {
+  SplitGeom g;
+  const double* L;
+  const double* R;
+  uint8_t* planes;     // [column tile][cpt_stride][kUnitBytes]
+  uint8_t* qu;         // [column tile][qu_slots][kBigTile]
+  int cpt_stride, qu_slots;
+  int* status;
+};
+
+// One CTA per (column tile, chunk): thread (arr, jrow) encodes row jrow of
+// plane arr (0: G^< from L, 1: Q from R) for the chunk's 16 K entries.
+__global__ void __launch_bounds__(256) split_encode(EncodeArgs a) {
+  const SplitGeom& g = a.g;
+  const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
+  const int ctile = (int)(blockIdx.x / (unsigned)g.cpt), kc = (int)(blockIdx.x % (unsigned)g.cpt);
+  __shared__ int ecol[128];
+  const int ct = threadIdx.x, arr = ct >> 7, jrow = ct & 127;
+  const bool row_live = jrow < CT * M;
+  const int cl = row_live ? jrow / M : 0, bb = jrow - cl * M;
+  const int c0 = ctile * CT;
+  const int kap0 = kc * kKC;
+  const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
+  if (ct < 128) ecol[ct] = 0;
+  __syncthreads();
+  const double2* base = reinterpret_cast<const double2*>(arr == 0 ? a.L : a.R);
+  const int c = c0 + cl;
+  const bool col_live = row_live && c <= n;
+  double er[kKC], ei[kKC];
+  unsigned keep = 0;
+  int ef = 0;
+  {
+    int m = kap0 / M, x = kap0 - m * M;
+#pragma unroll
+    for (int k = 0; k < kKC; ++k) {
+      double2 z = make_double2(0.0, 0.0);
+      if (col_live && m <= n) {
+        if (m >= c) {
+          z = __ldcs(base + tri(m, c) * MM + x * M + bb);
+        } else {
+          z = __ldcs(base + tri(c, m) * MM + bb * M + x);
+          z.x = -z.x;  // -conj
+        }
+      }
+      er[k] = z.x;
+      ei[k] = z.y;
+      keep |= (unsigned)(m <= c - g.band_w) << k;
+      if (++x == M) { x = 0; ++m; }
+    }
+#pragma unroll
+    for (int k = 0; k < kKC; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
+  }
+  if (row_live && ef > 0) atomicMax(&ecol[cl], ef);
+  __syncthreads();
+  uint8_t* unit = a.planes + ((size_t)ctile * a.cpt_stride + kc) * kUnitBytes;
+  uint8_t* dst = unit + arr * kBigTile;
+  uint8_t* QU = nullptr;
+  if (arr == 1 && cls == 2) {
+    const int slot = qu_slot(kc, c0, M, g.band_w);
+    if (slot >= 0 && slot < a.qu_slots) QU = a.qu + ((size_t)ctile * a.qu_slots + slot) * kBigTile;
+    else if (ct == 128) atomicOr(a.status, kStatusInternal);  // geometry error: reported, never written
+  }
+  const int e = scale_from_field(ecol[cl]);
+#pragma unroll
+  for (int kg = 0; kg < 4; ++kg) {
+    uint32_t w[kSlices][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t dr[kSlices], di[kSlices];
+      digits_bf16(fixed31(er[4 * kg + q], e), dr);
+      digits_bf16(fixed31(ei[4 * kg + q], e), di);
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) w[sl][q] = __byte_perm(dr[sl], di[sl], 0x5410);
+    }
+    const int off = (kg * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl) {
+      *reinterpret_cast<uint4*>(dst + sl * kBigSlice + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+      if (QU) {
+        const unsigned kb = keep >> (4 * kg);
+        *reinterpret_cast<uint4*>(QU + sl * kBigSlice + off) =
+            make_uint4(kb & 1u ? w[sl][0] : 0u, kb & 2u ? w[sl][1] : 0u, kb & 4u ? w[sl][2] : 0u,
+                       kb & 8u ? w[sl][3] : 0u);
+      }
+    }
+  }
+  if (ct < 128) reinterpret_cast<int*>(unit + 2 * kBigTile)[ct] = ecol[ct];
+}
+
+struct Smem2 {
+  uint8_t stage[kStages][kStage2Bytes];
+  uint64_t full[kStages], empty[kStages], accfull[2], accempty[2];
+  int accmeta[2][128];
+  uint32_t tmem;
+  int abort;
+};
+
+struct Split2Args {
+  SplitGeom g;
+  const uint8_t* planes;
+  const uint8_t* qu;
+  int cpt_stride, qu_slots;
+  const uint8_t* small;
+  const int* e_small;
+  double* part;
+  int* status;
+};
+
+__device__ __forceinline__ bool wait_bar2(Smem2& sm, void* bar, uint32_t parity, int* status) {
+  long long it = 0;
+  while (!mbar_try(bar, parity)) {
+    if (++it > kSpinLimit || *(volatile int*)&sm.abort) {
+      if (it > kSpinLimit) { atomicOr(status, kStatusTimeout); sm.abort = 1; }
+      return false;
+    }
+    if (it > 64) __nanosleep(64);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  Smem2& sm = *reinterpret_cast<Smem2*>(smem_raw);
+  const SplitGeom& g = a.g;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int M = g.M, n = g.n, CT = g.CT;
+  const long long u0 = unit_begin(g, blockIdx.x), u1 = unit_begin(g, blockIdx.x + 1);
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], 1); mbar_init(&sm.empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 2); mbar_init(&sm.accempty[b], kEpi2 * 32); }
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kEpi2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+
+  if (warp == kEpi2 + 1) {
+    // -------------------------------------------------------- producer --
+    if (lane == 0) {
+      long long issued = u0;
+      for (long long u = u0; u < u1; ++u) {
+        const int it = (int)(u - u0);
+        const int s = it % kStages;
+        if (!wait_bar2(sm, &sm.empty[s], ((it / kStages) & 1) ^ 1, a.status)) break;
+        const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
+        const int ctile = tile / g.parts, part = tile % g.parts;
+        const int c0 = ctile * CT;
+        const int kap0 = kc * kKC;
+        const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
+        const int slot = cls == 2 ? qu_slot(kc, c0, M, g.band_w) : 0;
+        const bool with_qu = cls == 2 && slot >= 0 && slot < a.qu_slots;
+        uint8_t* st = sm.stage[s];
+        mbar_arrive_expect_tx(&sm.full[s], kUnitBytes + kSmallBytes + (with_qu ? kBigTile : 0));
+        bulk_g2s(st, a.planes + ((size_t)ctile * a.cpt_stride + kc) * kUnitBytes, kUnitBytes, &sm.full[s]);
+        bulk_g2s(st + kUnitBytes + kBigTile, a.small + ((size_t)kc * g.parts + part) * kSmallBytes, kSmallBytes,
+                 &sm.full[s]);
+        if (with_qu)
+          bulk_g2s(st + kUnitBytes, a.qu + ((size_t)ctile * a.qu_slots + slot) * kBigTile, kBigTile, &sm.full[s]);
+        issued = u + 1;
+      }
+      // before the CTA can exit, the copies of the last units must have landed
+      // (after an abort the MMA warp may not have waited for them)
+      for (long long u = issued - 1; u >= u0 && u >= issued - kStages; --u) {
+        const int it = (int)(u - u0);
+        long long spins = 0;
+        while (!mbar_try(&sm.full[it % kStages], (it / kStages) & 1) && ++spins < kSpinLimit) __nanosleep(64);
+      }
+    }
+    __syncwarp();
+  } else if (warp == kEpi2) {
+    // --------------------------------------------------------- MMA warp --
+    if (lane == 0) {
+      long long last = -1;
+      for (long long u = u0; u < u1; ++u) {
+        const int it = (int)(u - u0);
+        const int s = it % kStages, b = it & 1;
+        if (!wait_bar2(sm, &sm.full[s], (it / kStages) & 1, a.status)) break;
+        if (!wait_bar2(sm, &sm.accempty[b], (it >> 1) & 1, a.status)) break;
+        tc_fence_after();
+        uint8_t* st = sm.stage[s];
+        const int* ecol = reinterpret_cast<const int*>(st + 2 * kBigTile);
+        for (int c = 0; c < CT; ++c) sm.accmeta[b][c] = ecol[c];
+        mbar_arrive(&sm.accfull[b]);  // releases accmeta; the commit below is the second arrival
+        const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
+        const int c0 = (tile / g.parts) * CT;
+        const int kap0 = kc * kKC;
+        int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
+        if (cls == 2) {
+          const int slot = qu_slot(kc, c0, M, g.band_w);
+          if (slot < 0 || slot >= a.qu_slots) cls = 0;  // reported by the encoder (status word)
+        }
+        const uint32_t aPL = smem_u32(st), aQ = smem_u32(st + kBigTile);
+        const uint32_t aQU = cls == 1 ? aQ : smem_u32(st + kUnitBytes);
+        const uint32_t bS = smem_u32(st + kUnitBytes + kBigTile);
+        const uint32_t dl = tmem + b * kAccCols, dg = dl + kGroupCols;
+        for (int i = 0; i < kSlices; ++i) {
+          const uint32_t idesc = umma_idesc_bf16(kNS * min(kSlices, kLevels - i));
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t ka = (uint32_t)(i * kBigSlice + kk * 2 * 2048);
+            const uint64_t dPL = umma_desc(aPL + ka, 2048, 128);
+            const uint64_t dQ = umma_desc(aQ + ka, 2048, 128);
+            const uint64_t dQU = umma_desc(aQU + ka, 2048, 128);
+            const uint32_t kb = (uint32_t)(kk * 2 * 1024);
+            const uint64_t dA1 = umma_desc(bS + 0 * kSmallVar + kb, 1024, 128);
+            const uint64_t dNl = umma_desc(bS + 1 * kSmallVar + kb, 1024, 128);
+            const uint64_t dNg = umma_desc(bS + 2 * kSmallVar + kb, 1024, 128);
+            umma_bf16(dl + i * kNS, dPL, dA1, idesc, 1);
+            umma_bf16(dg + i * kNS, dPL, dA1, idesc, 1);
+            umma_bf16(dg + i * kNS, dQ, dA1, idesc, 1);
+            if (cls != 0) {
+              umma_bf16(dl + i * kNS, dQU, dNl, idesc, 1);
+              umma_bf16(dg + i * kNS, dQU, dNg, idesc, 1);
+            }
+          }
+        }
+        umma_commit(&sm.accfull[b]);
+        umma_commit(&sm.empty[s]);
+        last = u;
+      }
+      if (last >= 0) {
+        const int it = (int)(last - u0);
+        long long spins = 0;
+        while (!mbar_try(&sm.empty[it % kStages], (it / kStages) & 1) && ++spins < kSpinLimit) __nanosleep(64);
+      }
+    }
+    __syncwarp();
+  } else {
+    // --------------------------------------------------------- epilogue --
+    // warp = 4 grp + quadrant: group grp drains accumulator group grp
+    // (0: I^<, 1: I^>) for the 32 TMEM lanes (= output rows) of its quadrant.
+    const int grp = warp >> 2, quad = warp & 3;
+    const int j = quad * 32 + lane;
+    const int cl = j / M, bb = j - cl * M;
+    const bool live_row = cl < CT;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
+    for (int bsel = 0; bsel < 2; ++bsel)
+      for (int col = 0; col < kGroupCols; col += 16) tmem_zero16(lane_addr + bsel * kAccCols + grp * kGroupCols + col);
+    tmem_wait_st();
+    tc_fence_before();
+    mbar_arrive(&sm.accempty[0]);
+    mbar_arrive(&sm.accempty[1]);
+    float run[kNS][2];
+#pragma unroll
+    for (int q = 0; q < kNS; ++q) { run[q][0] = 0.f; run[q][1] = 0.f; }
+    int local_seg = 0;
+    for (long long u = u0; u < u1; ++u) {
+      const int it = (int)(u - u0);
+      const int b = it & 1;
+      if (!__all_sync(0xffffffffu, wait_bar2(sm, &sm.accfull[b], (it >> 1) & 1, a.status))) break;
+      tc_fence_after();
+      const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
+      const int part = tile % g.parts;
+      const int ec = live_row ? sm.accmeta[b][cl] : 0;
+      const float sc = pow2f(scale_from_field(ec) + a.e_small[kc * g.parts + part] - 14);
+      const uint32_t buf = lane_addr + b * kAccCols + grp * kGroupCols;
+#pragma unroll
+      for (int q4 = 0; q4 < kNS; q4 += 4) {
+        float v[kLevels][4];
+        tmem_ld4xL(buf + q4, kNS, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float lv[kLevels] = {v[0][q], v[1][q], v[2][q], v[3][q], v[4][q]};
+          float hi, lo;
+          combine_levels(lv, hi, lo);
+          float& rh = run[q4 + q][0];
+          float& rl = run[q4 + q][1];
+          df_add(rh, rl, hi * sc);
+          rl += lo * sc;
+        }
+      }
+      for (int col = 0; col < kGroupCols; col += 16) tmem_zero16(buf + col);
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(&sm.accempty[b]);
+      if ((u + 1 == u1) || ((u + 1) / g.cpt != tile)) {
+        const int c = (tile / g.parts) * CT + cl;
+        if (live_row && c <= n) {
+          double2* out = reinterpret_cast<double2*>(a.part) + ((size_t)blockIdx.x * g.S + local_seg) * (2 * 128 * kNA);
+#pragma unroll
+          for (int al = 0; al < kNA; ++al) {
+            const double re = (double)run[2 * al][0] + (double)run[2 * al][1];
+            const double im = (double)run[2 * al + 1][0] + (double)run[2 * al + 1][1];
+            out[((size_t)grp * CT + cl) * kNA * M + al * M + bb] = make_double2(re, im);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kNS; ++q) { run[q][0] = 0.f; run[q][1] = 0.f; }
+        ++local_seg;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kEpi2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- reduce -
 // I_out[s][c][a][b] = sum of the partials of every CTA that covered the
 // tile of (c, a), in CTA order, plus the band of term 2 in FP64 with the
@@ -551,8 +883,62 @@ cudaError_t split_prepare() {
   const unsigned long long bit = 1ull << (dev & 63);
   if (done_mask.load() & bit) return cudaSuccess;
   e = cudaFuncSetAttribute(split_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(split_main2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem2));
   if (e == cudaSuccess) done_mask.fetch_or(bit);
   return e;
+}
+
+// Digit-plane buffers of the planes path for slices up to n_max - 1:
+// [column tile][chunk] units of kUnitBytes, then the QU slots.
+static int qu_slots_of(const SplitGeomHost& h) { return (h.CT * h.M + 15) / 16 + 2; }
+
+size_t split_planes_bytes(int M, int n_max) {
+  SplitGeomHost h;
+  if (!split_geometry(M, n_max - 1, &h)) return 0;
+  const size_t col_tiles = (size_t)(n_max + h.CT - 1) / h.CT;
+  return col_tiles * h.cpt * kUnitBytes + col_tiles * qu_slots_of(h) * kBigTile + 256;
+}
+
+cudaError_t launch_history_split2(const SplitLaunch& l, void* planes, size_t planes_bytes, cudaStream_t s,
+                                  int* launches) {
+  SplitGeomHost h;
+  *launches = 0;
+  if (!split_geometry(l.M, l.n, &h)) return cudaErrorInvalidValue;
+  SplitGeom g{h.M, h.M * h.M, h.n, h.CT, h.parts, h.cpt, h.tiles, h.U, h.G, h.S, l.w.band_w};
+  uint8_t* ws = reinterpret_cast<uint8_t*>(l.work);
+  uint8_t* small = ws;
+  int* e_small = reinterpret_cast<int*>(small + (size_t)h.cpt * h.parts * kSmallBytes);
+  size_t off = ((size_t)h.cpt * h.parts * kSmallBytes + (size_t)h.cpt * h.parts * sizeof(int) + 255) / 256 * 256;
+  double* part = reinterpret_cast<double*>(ws + off);
+  if (off + (size_t)h.G * h.S * 2 * 128 * kNA * 16 > l.work_bytes) return cudaErrorInvalidValue;
+  const int col_tiles = (h.n + 1 + h.CT - 1) / h.CT;
+  const int qs = qu_slots_of(h);
+  const size_t unit_bytes = (size_t)col_tiles * h.cpt * kUnitBytes;
+  if (unit_bytes + (size_t)col_tiles * qs * kBigTile > planes_bytes) return cudaErrorInvalidValue;
+  uint8_t* pl = reinterpret_cast<uint8_t*>(planes);
+  uint8_t* qu = pl + unit_bytes;
+
+  cudaError_t e = split_prepare();
+  if (e != cudaSuccess) return e;
+  split_prep<<<dim3(h.cpt, h.parts), 256, 0, s>>>(l.M, l.n, h.parts, l.Sl, l.Sg, l.w, small, e_small);
+  ++*launches;
+  EncodeArgs ea{g, l.L, l.R, pl, qu, h.cpt, qs, l.status};
+  split_encode<<<(unsigned)((size_t)col_tiles * h.cpt), 256, 0, s>>>(ea);
+  ++*launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  Split2Args args{g, pl, qu, h.cpt, qs, small, e_small, part, l.status};
+  if (l.ev_begin) cudaEventRecord(l.ev_begin, s);
+  split_main2<<<h.G, kThreads2, sizeof(Smem2), s>>>(args);
+  if (l.ev_end) cudaEventRecord(l.ev_end, s);
+  ++*launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long total = 2ll * (l.n + 1) * l.M * l.M;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  split_reduce<<<(unsigned)blocks, 256, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
+  ++*launches;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* launches) {

@@ -21,6 +21,7 @@ __host__ __device__ inline int64_t tri(int64_t r, int64_t c) { return r * (r + 1
 // Device status bits (reported by kbe_sync_status).
 constexpr int kStatusNumeric = 1;
 constexpr int kStatusTimeout = 2;
+constexpr int kStatusInternal = 4;  // a kernel found an inconsistent launch geometry
 
 // Read-only view of the composite weights on the device:
 //   w_{c,m} = band[c * band_w + (c - m)]  if c - m < band_w,
@@ -89,6 +90,9 @@ struct kbe_ctx {
   double* d_part = nullptr;   // split partials [kMaxSplit][2][n_max][M][M] complex
   void* d_split = nullptr;    // split-precision workspace (digit planes of the small operands, partials)
   size_t split_bytes = 0;
+  void* d_planes = nullptr;   // digit planes of the history (split path), allocated by the first split slice
+  size_t planes_bytes = 0;
+  bool planes_failed = false; // allocation failed once: the in-kernel conversion path is used
   int* d_status = nullptr;
   size_t part_bytes = 0;
   // reverse-mode workspace, allocated by the first adjoint call that needs it
@@ -147,6 +151,11 @@ bool split_geometry(int M, int n, SplitGeomHost* h);
 size_t split_workspace_bytes(int M, int n_max);
 cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* launches);
 cudaError_t split_prepare();  // one-time kernel attributes of the current device
+// Planes path: digit planes of the history encoded by a separate kernel and
+// streamed into the contraction (single systems; needs split_planes_bytes).
+size_t split_planes_bytes(int M, int n_max);
+cudaError_t launch_history_split2(const SplitLaunch& l, void* planes, size_t planes_bytes, cudaStream_t s,
+                                  int* launches);
 
 struct StepArgs {
   int M, n, K;

@@ -216,6 +216,31 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
   two_sum(s, lo, hi, lo);
 }
 
+// v0 + v1 2^-8 + v2 2^-16 + v3 2^-24 + v4 2^-32 for exact integer levels
+// |v_d| < 2^24, as hi + lo: the small levels are folded in FP32 (each
+// rounding is below 2^-32 of the level-0 scale), the last step is exact.
+__device__ __forceinline__ void combine_levels(const float v[kLevels], float& hi, float& lo) {
+  float t = fmaf(v[4], 0.00390625f, v[3]);
+  t = fmaf(t, 0.00390625f, v[2]);
+  t = fmaf(t, 0.00390625f, v[1]);
+  two_sum(v[0], t * 0.00390625f, hi, lo);
+}
+
+// Bulk copy global -> shared memory of this CTA, completing on an mbarrier
+// (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, void* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+// Arrive on an mbarrier and add `bytes` to its expected transaction count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(void* mbar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+
 // 2^k as a float for k in [-126, 127] (k clamped).
 __device__ __forceinline__ float pow2f(int k) {
   k = k < -126 ? -126 : (k > 127 ? 127 : k);
