@@ -179,7 +179,11 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
  *              kap+1 points t_{n-kap..n}, kap = min(k_n, n-c) (diagonal:
  *              min(k_n, n)), and R(n,c) = G^>(n,c) - L(n,c), R(n,n) = -i*1.
  * Row n of L, R and slot n of F_ring are written; S_less, S_great, I_work
- * hold row n's last self-energy and history slice.  1 <= P <= 16. */
+ * hold row n's last self-energy and history slice.  1 <= P <= 16.
+ * With KBE_SPLIT_BF16 the context keeps the tensor-core digit planes of the
+ * history between steps on the same L and R: rows below the row of the
+ * previous step are not encoded again.  A caller that rewrites those rows
+ * between steps (a restart into the same buffers) calls kbe_reset_cache. */
 kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* S_less,
                     void* S_great, void* I_work, void* F_ring, void* stream);
 
@@ -248,6 +252,10 @@ kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, cons
 kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* F_rows, int j0, int n_rows,
                             void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0,
                             void* stream);
+
+/* Forget per-history state kept between steps (the split path's digit
+ * planes); the next step encodes every row again.  No GPU work. */
+kbe_status kbe_reset_cache(kbe_ctx* ctx);
 
 /* Synchronize stream and return the device status word accumulated since
  * the last call (then cleared): KBE_OK, KBE_ENUMERIC or KBE_ETIMEOUT. */

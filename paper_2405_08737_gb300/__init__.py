@@ -74,6 +74,7 @@ def lib():
                                          ctypes.POINTER(d)]
         L.kbe_batch_sync_status.argtypes = [vp, vp]
         L.kbe_sync_status.argtypes = [vp, vp]
+        L.kbe_reset_cache.argtypes = [vp]
         L.kbe_set_profiling.argtypes = [vp, i]
         L.kbe_read_profiling.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d)]
         _lib = L
@@ -262,6 +263,10 @@ class Context:
         if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
             raise TypeError("expected a contiguous CUDA float64 tensor")
         return ctypes.c_void_p(x.data_ptr())
+
+    def reset_cache(self):
+        """Forget the split path's digit planes kept between steps."""
+        self._check(lib().kbe_reset_cache(self._h))
 
     def set_profiling(self, enable):
         """Record CUDA events around each contraction kernel (clears old records)."""

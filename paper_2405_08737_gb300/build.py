@@ -69,7 +69,8 @@ def build(force=False, verbose=False):
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
+        # -z defs: an unresolved symbol fails the link instead of the first load
+        run([nvcc] + ARCH + ["-shared", "-Xlinker", "-z,defs", "-o", tmp] + objs)
         os.replace(tmp, LIB)
     return LIB
 

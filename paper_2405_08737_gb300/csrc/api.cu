@@ -41,7 +41,9 @@ void release(kbe_ctx* ctx) {
   cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split); cudaFree(ctx->d_adj);
   cudaFree(ctx->d_planes);
   ctx->d_planes = nullptr;
-  ctx->planes_bytes = 0;
+  ctx->planes_layout = SplitPlanes{};
+  ctx->planes_L = ctx->planes_R = nullptr;
+  ctx->planes_rows = 0;
   ctx->d_split = nullptr;
   ctx->d_adj = nullptr;
   ctx->adj_bytes = 0;
@@ -77,25 +79,45 @@ bool next_events(kbe_ctx* ctx, cudaEvent_t* b, cudaEvent_t* e) {
   return true;
 }
 
+// History slice of row n.  `stepping` is set by the KBE step: rows below n
+// of L, R are then final, so digit planes encoded for them by earlier slices
+// of the same arrays are reused (the split path re-encodes only units that
+// involve rows >= the cached row count).
 kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void* R, const void* Sl,
-                   const void* Sg, void* I_out, cudaStream_t s, int* launches) {
+                   const void* Sg, void* I_out, cudaStream_t s, int* launches, bool stepping = false) {
   if (precision == KBE_SPLIT_BF16) {
     if (!ctx->d_split) return fail(ctx, KBE_EINVAL, "split precision needs 1 <= norb <= 32");
     SplitLaunch l{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
                   weights_view(ctx), (double*)I_out, ctx->d_split, ctx->split_bytes, ctx->d_status};
     if (!next_events(ctx, &l.ev_begin, &l.ev_end)) return fail(ctx, KBE_ECUDA, "profiling: cudaEventCreate");
     if (!ctx->d_planes && !ctx->planes_failed) {
-      const size_t bytes = split_planes_bytes(ctx->M, ctx->n_max);
-      if (bytes == 0 || cudaMalloc(&ctx->d_planes, bytes) != cudaSuccess) {
+      SplitPlanes lay;
+      if (!split_planes_layout(ctx->M, ctx->n_max, &lay) || cudaMalloc(&ctx->d_planes, lay.bytes) != cudaSuccess) {
         cudaGetLastError();
         ctx->d_planes = nullptr;
         ctx->planes_failed = true;  // not enough memory: convert inside the contraction kernel instead
       } else {
-        ctx->planes_bytes = bytes;
+        ctx->planes_layout = lay;
+        ctx->planes_rows = 0;
+        ctx->planes_L = ctx->planes_R = nullptr;
       }
     }
-    cudaError_t e = ctx->d_planes ? launch_history_split2(l, ctx->d_planes, ctx->planes_bytes, s, launches)
-                                  : launch_history_split(l, s, launches);
+    cudaError_t e;
+    if (ctx->d_planes) {
+      int r0 = 0;
+      if (stepping && ctx->planes_L == L && ctx->planes_R == R && ctx->planes_rows <= n) r0 = ctx->planes_rows;
+      e = launch_history_split2(l, ctx->planes_layout, ctx->d_planes, r0, s, launches);
+      if (e == cudaSuccess) {  // rows below n are final during a step; otherwise nothing is kept
+        ctx->planes_L = stepping ? L : nullptr;
+        ctx->planes_R = stepping ? R : nullptr;
+        ctx->planes_rows = stepping ? n : 0;
+      } else {
+        ctx->planes_L = ctx->planes_R = nullptr;
+        ctx->planes_rows = 0;
+      }
+    } else {
+      e = launch_history_split(l, s, launches);
+    }
     return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "split history slice launch");
   }
   if (precision != KBE_FP64) return fail(ctx, KBE_EINVAL, "unknown precision");
@@ -164,7 +186,7 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
                      (double*)Sg, ctx->d_status, s);
     *count_out = ++count;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: self-energy");
-    kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl);
+    kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl, true);
     *count_out = (count += nl);
     if (st != KBE_OK) return st;
     if ((e = launch_fock(a, s)) != cudaSuccess || (e = launch_rhs_corrector(a, s)) != cudaSuccess) {
@@ -319,6 +341,8 @@ kbe_status kbe_set_grid(kbe_ctx* ctx, const double* t, const int* order, int n_t
     return cuda_fail(ctx, e, "kbe_set_grid: upload");
   ctx->grid = std::move(g);
   ctx->grid_set = true;
+  ctx->planes_L = ctx->planes_R = nullptr;  // cached digit planes depend on the band of the weights
+  ctx->planes_rows = 0;
   return KBE_OK;
 }
 
@@ -610,6 +634,14 @@ kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* 
   if (e == cudaSuccess) e = cudaMemcpyAsync(Rrow, fin + row_bytes / 8, row_bytes, cudaMemcpyDeviceToDevice, s);
   if ((st = check("kbe_step_adjoint: restore")) != KBE_OK) return st;
   ctx->last_launches = count;
+  return KBE_OK;
+}
+
+kbe_status kbe_reset_cache(kbe_ctx* ctx) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  ctx->planes_L = ctx->planes_R = nullptr;
+  ctx->planes_rows = 0;
   return KBE_OK;
 }
 

@@ -484,6 +484,7 @@ struct EncodeArgs {
   uint8_t* planes;     // [column tile][cpt_stride][kUnitBytes]
   uint8_t* qu;         // [column tile][qu_slots][kBigTile]
   int cpt_stride, qu_slots;
+  int ct_base, kc_base, kc_count;  // units: ct_base + i / kc_count, kc_base + i % kc_count
   int* status;
 };
 
@@ -492,7 +493,8 @@ struct EncodeArgs {
 __global__ void __launch_bounds__(256) split_encode(EncodeArgs a) {
   const SplitGeom& g = a.g;
   const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
-  const int ctile = (int)(blockIdx.x / (unsigned)g.cpt), kc = (int)(blockIdx.x % (unsigned)g.cpt);
+  const int ctile = a.ct_base + (int)(blockIdx.x / (unsigned)a.kc_count);
+  const int kc = a.kc_base + (int)(blockIdx.x % (unsigned)a.kc_count);
   __shared__ int ecol[128];
   const int ct = threadIdx.x, arr = ct >> 7, jrow = ct & 127;
   const bool row_live = jrow < CT * M;
@@ -890,18 +892,23 @@ cudaError_t split_prepare() {
 }
 
 // Digit-plane buffers of the planes path for slices up to n_max - 1:
-// [column tile][chunk] units of kUnitBytes, then the QU slots.
+// [column tile][chunk] units of kUnitBytes at a fixed chunk stride (the
+// chunk count of slice n_max - 1), then the QU slots.  Units of earlier
+// slices stay valid at their places as the history grows.
 static int qu_slots_of(const SplitGeomHost& h) { return (h.CT * h.M + 15) / 16 + 2; }
 
-size_t split_planes_bytes(int M, int n_max) {
+bool split_planes_layout(int M, int n_max, SplitPlanes* p) {
   SplitGeomHost h;
-  if (!split_geometry(M, n_max - 1, &h)) return 0;
-  const size_t col_tiles = (size_t)(n_max + h.CT - 1) / h.CT;
-  return col_tiles * h.cpt * kUnitBytes + col_tiles * qu_slots_of(h) * kBigTile + 256;
+  if (!split_geometry(M, n_max - 1, &h)) return false;
+  p->cpt_stride = h.cpt;
+  p->col_tiles = (n_max + h.CT - 1) / h.CT;
+  p->qu_slots = qu_slots_of(h);
+  p->bytes = (size_t)p->col_tiles * h.cpt * kUnitBytes + (size_t)p->col_tiles * p->qu_slots * kBigTile + 256;
+  return true;
 }
 
-cudaError_t launch_history_split2(const SplitLaunch& l, void* planes, size_t planes_bytes, cudaStream_t s,
-                                  int* launches) {
+cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& pl_layout, void* planes, int r0,
+                                  cudaStream_t s, int* launches) {
   SplitGeomHost h;
   *launches = 0;
   if (!split_geometry(l.M, l.n, &h)) return cudaErrorInvalidValue;
@@ -914,20 +921,33 @@ cudaError_t launch_history_split2(const SplitLaunch& l, void* planes, size_t pla
   if (off + (size_t)h.G * h.S * 2 * 128 * kNA * 16 > l.work_bytes) return cudaErrorInvalidValue;
   const int col_tiles = (h.n + 1 + h.CT - 1) / h.CT;
   const int qs = qu_slots_of(h);
-  const size_t unit_bytes = (size_t)col_tiles * h.cpt * kUnitBytes;
-  if (unit_bytes + (size_t)col_tiles * qs * kBigTile > planes_bytes) return cudaErrorInvalidValue;
+  if (col_tiles > pl_layout.col_tiles || h.cpt > pl_layout.cpt_stride || qs != pl_layout.qu_slots)
+    return cudaErrorInvalidValue;
   uint8_t* pl = reinterpret_cast<uint8_t*>(planes);
-  uint8_t* qu = pl + unit_bytes;
+  uint8_t* qu = pl + (size_t)pl_layout.col_tiles * pl_layout.cpt_stride * kUnitBytes;
 
   cudaError_t e = split_prepare();
   if (e != cudaSuccess) return e;
   split_prep<<<dim3(h.cpt, h.parts), 256, 0, s>>>(l.M, l.n, h.parts, l.Sl, l.Sg, l.w, small, e_small);
   ++*launches;
-  EncodeArgs ea{g, l.L, l.R, pl, qu, h.cpt, qs, l.status};
-  split_encode<<<(unsigned)((size_t)col_tiles * h.cpt), 256, 0, s>>>(ea);
-  ++*launches;
+  // units whose data involve rows >= r0: every chunk of the column tiles
+  // from the one holding column r0, and the chunks from the one holding
+  // row r0 onwards in the tiles before it
+  if (r0 < 0) r0 = 0;
+  const int ct_lo = r0 > h.n ? col_tiles : r0 / h.CT;
+  const int kc_lo = (int)(((long long)r0 * h.M) / kKC);
+  if (ct_lo < col_tiles) {
+    EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, ct_lo, 0, h.cpt, l.status};
+    split_encode<<<(unsigned)((size_t)(col_tiles - ct_lo) * h.cpt), 256, 0, s>>>(ea);
+    ++*launches;
+  }
+  if (ct_lo > 0 && kc_lo < h.cpt) {
+    EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, 0, kc_lo, h.cpt - kc_lo, l.status};
+    split_encode<<<(unsigned)((size_t)ct_lo * (h.cpt - kc_lo)), 256, 0, s>>>(ea);
+    ++*launches;
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  Split2Args args{g, pl, qu, h.cpt, qs, small, e_small, part, l.status};
+  Split2Args args{g, pl, qu, pl_layout.cpt_stride, qs, small, e_small, part, l.status};
   if (l.ev_begin) cudaEventRecord(l.ev_begin, s);
   split_main2<<<h.G, kThreads2, sizeof(Smem2), s>>>(args);
   if (l.ev_end) cudaEventRecord(l.ev_end, s);

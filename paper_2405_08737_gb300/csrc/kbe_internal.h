@@ -54,6 +54,12 @@ struct HostGrid {
 kbe_status local_weights(const double* tau, int k, double lo, double hi, double* w, std::string* err);
 kbe_status build_grid(const double* t, const int* order, int n_t, HostGrid* g, std::string* err);
 
+// Layout of the digit-plane buffer of the split path (history_split.cu).
+struct SplitPlanes {
+  int cpt_stride = 0, col_tiles = 0, qu_slots = 0;
+  size_t bytes = 0;
+};
+
 // Record a context-free error message (returned by kbe_last_error(NULL)).
 void set_global_error(const char* msg);
 
@@ -91,8 +97,13 @@ struct kbe_ctx {
   void* d_split = nullptr;    // split-precision workspace (digit planes of the small operands, partials)
   size_t split_bytes = 0;
   void* d_planes = nullptr;   // digit planes of the history (split path), allocated by the first split slice
-  size_t planes_bytes = 0;
+  kbe::SplitPlanes planes_layout;
   bool planes_failed = false; // allocation failed once: the in-kernel conversion path is used
+  // Cache of the planes across KBE steps: rows < planes_rows of the arrays
+  // planes_L / planes_R are encoded with their final values.
+  const void* planes_L = nullptr;
+  const void* planes_R = nullptr;
+  int planes_rows = 0;
   int* d_status = nullptr;
   size_t part_bytes = 0;
   // reverse-mode workspace, allocated by the first adjoint call that needs it
@@ -153,9 +164,10 @@ cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* laun
 cudaError_t split_prepare();  // one-time kernel attributes of the current device
 // Planes path: digit planes of the history encoded by a separate kernel and
 // streamed into the contraction (single systems; needs split_planes_bytes).
-size_t split_planes_bytes(int M, int n_max);
-cudaError_t launch_history_split2(const SplitLaunch& l, void* planes, size_t planes_bytes, cudaStream_t s,
-                                  int* launches);
+bool split_planes_layout(int M, int n_max, SplitPlanes* p);
+// Encodes the units that involve rows >= r0 (r0 = 0: all), then contracts.
+cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& layout, void* planes, int r0,
+                                  cudaStream_t s, int* launches);
 
 struct StepArgs {
   int M, n, K;

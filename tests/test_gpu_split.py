@@ -179,3 +179,32 @@ def test_split_stepper_tracks_oracle(kbe):
         print(name, "split stepper max rel err over the run", err)
         assert err < 1e-8, (name, err)
         ctx.close()
+
+
+def test_split_plane_cache_is_exact(kbe):
+    """KBE steps that reuse the digit planes of earlier rows give bitwise the
+    rows of steps that encode every row again (kbe_reset_cache before each
+    step), including a repeated step of the same row."""
+    import torch
+    name, n_t = "chain_m8_n1024", 40
+    cfg = W.CONFIGS[name]
+    t, order = W.grid(cfg["n_t"], cfg["dt0"], cfg["sig"], 6)
+    t, order = t[:n_t], order[:n_t]
+    h, U, v, pulse = W.build_model(cfg, 6)
+    rho0 = W.half_filled_rho(h)
+    runs = []
+    for fresh in (False, True):
+        ctx = kbe.Context(cfg["M"], n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        run = kbe.Run(ctx)
+        run.init_uncorrelated(rho0)
+        for n in list(range(1, n_t)) + [n_t - 1]:
+            if fresh:
+                ctx.reset_cache()
+            run.step(n, P=2, precision="split")
+        ctx.sync_status()
+        runs.append(run)
+    assert torch.equal(runs[0].L, runs[1].L) and torch.equal(runs[0].R, runs[1].R)
+    for r in runs:
+        r.ctx.close()
