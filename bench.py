@@ -58,6 +58,7 @@ def parse():
                     help="truncate the grid to this many points (smaller profiling case)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batching form")
     ap.add_argument("--no-window", action="store_true", help="skip the differentiation form")
+    ap.add_argument("--no-selfenergy", action="store_true", help="skip the whole-triangle self-energy timing")
     return ap.parse_args()
 
 
@@ -516,7 +517,7 @@ def main():
         line["error_vs_oracle"] = dict(errs["fp64"], where="new row n and last history slice of the timed KBE "
                                                            "step, max-norm relative")
         line["precision_form"]["error_vs_oracle"] = errs["split"]
-    if rank == 0:
+    if rank == 0 and not args.no_selfenergy:
         line["selfenergy"] = sigma_bench(kbe, ctx, run, n + 1, stream)
     if rank == 0 and not args.no_window:
         line["differentiation_form"] = window_bench(kbe, args.seed, stream)

@@ -12,13 +12,16 @@
 // triangles through G(m,c) = -G(c,m)^+) and term 2 with
 // G^A(m,c) = R(c,m)^+ = -Q(m,c) for m <= c, where the plane Q(m,c) = R(m,c)
 // below and on the diagonal and -R(c,m)^+ above it (R(c,c) = -i*1 makes both
-// readings agree on the diagonal).  With A1[m] = w_{n,m}(S^> - S^<)[m] and
-// NB^s[m] = -wbar_m S^s[m] (settled weights):
-//   I^<[c] = sum_m A1[m] PL(m,c)                      + sum_{m<=c} NB^<[m] Q(m,c)
-//   I^>[c] = sum_m A1[m] PL(m,c) + sum_m A1[m] Q(m,c) + sum_{m<=c} NB^>[m] Q(m,c)
+// readings agree on the diagonal).  With A1[m] = w_{n,m}(S^> - S^<)[m],
+// NB^<[m] = -wbar_m S^<[m] and NBD[m] = -wbar_m (S^> - S^<)[m] (settled
+// weights), the tensor cores form
+//   I^<[c]          = sum_m A1[m] PL(m,c) + sum_{m<=c} NB^<[m] Q(m,c)
+//   D[c] = (I^> - I^<)[c] = sum_m A1[m] Q(m,c) + sum_{m<=c} NBD[m] Q(m,c)
+// (G^> - G^< = G^R gives the difference without a second PL product), and
+// the reduction adds I^> = I^< + D.
 // For one output tile (128 rows j = (c,b)) and one chunk of 16 complex K
 // entries (m,x), the big operands are the plane tiles PL, Q and the masked
-// QU = Q [m <= c]; the small operands A1, NB^<, NB^> (prepared once per
+// QU = Q [m <= c]; the small operands A1, NB^<, NBD (prepared once per
 // slice) are the "B" matrices of the MMA.  Term 2 for the band m > c - K,
 // where w_{c,m} still differs from wbar_m, is left out of QU and added in
 // FP64 with the exact weights by the reduction kernel.
@@ -83,7 +86,7 @@ struct SplitArgs {
 };
 
 // ---------------------------------------------------------------- prep ---
-// Small operands of chunk kc, part p: A1, NB^<, NB^> as bf16 digit planes in
+// Small operands of chunk kc, part p: A1, NB^<, NBD as bf16 digit planes in
 // the shared-memory layout [variant][kgroup 4][slice 4][colgroup 2][8][8],
 // entries B[(a, q_out)][(kappa, q_in)] of the real form of P z:
 //   (re,re) = P.re, (re,im) = -P.im, (im,re) = P.im, (im,im) = P.re.
@@ -113,10 +116,12 @@ __global__ void __launch_bounds__(256) split_prep(int M, int n, int parts, const
         if (v == 0) {
           const double wn = w.at(n, m);
           vr[r] = wn * (g.x - l.x); vi[r] = wn * (g.y - l.y);
+        } else if (v == 1) {
+          const double wb = -w.wbar[m];
+          vr[r] = wb * l.x; vi[r] = wb * l.y;
         } else {
           const double wb = -w.wbar[m];
-          const double2 s = v == 1 ? l : g;
-          vr[r] = wb * s.x; vi[r] = wb * s.y;
+          vr[r] = wb * (g.x - l.x); vi[r] = wb * (g.y - l.y);
         }
       }
       my_ef = max(my_ef, max(exp_field(vr[r]), exp_field(vi[r])));
@@ -348,7 +353,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_main(SplitArgs a) {
             const uint64_t dNl = umma_desc(bS + 1 * kSmallVar + kb, 1024, 128);
             const uint64_t dNg = umma_desc(bS + 2 * kSmallVar + kb, 1024, 128);
             umma_bf16(dl + i * kNS, dPL, dA1, idesc, 1);
-            umma_bf16(dg + i * kNS, dPL, dA1, idesc, 1);
             umma_bf16(dg + i * kNS, dQ, dA1, idesc, 1);
             if (cls != 0) {
               umma_bf16(dl + i * kNS, dQU, dNl, idesc, 1);
@@ -465,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_main(SplitArgs a) {
 
 constexpr int kUnitBytes = 2 * kBigTile + 1024;                 // PL | Q | column exponents (padded)
 constexpr int kStage2Bytes = kUnitBytes + kBigTile + kSmallBytes;  // + QU | small operand
-constexpr int kEpi2 = 8;
+constexpr int kEpi2 = 16;                                       // 4 lane quadrants x 2 groups x 2 column halves
 constexpr int kThreads2 = (kEpi2 + 2) * 32;                     // + MMA warp + producer warp
 
 // Slot of a straddling chunk kc in the QU buffer of the tile starting at
@@ -571,7 +575,6 @@ __global__ void __launch_bounds__(256) split_encode(EncodeArgs a) {
 struct Smem2 {
   uint8_t stage[kStages][kStage2Bytes];
   uint64_t full[kStages], empty[kStages], accfull[2], accempty[2];
-  int accmeta[2][128];
   uint32_t tmem;
   int abort;
 };
@@ -609,7 +612,7 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], 1); mbar_init(&sm.empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 2); mbar_init(&sm.accempty[b], kEpi2 * 32); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 1); mbar_init(&sm.accempty[b], kEpi2 * 32); }
     sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -660,7 +663,11 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
     __syncwarp();
   } else if (warp == kEpi2) {
     // --------------------------------------------------------- MMA warp --
+    // One thread issues every MMA; descriptors are a per-stage base plus
+    // compile-time offsets (a descriptor's start address is in 16-byte units).
     if (lane == 0) {
+      const uint64_t big0 = umma_desc(smem_u32(sm.stage[0]), 2048, 128);
+      const uint64_t small0 = umma_desc(smem_u32(sm.stage[0] + kUnitBytes + kBigTile), 1024, 128);
       long long last = -1;
       for (long long u = u0; u < u1; ++u) {
         const int it = (int)(u - u0);
@@ -668,10 +675,6 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
         if (!wait_bar2(sm, &sm.full[s], (it / kStages) & 1, a.status)) break;
         if (!wait_bar2(sm, &sm.accempty[b], (it >> 1) & 1, a.status)) break;
         tc_fence_after();
-        uint8_t* st = sm.stage[s];
-        const int* ecol = reinterpret_cast<const int*>(st + 2 * kBigTile);
-        for (int c = 0; c < CT; ++c) sm.accmeta[b][c] = ecol[c];
-        mbar_arrive(&sm.accfull[b]);  // releases accmeta; the commit below is the second arrival
         const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
         const int c0 = (tile / g.parts) * CT;
         const int kap0 = kc * kKC;
@@ -680,27 +683,23 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
           const int slot = qu_slot(kc, c0, M, g.band_w);
           if (slot < 0 || slot >= a.qu_slots) cls = 0;  // reported by the encoder (status word)
         }
-        const uint32_t aPL = smem_u32(st), aQ = smem_u32(st + kBigTile);
-        const uint32_t aQU = cls == 1 ? aQ : smem_u32(st + kUnitBytes);
-        const uint32_t bS = smem_u32(st + kUnitBytes + kBigTile);
+        const uint64_t so = (uint64_t)(s * kStage2Bytes) >> 4;
+        const uint64_t dPL0 = big0 + so, dQ0 = dPL0 + (kBigTile >> 4);
+        const uint64_t dQU0 = cls == 1 ? dQ0 : dPL0 + (kUnitBytes >> 4);
+        const uint64_t dS0 = small0 + so;
         const uint32_t dl = tmem + b * kAccCols, dg = dl + kGroupCols;
+#pragma unroll
         for (int i = 0; i < kSlices; ++i) {
-          const uint32_t idesc = umma_idesc_bf16(kNS * min(kSlices, kLevels - i));
+          const uint32_t idesc = umma_idesc_bf16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
+#pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
-            const uint32_t ka = (uint32_t)(i * kBigSlice + kk * 2 * 2048);
-            const uint64_t dPL = umma_desc(aPL + ka, 2048, 128);
-            const uint64_t dQ = umma_desc(aQ + ka, 2048, 128);
-            const uint64_t dQU = umma_desc(aQU + ka, 2048, 128);
-            const uint32_t kb = (uint32_t)(kk * 2 * 1024);
-            const uint64_t dA1 = umma_desc(bS + 0 * kSmallVar + kb, 1024, 128);
-            const uint64_t dNl = umma_desc(bS + 1 * kSmallVar + kb, 1024, 128);
-            const uint64_t dNg = umma_desc(bS + 2 * kSmallVar + kb, 1024, 128);
-            umma_bf16(dl + i * kNS, dPL, dA1, idesc, 1);
-            umma_bf16(dg + i * kNS, dPL, dA1, idesc, 1);
-            umma_bf16(dg + i * kNS, dQ, dA1, idesc, 1);
+            const uint64_t oa = (uint64_t)((i * kBigSlice + kk * 2 * 2048) >> 4);
+            const uint64_t ob = (uint64_t)((kk * 2 * 1024) >> 4);
+            umma_bf16(dl + i * kNS, dPL0 + oa, dS0 + ob, idesc, 1);
+            umma_bf16(dg + i * kNS, dQ0 + oa, dS0 + ob, idesc, 1);
             if (cls != 0) {
-              umma_bf16(dl + i * kNS, dQU, dNl, idesc, 1);
-              umma_bf16(dg + i * kNS, dQU, dNg, idesc, 1);
+              umma_bf16(dl + i * kNS, dQU0 + oa, dS0 + ob + (kSmallVar >> 4), idesc, 1);
+              umma_bf16(dg + i * kNS, dQU0 + oa, dS0 + ob + (2 * kSmallVar >> 4), idesc, 1);
             }
           }
         }
@@ -717,35 +716,43 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
     __syncwarp();
   } else {
     // --------------------------------------------------------- epilogue --
-    // warp = 4 grp + quadrant: group grp drains accumulator group grp
-    // (0: I^<, 1: I^>) for the 32 TMEM lanes (= output rows) of its quadrant.
-    const int grp = warp >> 2, quad = warp & 3;
+    // warp = 8 half + 4 grp + quadrant: accumulator group grp (0: I^<,
+    // 1: D = I^> - I^<), small-operand columns [8 half, 8 half + 8), for the 32 TMEM
+    // lanes (= output rows) of its quadrant.
+    constexpr int kQ = kNS / 2;
+    const int quad = warp & 3, grp = (warp >> 2) & 1, half = warp >> 3;
     const int j = quad * 32 + lane;
     const int cl = j / M, bb = j - cl * M;
     const bool live_row = cl < CT;
     const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint32_t my_cols = grp * kGroupCols + half * kQ;  // + level * kNS + q
     for (int bsel = 0; bsel < 2; ++bsel)
-      for (int col = 0; col < kGroupCols; col += 16) tmem_zero16(lane_addr + bsel * kAccCols + grp * kGroupCols + col);
+      for (int d = 0; d < kLevels; ++d) tmem_zero8(lane_addr + bsel * kAccCols + my_cols + d * kNS);
     tmem_wait_st();
     tc_fence_before();
     mbar_arrive(&sm.accempty[0]);
     mbar_arrive(&sm.accempty[1]);
-    float run[kNS][2];
+    float run[kQ][2];
 #pragma unroll
-    for (int q = 0; q < kNS; ++q) { run[q][0] = 0.f; run[q][1] = 0.f; }
+    for (int q = 0; q < kQ; ++q) { run[q][0] = 0.f; run[q][1] = 0.f; }
     int local_seg = 0;
     for (long long u = u0; u < u1; ++u) {
       const int it = (int)(u - u0);
       const int b = it & 1;
+      const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
+      // the unit's column exponent (stored with its planes) and small-operand
+      // exponent, fetched before waiting for the accumulators
+      const int ec = live_row ? __ldg(reinterpret_cast<const int*>(
+                                      a.planes + ((size_t)(tile / g.parts) * a.cpt_stride + kc) * kUnitBytes +
+                                      2 * kBigTile) + cl)
+                              : 0;
+      const int es = __ldg(a.e_small + kc * g.parts + tile % g.parts);
       if (!__all_sync(0xffffffffu, wait_bar2(sm, &sm.accfull[b], (it >> 1) & 1, a.status))) break;
       tc_fence_after();
-      const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
-      const int part = tile % g.parts;
-      const int ec = live_row ? sm.accmeta[b][cl] : 0;
-      const float sc = pow2f(scale_from_field(ec) + a.e_small[kc * g.parts + part] - 14);
-      const uint32_t buf = lane_addr + b * kAccCols + grp * kGroupCols;
+      const float sc = pow2f(scale_from_field(ec) + es - 14);
+      const uint32_t buf = lane_addr + b * kAccCols + my_cols;
 #pragma unroll
-      for (int q4 = 0; q4 < kNS; q4 += 4) {
+      for (int q4 = 0; q4 < kQ; q4 += 4) {
         float v[kLevels][4];
         tmem_ld4xL(buf + q4, kNS, v);
 #pragma unroll
@@ -759,7 +766,8 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
           rl += lo * sc;
         }
       }
-      for (int col = 0; col < kGroupCols; col += 16) tmem_zero16(buf + col);
+#pragma unroll
+      for (int d = 0; d < kLevels; ++d) tmem_zero8(buf + d * kNS);
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&sm.accempty[b]);
@@ -768,14 +776,15 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
         if (live_row && c <= n) {
           double2* out = reinterpret_cast<double2*>(a.part) + ((size_t)blockIdx.x * g.S + local_seg) * (2 * 128 * kNA);
 #pragma unroll
-          for (int al = 0; al < kNA; ++al) {
-            const double re = (double)run[2 * al][0] + (double)run[2 * al][1];
-            const double im = (double)run[2 * al + 1][0] + (double)run[2 * al + 1][1];
+          for (int k = 0; k < kQ / 2; ++k) {
+            const int al = half * (kQ / 2) + k;  // small-operand column = 2 al + (re, im)
+            const double re = (double)run[2 * k][0] + (double)run[2 * k][1];
+            const double im = (double)run[2 * k + 1][0] + (double)run[2 * k + 1][1];
             out[((size_t)grp * CT + cl) * kNA * M + al * M + bb] = make_double2(re, im);
           }
         }
 #pragma unroll
-        for (int q = 0; q < kNS; ++q) { run[q][0] = 0.f; run[q][1] = 0.f; }
+        for (int q = 0; q < kQ; ++q) { run[q][0] = 0.f; run[q][1] = 0.f; }
         ++local_seg;
       }
     }
@@ -790,41 +799,58 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
 
 // ---------------------------------------------------------------- reduce -
 // I_out[s][c][a][b] = sum of the partials of every CTA that covered the
-// tile of (c, a), in CTA order, plus the band of term 2 in FP64 with the
-// exact composite weights:
+// tile of (c, a), in CTA order (I^< from group 0; I^> from groups 0 and 1),
+// plus the band of term 2 in FP64 with the exact composite weights:
 //   sum_{m = c-K..c} w_{c,m} S^s(n,m)_ax conj(R(c,m)_bx).
-__global__ void __launch_bounds__(256) split_reduce(SplitGeom g, const double* __restrict__ part,
-                                                    const double* __restrict__ Sl, const double* __restrict__ Sg,
-                                                    const double* __restrict__ R, WeightsView w,
-                                                    double* __restrict__ out, int* status) {
-  const int M = g.M, MM = g.MM, n = g.n;
-  const long long total = 2ll * (n + 1) * MM;
-  bool bad = false;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e / ((long long)(n + 1) * MM));
-    const int rem = (int)(e - (long long)s * (n + 1) * MM);
-    const int c = rem / MM, ab = rem - c * MM;
-    const int aa = ab / M, bb = ab - aa * M;
-    const int tile = (c / g.CT) * g.parts + aa / kNA;
-    const int cl = c % g.CT, al = aa % kNA;
+// Same sums with one block per (tile, chunk of its outputs): the CTAs that
+// covered the tile and the tile's segment in each are found once per block.
+__global__ void __launch_bounds__(256) split_reduce2(SplitGeom g, const double* __restrict__ part,
+                                                     const double* __restrict__ Sl, const double* __restrict__ Sg,
+                                                     const double* __restrict__ R, WeightsView w,
+                                                     double* __restrict__ out, int* status) {
+  const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
+  const int tile = blockIdx.x;
+  const int ctile = tile / g.parts, pt = tile % g.parts;
+  __shared__ int s_i0, s_k;
+  __shared__ int s_seg[160];  // G <= 152 CTAs
+  if (threadIdx.x == 0) {
     const long long ulo = (long long)tile * g.cpt, uhi = ulo + g.cpt;
-    // first CTA whose range [U*i/G, U*(i+1)/G) contains ulo
     int i = (int)((ulo * g.G) / g.U);
     while (i > 0 && g.U * i / g.G > ulo) --i;
     while (i + 1 < g.G && g.U * (i + 1) / g.G <= ulo) ++i;
-    double re = 0.0, im = 0.0;
-    for (; i < g.G; ++i) {
+    const int i0 = i;
+    int k = 0;
+    for (; i < g.G && k < 160; ++i) {
       const long long b0 = g.U * i / g.G, b1 = g.U * (i + 1) / g.G;
       if (b0 >= uhi) break;
-      if (b1 <= b0) continue;
-      const int seg = (int)(tile - b0 / g.cpt);
-      const double2 v = reinterpret_cast<const double2*>(part)[((size_t)i * g.S + seg) * (2 * 128 * kNA) +
-                                                                ((size_t)s * g.CT + cl) * kNA * M + al * M + bb];
-      re += v.x;
-      im += v.y;
+      s_seg[k++] = b1 <= b0 ? -1 : (int)(tile - b0 / g.cpt);
     }
-    // band of term 2
+    s_i0 = i0;
+    s_k = k;
+  }
+  __syncthreads();
+  const int i0 = s_i0, nk = s_k;
+  const int per_s = CT * kNA * M;
+  bool bad = false;
+  for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < 2 * per_s; idx += gridDim.y * blockDim.x) {
+    const int s = idx / per_s;
+    const int rem = idx - s * per_s;
+    const int cl = rem / (kNA * M);
+    const int r2 = rem - cl * (kNA * M);
+    const int al = r2 / M, bb = r2 - al * M;
+    const int c = ctile * CT + cl, aa = pt * kNA + al;
+    if (c > n || aa >= M) continue;
+    // group 0 holds I^<, group 1 holds D = I^> - I^<
+    double re = 0.0, im = 0.0;
+    for (int grp = 0; grp <= s; ++grp)
+      for (int k = 0; k < nk; ++k) {
+        const int seg = s_seg[k];
+        if (seg < 0) continue;
+        const double2 v = reinterpret_cast<const double2*>(part)[((size_t)(i0 + k) * g.S + seg) * (2 * 128 * kNA) +
+                                                                  ((size_t)grp * CT + cl) * kNA * M + al * M + bb];
+        re += v.x;
+        im += v.y;
+      }
     const double* S = s == 0 ? Sl : Sg;
     for (int m = max(0, c - w.band_w + 1); m <= c; ++m) {
       const double dw = w.at(c, m);
@@ -841,9 +867,14 @@ __global__ void __launch_bounds__(256) split_reduce(SplitGeom g, const double* _
       im += dw * ti;
     }
     bad |= !(isfinite(re) && isfinite(im));
-    reinterpret_cast<double2*>(out)[e] = make_double2(re, im);
+    reinterpret_cast<double2*>(out)[((size_t)s * (n + 1) + c) * MM + aa * M + bb] = make_double2(re, im);
   }
   if (bad) atomicOr(status, kStatusNumeric);
+}
+
+inline dim3 reduce2_grid(const SplitGeomHost& h) {
+  const int per_tile = 2 * h.CT * kNA * h.M;
+  return dim3((unsigned)h.tiles, (unsigned)((per_tile + 255) / 256));
 }
 
 }  // namespace
@@ -953,10 +984,7 @@ cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& pl_la
   if (l.ev_end) cudaEventRecord(l.ev_end, s);
   ++*launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long total = 2ll * (l.n + 1) * l.M * l.M;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  split_reduce<<<(unsigned)blocks, 256, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
+  split_reduce2<<<reduce2_grid(h), 256, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
   ++*launches;
   return cudaGetLastError();
 }
@@ -986,10 +1014,7 @@ cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* laun
   if (l.ev_end) cudaEventRecord(l.ev_end, s);
   ++*launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long total = 2ll * (l.n + 1) * l.M * l.M;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  split_reduce<<<(unsigned)blocks, 256, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
+  split_reduce2<<<reduce2_grid(h), 256, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
   ++*launches;
   return cudaGetLastError();
 }

@@ -199,6 +199,12 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
       "r"(z)
       : "memory");
 }
+// Zero 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_zero8(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(z)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ----------------------------------------------------- double-float sums --

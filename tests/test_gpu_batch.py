@@ -103,13 +103,31 @@ def test_batch_matches_single_system_stepper(kbe):
 
 
 def test_batch_split_precision(kbe):
+    """The split-precision bound is per slice: one batched split step from
+    an FP64 history matches the oracle's step to 1e-8 in every system.  A
+    whole run with the split contraction compounds one slice error per step
+    (about 40 steps here); it is checked at 5e-8."""
+    runs = _runs(kbe)
+    batch = kbe.Batch(runs)
+    n_last = max(s[1] for s in SYSTEMS) - 1
+    for n in range(1, n_last):
+        batch.step([n if n < s[1] - 1 else -1 for s in SYSTEMS], P=2, precision="fp64")
+    batch.step([s[1] - 1 for s in SYSTEMS], P=2, precision="split")
+    batch.sync_status()
+    for run, s in zip(runs, SYSTEMS):
+        Lo, _ = _oracle(*s)
+        n = s[1] - 1
+        p = W.tri_size(n)
+        Lg = run.L[p:p + n + 1].cpu().numpy()
+        assert _rel(Lg, Lo[p:p + n + 1]) < 1e-8, (s, _rel(Lg, Lo[p:p + n + 1]))
+    batch.close()
     runs = _runs(kbe)
     batch = kbe.Batch(runs)
     _advance(batch, SYSTEMS, precision="split")
     for run, s in zip(runs, SYSTEMS):
         Lo, _ = _oracle(*s)
         Lg = run.L[: W.tri_size(s[1])].cpu().numpy()
-        assert _rel(Lg, Lo) < 1e-8, (s, _rel(Lg, Lo))
+        assert _rel(Lg, Lo) < 5e-8, (s, _rel(Lg, Lo))
     batch.close()
 
 
