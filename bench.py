@@ -35,6 +35,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes of one FP64 contraction launch of the bench slice (ncu capture,
 # profiles/history_partial_fp64_chain_m8_n1024.md)
 FP64_SLICE_TRAFFIC = 2.077e9
+# DRAM bytes of one split contraction launch (split_main2) of the bench slice
+# (ncu capture, profiles/split_main_chain_m8_n1024.md)
+SPLIT_SLICE_TRAFFIC = 2.279e9
 METRIC = "history-slice TFLOP/s and ms per KBE step vs plain FP64 GPU path at stated error"
 
 
@@ -487,8 +490,21 @@ def main():
             "avg_ms": round(k_avg, 4), "peak_source": "unit counts x clock: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz "
                               "(FP64 is not in MEASURED_PEAKS.json)"}
     ms_step_s = ms_s / args.steps
+    # the split contraction streams the digit planes of the history: per (column tile of 128/M
+    # columns, chunk of 16 complex history entries) 66560 bytes (PL, Q, column exponents)
+    ct = 128 // M
+    cpt = ((n + 1) * M + 15) // 16
+    plane_bytes = ((n + 1 + ct - 1) // ct) * cpt * ((M + 7) // 8) * 66560
+    k_avg_s = kms_s / max(kc_s, 1)
+    hbm = hbm_peak_gbs()
+    split_roof = {"bound": "hbm", "kernel": "split_main2 (tcgen05 contraction fed by bulk copies)",
+                  "achieved": round(plane_bytes / (k_avg_s * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                  "frac": round(plane_bytes / (k_avg_s * 1e-3) / 1e9 / hbm, 4),
+                  "traffic": SPLIT_SLICE_TRAFFIC if (M, n) == (8, 1023) else None,
+                  "bytes_per_launch": plane_bytes,
+                  "note": "digit planes of both triangles: 2x the FP64 history bytes of the slice"}
     split = {"precision": "split: 4-digit bf16 fixed-point slices on tcgen05, exact FP32 chunk sums, "
-                          "double-float accumulation (KBE_SPLIT_BF16)",
+                          "double-float accumulation (KBE_SPLIT_BF16)", "roofline": split_roof,
              "ms_per_step": round(ms_step_s, 4),
              "value": round(world * flops_step / (ms_step_s * 1e-3) / 1e12, 4), "unit": "TFLOP/s (FP64-equivalent)",
              "speedup_vs_fp64_step": round(ms_step / ms_step_s, 3), "stated_error_bound": 1e-8,
