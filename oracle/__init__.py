@@ -203,6 +203,64 @@ def run(t, order, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1):
     return L, R, I_last
 
 
+def run_adaptive(t, order, hord, K_sel, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1):
+    """``run`` with the history quadrature orders chosen per step (Sec. 3.2)
+    up to K_sel; ``hord`` gives the orders of intervals 1..n_start-1.  Returns
+    (L, R, I_last, hord) with the chosen orders filled in up to n_end-1."""
+    t, order = _f64(t), _i32(order)
+    h0 = _c128(h0)
+    U, v = _f64(U), _f64(v)
+    M = h0.shape[0]
+    L = np.array(L, dtype=np.complex128, copy=True)
+    R = np.array(R, dtype=np.complex128, copy=True)
+    ho = np.zeros(len(t), np.int32)
+    ho[: len(hord)] = np.asarray(hord, np.int32)[: len(t)]
+    need = f_rows_needed(order, n_start, n_end)
+    Fin = np.concatenate([_c128(F_rows[j]).ravel() for j in need]) if need else np.zeros(1, np.complex128)
+    I_last = np.zeros((2, n_end, M, M), np.complex128)
+    _check(lib().orc_run_adaptive(ctypes.c_int(M), ctypes.c_int(n_start), ctypes.c_int(n_end), _p(t), _p(order),
+                                  _p(ho), ctypes.c_int(K_sel), _p(h0), _p(U), _p(v), _p(_pulse4(pulse)),
+                                  ctypes.c_int(P), _p(L), _p(R), _p(Fin), _p(I_last), ctypes.c_int(nthreads)),
+           "run_adaptive")
+    return L, R, I_last, ho
+
+
+def choose_order(t, n, K, u):
+    """Order chosen from test-integrand values u [kmax+1, M, M] at
+    t_{n-kmax}..t_n, and the differences |I^(k) - I^(k-1)| (index k)."""
+    t = _f64(t)
+    u = _c128(u)
+    M = u.shape[-1]
+    diffs = np.zeros(13)
+    k = ctypes.c_int()
+    _check(lib().orc_choose_order(ctypes.c_int(M), ctypes.c_int(n), _p(t), ctypes.c_int(K), _p(u), _p(diffs),
+                                  ctypes.byref(k)), "choose_order")
+    return k.value, diffs
+
+
+def select_order(t, n, K, L, R, Sl, Sg):
+    """(chosen order, test-integrand values [kmax+1, M, M]) of row n."""
+    t = _f64(t)
+    L, R, Sl, Sg = _c128(L), _c128(R), _c128(Sl), _c128(Sg)
+    M = L.shape[-1]
+    kmax = min(K, n)
+    u = np.zeros((kmax + 1, M, M), np.complex128)
+    k = ctypes.c_int()
+    _check(lib().orc_select_order(ctypes.c_int(M), ctypes.c_int(n), _p(t), ctypes.c_int(K), _p(L), _p(R), _p(Sl),
+                                  _p(Sg), _p(u), ctypes.byref(k)), "select_order")
+    return k.value, u
+
+
+def order_test_integrand(n, l, L, R, Sl, Sg):
+    """u(t_l) of row n (Sec. 3.2 order selection), [M, M]."""
+    L, R, Sl, Sg = _c128(L), _c128(R), _c128(Sl), _c128(Sg)
+    M = L.shape[-1]
+    u = np.zeros((M, M), np.complex128)
+    _check(lib().orc_test_integrand(ctypes.c_int(M), ctypes.c_int(n), ctypes.c_int(l), _p(L), _p(R), _p(Sl),
+                                    _p(Sg), _p(u)), "test_integrand")
+    return u
+
+
 def run_tangent(t, order, h0, U, dU, v, pulse, dE0, P, L, R, F_rows, n_start, n_end, nthreads=1):
     """Forward-mode derivative of ``run`` along (dU, dE0).  Returns the value
     and derivative of the final diagonal block L(n_end-1, n_end-1)."""

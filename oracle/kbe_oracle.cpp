@@ -30,6 +30,7 @@
 // parameter so that the stepper also runs on forward-mode dual numbers,
 // which gives exact directional derivatives of the discrete map.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -158,6 +159,52 @@ void composite_row(const double* t, const int* order, int n, double* row) {
   }
 }
 
+// ------------------------------------------- adaptive history orders ---
+// Order selection of Sec. 3.2 for interval n: the test integral of u over
+// [t_{n-1}, t_n] with the order-k interpolatory rule through t_{n-k..n},
+//   I^(k) = sum_j w^(k)_j u(t_{n-k+j}),  k = 1..kmax (kmax = min(K, n)),
+// and k_opt = argmin_{k >= 2} |I^(k) - I^(k-1)| in the max norm over the
+// M x M entries (k_opt = 1 when kmax = 1).  Differences that lie within a
+// rounding tolerance (64 eps times the largest |I^(k)|) of the minimum are
+// not distinguished: the lowest such order is taken.
+// u: [kmax+1][M*M] values at t_{n-kmax} .. t_n; diffs[k] = |I^(k) - I^(k-1)|.
+int choose_order(const double* t, int n, int K, int M, const C64* u, double* diffs) {
+  const int kmax = K < n ? K : n;
+  if (kmax <= 1) {
+    if (diffs) diffs[1] = 0.0;
+    return 1;
+  }
+  const int MM = M * M;
+  std::vector<C64> I((size_t)(kmax + 1) * MM);
+  double w[64];
+  double mag = 0.0;
+  for (int k = 1; k <= kmax; ++k) {
+    lagrange_weights(t + (n - k), k, t[n - 1], t[n], w);
+    for (int e = 0; e < MM; ++e) {
+      C64 acc;
+      for (int j = 0; j <= k; ++j) acc = acc + scale(w[j], u[(size_t)(kmax - k + j) * MM + e]);
+      I[(size_t)k * MM + e] = acc;
+      mag = std::max(mag, std::hypot(acc.re, acc.im));
+    }
+  }
+  std::vector<double> d(kmax + 1, 0.0);
+  double dmin = 1e300;
+  for (int k = 2; k <= kmax; ++k) {
+    double m = 0.0;
+    for (int e = 0; e < MM; ++e) {
+      const C64 x = I[(size_t)k * MM + e] - I[(size_t)(k - 1) * MM + e];
+      m = std::max(m, std::hypot(x.re, x.im));
+    }
+    d[k] = m;
+    dmin = std::min(dmin, m);
+  }
+  if (diffs) for (int k = 1; k <= kmax; ++k) diffs[k] = d[k];
+  const double tol = 64.0 * 2.220446049250313e-16 * mag;
+  for (int k = 2; k <= kmax; ++k)
+    if (d[k] <= dmin + tol) return k;
+  return kmax;
+}
+
 // -------------------------------------------------- two-time plane access --
 // Values anywhere in the (t,t') plane from the stored lower triangles:
 // G^<> (t,t') = -G^<>(t',t)^+ (Sec. 2), G^> = G^R + G^< on and below the
@@ -244,6 +291,35 @@ template <class T> struct SigmaRow {
   }
   Cx<T> adv_mn(int m, int a, int b) const { return conj(ret_nm(m, b, a)); }
 };
+
+inline double value_of(double x) { return x; }
+inline double value_of(Dual x) { return x.v; }
+
+// Test integrand of the order selection (Sec. 3.2) at t_bar = t_l, l <= n:
+//   u(t_l) = G^R(t_n, t_l) Sigma^<(t_l, t_n) + G^<(t_n, t_l) Sigma^A(t_l, t_n),
+// the integrand of Eq. (KBE1) for G^<(t_n, t_n); values only (no tangents).
+template <class T>
+void test_integrand(const Plane<T>& G, const SigmaRow<T>& S, int n, int l, C64* u) {
+  const int M = G.M;
+  for (int a = 0; a < M; ++a)
+    for (int b = 0; b < M; ++b) {
+      Cx<T> acc;
+      for (int x = 0; x < M; ++x)
+        acc = acc + G.ret(n, l, a, x) * S.s_mn(0, l, n, x, b) + G.less(n, l, a, x) * S.adv_mn(l, x, b);
+      u[a * M + b] = C64(value_of(acc.re), value_of(acc.im));
+    }
+}
+
+// Chooses the history order of interval n from the current rows (Sec. 3.2).
+template <class T>
+int select_history_order(const Plane<T>& G, const SigmaRow<T>& S, const double* t, int n, int K) {
+  const int kmax = K < n ? K : n;
+  if (kmax <= 1) return 1;
+  const int MM = G.M * G.M;
+  std::vector<C64> u((size_t)(kmax + 1) * MM);
+  for (int i = 0; i <= kmax; ++i) test_integrand(G, S, n, n - kmax + i, u.data() + (size_t)i * MM);
+  return choose_order(t, n, K, G.M, u.data(), nullptr);
+}
 
 // Eq. (KBE2) history integrals for row n, both s in {<, >} and c = 0..n:
 //   I^s(n,c) = sum_{m=0..n} w_{n,m} Sigma^R(n,m) G^s(m,c)
@@ -367,10 +443,15 @@ template <class T> struct Ring {
 //              (Adams-Moulton type, points t_{n-kap..n}), diagonal kap = min(k_n, n).
 //  G^>(n,c) for c < n comes from the stepped G^> and G^<:  R(n,c) = G^>(n,c) - L(n,c);
 //  R(n,n) = -i*1.  F row n keeps the value of the last evaluation.
+// hord: orders of the history quadrature per interval (the stepper's orders
+// `order` are separate); with K_sel > 0, hord[n] is chosen in every sweep by
+// select_history_order (Sec. 3.2), otherwise hord is read only.
 template <class T>
 void kbe_step(const Model<T>& md, const double* t, const int* order, int n, int P,
-              const T* U4, Cx<T>* L, Cx<T>* R, Ring<T>& ring, Cx<T>* I_last, int nthreads) {
+              const T* U4, Cx<T>* L, Cx<T>* R, Ring<T>& ring, Cx<T>* I_last, int nthreads,
+              int* hord = nullptr, int K_sel = 0) {
   const int M = md.M;
+  const int* horder = hord ? hord : order;
   const int MM = M * M;
   const int kn = order[n];
   Plane<T> G{M, L, R};
@@ -420,7 +501,8 @@ void kbe_step(const Model<T>& md, const double* t, const int* order, int n, int 
   for (int sweep = 0; sweep < P; ++sweep) {
     sigma_row(G, U4, n, Sl.data(), Sg.data());
     SigmaRow<T> S{M, Sl.data(), Sg.data()};
-    history_slice(G, S, t, order, n, I.data(), nthreads);
+    if (K_sel > 0 && hord) hord[n] = select_history_order(G, S, t, n, K_sel);
+    history_slice(G, S, t, horder, n, I.data(), nthreads);
     rhs_row(md, G, t, I.data(), n, ring.row(n));
     // corrector
     for (int c = 0; c < n; ++c) {
@@ -590,6 +672,63 @@ int orc_run(int M, int n_start, int n_end, const double* t, const int* order, co
   for (int n = n_start; n < n_end; ++n)
     kbe_step(md, t, order, n, P, U4.data(), (C64*)L, (C64*)R, ring,
              (n == n_end - 1) ? (C64*)I_last : nullptr, nthreads);
+  return 0;
+}
+
+// The same run with adaptive history orders (Sec. 3.2): hord[1..n_start-1]
+// hold the orders chosen before n_start (the history quadrature of the given
+// rows); each step n chooses hord[n] with orders up to K_sel (1..12) in every
+// sweep (K_sel = 0: hord[1..n_end-1] are given and used as they are).  The
+// stepper's own orders stay `order`.
+int orc_run_adaptive(int M, int n_start, int n_end, const double* t, const int* order, int* hord, int K_sel,
+                     const double* h0, const double* U, const double* v, const double* pulse4, int P, void* L,
+                     void* R, const void* F_in, void* I_last, int nthreads) {
+  if (M < 1 || n_start < 1 || n_end < n_start || P < 1 || nthreads < 1 || K_sel < 0 || K_sel > 12) return 1;
+  int K = 1;
+  for (int l = 1; l < n_end; ++l) if (order[l] > K) K = order[l];
+  Model<double> md{M, (const C64*)h0, U, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  std::vector<double> U4 = local_U4(M, U);
+  Ring<double> ring{M, n_end, K, std::vector<C64>((size_t)(K + 1) * 2 * n_end * M * M)};
+  const C64* f = (const C64*)F_in;
+  for (int j = (n_start - K > 0 ? n_start - K : 0); j <= n_start - 1; ++j) {
+    const size_t cnt = (size_t)2 * (j + 1) * M * M;
+    std::memcpy((void*)ring.row(j), f, cnt * sizeof(C64));
+    f += cnt;
+  }
+  for (int n = n_start; n < n_end; ++n)
+    kbe_step(md, t, order, n, P, U4.data(), (C64*)L, (C64*)R, ring,
+             (n == n_end - 1) ? (C64*)I_last : nullptr, nthreads, hord, K_sel);
+  return 0;
+}
+
+// Order selection from given test-integrand values u [kmax+1][M][M] at
+// t_{n-kmax} .. t_n (kmax = min(K, n)); diffs[k] = |I^(k) - I^(k-1)|_max.
+int orc_choose_order(int M, int n, const double* t, int K, const void* u, double* diffs, int* kopt) {
+  if (M < 1 || n < 1 || K < 1 || K > 12) return 1;
+  *kopt = choose_order(t, n, K, M, (const C64*)u, diffs);
+  return 0;
+}
+
+// Test integrand values u(t_l), l = n-kmax .. n, from row n of L, R and the
+// self-energy row n; and the order chosen from them.
+int orc_select_order(int M, int n, const double* t, int K, const void* L, const void* R, const void* Sl,
+                     const void* Sg, void* u_out, int* kopt) {
+  if (M < 1 || n < 1 || K < 1 || K > 12) return 1;
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  SigmaRow<double> S{M, (const C64*)Sl, (const C64*)Sg};
+  const int kmax = K < n ? K : n;
+  for (int i = 0; i <= kmax; ++i) test_integrand(G, S, n, n - kmax + i, (C64*)u_out + (size_t)i * M * M);
+  *kopt = select_history_order(G, S, t, n, K);
+  return 0;
+}
+
+// Test integrand value u(t_l) for any l <= n (Sec. 3.2).
+int orc_test_integrand(int M, int n, int l, const void* L, const void* R, const void* Sl, const void* Sg,
+                       void* u_out) {
+  if (M < 1 || n < 0 || l < 0 || l > n) return 1;
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  SigmaRow<double> S{M, (const C64*)Sl, (const C64*)Sg};
+  test_integrand(G, S, n, l, (C64*)u_out);
   return 0;
 }
 
