@@ -253,6 +253,28 @@ kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* 
                             void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0,
                             void* stream);
 
+/* Adaptive history orders (Sec. 3.2).  With K in 1..12, every fixed-point
+ * sweep of kbe_step / kbe_step_rows chooses the order of the history
+ * quadrature over [t_{n-1}, t_n] on the device: it integrates the test
+ * function u(t) = G^R(t_n,t) Sigma^<(t,t_n) + G^<(t_n,t) Sigma^A(t,t_n) over
+ * the interval with every order k <= min(K, n) (interpolatory rules of
+ * Eq. weights through t_{n-k..n}) and takes the order that minimises the
+ * max-norm change from order k-1; differences within 64 eps of the largest
+ * test integral from the minimum are not distinguished (the lowest order is
+ * taken).  The composite weights of row n follow from row n-1 and the local
+ * weights of that order (the row recursion of Sec. 3.2).  The grid's own
+ * orders keep driving the stepper's predictor and corrector.  The band of
+ * the weights widens to K+1 points.  Steps must run in order from row 1
+ * (kbe_step at row n requires rows 1..n-1 stepped; stepping a row again
+ * restarts from it), else KBE_ESTATE.  K = 0 returns to the grid's orders.
+ * Calls kbe_set_grid first; kbe_set_grid returns to the grid's orders.
+ * Batches (kbe_batch_*) need the grids' orders. */
+kbe_status kbe_set_adaptive_orders(kbe_ctx* ctx, int K);
+
+/* The history order of each interval 0..n-1 (0 for row 0): the chosen ones
+ * in adaptive mode (synchronises the device), else min(order[l], l). */
+kbe_status kbe_get_history_orders(kbe_ctx* ctx, int* orders, int n);
+
 /* Forget per-history state kept between steps (the split path's digit
  * planes); the next step encodes every row again.  No GPU work. */
 kbe_status kbe_reset_cache(kbe_ctx* ctx);

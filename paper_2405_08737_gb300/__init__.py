@@ -75,6 +75,8 @@ def lib():
         L.kbe_batch_sync_status.argtypes = [vp, vp]
         L.kbe_sync_status.argtypes = [vp, vp]
         L.kbe_reset_cache.argtypes = [vp]
+        L.kbe_set_adaptive_orders.argtypes = [vp, i]
+        L.kbe_get_history_orders.argtypes = [vp, vp, i]
         L.kbe_set_profiling.argtypes = [vp, i]
         L.kbe_read_profiling.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d)]
         _lib = L
@@ -263,6 +265,18 @@ class Context:
         if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
             raise TypeError("expected a contiguous CUDA float64 tensor")
         return ctypes.c_void_p(x.data_ptr())
+
+    def set_adaptive_orders(self, K):
+        """Choose the history quadrature order of each step on the device
+        (Sec. 3.2), up to K (0: the grid's orders)."""
+        self._check(lib().kbe_set_adaptive_orders(self._h, int(K)))
+
+    def history_orders(self, n=None):
+        """History order per interval 0..n-1 (the chosen ones in adaptive mode)."""
+        n = self.n_max if n is None else int(n)
+        out = np.zeros(n, np.int32)
+        self._check(lib().kbe_get_history_orders(self._h, _np_ptr(out), n))
+        return out
 
     def reset_cache(self):
         """Forget the split path's digit planes kept between steps."""

@@ -26,7 +26,7 @@ kbe_status cuda_fail(kbe_ctx* ctx, cudaError_t e, const char* where) {
 bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 WeightsView weights_view(const kbe_ctx* ctx) {
-  return WeightsView{ctx->d_wbar, ctx->d_band, ctx->grid.K + 1};
+  return WeightsView{ctx->d_wbar, ctx->d_band, ctx->band_w};
 }
 
 template <class T> cudaError_t dev_alloc(T** p, size_t count) {
@@ -40,6 +40,10 @@ void release(kbe_ctx* ctx) {
   cudaFree(ctx->d_h0); cudaFree(ctx->d_U); cudaFree(ctx->d_v); cudaFree(ctx->d_eps);
   cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split); cudaFree(ctx->d_adj);
   cudaFree(ctx->d_planes);
+  cudaFree(ctx->d_hist);
+  cudaFree(ctx->d_korder);
+  ctx->d_hist = nullptr;
+  ctx->d_korder = nullptr;
   ctx->d_planes = nullptr;
   ctx->planes_layout = SplitPlanes{};
   ctx->planes_L = ctx->planes_R = nullptr;
@@ -186,6 +190,14 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
                      (double*)Sg, ctx->d_status, s);
     *count_out = ++count;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: self-energy");
+    if (ctx->adaptive_K > 0) {  // history order of interval n from this sweep's rows (Sec. 3.2)
+      SelectArgs sa{ctx->M, n, ctx->adaptive_K, (const double*)L, (const double*)R, (const double*)Sl,
+                    (const double*)Sg, ctx->d_hist + (size_t)n * kMaxOrder * kWTab, ctx->d_band, ctx->d_wbar,
+                    ctx->band_w, ctx->d_korder};
+      e = launch_select_order(sa, s);
+      *count_out = ++count;
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: history order selection");
+    }
     kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl, true);
     *count_out = (count += nl);
     if (st != KBE_OK) return st;
@@ -209,6 +221,12 @@ kbe_status check_step_call(kbe_ctx* ctx, int n, int P, int precision, const void
   if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_work) || !aligned16(F))
     return fail(ctx, KBE_EINVAL, "kbe_step: NULL or misaligned pointer");
   if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16) return fail(ctx, KBE_EINVAL, "kbe_step: unknown precision");
+  if (ctx->adaptive_K > 0) {
+    if (n > ctx->adaptive_rows)
+      return fail(ctx, KBE_ESTATE, "kbe_step: adaptive history orders need the steps in order (row " +
+                                       std::to_string(ctx->adaptive_rows) + " is next)");
+    ctx->adaptive_rows = n + 1;  // rows above n are stepped again
+  }
   return use_device(ctx);
 }
 
@@ -341,6 +359,9 @@ kbe_status kbe_set_grid(kbe_ctx* ctx, const double* t, const int* order, int n_t
     return cuda_fail(ctx, e, "kbe_set_grid: upload");
   ctx->grid = std::move(g);
   ctx->grid_set = true;
+  ctx->band_w = ctx->grid.K + 1;
+  ctx->adaptive_K = 0;
+  ctx->adaptive_rows = 0;
   ctx->planes_L = ctx->planes_R = nullptr;  // cached digit planes depend on the band of the weights
   ctx->planes_rows = 0;
   return KBE_OK;
@@ -635,6 +656,68 @@ kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* 
   if ((st = check("kbe_step_adjoint: restore")) != KBE_OK) return st;
   ctx->last_launches = count;
   return KBE_OK;
+}
+
+kbe_status kbe_set_adaptive_orders(kbe_ctx* ctx, int K) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!ctx->grid_set) return fail(ctx, KBE_ESTATE, "no grid: call kbe_set_grid first");
+  if (K < 0 || K > kMaxOrder) return fail(ctx, KBE_ERANGE, "kbe_set_adaptive_orders: K outside [0, 12]");
+  kbe_status st = use_device(ctx);
+  if (st != KBE_OK) return st;
+  const HostGrid& g = ctx->grid;
+  cudaError_t e = cudaSuccess;
+  ctx->planes_L = ctx->planes_R = nullptr;  // the band width changes
+  ctx->planes_rows = 0;
+  if (K == 0) {  // back to the grid's orders
+    const int bw = g.K + 1;
+    if ((e = cudaMemcpy(ctx->d_wbar, g.wbar.data(), g.n_t * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(ctx->d_band, g.band.data(), (size_t)g.n_t * bw * sizeof(double), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+      return cuda_fail(ctx, e, "kbe_set_adaptive_orders: upload");
+    ctx->adaptive_K = 0;
+    ctx->band_w = bw;
+    return KBE_OK;
+  }
+  const size_t tab = (size_t)ctx->n_max * kMaxOrder * kWTab;
+  if (!ctx->d_hist && (e = cudaMalloc(&ctx->d_hist, tab * sizeof(double))) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_set_adaptive_orders: allocation");
+  if (!ctx->d_korder && (e = cudaMalloc(&ctx->d_korder, ctx->n_max * sizeof(int))) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_set_adaptive_orders: allocation");
+  // local weights of every order k <= min(K, n) for each interval n (host FP64, Eq. weights)
+  std::vector<double> hist(tab, 0.0);
+  double w[kWTab];
+  for (int n = 1; n < g.n_t; ++n)
+    for (int k = 1; k <= (K < n ? K : n); ++k) {
+      st = local_weights(g.t.data() + n - k, k, g.t[n - 1], g.t[n], w, &ctx->err);
+      if (st != KBE_OK) return st;
+      for (int j = 0; j <= k; ++j) hist[((size_t)n * kMaxOrder + (k - 1)) * kWTab + j] = w[j];
+    }
+  const int bw = K + 1;
+  if ((e = cudaMemcpy(ctx->d_hist, hist.data(), tab * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(ctx->d_band, 0, (size_t)ctx->n_max * bw * sizeof(double))) != cudaSuccess ||
+      (e = cudaMemset(ctx->d_wbar, 0, ctx->n_max * sizeof(double))) != cudaSuccess ||
+      (e = cudaMemset(ctx->d_korder, 0, ctx->n_max * sizeof(int))) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_set_adaptive_orders: upload");
+  ctx->adaptive_K = K;
+  ctx->band_w = bw;
+  ctx->adaptive_rows = 1;  // row 0 has no interval
+  return KBE_OK;
+}
+
+kbe_status kbe_get_history_orders(kbe_ctx* ctx, int* orders, int n) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!orders || n < 0 || n > ctx->n_max) return fail(ctx, KBE_EINVAL, "kbe_get_history_orders: bad arguments");
+  if (ctx->adaptive_K == 0) {
+    for (int l = 0; l < n; ++l) orders[l] = l == 0 ? 0 : (ctx->grid.order[l] < l ? ctx->grid.order[l] : l);
+    return KBE_OK;
+  }
+  kbe_status st = use_device(ctx);
+  if (st != KBE_OK) return st;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(orders, ctx->d_korder, n * sizeof(int), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_get_history_orders");
 }
 
 kbe_status kbe_reset_cache(kbe_ctx* ctx) {

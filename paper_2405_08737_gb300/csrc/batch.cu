@@ -368,6 +368,8 @@ kbe_status kbe_batch_create(kbe_ctx* const* ctxs, int n_sys, kbe_batch** out) {
     if (!c) return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: NULL context");
     if (!c->grid_set || !c->model.set)
       return bfail(nullptr, KBE_ESTATE, "kbe_batch_create: every context needs its grid and model set");
+    if (c->adaptive_K > 0)
+      return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: batched steps use the grids' history orders");
     if (dev0 < 0) dev0 = c->device;
     if (c->device != dev0) return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: contexts on different devices");
   }

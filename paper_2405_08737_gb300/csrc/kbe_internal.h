@@ -109,6 +109,13 @@ struct kbe_ctx {
   // reverse-mode workspace, allocated by the first adjoint call that needs it
   double* d_adj = nullptr;
   size_t adj_bytes = 0;
+  // adaptive history orders (Sec. 3.2): 0 = the grid's orders; else the
+  // largest order the selection may choose
+  int adaptive_K = 0;
+  int band_w = 0;             // width of the composite-weight band on the device
+  int adaptive_rows = 0;      // band rows 0 .. adaptive_rows-1 are set
+  double* d_hist = nullptr;   // local weights of every order per interval [n_max][kMaxOrder][kWTab]
+  int* d_korder = nullptr;    // chosen history order per interval [n_max]
   // measurement: event pairs around each contraction kernel
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -192,6 +199,21 @@ cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fock(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rhs(const StepArgs& a, cudaStream_t s);          // F row n only
 cudaError_t launch_rhs_corrector(const StepArgs& a, cudaStream_t s);  // F row n, then new row n
+
+// ---- adaptive history orders (adaptive.cu) -------------------------------
+struct SelectArgs {
+  int M, n, K;
+  const double* L;     // triangles (row n = the current iterate)
+  const double* R;
+  const double* Sl;    // self-energy row n
+  const double* Sg;
+  const double* hist;  // local weights of interval n for orders 1..K: [kMaxOrder][kWTab]
+  double* band;        // composite-weight band [n_t][band_w] (row n written)
+  double* wbar;        // settled weights (entry n - band_w written)
+  int band_w;
+  int* korder;         // chosen order per interval (entry n written)
+};
+cudaError_t launch_select_order(const SelectArgs& a, cudaStream_t s);
 
 // ---- reverse mode (adjoint.cu) ------------------------------------------
 // Cotangent convention: for a real loss, zbar = dF/dRe z + i dF/dIm z.
