@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batching form")
     ap.add_argument("--no-window", action="store_true", help="skip the differentiation form")
     ap.add_argument("--no-selfenergy", action="store_true", help="skip the whole-triangle self-energy timing")
+    ap.add_argument("--no-adaptive", action="store_true", help="skip the adaptive history-order run")
     return ap.parse_args()
 
 
@@ -396,6 +397,45 @@ def hbm_peak_gbs():
     return 6800.0
 
 
+def adaptive_bench(kbe, seed, stream, n_rows=256, K=6):
+    """Adaptive history orders (Sec. 3.2): the first n_rows steps of the
+    8-orbital chain from the uncorrelated state, with the history order of
+    every interval chosen on the device (orders up to K) and with the grid's
+    orders; reports the time of both runs and the chosen orders."""
+    import torch
+    import workloads as W
+    cfg = W.CONFIGS[WORKLOAD]
+    M = cfg["M"]
+    t, order = W.grid(cfg["n_t"], cfg["dt0"], cfg["sig"], seed)
+    t, order = t[:n_rows], order[:n_rows]
+    h, U, v, pulse = W.build_model(cfg, seed)
+    out = {"workload": "%s: first %d steps from the uncorrelated state, P=2, FP64" % (WORKLOAD, n_rows), "K": K}
+    for mode in ("grid", "adaptive"):
+        ctx = kbe.Context(M, n_rows)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        if mode == "adaptive":
+            ctx.set_adaptive_orders(K)
+        run = kbe.Run(ctx)
+        run.init_uncorrelated(W.half_filled_rho(h))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for n in range(1, n_rows):
+            run.step(n, P=2, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        out[mode + "_ms"] = round(e0.elapsed_time(e1), 2)
+        if mode == "adaptive":
+            ko = ctx.history_orders(n_rows)
+            out["chosen_orders_histogram"] = {int(k): int(c) for k, c in zip(*np.unique(ko[1:], return_counts=True))}
+        ctx.close()
+    out["overhead_vs_grid_orders"] = round(out["adaptive_ms"] / out["grid_ms"] - 1.0, 4)
+    return out
+
+
 def window_bench(kbe, seed, stream):
     """The differentiation form: gradient of the final site-0 density
     2 Im L(N-1,N-1)_00 with respect to U (uniform) and E0 through the last 32
@@ -434,9 +474,19 @@ def window_bench(kbe, seed, stream):
     fdU = (dens(U + hh, pulse["E0"]) - dens(U - hh, pulse["E0"])) / (2 * hh)
     fdE = (dens(U, pulse["E0"] + hh) - dens(U, pulse["E0"] - hh)) / (2 * hh)
     ctx.close()
+    # FP64 work: the forward window is 2 slices per step; the reverse sweep recomputes them and
+    # runs 2 adjoint slices per step (Sigma-row cotangent, 24 M^3 (n+1)^2 flops each; the
+    # cotangents of the window rows add 64 M^3 (n - n_start + 1)(n+1))
+    fwd_flops = sum(2 * slice_flops(M, n) for n in range(n_start, nt))
+    bwd_flops = sum(2 * slice_flops(M, n) + 2 * (24.0 * M ** 3 * (n + 1) ** 2 +
+                                                  64.0 * M ** 3 * (n - n_start + 1) * (n + 1))
+                    for n in range(n_start, nt))
     return {"workload": "chain_m16_n512_w32: M=16, N_t=512, gradient through the last %d steps (P=2), "
                         "pulse centred 0.35 before the final time" % Wn,
             "forward_ms": round(fwd, 2), "backward_ms": round(bwd, 2),
+            "forward_tflops": round(fwd_flops / (fwd * 1e-3) / 1e12, 4),
+            "backward_tflops": round(bwd_flops / (bwd * 1e-3) / 1e12, 4),
+            "backward_frac_of_fp64_peak": round(bwd_flops / (bwd * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
             "dF_dU": gU, "dF_dU_fd": fdU, "rel_err_U": abs(gU - fdU) / abs(fdU),
             "dF_dE0": gE, "dF_dE0_fd": fdE, "rel_err_E0": abs(gE - fdE) / abs(fdE)}
 
@@ -537,6 +587,8 @@ def main():
         line["selfenergy"] = sigma_bench(kbe, ctx, run, n + 1, stream)
     if rank == 0 and not args.no_window:
         line["differentiation_form"] = window_bench(kbe, args.seed, stream)
+    if rank == 0 and not args.no_adaptive:
+        line["adaptive_orders"] = adaptive_bench(kbe, args.seed, stream)
     ctx.close()
     del run
     torch.cuda.empty_cache()
