@@ -161,13 +161,34 @@ def _pulse4(pulse):
     return _f64([pulse["E0"], pulse["t0"], pulse["sigma"], pulse["omega"]])
 
 
-def rhs_row(j, t, order, h0, U, v, pulse, L, R, nthreads=1):
-    """F^s(j,c) = -i(eps(t_j) G^s(j,c) + I^s(j,c)), c = 0..j; [2, j+1, M, M]."""
+def fock(t, h0, U, v, pulse, Lnn, U4=None):
+    """Fock matrix of Eq. (eps) at time t from G^<(t,t) = Lnn: [M, M].  With
+    ``U4`` (real [M, M, M, M], ``U4[i, a, b, j] = U_iabj``) the general
+    tensor, else the local interaction ``U``."""
+    h0, Lnn, v = _c128(h0), _c128(Lnn), _f64(v)
+    M = h0.shape[0]
+    Uv = _f64(U if U is not None else np.zeros(M))
+    U4p = _p(_f64(U4)) if U4 is not None else None
+    eps = np.zeros((M, M), np.complex128)
+    _check(lib().orc_fock(ctypes.c_int(M), ctypes.c_double(t), _p(h0), _p(Uv), U4p, _p(v),
+                          _p(_pulse4(pulse)), _p(Lnn), _p(eps)), "fock")
+    return eps
+
+
+def rhs_row(j, t, order, h0, U, v, pulse, L, R, nthreads=1, U4=None):
+    """F^s(j,c) = -i(eps(t_j) G^s(j,c) + I^s(j,c)), c = 0..j; [2, j+1, M, M].
+    ``U4`` selects the general tensor in Eq. (SE) and Eq. (eps)."""
     t, order = _f64(t), _i32(order)
     h0, L, R = _c128(h0), _c128(L), _c128(R)
-    U, v = _f64(U), _f64(v)
+    v = _f64(v)
     M = h0.shape[0]
     F = np.zeros((2, j + 1, M, M), np.complex128)
+    if U4 is not None:
+        _check(lib().orc_rhs_row_u4(ctypes.c_int(M), ctypes.c_int(j), _p(t), _p(order), _p(h0), _p(_f64(U4)),
+                                    _p(v), _p(_pulse4(pulse)), _p(L), _p(R), _p(F), ctypes.c_int(nthreads)),
+               "rhs_row_u4")
+        return F
+    U = _f64(U)
     _check(lib().orc_rhs_row(ctypes.c_int(M), ctypes.c_int(j), _p(t), _p(order), _p(h0), _p(U), _p(v),
                              _p(_pulse4(pulse)), _p(L), _p(R), _p(F), ctypes.c_int(nthreads)), "rhs_row")
     return F
@@ -183,11 +204,30 @@ def f_rows_needed(order, n_start, n_end):
     return list(range(max(0, n_start - K), n_start))
 
 
-def run(t, order, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1):
+def _run_u4(t, order, hord, K_sel, h0, U4, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads):
+    t, order = _f64(t), _i32(order)
+    h0, v = _c128(h0), _f64(v)
+    M = h0.shape[0]
+    L = np.array(L, dtype=np.complex128, copy=True)
+    R = np.array(R, dtype=np.complex128, copy=True)
+    need = f_rows_needed(order, n_start, n_end)
+    Fin = np.concatenate([_c128(F_rows[j]).ravel() for j in need]) if need else np.zeros(1, np.complex128)
+    I_last = np.zeros((2, n_end, M, M), np.complex128)
+    hp = _p(hord) if hord is not None else None
+    _check(lib().orc_run_u4(ctypes.c_int(M), ctypes.c_int(n_start), ctypes.c_int(n_end), _p(t), _p(order), hp,
+                            ctypes.c_int(K_sel), _p(h0), _p(_f64(U4)), _p(v), _p(_pulse4(pulse)), ctypes.c_int(P),
+                            _p(L), _p(R), _p(Fin), _p(I_last), ctypes.c_int(nthreads)), "run_u4")
+    return L, R, I_last
+
+
+def run(t, order, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1, U4=None):
     """KBE steps n_start..n_end-1.  ``L``/``R`` are triangles of n_end rows,
     filled for rows < n_start; ``F_rows`` maps each row j of
     ``f_rows_needed`` to its [2, j+1, M, M] right-hand side.  Returns
-    (L, R, I_last) with the history slice of the last row."""
+    (L, R, I_last) with the history slice of the last row.  ``U4`` selects
+    the general tensor in Eq. (SE) and Eq. (eps) (``U`` is then unused)."""
+    if U4 is not None:
+        return _run_u4(t, order, None, 0, h0, U4, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads)
     t, order = _f64(t), _i32(order)
     h0 = _c128(h0)
     U, v = _f64(U), _f64(v)
@@ -203,10 +243,15 @@ def run(t, order, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1):
     return L, R, I_last
 
 
-def run_adaptive(t, order, hord, K_sel, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1):
+def run_adaptive(t, order, hord, K_sel, h0, U, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads=1, U4=None):
     """``run`` with the history quadrature orders chosen per step (Sec. 3.2)
     up to K_sel; ``hord`` gives the orders of intervals 1..n_start-1.  Returns
     (L, R, I_last, hord) with the chosen orders filled in up to n_end-1."""
+    if U4 is not None:
+        ho = np.zeros(len(t), np.int32)
+        ho[: len(hord)] = np.asarray(hord, np.int32)[: len(t)]
+        out = _run_u4(t, order, ho, K_sel, h0, U4, v, pulse, P, L, R, F_rows, n_start, n_end, nthreads)
+        return out + (ho,)
     t, order = _f64(t), _i32(order)
     h0 = _c128(h0)
     U, v = _f64(U), _f64(v)
@@ -280,7 +325,7 @@ def run_tangent(t, order, h0, U, dU, v, pulse, dE0, P, L, R, F_rows, n_start, n_
     return Lv, Ld
 
 
-def initial_rhs(t, order, h0, U, v, pulse, rho0):
+def initial_rhs(t, order, h0, U, v, pulse, rho0, U4=None):
     """Row 0 of a run from an uncorrelated state: L(0,0) = i rho0,
     R(0,0) = -i, and its right-hand side (the history integral over a
     zero-length interval vanishes)."""
@@ -288,5 +333,5 @@ def initial_rhs(t, order, h0, U, v, pulse, rho0):
     M = h0.shape[0]
     L0 = (1j * _c128(rho0)).reshape(1, M, M)
     R0 = (-1j * np.eye(M)).reshape(1, M, M).astype(np.complex128)
-    F0 = rhs_row(0, t, order, h0, U, v, pulse, L0, R0)
+    F0 = rhs_row(0, t, order, h0, U, v, pulse, L0, R0, U4=U4)
     return L0, R0, F0

@@ -15,6 +15,7 @@
 //     the local weights, summed directly (the recursion is not used here).
 //   * self-energy -- Sec. 2, Eq. (SE), summed over the non-zero entries of
 //     the four-index Coulomb tensor.
+//   * Fock matrix -- Eq. (eps), for the local tensor or a general real one.
 //   * history integrals -- Sec. 2, Eq. (KBE2), and Eq. (KBE1) for the adjoint
 //     identity, with theta(0) = 1 and G(t,t') = -G(t',t)^+.
 //   * stepper -- integral-form Adams-Moulton on the same kind of weights with
@@ -374,9 +375,12 @@ void kbe1_slice(const Plane<T>& G, const SigmaRow<T>& S, const double* t, const 
 
 // ---------------------------------------------------------------- stepper --
 // Model: h(t) = h0 + E(t) diag(v), E(t) = E0 exp(-(t-t0)^2/(2 sigma^2)) cos(omega t);
-// local interaction U_a (Coulomb tensor U_abcd = U_a delta_abcd).
-// Fock matrix (Eq. eps) for that tensor: eps = h(t) + diag(U_a n_a),
-// n_a = Im L(t,t)_aa (the real part of -i G^<_aa(t,t)).
+// local interaction U_a (Coulomb tensor U_abcd = U_a delta_abcd), or, when
+// U4d is set, a general real tensor U4d[((i*M + a)*M + b)*M + j] = U_iabj.
+// Fock matrix (Eq. eps):
+//   eps_ij = h_ij(t) + i sum_ab (U_iabj - 2 U_ijba) G^<_ba(t,t);
+// for the local tensor this is eps = h(t) + diag(U_a n_a), n_a = Im L(t,t)_aa
+// (the real part of -i G^<_aa(t,t)).
 template <class T> struct Model {
   int M;
   const C64* h0;
@@ -384,6 +388,7 @@ template <class T> struct Model {
   const double* v;
   T E0;
   double t0, sig, om;
+  const T* U4d = nullptr;
 };
 
 template <class T> T pulse(const Model<T>& md, double t) {
@@ -396,9 +401,22 @@ template <class T> void fock(const Model<T>& md, double t, const Cx<T>* Lnn, Cx<
   const T e = pulse(md, t);
   for (int a = 0; a < M; ++a)
     for (int b = 0; b < M; ++b) eps[a * M + b] = Cx<T>(T(md.h0[a * M + b].re), T(md.h0[a * M + b].im));
-  for (int a = 0; a < M; ++a) {
-    eps[a * M + a].re = eps[a * M + a].re + e * T(md.v[a]) + md.U[a] * Lnn[a * M + a].im;
+  if (!md.U4d) {
+    for (int a = 0; a < M; ++a) {
+      eps[a * M + a].re = eps[a * M + a].re + e * T(md.v[a]) + md.U[a] * Lnn[a * M + a].im;
+    }
+    return;
   }
+  auto at = [M](int p, int q, int r, int s) { return ((p * M + q) * M + r) * M + s; };
+  for (int a = 0; a < M; ++a) eps[a * M + a].re = eps[a * M + a].re + e * T(md.v[a]);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      Cx<T> hf;
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b)
+          hf = hf + scale(md.U4d[at(i, a, b, j)] - T(2.0) * md.U4d[at(i, j, b, a)], Lnn[b * M + a]);
+      eps[i * M + j] = eps[i * M + j] + Cx<T>(-hf.im, hf.re);  // + i * hf
+    }
 }
 
 // Row of right-hand sides F^s(j,c) = -i ( eps(t_j) G^s(j,c) + I^s(j,c) ), c = 0..j
@@ -729,6 +747,58 @@ int orc_test_integrand(int M, int n, int l, const void* L, const void* R, const 
   Plane<double> G{M, (const C64*)L, (const C64*)R};
   SigmaRow<double> S{M, (const C64*)Sl, (const C64*)Sg};
   test_integrand(G, S, n, l, (C64*)u_out);
+  return 0;
+}
+
+// Fock matrix of Eq. (eps) at time t from the equal-time block Lnn = G^<(t,t):
+// eps [M][M].  U4 (M^4, U4[((i*M + a)*M + b)*M + j] = U_iabj) selects the
+// general tensor; NULL selects the local interaction U.
+int orc_fock(int M, double t, const double* h0, const double* U, const double* U4, const double* v,
+             const double* pulse4, const void* Lnn, void* eps) {
+  if (M < 1 || (!U && !U4)) return 1;
+  Model<double> md{M, (const C64*)h0, U, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  md.U4d = U4;
+  fock(md, t, (const C64*)Lnn, (C64*)eps);
+  return 0;
+}
+
+// Right-hand-side row j with the general tensor U4 in Eq. (SE) and Eq. (eps).
+int orc_rhs_row_u4(int M, int j, const double* t, const int* order, const double* h0, const double* U4,
+                   const double* v, const double* pulse4, const void* L, const void* R, void* F, int nthreads) {
+  if (M < 1 || j < 0 || nthreads < 1) return 1;
+  Model<double> md{M, (const C64*)h0, nullptr, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  md.U4d = U4;
+  Plane<double> G{M, (const C64*)L, (const C64*)R};
+  std::vector<C64> Sl((j + 1) * M * M), Sg((j + 1) * M * M), I(2 * (j + 1) * M * M);
+  sigma_row(G, U4, j, Sl.data(), Sg.data());
+  SigmaRow<double> S{M, Sl.data(), Sg.data()};
+  history_slice(G, S, t, order, j, I.data(), nthreads);
+  rhs_row(md, G, t, I.data(), j, (C64*)F);
+  return 0;
+}
+
+// orc_run / orc_run_adaptive with the general tensor U4 in Eq. (SE) and
+// Eq. (eps).  hord = NULL: the history quadrature uses the grid's orders;
+// otherwise as in orc_run_adaptive (K_sel 0..12).
+int orc_run_u4(int M, int n_start, int n_end, const double* t, const int* order, int* hord, int K_sel,
+               const double* h0, const double* U4, const double* v, const double* pulse4, int P, void* L, void* R,
+               const void* F_in, void* I_last, int nthreads) {
+  if (M < 1 || n_start < 1 || n_end < n_start || P < 1 || nthreads < 1 || K_sel < 0 || K_sel > 12) return 1;
+  if (!hord && K_sel != 0) return 1;
+  int K = 1;
+  for (int l = 1; l < n_end; ++l) if (order[l] > K) K = order[l];
+  Model<double> md{M, (const C64*)h0, nullptr, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  md.U4d = U4;
+  Ring<double> ring{M, n_end, K, std::vector<C64>((size_t)(K + 1) * 2 * n_end * M * M)};
+  const C64* f = (const C64*)F_in;
+  for (int j = (n_start - K > 0 ? n_start - K : 0); j <= n_start - 1; ++j) {
+    const size_t cnt = (size_t)2 * (j + 1) * M * M;
+    std::memcpy((void*)ring.row(j), f, cnt * sizeof(C64));
+    f += cnt;
+  }
+  for (int n = n_start; n < n_end; ++n)
+    kbe_step(md, t, order, n, P, U4, (C64*)L, (C64*)R, ring, (n == n_end - 1) ? (C64*)I_last : nullptr,
+             nthreads, hord, K_sel);
   return 0;
 }
 

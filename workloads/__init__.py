@@ -19,7 +19,13 @@ paper's own inputs are not available):
   * GOE one-body matrix: ``A_ij ~ N(0, 1/M)``, ``h = (A + A^T)/2``;
   * half filling: the lowest ``M//2`` eigenvectors of h occupied, per spin;
   * pulse: ``E(t) = E0 exp(-(t-t0)^2/(2 sigma^2)) cos(omega t)`` entering as
-    the site potential ``E(t) * (i - (M-1)/2)``.
+    the site potential ``E(t) * (i - (M-1)/2)``;
+  * dense Coulomb tensor (chemists' order, ``U[p,q,r,s] = (pq|rs)``, the
+    shape of quantum-chemistry integrals, which the paper takes from pyscf):
+    ``(pq|rs) = sum_k B^k_pq B^k_rs`` with symmetric ``B^k``, entries
+    ``N(0,1)`` symmetrised, scaled so that the mean of ``(pp|pp)`` is ``U``.
+    This has the 8-fold symmetry of real-orbital integrals and is positive
+    semidefinite as a matrix over orbital pairs.
 """
 import numpy as np
 
@@ -73,6 +79,17 @@ def goe_h(M, seed):
 
 def site_potential(M):
     return np.arange(M, dtype=np.float64) - (M - 1) / 2.0
+
+
+def coulomb_tensor(M, seed, U=1.0, rank=None):
+    """Real [M, M, M, M] tensor with the symmetries of Coulomb integrals."""
+    rng = np.random.default_rng(seed)
+    K = M * (M + 1) // 2 if rank is None else rank
+    B = rng.standard_normal((K, M, M))
+    B = (B + B.transpose(0, 2, 1)) / 2
+    T = np.einsum("kpq,krs->pqrs", B, B)
+    d = np.mean([T[p, p, p, p] for p in range(M)])
+    return T * (U / d)
 
 
 def half_filled_rho(h):
