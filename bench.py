@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-window", action="store_true", help="skip the differentiation form")
     ap.add_argument("--no-selfenergy", action="store_true", help="skip the whole-triangle self-energy timing")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the adaptive history-order run")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense-interaction self-energy and step")
     return ap.parse_args()
 
 
@@ -385,6 +386,52 @@ def sigma_bench(kbe, ctx, run, n_t, stream, reps=10):
             "note": "algorithmic bytes: L, R read and S^<, S^> written once (64 B per complex entry)"}
 
 
+def dense_bench(kbe, seed, stream, n_t=1024, norbs=(2, 8, 16, 32)):
+    """The self-energy of Eq. (SE) with a dense four-index interaction
+    (synthetic Coulomb tensors with the symmetries of real-orbital
+    integrals): row n = n_t-1 of random two-time data, one kernel per call.
+    Algorithmic work: 12 M^5 FP64 multiply-adds per block and component,
+    2 n_t (block, component) units per row."""
+    import torch
+    import workloads as W
+    out = {"kernel": "sigma_dense_kernel (FP64 DFMA)", "n": n_t - 1, "bound": "alu", "unit": "TFLOP/s",
+           "peak": round(FP64_PEAK_TFLOPS, 4), "rows": []}
+    n = n_t - 1
+    for M in norbs:
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(*W.grid(n_t, 0.02, 0.4, seed))
+        ctx.set_model(W.chain_h(M), np.ones(M), W.site_potential(M), None)
+        ctx.set_interaction(W.coulomb_tensor(M, seed, U=1.0))
+        Lr, Rr = W.random_rows(M, n, seed + M)
+        Rr[n] = -1j * np.eye(M)
+        L = torch.zeros((W.tri_size(n_t), M, M), dtype=torch.complex128, device="cuda")
+        R = torch.zeros_like(L)
+        L[W.tri_index(n, 0):] = torch.as_tensor(Lr, device="cuda")
+        R[W.tri_index(n, 0):] = torch.as_tensor(Rr, device="cuda")
+        Sl = torch.empty((n_t, M, M), dtype=torch.complex128, device="cuda")
+        Sg = torch.empty_like(Sl)
+        flops = 24.0 * M ** 5 * 2 * n_t
+        reps = max(2, min(20, int(2e11 / flops)))
+        for _ in range(2):
+            ctx.selfenergy_slice(n, L, R, Sl, Sg, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.selfenergy_slice(n, L, R, Sl, Sg, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        ms = e0.elapsed_time(e1) / reps
+        tf = flops / (ms * 1e-3) / 1e12
+        out["rows"].append({"norb": M, "ms": round(ms, 4), "achieved": round(tf, 4),
+                            "frac": round(tf / FP64_PEAK_TFLOPS, 4), "reps": reps})
+        del L, R, Sl, Sg
+        ctx.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def hbm_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -589,6 +636,20 @@ def main():
         line["differentiation_form"] = window_bench(kbe, args.seed, stream)
     if rank == 0 and not args.no_adaptive:
         line["adaptive_orders"] = adaptive_bench(kbe, args.seed, stream)
+    if rank == 0 and not args.no_dense:
+        import workloads as W
+        # the same chain and step with a dense Coulomb tensor in Eq. (SE) and Eq. (eps)
+        ctx.set_interaction(W.coulomb_tensor(M, args.seed, U=1.0))
+        steps_d = max(3, args.steps // 4)
+        ms_d, launches_d, _, _ = time_steps(ctx, run, n, args.P, steps_d, 2, stream)
+        ms_ds, _, _, _ = time_steps(ctx, run, n, args.P, steps_d, 2, stream, "split")
+        ctx.set_interaction(None)
+        dense = dense_bench(kbe, args.seed, stream, n + 1)
+        dense["step"] = {"workload": "%s with a dense synthetic Coulomb tensor (norb %d), row n=%d, P=%d"
+                                     % (WORKLOAD, M, n, args.P),
+                         "fp64_ms_per_step": round(ms_d / steps_d, 4), "split_ms_per_step": round(ms_ds / steps_d, 4),
+                         "local_fp64_ms_per_step": round(ms_step, 4), "gpu_launches": launches_d}
+        line["dense_interaction"] = dense
     ctx.close()
     del run
     torch.cuda.empty_cache()

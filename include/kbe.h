@@ -62,6 +62,7 @@ typedef int kbe_status;
 
 #define KBE_MAX_ORDER 12   /* largest per-interval quadrature order k      */
 #define KBE_RING_ROWS 13   /* right-hand-side rows kept by the stepper     */
+#define KBE_DENSE_MAX_NORB 32  /* largest norb for a dense interaction      */
 
 /* precision argument of kbe_history_slice / kbe_step */
 #define KBE_FP64 0        /* plain FP64 arithmetic, deterministic            */
@@ -126,10 +127,27 @@ kbe_status kbe_local_weights(const double* tau, int k, double lo, double hi, dou
 kbe_status kbe_set_model(kbe_ctx* ctx, const double* h0, const double* U, const double* v,
                          const double* pulse);
 
+/* General four-index interaction (Sec. 2, Eq. SE and Eq. eps) in place of
+ * the model's local U.  U4: host, M^4 real doubles, row-major
+ * U4[((i*M + f)*M + d)*M + e] = U_ifde (chemists' order for Coulomb
+ * integrals; no symmetry is assumed or used).  The self-energy becomes
+ *   Sigma^<>_ij(t,t') = U_ifde UEx_jabc G^<>_fb(t,t') G^<>_ea(t,t') G^><_cd(t',t),
+ *   UEx_jabc = 2 U_jbac - U_jabc,
+ * evaluated in FP64 with 12 M^5 multiply-adds per block and component, and
+ * the Fock matrix eps_ij = h_ij(t) + i (U_iabj - 2 U_ijba) G^<_ba(t,t).  The
+ * tensor is copied (3 M^4 doubles on the device, synchronously); the
+ * model's pulse and v stay in force and its U is unused.  U4 = NULL returns
+ * to the local U.  KBE_ERANGE for M > KBE_DENSE_MAX_NORB, KBE_EINVAL for
+ * non-finite entries.  With a dense interaction the reverse-mode calls that
+ * differentiate the self-energy or the Fock matrix (kbe_adjoint_selfenergy_
+ * slice, kbe_step_adjoint) and batches return KBE_ESTATE / KBE_EINVAL;
+ * kbe_adjoint_slice (the history contraction alone) is unaffected. */
+kbe_status kbe_set_interaction(kbe_ctx* ctx, const double* U4);
+
 /* ------------------------------------------------------- hot path ------ */
 
 /* Self-energy row n (Sec. 2, Eq. SE with the local interaction of the
- * model): for c = 0..n and every (a,b)
+ * model, or the tensor of kbe_set_interaction): for c = 0..n and every (a,b)
  *   S^>(n,c)_ab = -U_a U_b [G^>(n,c)_ab]^2 conj(G^<(n,c)_ab),
  *   S^<(n,c)_ab = -U_a U_b [G^<(n,c)_ab]^2 conj(G^>(n,c)_ab),
  * with G^< = L and G^> = R + L from row n.  (G^<>(t_c,t_n)_ba =
@@ -308,7 +326,8 @@ typedef struct kbe_batch kbe_batch;
  * and model already set (later kbe_set_grid / kbe_set_model calls on them
  * are not seen by the batch).  The contexts stay owned by the caller and
  * must outlive the batch; their workspaces are used by the batched calls,
- * so they must not run other calls concurrently. */
+ * so they must not run other calls concurrently.  Contexts with adaptive
+ * history orders or a dense interaction are KBE_EINVAL. */
 kbe_status kbe_batch_create(kbe_ctx* const* ctxs, int n_sys, kbe_batch** out);
 kbe_status kbe_batch_destroy(kbe_batch* b);
 const char* kbe_batch_last_error(const kbe_batch* b);

@@ -52,6 +52,7 @@ def lib():
         L.kbe_grid_weights.argtypes = [vp, vp, i, i, vp]
         L.kbe_local_weights.argtypes = [vp, i, d, d, vp]
         L.kbe_set_model.argtypes = [vp, vp, vp, vp, vp]
+        L.kbe_set_interaction.argtypes = [vp, vp]
         L.kbe_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_selfenergy_all.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_history_slice.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
@@ -208,6 +209,17 @@ class Context:
         p = np.array([0.0, 0.0, 1.0, 0.0]) if pulse is None else np.array(
             [pulse["E0"], pulse["t0"], pulse["sigma"], pulse["omega"]], np.float64)
         self._check(lib().kbe_set_model(self._h, _np_ptr(h0), _np_ptr(U), _np_ptr(v), _np_ptr(p)))
+
+    def set_interaction(self, U4):
+        """General real four-index interaction U4[i, f, d, e] = U_ifde for
+        Eq. (SE) and Eq. (eps); None returns to the model's local U."""
+        if U4 is None:
+            self._check(lib().kbe_set_interaction(self._h, None))
+            return
+        U4 = np.ascontiguousarray(U4, np.float64)
+        if U4.shape != (self.M,) * 4:
+            raise ValueError("U4 must have shape (M, M, M, M)")
+        self._check(lib().kbe_set_interaction(self._h, _np_ptr(U4)))
 
     def selfenergy_slice(self, n, L, R, Sl, Sg, stream=None):
         self._check(lib().kbe_selfenergy_slice(self._h, n, self._dev(L), self._dev(R), self._dev(Sl),

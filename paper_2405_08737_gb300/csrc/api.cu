@@ -42,6 +42,9 @@ void release(kbe_ctx* ctx) {
   cudaFree(ctx->d_planes);
   cudaFree(ctx->d_hist);
   cudaFree(ctx->d_korder);
+  cudaFree(ctx->d_Ut); cudaFree(ctx->d_Xt); cudaFree(ctx->d_HF);
+  ctx->d_Ut = ctx->d_Xt = ctx->d_HF = nullptr;
+  ctx->dense = false;
   ctx->d_hist = nullptr;
   ctx->d_korder = nullptr;
   ctx->d_planes = nullptr;
@@ -132,6 +135,17 @@ kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "history slice launch");
 }
 
+// Self-energy of n_blocks blocks from first_block (launch_sigma geometry),
+// with the context's interaction: the local U or the dense tensor.
+cudaError_t sigma_blocks(kbe_ctx* ctx, int64_t first_block, int64_t n_blocks, int64_t diag_rel, const void* L,
+                         const void* R, void* Sl, void* Sg, cudaStream_t s) {
+  if (ctx->dense)
+    return launch_sigma_dense(ctx->M, first_block, n_blocks, diag_rel, (const double*)L, (const double*)R,
+                              ctx->d_Ut, ctx->d_Xt, (double*)Sl, (double*)Sg, ctx->d_status, s);
+  return launch_sigma(ctx->M, first_block, n_blocks, diag_rel, (const double*)L, (const double*)R, ctx->d_U,
+                      (double*)Sl, (double*)Sg, ctx->d_status, s);
+}
+
 StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F) {
   const HostGrid& g = ctx->grid;
   StepArgs a{};
@@ -149,6 +163,7 @@ StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F
   a.I = (const double*)I;
   a.h0 = ctx->d_h0;
   a.U = ctx->d_U;
+  a.HF = ctx->dense ? ctx->d_HF : nullptr;
   a.v = ctx->d_v;
   a.eps = ctx->d_eps;
   a.corr = ctx->d_corr + (size_t)n * kMaxOrder * kWTab;
@@ -186,8 +201,7 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
   if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: predictor");
   for (int it = 0; it < P; ++it) {
     if ((e = keep(it)) != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: iterate copy");
-    e = launch_sigma(ctx->M, tri(n, 0), n + 1, n, (const double*)L, (const double*)R, ctx->d_U, (double*)Sl,
-                     (double*)Sg, ctx->d_status, s);
+    e = sigma_blocks(ctx, tri(n, 0), n + 1, n, L, R, Sl, Sg, s);
     *count_out = ++count;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: self-energy");
     if (ctx->adaptive_K > 0) {  // history order of interval n from this sweep's rows (Sec. 3.2)
@@ -395,6 +409,51 @@ kbe_status kbe_set_model(kbe_ctx* ctx, const double* h0, const double* U, const 
   return KBE_OK;
 }
 
+kbe_status kbe_set_interaction(kbe_ctx* ctx, const double* U4) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!U4) {
+    ctx->dense = false;
+    return KBE_OK;
+  }
+  const int M = ctx->M;
+  if (M > kDenseMaxM) return fail(ctx, KBE_ERANGE, "kbe_set_interaction: norb above KBE_DENSE_MAX_NORB");
+  const size_t M4 = (size_t)M * M * M * M;
+  for (size_t k = 0; k < M4; ++k)
+    if (!std::isfinite(U4[k])) return fail(ctx, KBE_EINVAL, "kbe_set_interaction: non-finite tensor entry");
+  kbe_status st = use_device(ctx);
+  if (st != KBE_OK) return st;
+  auto at = [M](int p, int q, int r, int t) { return (((size_t)p * M + q) * M + r) * M + t; };
+  std::vector<double> Ut(M4), Xt(M4), HF(M4);
+  for (int i = 0; i < M; ++i)
+    for (int f = 0; f < M; ++f)
+      for (int d = 0; d < M; ++d)
+        for (int e = 0; e < M; ++e) {
+          Ut[at(d, i, e, f)] = U4[at(i, f, d, e)];
+          // (j,a,b,c) := (i,f,d,e): UEx_jabc = 2 U_jbac - U_jabc, stored at [b][j][a][c]
+          Xt[at(d, i, f, e)] = 2.0 * U4[at(i, d, f, e)] - U4[at(i, f, d, e)];
+          // (i,j,b,a) := (i,f,d,e): HF[(i,j)][(b,a)] = U_iabj - 2 U_ijba
+          HF[at(i, f, d, e)] = U4[at(i, e, d, f)] - 2.0 * U4[at(i, f, d, e)];
+        }
+  cudaError_t e = cudaSuccess;
+  if (!ctx->d_Ut) {
+    if ((e = dev_alloc(&ctx->d_Ut, M4)) != cudaSuccess || (e = dev_alloc(&ctx->d_Xt, M4)) != cudaSuccess ||
+        (e = dev_alloc(&ctx->d_HF, M4)) != cudaSuccess) {
+      cudaFree(ctx->d_Ut); cudaFree(ctx->d_Xt); cudaFree(ctx->d_HF);
+      ctx->d_Ut = ctx->d_Xt = ctx->d_HF = nullptr;
+      cudaGetLastError();
+      return fail(ctx, e == cudaErrorMemoryAllocation ? KBE_ENOMEM : KBE_ECUDA, "kbe_set_interaction: allocation");
+    }
+  }
+  if ((e = cudaMemcpy(ctx->d_Ut, Ut.data(), M4 * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(ctx->d_Xt, Xt.data(), M4 * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(ctx->d_HF, HF.data(), M4 * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = dense_sigma_prepare(M)) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_set_interaction: upload");
+  ctx->dense = true;
+  return KBE_OK;
+}
+
 kbe_status kbe_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, const void* R, void* Sl, void* Sg,
                                 void* stream) {
   if (!ctx) return KBE_EINVAL;
@@ -405,8 +464,7 @@ kbe_status kbe_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, const void* 
   if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg))
     return fail(ctx, KBE_EINVAL, "kbe_selfenergy_slice: NULL or misaligned pointer");
   if ((st = use_device(ctx)) != KBE_OK) return st;
-  cudaError_t e = launch_sigma(ctx->M, tri(n, 0), n + 1, n, (const double*)L, (const double*)R, ctx->d_U,
-                               (double*)Sl, (double*)Sg, ctx->d_status, (cudaStream_t)stream);
+  cudaError_t e = sigma_blocks(ctx, tri(n, 0), n + 1, n, L, R, Sl, Sg, (cudaStream_t)stream);
   ctx->last_launches = 1;
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_selfenergy_slice");
 }
@@ -421,8 +479,7 @@ kbe_status kbe_selfenergy_all(kbe_ctx* ctx, int n_rows, const void* L, const voi
     return fail(ctx, KBE_EINVAL, "kbe_selfenergy_all: NULL or misaligned pointer");
   kbe_status st = use_device(ctx);
   if (st != KBE_OK) return st;
-  cudaError_t e = launch_sigma(ctx->M, 0, tri(n_rows, 0), -1, (const double*)L, (const double*)R, ctx->d_U,
-                               (double*)Sl, (double*)Sg, ctx->d_status, (cudaStream_t)stream);
+  cudaError_t e = sigma_blocks(ctx, 0, tri(n_rows, 0), -1, L, R, Sl, Sg, (cudaStream_t)stream);
   ctx->last_launches = 1;
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_selfenergy_all");
 }
@@ -454,8 +511,7 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
   if ((st = use_device(ctx)) != KBE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   int count = 0, nl = 0;
-  cudaError_t e = launch_sigma(ctx->M, tri(j, 0), j + 1, j, (const double*)L, (const double*)R, ctx->d_U,
-                               (double*)Sl, (double*)Sg, ctx->d_status, s);
+  cudaError_t e = sigma_blocks(ctx, tri(j, 0), j + 1, j, L, R, Sl, Sg, s);
   ++count;
   if (e != cudaSuccess) { ctx->last_launches = count; return cuda_fail(ctx, e, "kbe_rhs_row: self-energy"); }
   st = history(ctx, j, precision, L, R, Sl, Sg, I_work, s, &nl);
@@ -526,6 +582,7 @@ kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, cons
   kbe_status st = check_row_call(ctx, n);
   if (st != KBE_OK) return st;
   if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
+  if (ctx->dense) return fail(ctx, KBE_ESTATE, "kbe_adjoint_selfenergy_slice: needs the local interaction");
   if (!aligned16(L) || !aligned16(R) || !aligned16(dS_less) || !aligned16(dS_great) || !aligned16(dL_row) ||
       !aligned16(dR_row) || !dU || (reinterpret_cast<uintptr_t>(dU) & 7u))
     return fail(ctx, KBE_EINVAL, "kbe_adjoint_selfenergy_slice: NULL or misaligned pointer");
@@ -548,6 +605,7 @@ kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* 
       (reinterpret_cast<uintptr_t>(dU) & 7u) || (reinterpret_cast<uintptr_t>(dE0) & 7u))
     return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: NULL or misaligned pointer");
   if (!ctx->grid_set) return fail(ctx, KBE_ESTATE, "no grid: call kbe_set_grid first");
+  if (ctx->dense) return fail(ctx, KBE_ESTATE, "kbe_step_adjoint: needs the local interaction");
   if (n < 1 || n >= ctx->grid.n_t) return fail(ctx, KBE_ERANGE, "kbe_step_adjoint: n outside [1, n_t)");
   if (row_lo < 0 || row_lo > n) return fail(ctx, KBE_ERANGE, "kbe_step_adjoint: row_lo outside [0, n]");
   if (P < 1 || P > 16) return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: P outside [1, 16]");

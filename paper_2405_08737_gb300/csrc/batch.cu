@@ -99,6 +99,7 @@ __device__ __forceinline__ StepArgs step_of(const BatchSys& s, int* status) {
   a.I = s.I;
   a.h0 = s.h0;
   a.U = s.U;
+  a.HF = nullptr;  // batches hold local interactions only
   a.v = s.v;
   a.eps = s.eps;
   a.corr = s.corr + (int64_t)s.n * kMaxOrder * kWTab;
@@ -370,6 +371,8 @@ kbe_status kbe_batch_create(kbe_ctx* const* ctxs, int n_sys, kbe_batch** out) {
       return bfail(nullptr, KBE_ESTATE, "kbe_batch_create: every context needs its grid and model set");
     if (c->adaptive_K > 0)
       return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: batched steps use the grids' history orders");
+    if (c->dense)
+      return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: batched steps use the local interaction");
     if (dev0 < 0) dev0 = c->device;
     if (c->device != dev0) return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: contexts on different devices");
   }

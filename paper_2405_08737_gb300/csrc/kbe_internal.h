@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -15,6 +16,7 @@ constexpr int kRing = KBE_RING_ROWS;
 constexpr int kMaxNorb = 64;
 constexpr int kMaxSplit = 16;      // largest split of the history index m
 constexpr int kWTab = kMaxOrder + 1;  // row stride of the stepper weight tables
+constexpr int kDenseMaxM = KBE_DENSE_MAX_NORB;  // largest norb of the dense-interaction self-energy
 
 __host__ __device__ inline int64_t tri(int64_t r, int64_t c) { return r * (r + 1) / 2 + c; }
 
@@ -116,6 +118,11 @@ struct kbe_ctx {
   int adaptive_rows = 0;      // band rows 0 .. adaptive_rows-1 are set
   double* d_hist = nullptr;   // local weights of every order per interval [n_max][kMaxOrder][kWTab]
   int* d_korder = nullptr;    // chosen history order per interval [n_max]
+  // general four-index interaction (Eq. SE, Eq. eps); unset: the local U
+  bool dense = false;
+  double* d_Ut = nullptr;     // [d][i][e][f] = U_ifde
+  double* d_Xt = nullptr;     // [b][j][a][c] = UEx_jabc = 2 U_jbac - U_jabc
+  double* d_HF = nullptr;     // [(i,j)][(b,a)] = U_iabj - 2 U_ijba (Fock matrix)
   // measurement: event pairs around each contraction kernel
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -127,6 +134,26 @@ namespace kbe {
 // ---- launchers (each returns cudaGetLastError() after the launch) -------
 cudaError_t launch_sigma(int M, int64_t first_block, int64_t n_blocks, int64_t diag_rel, const double* L,
                          const double* R, const double* U, double* Sl, double* Sg, int* status, cudaStream_t s);
+
+// Dense-interaction self-energy (sigma_dense.cu): same launch geometry as
+// launch_sigma; Ut, Xt are the reordered tensors of the context.
+struct DenseSigmaArgs {
+  int M;
+  int64_t first_block, n_blocks, diag_rel;
+  const double2* L;   // block first_block of the triangles
+  const double2* R;
+  const double* Ut;
+  const double* Xt;
+  double2* Sl;        // outputs, relative block index
+  double2* Sg;
+  int* status;
+  int g, g3;          // pairs per tile, accumulator groups
+};
+cudaError_t launch_sigma_dense(int M, int64_t first_block, int64_t n_blocks, int64_t diag_rel, const double* L,
+                               const double* R, const double* Ut, const double* Xt, double* Sl, double* Sg,
+                               int* status, cudaStream_t s);
+cudaError_t dense_sigma_prepare(int M);  // shared-memory opt-in, outside stream capture
+size_t dense_sigma_smem(int M);
 
 struct HistoryArgs {
   int M, n;
@@ -189,6 +216,7 @@ struct StepArgs {
   const double* I;   // [2][n+1][M][M]
   const double* h0;
   const double* U;
+  const double* HF;    // dense Fock tensor [(i,j)][(b,a)] or NULL for the local U
   const double* v;
   double* eps;
   const double* corr;  // weights of interval n: [kMaxOrder][kWTab]

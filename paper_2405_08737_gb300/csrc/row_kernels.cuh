@@ -234,7 +234,20 @@ __device__ __forceinline__ void fock_entry(const StepArgs& a, int ab) {
   const double* Lnn = a.L + tri(a.n, a.n) * MM * 2;
   const int i = ab / M, j = ab - i * M;
   double2 e = ldd(a.h0 + 2 * ab);
-  if (i == j) e.x += a.field * a.v[i] + a.U[i] * Lnn[2 * ab + 1];
+  if (!a.HF) {
+    if (i == j) e.x += a.field * a.v[i] + a.U[i] * Lnn[2 * ab + 1];
+  } else {
+    // Eq. (eps): eps_ij = h_ij(t) + i sum_ba (U_iabj - 2 U_ijba) G^<_ba(t,t)
+    if (i == j) e.x += a.field * a.v[i];
+    const double* hf = a.HF + (int64_t)ab * MM;
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < MM; ++k) {
+      sr = fma(hf[k], Lnn[2 * k], sr);
+      si = fma(hf[k], Lnn[2 * k + 1], si);
+    }
+    e.x -= si;
+    e.y += sr;
+  }
   std2(a.eps + 2 * ab, e);
 }
 
