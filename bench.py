@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-selfenergy", action="store_true", help="skip the whole-triangle self-energy timing")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the adaptive history-order run")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-interaction self-energy and step")
+    ap.add_argument("--dense-norb", default="2,8,16,32",
+                    help="comma-separated orbital counts of the dense self-energy rows")
     return ap.parse_args()
 
 
@@ -644,7 +646,7 @@ def main():
         ms_d, launches_d, _, _ = time_steps(ctx, run, n, args.P, steps_d, 2, stream)
         ms_ds, _, _, _ = time_steps(ctx, run, n, args.P, steps_d, 2, stream, "split")
         ctx.set_interaction(None)
-        dense = dense_bench(kbe, args.seed, stream, n + 1)
+        dense = dense_bench(kbe, args.seed, stream, n + 1, [int(x) for x in args.dense_norb.split(",") if x])
         dense["step"] = {"workload": "%s with a dense synthetic Coulomb tensor (norb %d), row n=%d, P=%d"
                                      % (WORKLOAD, M, n, args.P),
                          "fp64_ms_per_step": round(ms_d / steps_d, 4), "split_ms_per_step": round(ms_ds / steps_d, 4),
