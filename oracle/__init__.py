@@ -335,3 +335,52 @@ def initial_rhs(t, order, h0, U, v, pulse, rho0, U4=None):
     R0 = (-1j * np.eye(M)).reshape(1, M, M).astype(np.complex128)
     F0 = rhs_row(0, t, order, h0, U, v, pulse, L0, R0, U4=U4)
     return L0, R0, F0
+
+def run_controlled(h0, U, v, pulse, rho0, rtol, atol, dt0, t_end, n_max, q_max=12, k_hist=5, K_sel=0,
+                   h_max=0.0, U4=None):
+    """Adaptive time stepping of Sec. 3.1 from the uncorrelated state rho0
+    (L(0,0) = i rho0, R(0,0) = -i): variable-step, variable-order Adams
+    (orders 1..q_max) with fixed-point iteration, WRMS error control
+    (rtol, atol), step dt0 to start, history orders k_hist per interval (or
+    chosen up to K_sel, Sec. 3.2).  Returns a dict with the accepted grid
+    ``t``, step orders ``q``, history orders ``korder``, triangles ``L``,
+    ``R`` of the accepted rows, ``stats`` = (steps, error-test failures,
+    convergence failures, right-hand-side evaluations, reconstructed blocks)
+    and the run ``status`` (0 reached t_end, 1 storage full, 2 failure)."""
+    h0 = _c128(h0)
+    M = h0.shape[0]
+    v = _f64(v)
+    Uv = _f64(U if U is not None else np.zeros(M))
+    U4p = _p(_f64(U4)) if U4 is not None else None
+    L = np.zeros((_tri_size(n_max), M, M), np.complex128)
+    R = np.zeros_like(L)
+    L[0] = 1j * _c128(rho0)
+    R[0] = -1j * np.eye(M)
+    t = np.zeros(n_max)
+    q = np.zeros(n_max, np.int32)
+    ko = np.zeros(n_max, np.int32)
+    n_rows = ctypes.c_int()
+    stats = np.zeros(5, np.int32)
+    opts = _f64([rtol, atol, dt0, h_max, t_end])
+    iopts = _i32([q_max, k_hist, K_sel, n_max])
+    rc = lib().orc_run_controlled(ctypes.c_int(M), _p(opts), _p(iopts), _p(h0), _p(Uv), U4p, _p(v),
+                                  _p(_pulse4(pulse)), _p(L), _p(R), _p(t), _p(q), _p(ko), ctypes.byref(n_rows),
+                                  _p(stats))
+    if rc < 0:
+        raise RuntimeError("oracle run_controlled: invalid arguments")
+    n = n_rows.value
+    return {"t": t[:n], "q": q[:n], "korder": ko[:n], "L": L[:_tri_size(n)], "R": R[:_tri_size(n)],
+            "stats": tuple(int(x) for x in stats), "status": int(rc), "n": n}
+
+
+def adams_error_integrals(t, n, q):
+    """(E_p, E_c, C) of the order-q Adams pair at step n (without 1/q!)."""
+    out = np.zeros(3)
+    _check(lib().orc_adams_error_integrals(_p(_f64(t)), ctypes.c_int(n), ctypes.c_int(q), _p(out)),
+           "adams_error_integrals")
+    return tuple(out)
+
+
+def _tri_size(n):
+    return n * (n + 1) // 2
+

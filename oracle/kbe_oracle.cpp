@@ -36,6 +36,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -557,6 +558,314 @@ std::vector<T> local_U4(int M, const T* U) {
   return U4;
 }
 
+
+// ------------------------------------------------- adaptive time stepping --
+// Sec. 3.1: variable-step, variable-order Adams methods (orders q = 1..12)
+// on the growing grid, written in integral form.  With derivative data
+// f_j at the grid points,
+//   predictor  y_n(0) = y_{n-1} + int_{t_{n-1}}^{t_n} P,  P interpolating f at t_{n-1..n-q},
+//   corrector  y_n    = y_{n-1} + int_{t_{n-1}}^{t_n} Q,  Q interpolating f at t_{n..n-q+1},
+// which is the polynomial pair pi_{n-1}, pi_n of Eq. (predictor) and
+// Eq. (corrector) (the Nordsieck array represents the same polynomials).
+// The state of step n is row n: G^<(t_n,t_c) for c <= n (the diagonal
+// evolves with D = F^< - F^<^+) and G^>(t_n,t_c) for c < n.  The component
+// of column c = n-1 starts from the diagonal value G(t_{n-1},t_{n-1}), and
+// its derivative data at t_j < t_c are the right-hand sides of Eq. (KBE2)
+// at points above the diagonal, evaluated once row c is accepted (the
+// history reconstruction of Sec. 3.1 and Sec. 4).
+//   Fixed point: y(m) = corrector with f(t_n, y(m-1)); stop when
+//     R ||y(m) - y(m-1)||_wrms < 0.1 / |C|   (R = max(0.3 R, ratio), R = 1 at m = 1),
+//     at most 3 iterations, divergence when the change more than doubles.
+//   Local error: LTE = C (y_n - y_n(0)), C = E_c / (E_p - E_c) with the
+//     error integrals E_p = int prod_{i=1..q} (t - t_{n-i}), E_c = int prod_{i=0..q-1} (t - t_{n-i})
+//     (Milne's device); the step passes when ||LTE||_wrms <= 1.
+//   Weights: w_j = 1 / (rtol |y_{n-1,j}| + atol), complex modulus, N complex components.
+//   Orders q-1 and q+1 (Sec. 3.1; considered after q+1 steps at order q):
+//     LTE(q') = int prod_{i=0..q'-1} (t - t_{n-i}) * f[t_n, ..., t_{n-q'}]  (divided difference).
+//   Step factors eta = 1 / ((b ||LTE||)^{1/(q'+1)} + 1e-6), b = 6 (q-1, q), 10 (q+1); the
+//   largest wins (ties keep q); eta < 1.5 keeps h; growth at most 1e4 on the first step,
+//   10 later and none right after a failed attempt.  Error-test failure: h *= max(0.1,
+//   min(0.9, eta_q)); from the third failure of a step on, q = 1 and h *= 0.1.
+//   Convergence failure: h *= 0.25.
+struct CtlOpts {
+  double rtol, atol, h0, h_max, t_end;
+  int q_max, k_hist, K_sel, n_max;
+};
+
+// integral over [t_{n-1}, t_n] of prod_{i in nodes} (t - t_i)
+double node_poly_integral(const double* t, int n, const int* nodes, int cnt) {
+  const int q = 12;
+  double gx[q], gw[q];
+  gauss_legendre(q, gx, gw);
+  const double lo = t[n - 1], hi = t[n], mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+  double s = 0.0;
+  for (int g = 0; g < q; ++g) {
+    const double x = mid + half * gx[g];
+    double p = 1.0;
+    for (int i = 0; i < cnt; ++i) p *= x - t[nodes[i]];
+    s += gw[g] * p;
+  }
+  return half * s;
+}
+
+// Milne constant C = E_c / (E_p - E_c) of the order-q pair at step n.
+double milne_constant(const double* t, int n, int q) {
+  int np[13], nc[13];
+  for (int i = 1; i <= q; ++i) np[i - 1] = n - i;
+  for (int i = 0; i < q; ++i) nc[i] = n - i;
+  const double Ep = node_poly_integral(t, n, np, q), Ec = node_poly_integral(t, n, nc, q);
+  return Ec / (Ep - Ec);
+}
+
+struct CtlState {
+  int M;
+  std::vector<double> t;
+  std::vector<int> korder, qused;
+  C64* L;
+  C64* R;
+  std::vector<std::vector<C64>> Fb;                 // row j: [2][j+1][M*M]
+  std::vector<std::map<int, std::vector<C64>>> Fa;  // row j: column c > j -> [2][M*M]
+  std::vector<std::vector<C64>> Sl, Sg;             // self-energy rows of accepted rows
+  int nfev = 0, nrecon = 0;
+  C64 F(int s, int j, int c, int a, int b) const {
+    const int MM = M * M;
+    if (c <= j) return Fb[j][((size_t)s * (j + 1) + c) * MM + a * M + b];
+    return Fa[j].at(c)[(size_t)s * MM + a * M + b];
+  }
+  // derivative of the component (s, c) of the row-n state at t_j
+  C64 deriv(int s, int j, int c, int n, int a, int b) const {
+    if (s == 0 && c == n) return F(0, j, j, a, b) - conj(F(0, j, j, b, a));  // diagonal: D(j)
+    return F(s, j, c, a, b);
+  }
+};
+
+// Value of component (s, c) of row r (c <= r; the greater diagonal is fixed).
+inline C64 comp_value(const Plane<double>& G, int s, int r, int c, int a, int b) {
+  return s == 0 ? G.less(r, c, a, b) : G.great(r, c, a, b);
+}
+
+// Eq. (KBE2) right-hand side at the point (t_j, t_c) above the diagonal
+// (j < c, rows up to c accepted):
+//   I^s(j,c) = sum_{m<=j} w_{j,m} Sigma^R(j,m) G^s(m,c) + sum_{m<=c} w_{c,m} Sigma^s(j,m) G^A(m,c),
+//   F^s(j,c) = -i (eps(t_j) G^s(j,c) + I^s(j,c)),
+// with Sigma^s(j,m) = -Sigma^s(m,j)^+ for m > j.
+void rhs_above(const Model<double>& md, const Plane<double>& G, CtlState& st, int j, int c, C64* out) {
+  const int M = st.M, MM = M * M;
+  std::vector<double> wj(j + 1), wc(c + 1);
+  composite_row(st.t.data(), st.korder.data(), j, wj.data());
+  composite_row(st.t.data(), st.korder.data(), c, wc.data());
+  auto sig = [&](int s, int r, int m, int a, int b) -> C64 {  // Sigma^s(t_r, t_m)
+    const auto& S = s == 0 ? st.Sl : st.Sg;
+    if (m <= r) return S[r][(size_t)m * MM + a * M + b];
+    return -conj(S[m][(size_t)r * MM + b * M + a]);
+  };
+  std::vector<C64> eps(MM);
+  fock(md, st.t[j], G.L + tri(j, j) * MM, eps.data());
+  for (int s = 0; s < 2; ++s)
+    for (int a = 0; a < M; ++a)
+      for (int b = 0; b < M; ++b) {
+        Acc<double> acc;
+        for (int m = 0; m <= j; ++m)
+          for (int x = 0; x < M; ++x)
+            acc.add(scale(wj[m], (sig(1, j, m, a, x) - sig(0, j, m, a, x)) * G.get(s, m, c, x, b)));
+        for (int m = 0; m <= c; ++m)
+          for (int x = 0; x < M; ++x) acc.add(scale(wc[m], sig(s, j, m, a, x) * G.adv(m, c, x, b)));
+        C64 v = acc.get();
+        for (int x = 0; x < M; ++x) v = v + eps[a * M + x] * G.get(s, j, c, x, b);
+        out[(size_t)s * MM + a * M + b] = mul_mi(v);
+      }
+  ++st.nrecon;
+}
+
+// WRMS norm over the components of row n of v(s, c, a, b) with weights
+// w(s, c, a, b): lesser c <= n, greater c < n; N = (2n+1) M^2 complex entries.
+template <class Fn, class Wn>
+double wrms(int M, int n, Fn v, Wn w) {
+  double s = 0.0;
+  for (int sc = 0; sc < 2; ++sc)
+    for (int c = 0; c <= n - sc; ++c)
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+          const C64 x = v(sc, c, a, b);
+          const double ww = w(sc, c, a, b);
+          s += (x.re * x.re + x.im * x.im) * ww * ww;
+        }
+  return std::sqrt(s / ((2.0 * n + 1.0) * M * M));
+}
+
+// Returns 0 on success (t_end reached), 1 when n_max rows are full first,
+// 2 when a step fails too often.
+int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, CtlState& st, int* n_out,
+                   int* stats) {
+  const int M = md.M, MM = M * M;
+  Plane<double> G{M, st.L, st.R};
+  auto f_eval = [&](int n) {
+    std::vector<C64> Sl((n + 1) * MM), Sg((n + 1) * MM), I(2 * (n + 1) * MM);
+    sigma_row(G, U4, n, Sl.data(), Sg.data());
+    SigmaRow<double> S{M, Sl.data(), Sg.data()};
+    if (o.K_sel > 0) st.korder[n] = select_history_order(G, S, st.t.data(), n, o.K_sel);
+    history_slice(G, S, st.t.data(), st.korder.data(), n, I.data(), 1);
+    st.Fb[n].assign(2 * (n + 1) * MM, C64());
+    rhs_row(md, G, st.t.data(), I.data(), n, st.Fb[n].data());
+    ++st.nfev;
+  };
+  auto store_sigma = [&](int n) {
+    st.Sl[n].assign((n + 1) * MM, C64());
+    st.Sg[n].assign((n + 1) * MM, C64());
+    sigma_row(G, U4, n, st.Sl[n].data(), st.Sg[n].data());
+  };
+  auto finish = [&](int n, int n_err, int n_conv, int rc) {
+    *n_out = n;
+    stats[0] = n - 1; stats[1] = n_err; stats[2] = n_conv; stats[3] = st.nfev;
+    return rc;
+  };
+  st.korder[0] = 0;
+  f_eval(0);
+  store_sigma(0);
+  double h = o.h0, eta_max = 1e4;
+  int q = 1, qsteps = 0, n = 1, n_err = 0, n_conv = 0;
+  std::vector<C64> ypred, yprev, ycur, ynew;
+  double wp[16], wc[16];
+  while (st.t[n - 1] < o.t_end * (1.0 - 1e-14)) {
+    if (n >= o.n_max) return finish(n, n_err, n_conv, 1);
+    int nef = 0, ncf = 0;
+    bool failed = false;
+    double E = 0.0, Cm = 0.0;
+    for (;;) {  // attempts of step n
+      if (o.h_max > 0.0 && h > o.h_max) h = o.h_max;
+      if (st.t[n - 1] + h > o.t_end) h = o.t_end - st.t[n - 1];
+      if (q > n) q = n;
+      st.t[n] = st.t[n - 1] + h;
+      st.korder[n] = o.k_hist;
+      span_weights(st.t.data(), n - q, n - 1, n, wp);      // nodes t_{n-q} .. t_{n-1}
+      span_weights(st.t.data(), n - q + 1, n, n, wc);      // nodes t_{n-q+1} .. t_n
+      Cm = milne_constant(st.t.data(), n, q);
+      const size_t cnt = (size_t)2 * (n + 1) * MM;          // [s][c][a][b], c <= n
+      ypred.assign(cnt, C64()); yprev.assign(cnt, C64());
+      auto at = [&](int s, int c, int a, int b) { return (((size_t)s * (n + 1) + c) * M + a) * M + b; };
+      for (int s = 0; s < 2; ++s)
+        for (int c = 0; c <= n - s; ++c)
+          for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b) {
+              // previous value from row n-1; column n-1 and the diagonal start from G(t_{n-1},t_{n-1})
+              const C64 y0 = comp_value(G, s, n - 1, std::min(c, n - 1), a, b);
+              C64 y = y0;
+              for (int i = 0; i < q; ++i) y = y + scale(wp[i], st.deriv(s, n - q + i, c, n, a, b));
+              yprev[at(s, c, a, b)] = y0;
+              ypred[at(s, c, a, b)] = y;
+            }
+      auto weight = [&](int s, int c, int a, int b) {
+        const C64 y = yprev[at(s, c, a, b)];
+        return 1.0 / (o.rtol * std::sqrt(y.re * y.re + y.im * y.im) + o.atol);
+      };
+      auto commit = [&](const std::vector<C64>& y) {
+        for (int c = 0; c <= n; ++c)
+          for (int k = 0; k < MM; ++k) {
+            const C64 l = y[at(0, c, k / M, k % M)];
+            st.L[tri(n, c) * MM + k] = l;
+            if (c < n) st.R[tri(n, c) * MM + k] = y[at(1, c, k / M, k % M)] - l;
+            else st.R[tri(n, c) * MM + k] = (k / M == k % M) ? C64(0.0, -1.0) : C64();
+          }
+      };
+      commit(ypred);
+      ycur = ypred;
+      bool conv = false;
+      double Rr = 1.0, dprev = 0.0;
+      for (int m = 1; m <= 3; ++m) {
+        f_eval(n);
+        ynew.assign(cnt, C64());
+        for (int s = 0; s < 2; ++s)
+          for (int c = 0; c <= n - s; ++c)
+            for (int a = 0; a < M; ++a)
+              for (int b = 0; b < M; ++b) {
+                C64 y = yprev[at(s, c, a, b)];
+                for (int i = 0; i < q; ++i) y = y + scale(wc[i], st.deriv(s, n - q + 1 + i, c, n, a, b));
+                ynew[at(s, c, a, b)] = y;
+              }
+        const double d = wrms(M, n, [&](int s, int c, int a, int b) {
+          return ynew[at(s, c, a, b)] - ycur[at(s, c, a, b)]; }, weight);
+        if (m > 1) Rr = std::max(0.3 * Rr, d / dprev);
+        commit(ynew);
+        ycur = ynew;
+        if (Rr * d * std::fabs(Cm) < 0.1) { conv = true; break; }
+        if (m > 1 && d > 2.0 * dprev) break;
+        dprev = d;
+      }
+      if (!conv) {
+        ++n_conv; ++ncf; failed = true;
+        if (ncf > 10) return finish(n, n_err, n_conv, 2);
+        h *= 0.25;
+        continue;
+      }
+      E = std::fabs(Cm) * wrms(M, n, [&](int s, int c, int a, int b) {
+        return ycur[at(s, c, a, b)] - ypred[at(s, c, a, b)]; }, weight);
+      if (E > 1.0) {
+        ++n_err; ++nef; failed = true;
+        if (nef > 7) return finish(n, n_err, n_conv, 2);
+        if (nef >= 3) { q = 1; qsteps = 0; h *= 0.1; continue; }
+        const double eta = 1.0 / (std::pow(6.0 * E, 1.0 / (q + 1)) + 1e-6);
+        h *= std::max(0.1, std::min(0.9, eta));
+        continue;
+      }
+      break;
+    }
+    // accepted: self-energy of the accepted row, then the derivative data of
+    // column n above the diagonal
+    st.qused[n] = q;
+    store_sigma(n);
+    const int jlo = std::max(0, n - std::min(q + 1, 12));
+    for (int j = jlo; j < n; ++j) {
+      std::vector<C64> blk(2 * MM);
+      rhs_above(md, G, st, j, n, blk.data());
+      st.Fa[j][n] = blk;
+    }
+    // next step size and order
+    ++qsteps;
+    const double addon = 1e-6;
+    double eta = E > 0.0 ? 1.0 / (std::pow(6.0 * E, 1.0 / (q + 1)) + addon) : eta_max;
+    int qn = q;
+    if (qsteps > q) {
+      auto divdiff_est = [&](int qq) {  // |int prod_{i<qq} (t - t_{n-i})| * ||f[t_n .. t_{n-qq}]||
+        int nodes[14];
+        for (int i = 0; i < qq; ++i) nodes[i] = n - i;
+        const double P = std::fabs(node_poly_integral(st.t.data(), n, nodes, qq));
+        double alpha[14];
+        for (int i = 0; i <= qq; ++i) {
+          double d = 1.0;
+          for (int k = 0; k <= qq; ++k)
+            if (k != i) d *= st.t[n - i] - st.t[n - k];
+          alpha[i] = 1.0 / d;
+        }
+        auto w = [&](int s, int c, int a, int b) {
+          const C64 y = yprev[(((size_t)s * (n + 1) + c) * M + a) * M + b];
+          return 1.0 / (o.rtol * std::sqrt(y.re * y.re + y.im * y.im) + o.atol);
+        };
+        return P * wrms(M, n, [&](int s, int c, int a, int b) {
+          C64 v;
+          for (int i = 0; i <= qq; ++i) v = v + scale(alpha[i], st.deriv(s, n - i, c, n, a, b));
+          return v; }, w);
+      };
+      if (q > 1) {
+        const double Eq = divdiff_est(q - 1);
+        const double e2 = Eq > 0.0 ? 1.0 / (std::pow(6.0 * Eq, 1.0 / q) + addon) : eta_max;
+        if (e2 > eta) { eta = e2; qn = q - 1; }
+      }
+      if (q < o.q_max && n - q - 1 >= 0) {
+        const double Eq = divdiff_est(q + 1);
+        const double e2 = Eq > 0.0 ? 1.0 / (std::pow(10.0 * Eq, 1.0 / (q + 2)) + addon) : eta_max;
+        if (e2 > eta) { eta = e2; qn = q + 1; }
+      }
+    }
+    if (qn != q) { q = qn; qsteps = 0; }
+    if (eta < 1.5) eta = 1.0;
+    else eta = std::min(eta, failed ? 1.0 : eta_max);
+    h *= eta;
+    eta_max = 10.0;
+    ++n;
+  }
+  return finish(n, n_err, n_conv, 0);
+}
+
 }  // namespace
 
 // =================================================================== C ABI ==
@@ -799,6 +1108,59 @@ int orc_run_u4(int M, int n_start, int n_end, const double* t, const int* order,
   for (int n = n_start; n < n_end; ++n)
     kbe_step(md, t, order, n, P, U4, (C64*)L, (C64*)R, ring, (n == n_end - 1) ? (C64*)I_last : nullptr,
              nthreads, hord, K_sel);
+  return 0;
+}
+
+// Adaptive time stepping (Sec. 3.1) from row 0 (L, R hold L(0,0), R(0,0)):
+// opts = {rtol, atol, h0, h_max, t_end}, iopts = {q_max, k_hist, K_sel, n_max}.
+// U4 = NULL selects the local interaction U.  Outputs: the triangles of the
+// accepted rows (n_max rows of storage), t[0..n_max-1], q[n] (order of step
+// n), korder[n] (history order of interval n), n_rows (accepted rows
+// including row 0), stats = {steps, error-test failures, convergence
+// failures, right-hand-side evaluations, reconstructed blocks}.
+// Returns the run status (0 reached t_end, 1 storage full, 2 step failure).
+int orc_run_controlled(int M, const double* opts, const int* iopts, const double* h0, const double* U,
+                       const double* U4, const double* v, const double* pulse4, void* L, void* R, double* t,
+                       int* q, int* korder, int* n_rows, int* stats) {
+  if (M < 1) return -1;
+  CtlOpts o{opts[0], opts[1], opts[2], opts[3], opts[4], iopts[0], iopts[1], iopts[2], iopts[3]};
+  if (o.q_max < 1 || o.q_max > 12 || o.n_max < 2 || o.k_hist < 1 || o.k_hist > 12 || o.K_sel < 0 ||
+      o.K_sel > 12 || !(o.h0 > 0.0) || !(o.rtol >= 0.0) || !(o.atol > 0.0))
+    return -1;
+  std::vector<double> U4loc;
+  if (!U4) { U4loc = local_U4(M, U); U4 = U4loc.data(); }
+  Model<double> md{M, (const C64*)h0, U, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  if (U4loc.empty()) md.U4d = U4;
+  CtlState st;
+  st.M = M;
+  st.t.assign(o.n_max, 0.0);
+  st.korder.assign(o.n_max, 0);
+  st.qused.assign(o.n_max, 0);
+  st.L = (C64*)L;
+  st.R = (C64*)R;
+  st.Fb.resize(o.n_max);
+  st.Fa.resize(o.n_max);
+  st.Sl.resize(o.n_max);
+  st.Sg.resize(o.n_max);
+  int n_out = 0, st5[4] = {0, 0, 0, 0};
+  const int rc = run_controlled(md, U4, o, st, &n_out, st5);
+  for (int i = 0; i < o.n_max; ++i) { t[i] = st.t[i]; q[i] = st.qused[i]; korder[i] = st.korder[i]; }
+  *n_rows = n_out;
+  for (int i = 0; i < 4; ++i) stats[i] = st5[i];
+  stats[4] = st.nrecon;
+  return rc;
+}
+
+// Error integrals of the order-q Adams pair at step n on the nodes t:
+// out = {E_p, E_c} (without the 1/q! factor) and the Milne constant.
+int orc_adams_error_integrals(const double* t, int n, int q, double* out) {
+  if (q < 1 || q > 12 || n < q) return 1;
+  int np[13], nc[13];
+  for (int i = 1; i <= q; ++i) np[i - 1] = n - i;
+  for (int i = 0; i < q; ++i) nc[i] = n - i;
+  out[0] = node_poly_integral(t, n, np, q);
+  out[1] = node_poly_integral(t, n, nc, q);
+  out[2] = milne_constant(t, n, q);
   return 0;
 }
 
