@@ -293,6 +293,54 @@ kbe_status kbe_set_adaptive_orders(kbe_ctx* ctx, int K);
  * in adaptive mode (synchronises the device), else min(order[l], l). */
 kbe_status kbe_get_history_orders(kbe_ctx* ctx, int* orders, int n);
 
+/* Adaptive time stepping (Sec. 3.1): from row 0 (L(0,0) = i rho(0),
+ * R(0,0) = -i, set by the caller) to t_end, the run chooses its own grid.
+ * Step n takes variable-step Adams formulas of order q (1..q_max) in
+ * integral form on the accepted points: the predictor integrates the
+ * interpolant of the derivative data at t_{n-1..n-q}, the corrector the one
+ * at t_{n..n-q+1} (Eq. predictor, Eq. corrector).  The corrector is iterated
+ * with the right-hand side of Eq. (KBE2) evaluated on the device (self-
+ * energy, history slice in the given precision, Fock matrix) until
+ * R ||dy||_wrms < 0.1 / |C| (Eq. wrms_norm with the weights of Eq. ewt,
+ * complex modulus; at most 3 iterations; R the estimated contraction rate).
+ * The local error C (y_n - y_n(0)), with C = E_c / (E_p - E_c) from the
+ * error integrals of the two formulas, must have WRMS norm <= 1, else the
+ * step is retried smaller.  After q+1 steps at order q the orders q-1 and
+ * q+1 are weighed by error estimates from divided differences of the
+ * derivative data.  Step factors 1 / ((b E)^(1/(q+1)) + 1e-6) (b = 6, 6, 10
+ * for q-1, q, q+1) pick the next step and order, with CVODE's safeguards:
+ * no change below a factor 1.5, growth at most 1e4 on the first step, 10
+ * later and none right after a failure; a failed error test shrinks the
+ * step by 0.1..0.9 and the third one of a step falls back to order 1 with a
+ * factor 0.1; a failed iteration shrinks it by 0.25.  When a step is
+ * accepted, the derivative data of the new column at the last q+1 earlier
+ * times are evaluated above the diagonal (the history reconstruction of
+ * Sec. 3.1): Eq. (KBE2) at (t_j, t_n), j < n.  History quadrature: order
+ * k_hist on every interval, or chosen per interval up to K_sel (Sec. 3.2,
+ * as with kbe_set_adaptive_orders) when K_sel > 0.
+ *   opts (host double[5]) = {rtol >= 0, atol > 0, h0 > 0 (first step),
+ *                           h_max >= 0 (0: unbounded), t_end > 0};
+ *   iopts (host int[4]) = {q_max 1..12, k_hist 1..12, K_sel 0..12, precision};
+ *   L, R: device triangles of n_max rows; S_less, S_great: device rows
+ *   [n_max][M][M]; I_work [2][n_max][M][M]; F_ring
+ *   [KBE_RING_ROWS][2][n_max][M][M] (the layouts of kbe_step);
+ *   t_out (double), q_out, korder_out (int): host arrays of n_max entries:
+ *   the accepted times, the order of each step and the history order of
+ *   each interval (0 past the last row); n_rows: accepted rows including
+ *   row 0; stats (host int[5]) = {steps, error-test failures, convergence
+ *   failures, right-hand-side evaluations, reconstructed blocks}.
+ * Needs a model (and uses the dense interaction when one is set).  The first
+ * call allocates a workspace of (2 KBE_RING_ROWS + 4) n_max M^2 complex
+ * entries held by the context.  The host reads two numbers per fixed-point
+ * iteration (the stream is synchronised each time).  Returns KBE_OK at
+ * t_end, KBE_ERANGE when n_max rows fill first, KBE_ENUMERIC when a step
+ * fails 7 error tests or 10 iterations; the outputs describe the rows
+ * accepted so far.  On KBE_OK and KBE_ERANGE the context's grid becomes the
+ * accepted grid with the history orders used (as kbe_set_grid sets it). */
+kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts, void* L, void* R,
+                              void* S_less, void* S_great, void* I_work, void* F_ring, double* t_out,
+                              int* q_out, int* korder_out, int* n_rows, int* stats, void* stream);
+
 /* Forget per-history state kept between steps (the split path's digit
  * planes); the next step encodes every row again.  No GPU work. */
 kbe_status kbe_reset_cache(kbe_ctx* ctx);

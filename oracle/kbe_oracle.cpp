@@ -703,7 +703,7 @@ int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, 
     std::vector<C64> Sl((n + 1) * MM), Sg((n + 1) * MM), I(2 * (n + 1) * MM);
     sigma_row(G, U4, n, Sl.data(), Sg.data());
     SigmaRow<double> S{M, Sl.data(), Sg.data()};
-    if (o.K_sel > 0) st.korder[n] = select_history_order(G, S, st.t.data(), n, o.K_sel);
+    if (o.K_sel > 0 && n > 0) st.korder[n] = select_history_order(G, S, st.t.data(), n, o.K_sel);
     history_slice(G, S, st.t.data(), st.korder.data(), n, I.data(), 1);
     st.Fb[n].assign(2 * (n + 1) * MM, C64());
     rhs_row(md, G, st.t.data(), I.data(), n, st.Fb[n].data());

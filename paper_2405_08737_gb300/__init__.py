@@ -53,6 +53,7 @@ def lib():
         L.kbe_local_weights.argtypes = [vp, i, d, d, vp]
         L.kbe_set_model.argtypes = [vp, vp, vp, vp, vp]
         L.kbe_set_interaction.argtypes = [vp, vp]
+        L.kbe_run_controlled.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_selfenergy_all.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_history_slice.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
@@ -293,6 +294,38 @@ class Context:
     def reset_cache(self):
         """Forget the split path's digit planes kept between steps."""
         self._check(lib().kbe_reset_cache(self._h))
+
+    def run_controlled(self, rho0, rtol, atol, dt0, t_end, q_max=12, k_hist=5, K_sel=0, h_max=0.0,
+                       precision="fp64", stream=None):
+        """Adaptive time stepping (Sec. 3.1, kbe_run_controlled) from the
+        uncorrelated state rho0 to t_end; the run chooses the grid.  Returns
+        a dict: ``t``, ``q`` (order per step), ``korder`` (history order per
+        interval), ``n`` (rows), ``stats`` (steps, error-test failures,
+        convergence failures, right-hand-side evaluations, reconstructed
+        blocks), the device triangles ``L``, ``R`` and ``status`` (KBE_OK, or
+        KBE_ERANGE when n_max rows filled first)."""
+        import torch
+        M = self.M
+        L, R = self.empty_triangle(), self.empty_triangle()
+        L[0].copy_(1j * torch.as_tensor(np.asarray(rho0, np.complex128), device="cuda"))
+        R[0].copy_(-1j * torch.eye(M, dtype=torch.complex128, device="cuda"))
+        Sl, Sg, I, F = self.empty_rows(), self.empty_rows(), self.empty_slice(), self.empty_ring()
+        opts = np.array([rtol, atol, dt0, h_max, t_end], np.float64)
+        iopts = np.array([q_max, k_hist, K_sel, PRECISIONS[precision]], np.int32)
+        t = np.zeros(self.n_max)
+        q = np.zeros(self.n_max, np.int32)
+        ko = np.zeros(self.n_max, np.int32)
+        n_rows = ctypes.c_int()
+        stats = np.zeros(5, np.int32)
+        st = lib().kbe_run_controlled(self._h, _np_ptr(opts), _np_ptr(iopts), self._dev(L), self._dev(R),
+                                      self._dev(Sl), self._dev(Sg), self._dev(I), self._dev(F), _np_ptr(t),
+                                      _np_ptr(q), _np_ptr(ko), ctypes.byref(n_rows), _np_ptr(stats),
+                                      self._stream(stream))
+        if st not in (KBE_OK, KBE_ERANGE):
+            self._check(st)
+        n = n_rows.value
+        return {"t": t[:n], "q": q[:n], "korder": ko[:n], "n": n, "stats": tuple(int(x) for x in stats),
+                "L": L, "R": R, "status": int(st)}
 
     def set_profiling(self, enable):
         """Record CUDA events around each contraction kernel (clears old records)."""

@@ -44,6 +44,9 @@ void release(kbe_ctx* ctx) {
   cudaFree(ctx->d_korder);
   cudaFree(ctx->d_Ut); cudaFree(ctx->d_Xt); cudaFree(ctx->d_HF);
   ctx->d_Ut = ctx->d_Xt = ctx->d_HF = nullptr;
+  cudaFree(ctx->d_ctl);
+  ctx->d_ctl = nullptr;
+  ctx->ctl_bytes = 0;
   ctx->dense = false;
   ctx->d_hist = nullptr;
   ctx->d_korder = nullptr;
@@ -269,6 +272,153 @@ kbe_status adjoint_workspace(kbe_ctx* ctx, int P) {
   }
   ctx->adj_bytes = need;
   return KBE_OK;
+}
+
+
+// ------------------------------------------------- adaptive time stepping --
+// Host side of kbe_run_controlled (Sec. 3.1): the step/order controller in
+// FP64 on the host, every vector operation on the device.
+
+// integral over [t_{n-1}, t_n] of prod_i (t - nodes_i): the polynomial in
+// u = (t - t_{n-1}) / h is expanded in monomials and integrated over [0, 1]
+double error_integral(const double* t, int n, const int* nodes, int cnt) {
+  const double h = t[n] - t[n - 1];
+  double c[kWTab + 2] = {1.0};
+  int deg = 0;
+  for (int i = 0; i < cnt; ++i) {  // multiply by (u - u_i)
+    const double ui = (t[nodes[i]] - t[n - 1]) / h;
+    c[deg + 1] = 0.0;
+    for (int k = deg + 1; k >= 1; --k) c[k] = c[k - 1] - ui * c[k];
+    c[0] = -ui * c[0];
+    ++deg;
+  }
+  double s = 0.0;
+  for (int k = 0; k <= deg; ++k) s += c[k] / (k + 1);
+  return s * std::pow(h, cnt + 1);
+}
+
+// divided-difference coefficients over t_n, t_{n-1}, ..., t_{n-qq}
+void divdiff_coeffs(const double* t, int n, int qq, double* alpha) {
+  for (int i = 0; i <= qq; ++i) {
+    double d = 1.0;
+    for (int k = 0; k <= qq; ++k)
+      if (k != i) d *= t[n - i] - t[n - k];
+    alpha[i] = 1.0 / d;
+  }
+}
+
+struct CtlRun {
+  kbe_ctx* ctx;
+  cudaStream_t s;
+  int M, n_max, precision, K_sel, k_hist, bw;
+  void *L, *R, *Sl, *Sg, *I, *F;
+  double *Sring, *eps_ring, *ypred, *ycur, *partial, *out;
+  int nfev = 0, nrecon = 0, launches = 0;
+};
+
+kbe_status ctl_workspace(kbe_ctx* ctx) {
+  const size_t MM = (size_t)ctx->M * ctx->M, nm = ctx->n_max;
+  const size_t need = (kRing * 2 * nm * MM + kRing * MM + 4 * nm * MM) * 16 +
+                      (2 * (size_t)ctl_partial_count(ctx->n_max, ctx->M) + 4) * sizeof(double);
+  if (ctx->ctl_bytes >= need) return KBE_OK;
+  cudaFree(ctx->d_ctl);
+  ctx->d_ctl = nullptr;
+  ctx->ctl_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_ctl, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? KBE_ENOMEM : KBE_ECUDA,
+                std::string("kbe_run_controlled: workspace: ") + cudaGetErrorString(e));
+  }
+  ctx->ctl_bytes = need;
+  return KBE_OK;
+}
+
+// right-hand side row n from the current row n (Sigma, order choice, slice, eps, F)
+kbe_status ctl_feval(CtlRun& r, int n) {
+  kbe_ctx* ctx = r.ctx;
+  cudaError_t e = sigma_blocks(ctx, tri(n, 0), n + 1, n, r.L, r.R, r.Sl, r.Sg, r.s);
+  ++r.launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_run_controlled: self-energy");
+  if (r.K_sel > 0 && n > 0) {
+    SelectArgs sa{ctx->M, n, r.K_sel, (const double*)r.L, (const double*)r.R, (const double*)r.Sl,
+                  (const double*)r.Sg, ctx->d_hist + (size_t)n * kMaxOrder * kWTab, ctx->d_band, ctx->d_wbar,
+                  ctx->band_w, ctx->d_korder};
+    if ((e = launch_select_order(sa, r.s)) != cudaSuccess) return cuda_fail(ctx, e, "kbe_run_controlled: order");
+    ++r.launches;
+  }
+  int nl = 0;
+  kbe_status st = history(ctx, n, r.precision, r.L, r.R, r.Sl, r.Sg, r.I, r.s, &nl, true);
+  r.launches += nl;
+  if (st != KBE_OK) return st;
+  StepArgs a = step_args(ctx, n, r.L, r.R, r.I, r.F);
+  if ((e = launch_fock(a, r.s)) != cudaSuccess || (e = launch_rhs(a, r.s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_run_controlled: right-hand side");
+  r.launches += 2;
+  ++r.nfev;
+  return KBE_OK;
+}
+
+// self-energy row and Fock matrix of the accepted row n into the rings
+kbe_status ctl_store(CtlRun& r, int n) {
+  kbe_ctx* ctx = r.ctx;
+  const size_t srow = (size_t)r.n_max * ctx->M * ctx->M * 2;  // doubles per s-row
+  double* slot = r.Sring + (size_t)(n % kRing) * 2 * srow;
+  cudaError_t e = sigma_blocks(ctx, tri(n, 0), n + 1, n, r.L, r.R, slot, slot + srow, r.s);
+  StepArgs a = step_args(ctx, n, r.L, r.R, r.I, r.F);
+  a.eps = r.eps_ring + (size_t)(n % kRing) * ctx->M * ctx->M * 2;
+  if (e == cudaSuccess) e = launch_fock(a, r.s);
+  r.launches += 2;
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_run_controlled: accepted row");
+}
+
+kbe_status ctl_read(CtlRun& r, double* host) {
+  cudaError_t e = cudaMemcpyAsync(host, r.out, 2 * sizeof(double), cudaMemcpyDeviceToHost, r.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r.s);
+  return e == cudaSuccess ? KBE_OK : cuda_fail(r.ctx, e, "kbe_run_controlled: norm read");
+}
+
+// weights of interval n for the history quadrature: band row n and the
+// settled entry n - bw (fixed orders), or the local weights of every order
+// for the device's order choice
+kbe_status ctl_interval_weights(CtlRun& r, int n) {
+  kbe_ctx* ctx = r.ctx;
+  HostGrid& g = ctx->grid;
+  double w[kWTab];
+  cudaError_t e;
+  if (r.K_sel > 0) {
+    std::vector<double> hist((size_t)kMaxOrder * kWTab, 0.0);
+    for (int k = 1; k <= std::min(r.K_sel, n); ++k) {
+      kbe_status st = local_weights(g.t.data() + n - k, k, g.t[n - 1], g.t[n], w, &ctx->err);
+      if (st != KBE_OK) return st;
+      for (int j = 0; j <= k; ++j) hist[(size_t)(k - 1) * kWTab + j] = w[j];
+    }
+    e = cudaMemcpyAsync(ctx->d_hist + (size_t)n * kMaxOrder * kWTab, hist.data(), hist.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, r.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r.s);  // the host buffer is released on return
+    return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_run_controlled: weights upload");
+  }
+  const int bw = r.bw, kap = std::min(r.k_hist, n);
+  kbe_status st = local_weights(g.t.data() + n - kap, kap, g.t[n - 1], g.t[n], w, &ctx->err);
+  if (st != KBE_OK) return st;
+  // band row n from row n-1 (row recursion of Sec. 3.2) plus the local weights
+  for (int d = 0; d < bw; ++d) {
+    const int m = n - d;
+    double v = 0.0;
+    if (m >= 0) {
+      if (d >= 1) v = g.band[(size_t)(n - 1) * bw + (d - 1)];
+      if (d <= kap) v += w[kap - d];
+    }
+    g.band[(size_t)n * bw + d] = v;
+  }
+  if (n - bw >= 0) g.wbar[n - bw] = g.band[(size_t)(n - 1) * bw + (bw - 1)];
+  e = cudaMemcpyAsync(ctx->d_band + (size_t)n * bw, g.band.data() + (size_t)n * bw, bw * sizeof(double),
+                      cudaMemcpyHostToDevice, r.s);
+  if (e == cudaSuccess && n - bw >= 0)
+    e = cudaMemcpyAsync(ctx->d_wbar + (n - bw), g.wbar.data() + (n - bw), sizeof(double), cudaMemcpyHostToDevice,
+                        r.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r.s);  // a retry rewrites these host entries
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_run_controlled: weights upload");
 }
 
 }  // namespace
@@ -810,6 +960,226 @@ kbe_status kbe_read_profiling(kbe_ctx* ctx, int* count, double* total_ms) {
   *count = (int)ctx->ev_used;
   *total_ms = tot;
   return KBE_OK;
+}
+
+kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts, void* L, void* R, void* Sl,
+                              void* Sg, void* I_work, void* F_ring, double* t_out, int* q_out, int* korder_out,
+                              int* n_rows, int* stats, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!opts || !iopts || !t_out || !q_out || !korder_out || !n_rows || !stats)
+    return fail(ctx, KBE_EINVAL, "kbe_run_controlled: NULL host argument");
+  if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_work) || !aligned16(F_ring))
+    return fail(ctx, KBE_EINVAL, "kbe_run_controlled: NULL or misaligned device pointer");
+  if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
+  const double rtol = opts[0], atol = opts[1], h0 = opts[2], h_max = opts[3], t_end = opts[4];
+  const int q_max = iopts[0], k_hist = iopts[1], K_sel = iopts[2], precision = iopts[3];
+  for (int i = 0; i < 5; ++i)
+    if (!std::isfinite(opts[i])) return fail(ctx, KBE_EINVAL, "kbe_run_controlled: non-finite option");
+  if (!(rtol >= 0.0) || !(atol > 0.0) || !(h0 > 0.0) || !(h_max >= 0.0) || !(t_end > 0.0))
+    return fail(ctx, KBE_EINVAL, "kbe_run_controlled: need rtol >= 0, atol > 0, h0 > 0, h_max >= 0, t_end > 0");
+  if (q_max < 1 || q_max > kMaxOrder || k_hist < 1 || k_hist > kMaxOrder || K_sel < 0 || K_sel > kMaxOrder)
+    return fail(ctx, KBE_ERANGE, "kbe_run_controlled: q_max, k_hist in [1, 12], K_sel in [0, 12]");
+  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16)
+    return fail(ctx, KBE_EINVAL, "kbe_run_controlled: unknown precision");
+  if (ctx->n_max < 2) return fail(ctx, KBE_EINVAL, "kbe_run_controlled: n_max < 2");
+  kbe_status st = use_device(ctx);
+  if (st != KBE_OK) return st;
+  if ((st = ctl_workspace(ctx)) != KBE_OK) return st;
+  const int M = ctx->M, MM = M * M, n_max = ctx->n_max;
+  cudaError_t e = cudaSuccess;
+  if (K_sel > 0) {
+    const size_t tab = (size_t)n_max * kMaxOrder * kWTab;
+    if (!ctx->d_hist && (e = cudaMalloc(&ctx->d_hist, tab * sizeof(double))) != cudaSuccess)
+      return cuda_fail(ctx, e, "kbe_run_controlled: allocation");
+    if (!ctx->d_korder && (e = cudaMalloc(&ctx->d_korder, n_max * sizeof(int))) != cudaSuccess)
+      return cuda_fail(ctx, e, "kbe_run_controlled: allocation");
+  }
+  CtlRun r;
+  r.ctx = ctx;
+  r.s = (cudaStream_t)stream;
+  r.M = M; r.n_max = n_max; r.precision = precision; r.K_sel = K_sel; r.k_hist = k_hist;
+  r.bw = (K_sel > 0 ? K_sel : k_hist) + 1;
+  r.L = L; r.R = R; r.Sl = Sl; r.Sg = Sg; r.I = I_work; r.F = F_ring;
+  {
+    double* w = (double*)ctx->d_ctl;
+    const size_t srow = (size_t)n_max * MM * 2;
+    r.Sring = w;               w += (size_t)kRing * 2 * srow;
+    r.eps_ring = w;            w += (size_t)kRing * MM * 2;
+    r.ypred = w;               w += 2 * srow;
+    r.ycur = w;                w += 2 * srow;
+    r.out = w;                 w += 4;
+    r.partial = w;
+  }
+  // the growing grid: point 0 now, point n per attempt of step n
+  HostGrid& g = ctx->grid;
+  g = HostGrid{};
+  g.n_t = 1;
+  g.K = r.bw - 1;
+  g.t.assign(n_max, 0.0);
+  g.order.assign(n_max, 0);
+  g.wbar.assign(n_max, 0.0);
+  g.band.assign((size_t)n_max * r.bw, 0.0);
+  ctx->grid_set = true;
+  ctx->band_w = r.bw;
+  ctx->adaptive_K = K_sel;
+  ctx->adaptive_rows = 1;
+  ctx->planes_L = ctx->planes_R = nullptr;
+  ctx->planes_rows = 0;
+  if ((e = cudaMemsetAsync(ctx->d_band, 0, (size_t)n_max * r.bw * sizeof(double), r.s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->d_wbar, 0, n_max * sizeof(double), r.s)) != cudaSuccess ||
+      (K_sel > 0 && (e = cudaMemsetAsync(ctx->d_korder, 0, n_max * sizeof(int), r.s)) != cudaSuccess))
+    return cuda_fail(ctx, e, "kbe_run_controlled: reset");
+  std::vector<int> qused(n_max, 0);
+  int n_err = 0, n_conv = 0, n = 1, rc = 0;
+  auto finish = [&](kbe_status status) -> kbe_status {
+    ctx->last_launches = r.launches;
+    stats[0] = n - 1; stats[1] = n_err; stats[2] = n_conv; stats[3] = r.nfev; stats[4] = r.nrecon;
+    *n_rows = n;
+    std::vector<int> ko(n_max, 0);
+    if (K_sel > 0) {
+      cudaError_t e2 = cudaStreamSynchronize(r.s);
+      if (e2 == cudaSuccess) e2 = cudaMemcpy(ko.data(), ctx->d_korder, n_max * sizeof(int), cudaMemcpyDeviceToHost);
+      if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "kbe_run_controlled: orders");
+    } else {
+      for (int l = 1; l < n; ++l) ko[l] = k_hist;
+    }
+    for (int i = 0; i < n_max; ++i) {
+      t_out[i] = i < n ? g.t[i] : 0.0;
+      q_out[i] = i < n ? qused[i] : 0;
+      korder_out[i] = i < n ? ko[i] : 0;
+    }
+    if (status != KBE_OK) return status;
+    // the context's grid becomes the accepted grid with the history orders used
+    std::vector<double> tg(g.t.begin(), g.t.begin() + n);
+    std::vector<int> og(ko.begin(), ko.begin() + n);
+    cudaError_t e2 = cudaStreamSynchronize(r.s);
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "kbe_run_controlled: stream");
+    kbe_status st2 = kbe_set_grid(ctx, tg.data(), og.data(), n);
+    if (st2 != KBE_OK) return st2;
+    ctx->last_launches = r.launches;
+    if (rc == 1) return fail(ctx, KBE_ERANGE, "kbe_run_controlled: n_max rows filled before t_end");
+    return KBE_OK;
+  };
+  // row 0: its right-hand side, self-energy and Fock matrix
+  if ((st = ctl_feval(r, 0)) != KBE_OK || (st = ctl_store(r, 0)) != KBE_OK) return finish(st);
+  double h = h0, eta_max = 1e4;
+  int q = 1, qsteps = 0;
+  double host[2];
+  const double addon = 1e-6;
+  while (g.t[n - 1] < t_end * (1.0 - 1e-14)) {
+    if (n >= n_max) { rc = 1; break; }
+    int nef = 0, ncf = 0;
+    bool failed = false;
+    double E = 0.0;
+    const double N = (2.0 * n + 1.0) * MM;
+    for (;;) {  // attempts of step n
+      if (h_max > 0.0 && h > h_max) h = h_max;
+      if (g.t[n - 1] + h > t_end) h = t_end - g.t[n - 1];
+      if (q > n) q = n;
+      g.t[n] = g.t[n - 1] + h;
+      g.order[n] = k_hist;
+      g.n_t = n + 1;
+      if ((st = ctl_interval_weights(r, n)) != KBE_OK) return finish(st);
+      CtlArgs a{};
+      a.M = M; a.n = n; a.q = q; a.n_max = n_max;
+      a.L = (double*)L; a.R = (double*)R; a.F = (const double*)F_ring;
+      a.rtol = rtol; a.atol = atol;
+      a.ypred = r.ypred; a.ycur = r.ycur; a.partial = r.partial; a.status = ctx->d_status;
+      a.q1 = a.q2 = -1;
+      if ((st = local_weights(g.t.data() + n - q, q - 1, g.t[n - 1], g.t[n], a.wp, &ctx->err)) != KBE_OK ||
+          (st = local_weights(g.t.data() + n - q + 1, q - 1, g.t[n - 1], g.t[n], a.wc, &ctx->err)) != KBE_OK)
+        return finish(st);
+      int np[kWTab], nc[kWTab];
+      for (int i = 1; i <= q; ++i) np[i - 1] = n - i;
+      for (int i = 0; i < q; ++i) nc[i] = n - i;
+      const double Ep = error_integral(g.t.data(), n, np, q), Ec = error_integral(g.t.data(), n, nc, q);
+      const double Cm = Ec / (Ep - Ec);
+      if ((e = launch_ctl_predict(a, r.s)) != cudaSuccess) return finish(cuda_fail(ctx, e, "kbe_run_controlled: predictor"));
+      ++r.launches;
+      bool conv = false;
+      double Rr = 1.0, dprev = 0.0, esq = 0.0;
+      for (int m = 1; m <= 3; ++m) {
+        if ((st = ctl_feval(r, n)) != KBE_OK) return finish(st);
+        if ((e = launch_ctl_correct(a, r.out, r.s)) != cudaSuccess)
+          return finish(cuda_fail(ctx, e, "kbe_run_controlled: corrector"));
+        r.launches += 2;
+        if ((st = ctl_read(r, host)) != KBE_OK) return finish(st);
+        const double d = std::sqrt(host[0] / N);
+        esq = host[1];
+        if (m > 1) Rr = std::max(0.3 * Rr, d / dprev);
+        if (Rr * d * std::fabs(Cm) < 0.1) { conv = true; break; }
+        if (m > 1 && d > 2.0 * dprev) break;
+        dprev = d;
+      }
+      if (!conv) {
+        ++n_conv; ++ncf; failed = true;
+        if (ncf > 10) return finish(fail(ctx, KBE_ENUMERIC, "kbe_run_controlled: fixed-point iteration failed 10 times"));
+        h *= 0.25;
+        continue;
+      }
+      E = std::fabs(Cm) * std::sqrt(esq / N);
+      if (E > 1.0) {
+        ++n_err; ++nef; failed = true;
+        if (nef > 7) return finish(fail(ctx, KBE_ENUMERIC, "kbe_run_controlled: error test failed 7 times"));
+        if (nef >= 3) { q = 1; qsteps = 0; h *= 0.1; continue; }
+        const double eta = 1.0 / (std::pow(6.0 * E, 1.0 / (q + 1)) + addon);
+        h *= std::max(0.1, std::min(0.9, eta));
+        continue;
+      }
+      break;
+    }
+    // accepted row n
+    qused[n] = q;
+    if ((st = ctl_store(r, n)) != KBE_OK) return finish(st);
+    {
+      ReconArgs rr{M, n, std::max(0, n - std::min(q + 1, 12)), n_max, (const double*)L, (const double*)R, r.Sring,
+                   r.eps_ring, weights_view(ctx), (double*)F_ring, ctx->d_status};
+      if ((e = launch_ctl_reconstruct(rr, r.s)) != cudaSuccess)
+        return finish(cuda_fail(ctx, e, "kbe_run_controlled: reconstruction"));
+      ++r.launches;
+      r.nrecon += n - rr.jlo;
+    }
+    ++qsteps;
+    double eta = E > 0.0 ? 1.0 / (std::pow(6.0 * E, 1.0 / (q + 1)) + addon) : eta_max;
+    int qn = q;
+    if (qsteps > q) {
+      CtlArgs a{};
+      a.M = M; a.n = n; a.q = q; a.n_max = n_max;
+      a.L = (double*)L; a.R = (double*)R; a.F = (const double*)F_ring;
+      a.rtol = rtol; a.atol = atol; a.partial = r.partial; a.status = ctx->d_status;
+      a.q1 = q > 1 ? q - 1 : -1;
+      a.q2 = (q < q_max && n - q - 1 >= 0) ? q + 1 : -1;
+      double P1 = 0.0, P2 = 0.0;
+      int nodes[kWTab + 1];
+      for (int i = 0; i <= q; ++i) nodes[i] = n - i;
+      if (a.q1 >= 0) { divdiff_coeffs(g.t.data(), n, a.q1, a.wp); P1 = std::fabs(error_integral(g.t.data(), n, nodes, a.q1)); }
+      if (a.q2 >= 0) { divdiff_coeffs(g.t.data(), n, a.q2, a.wc); P2 = std::fabs(error_integral(g.t.data(), n, nodes, a.q2)); }
+      if (a.q1 >= 0 || a.q2 >= 0) {
+        if ((e = launch_ctl_divdiff(a, r.out, r.s)) != cudaSuccess)
+          return finish(cuda_fail(ctx, e, "kbe_run_controlled: order estimates"));
+        r.launches += 2;
+        if ((st = ctl_read(r, host)) != KBE_OK) return finish(st);
+        if (a.q1 >= 0) {
+          const double Eq = P1 * std::sqrt(host[0] / N);
+          const double e2 = Eq > 0.0 ? 1.0 / (std::pow(6.0 * Eq, 1.0 / q) + addon) : eta_max;
+          if (e2 > eta) { eta = e2; qn = q - 1; }
+        }
+        if (a.q2 >= 0) {
+          const double Eq = P2 * std::sqrt(host[1] / N);
+          const double e2 = Eq > 0.0 ? 1.0 / (std::pow(10.0 * Eq, 1.0 / (q + 2)) + addon) : eta_max;
+          if (e2 > eta) { eta = e2; qn = q + 1; }
+        }
+      }
+    }
+    if (qn != q) { q = qn; qsteps = 0; }
+    if (eta < 1.5) eta = 1.0;
+    else eta = std::min(eta, failed ? 1.0 : eta_max);
+    h *= eta;
+    eta_max = 10.0;
+    ++n;
+  }
+  return finish(KBE_OK);
 }
 
 kbe_status kbe_sync_status(kbe_ctx* ctx, void* stream) {

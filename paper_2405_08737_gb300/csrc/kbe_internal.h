@@ -123,6 +123,9 @@ struct kbe_ctx {
   double* d_Ut = nullptr;     // [d][i][e][f] = U_ifde
   double* d_Xt = nullptr;     // [b][j][a][c] = UEx_jabc = 2 U_jbac - U_jabc
   double* d_HF = nullptr;     // [(i,j)][(b,a)] = U_iabj - 2 U_ijba (Fock matrix)
+  // adaptive time stepping: self-energy and Fock rings, iterates, sums
+  double* d_ctl = nullptr;
+  size_t ctl_bytes = 0;
   // measurement: event pairs around each contraction kernel
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -242,6 +245,37 @@ struct SelectArgs {
   int* korder;         // chosen order per interval (entry n written)
 };
 cudaError_t launch_select_order(const SelectArgs& a, cudaStream_t s);
+
+// ---- adaptive time stepping (controller.cu) -----------------------------
+struct CtlArgs {
+  int M, n, q, n_max;
+  double* L;           // triangles; row n is written
+  double* R;
+  const double* F;     // right-hand-side ring [kRing][2][n_max][M][M]
+  double wp[kWTab];    // predictor weights (nodes t_{n-q..n-1}); divided differences: coefficients over t_{n..n-q1}
+  double wc[kWTab];    // corrector weights (nodes t_{n-q+1..n}); divided differences: over t_{n..n-q2}
+  int q1, q2;          // orders of the two divided differences (-1: none)
+  double rtol, atol;
+  double* ypred;       // [2][n+1][M][M] predicted row
+  double* ycur;        // [2][n+1][M][M] current iterate
+  double* partial;     // [blocks][2] per-block sums
+  int* status;
+};
+struct ReconArgs {
+  int M, n, jlo, n_max;
+  const double* L;
+  const double* R;
+  const double* Sring;     // self-energy rows [kRing][2][n_max][M][M] of accepted rows
+  const double* eps_ring;  // Fock matrices [kRing][M][M] of accepted rows
+  WeightsView w;
+  double* F;               // right-hand-side ring; row j gets column n
+  int* status;
+};
+int ctl_partial_count(int n_max, int M);
+cudaError_t launch_ctl_predict(const CtlArgs& a, cudaStream_t s);
+cudaError_t launch_ctl_correct(const CtlArgs& a, double* out, cudaStream_t s);
+cudaError_t launch_ctl_divdiff(const CtlArgs& a, double* out, cudaStream_t s);
+cudaError_t launch_ctl_reconstruct(const ReconArgs& r, cudaStream_t s);
 
 // ---- reverse mode (adjoint.cu) ------------------------------------------
 // Cotangent convention: for a real loss, zbar = dF/dRe z + i dF/dIm z.
