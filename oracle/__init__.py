@@ -337,7 +337,7 @@ def initial_rhs(t, order, h0, U, v, pulse, rho0, U4=None):
     return L0, R0, F0
 
 def run_controlled(h0, U, v, pulse, rho0, rtol, atol, dt0, t_end, n_max, q_max=12, k_hist=5, K_sel=0,
-                   h_max=0.0, U4=None):
+                   h_max=0.0, U4=None, replay=None):
     """Adaptive time stepping of Sec. 3.1 from the uncorrelated state rho0
     (L(0,0) = i rho0, R(0,0) = -i): variable-step, variable-order Adams
     (orders 1..q_max) with fixed-point iteration, WRMS error control
@@ -346,7 +346,9 @@ def run_controlled(h0, U, v, pulse, rho0, rtol, atol, dt0, t_end, n_max, q_max=1
     ``t``, step orders ``q``, history orders ``korder``, triangles ``L``,
     ``R`` of the accepted rows, ``stats`` = (steps, error-test failures,
     convergence failures, right-hand-side evaluations, reconstructed blocks)
-    and the run ``status`` (0 reached t_end, 1 storage full, 2 failure)."""
+    and the run ``status`` (0 reached t_end, 1 storage full, 2 failure).
+    ``replay = (t, q)`` takes exactly those accepted points and step orders
+    instead of choosing them."""
     h0 = _c128(h0)
     M = h0.shape[0]
     v = _f64(v)
@@ -363,9 +365,15 @@ def run_controlled(h0, U, v, pulse, rho0, rtol, atol, dt0, t_end, n_max, q_max=1
     stats = np.zeros(5, np.int32)
     opts = _f64([rtol, atol, dt0, h_max, t_end])
     iopts = _i32([q_max, k_hist, K_sel, n_max])
+    tf = qf = None
+    nf = 0
+    if replay is not None:
+        tf, qf = _f64(replay[0]), _i32(replay[1])
+        nf = len(tf)
     rc = lib().orc_run_controlled(ctypes.c_int(M), _p(opts), _p(iopts), _p(h0), _p(Uv), U4p, _p(v),
                                   _p(_pulse4(pulse)), _p(L), _p(R), _p(t), _p(q), _p(ko), ctypes.byref(n_rows),
-                                  _p(stats))
+                                  _p(stats), _p(tf) if tf is not None else None,
+                                  _p(qf) if qf is not None else None, ctypes.c_int(nf))
     if rc < 0:
         raise RuntimeError("oracle run_controlled: invalid arguments")
     n = n_rows.value

@@ -590,6 +590,12 @@ std::vector<T> local_U4(int M, const T* U) {
 struct CtlOpts {
   double rtol, atol, h0, h_max, t_end;
   int q_max, k_hist, K_sel, n_max;
+  // replay: take exactly the points t_force[1..n_force-1] with the orders
+  // q_force[n] (no error test, no step selection; the fixed-point iteration
+  // and everything else as above)
+  const double* t_force = nullptr;
+  const int* q_force = nullptr;
+  int n_force = 0;
 };
 
 // integral over [t_{n-1}, t_n] of prod_{i in nodes} (t - t_i)
@@ -726,7 +732,8 @@ int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, 
   int q = 1, qsteps = 0, n = 1, n_err = 0, n_conv = 0;
   std::vector<C64> ypred, yprev, ycur, ynew;
   double wp[16], wc[16];
-  while (st.t[n - 1] < o.t_end * (1.0 - 1e-14)) {
+  const bool replay = o.t_force != nullptr;
+  while (replay ? n < o.n_force : st.t[n - 1] < o.t_end * (1.0 - 1e-14)) {
     if (n >= o.n_max) return finish(n, n_err, n_conv, 1);
     int nef = 0, ncf = 0;
     bool failed = false;
@@ -736,6 +743,7 @@ int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, 
       if (st.t[n - 1] + h > o.t_end) h = o.t_end - st.t[n - 1];
       if (q > n) q = n;
       st.t[n] = st.t[n - 1] + h;
+      if (replay) { st.t[n] = o.t_force[n]; q = o.q_force[n]; }
       st.korder[n] = o.k_hist;
       span_weights(st.t.data(), n - q, n - 1, n, wp);      // nodes t_{n-q} .. t_{n-1}
       span_weights(st.t.data(), n - q + 1, n, n, wc);      // nodes t_{n-q+1} .. t_n
@@ -791,6 +799,7 @@ int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, 
         if (m > 1 && d > 2.0 * dprev) break;
         dprev = d;
       }
+      if (!conv && replay) return finish(n, n_err, n_conv, 2);
       if (!conv) {
         ++n_conv; ++ncf; failed = true;
         if (ncf > 10) return finish(n, n_err, n_conv, 2);
@@ -799,7 +808,7 @@ int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, 
       }
       E = std::fabs(Cm) * wrms(M, n, [&](int s, int c, int a, int b) {
         return ycur[at(s, c, a, b)] - ypred[at(s, c, a, b)]; }, weight);
-      if (E > 1.0) {
+      if (E > 1.0 && !replay) {
         ++n_err; ++nef; failed = true;
         if (nef > 7) return finish(n, n_err, n_conv, 2);
         if (nef >= 3) { q = 1; qsteps = 0; h *= 0.1; continue; }
@@ -819,6 +828,7 @@ int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, 
       rhs_above(md, G, st, j, n, blk.data());
       st.Fa[j][n] = blk;
     }
+    if (replay) { ++n; continue; }
     // next step size and order
     ++qsteps;
     const double addon = 1e-6;
@@ -1119,11 +1129,20 @@ int orc_run_u4(int M, int n_start, int n_end, const double* t, const int* order,
 // including row 0), stats = {steps, error-test failures, convergence
 // failures, right-hand-side evaluations, reconstructed blocks}.
 // Returns the run status (0 reached t_end, 1 storage full, 2 step failure).
+// With t_force (and q_force, n_force) the run replays the given points and
+// step orders instead of choosing them (rows 1..n_force-1).
 int orc_run_controlled(int M, const double* opts, const int* iopts, const double* h0, const double* U,
                        const double* U4, const double* v, const double* pulse4, void* L, void* R, double* t,
-                       int* q, int* korder, int* n_rows, int* stats) {
+                       int* q, int* korder, int* n_rows, int* stats, const double* t_force, const int* q_force,
+                       int n_force) {
   if (M < 1) return -1;
   CtlOpts o{opts[0], opts[1], opts[2], opts[3], opts[4], iopts[0], iopts[1], iopts[2], iopts[3]};
+  if (t_force) {
+    if (!q_force || n_force < 1 || n_force > iopts[3]) return -1;
+    o.t_force = t_force;
+    o.q_force = q_force;
+    o.n_force = n_force;
+  }
   if (o.q_max < 1 || o.q_max > 12 || o.n_max < 2 || o.k_hist < 1 || o.k_hist > 12 || o.K_sel < 0 ||
       o.K_sel > 12 || !(o.h0 > 0.0) || !(o.rtol >= 0.0) || !(o.atol > 0.0))
     return -1;

@@ -1,6 +1,14 @@
 """GPU checks of the adaptive time stepping (Sec. 3.1, kbe_run_controlled)
-against the oracle's controlled runs: the same accepted grid, step orders,
-history orders and failure counts, and rows within 1e-12."""
+against the oracle's controlled runs.
+
+Decisions: the same number of steps, failures, step orders and history
+orders.  Step sizes follow from the error estimate ||y - y(0)||, a
+difference of two values that agree to about rtol, so its relative
+precision is about eps / rtol; two correct evaluations therefore place the
+points apart by up to ~1e-11 of t (checked at 1e-9), and the rows differ by
+the solution's change over that distance (checked at 1e-8).  Arithmetic:
+the oracle replaying the device's accepted points and orders gives the
+device's rows within 1e-12."""
 import numpy as np
 import pytest
 
@@ -63,11 +71,18 @@ def test_controlled_run_matches_oracle(kbe, name):
     assert o["status"] == 0 and g["status"] == kbe.KBE_OK
     assert g["n"] == o["n"] and g["stats"] == o["stats"], (g["stats"], o["stats"])
     assert np.array_equal(g["q"], o["q"]) and np.array_equal(g["korder"], o["korder"])
-    assert np.abs(g["t"] - o["t"]).max() <= 1e-12 * o["t"][-1]
+    assert np.abs(g["t"] - o["t"]).max() <= 1e-9 * o["t"][-1]
     assert g["q"].max() >= 3 and g["stats"][4] > 0
     p = W.tri_size(o["n"])
-    assert _rel(g["L"][:p].cpu().numpy(), o["L"]) < TOL
-    assert _rel(g["R"][:p].cpu().numpy(), o["R"]) < TOL
+    Lg, Rg = g["L"][:p].cpu().numpy(), g["R"][:p].cpu().numpy()
+    assert _rel(Lg, o["L"]) < 1e-8 and _rel(Rg, o["R"]) < 1e-8
+    # the oracle on the device's accepted points and orders: the same rows
+    M, kind, U, dense, pulse_on, rtol, t_end, K_sel = CASES[name]
+    h, Uv, U4, v, pulse = _model(M, kind, U, dense, pulse_on)
+    r = oracle.run_controlled(h, None if dense else Uv, v, pulse, W.half_filled_rho(h), rtol, rtol * 1e-2, 0.01,
+                              t_end, 400, K_sel=K_sel, U4=U4, replay=(g["t"], g["q"]))
+    assert r["status"] == 0 and r["n"] == g["n"] and np.array_equal(r["korder"], g["korder"])
+    assert _rel(Lg, r["L"]) < TOL and _rel(Rg, r["R"]) < TOL
     ctx.close()
 
 
@@ -134,6 +149,6 @@ def test_controlled_run_errors_and_full_storage(kbe):
     g = ctx.run_controlled(rho, 1e-8, 1e-10, 0.01, 5.0)  # 12 rows cannot reach t = 5
     assert g["status"] == kbe.KBE_ERANGE and g["n"] == 12 and g["t"][-1] < 5.0
     o = oracle.run_controlled(h, np.ones(M), W.site_potential(M), None, rho, 1e-8, 1e-10, 0.01, 5.0, 12)
-    assert o["status"] == 1 and np.abs(g["t"] - o["t"]).max() < 1e-12
+    assert o["status"] == 1 and np.abs(g["t"] - o["t"]).max() < 1e-9
     ctx.sync_status()
     ctx.close()

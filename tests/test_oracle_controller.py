@@ -136,3 +136,16 @@ def test_dense_interaction_and_adaptive_history_orders():
         assert len(set(r["korder"][7:])) > 1
         out.append(r["L"][tri(r["n"] - 1, r["n"] - 1)])
     assert np.abs(out[0] - out[1]).max() < 1e-5
+
+
+def test_replay_reproduces_the_run():
+    """Replaying a run's accepted points and step orders gives the same rows
+    bitwise (rejected attempts leave nothing behind)."""
+    h = W.chain_h(2)
+    rho = W.half_filled_rho(h)
+    a = oracle.run_controlled(h, np.ones(2), W.site_potential(2), None, rho, 1e-7, 1e-9, 0.01, 1.0, 300)
+    assert a["stats"][1] > 0  # the run had rejected attempts
+    b = oracle.run_controlled(h, np.ones(2), W.site_potential(2), None, rho, 1e-7, 1e-9, 0.01, 1.0, 300,
+                              replay=(a["t"], a["q"]))
+    assert b["status"] == 0 and b["n"] == a["n"] and b["stats"][1] == 0
+    assert np.array_equal(a["t"], b["t"]) and np.array_equal(a["L"], b["L"]) and np.array_equal(a["R"], b["R"])
