@@ -332,7 +332,8 @@ kbe_status kbe_get_history_orders(kbe_ctx* ctx, int* orders, int n);
  * Needs a model (and uses the dense interaction when one is set).  The first
  * call allocates a workspace of (2 KBE_RING_ROWS + 4) n_max M^2 complex
  * entries held by the context.  The host reads two numbers per fixed-point
- * iteration (the stream is synchronised each time).  Returns KBE_OK at
+ * iteration (the stream is synchronised each time).  Invalid options are
+ * KBE_EINVAL (ranges above; also an unknown precision).  Returns KBE_OK at
  * t_end, KBE_ERANGE when n_max rows fill first, KBE_ENUMERIC when a step
  * fails 7 error tests or 10 iterations; the outputs describe the rows
  * accepted so far.  On KBE_OK and KBE_ERANGE the context's grid becomes the

@@ -979,7 +979,7 @@ kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts
   if (!(rtol >= 0.0) || !(atol > 0.0) || !(h0 > 0.0) || !(h_max >= 0.0) || !(t_end > 0.0))
     return fail(ctx, KBE_EINVAL, "kbe_run_controlled: need rtol >= 0, atol > 0, h0 > 0, h_max >= 0, t_end > 0");
   if (q_max < 1 || q_max > kMaxOrder || k_hist < 1 || k_hist > kMaxOrder || K_sel < 0 || K_sel > kMaxOrder)
-    return fail(ctx, KBE_ERANGE, "kbe_run_controlled: q_max, k_hist in [1, 12], K_sel in [0, 12]");
+    return fail(ctx, KBE_EINVAL, "kbe_run_controlled: q_max, k_hist in [1, 12], K_sel in [0, 12]");
   if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16)
     return fail(ctx, KBE_EINVAL, "kbe_run_controlled: unknown precision");
   if (ctx->n_max < 2) return fail(ctx, KBE_EINVAL, "kbe_run_controlled: n_max < 2");

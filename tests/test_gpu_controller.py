@@ -145,7 +145,7 @@ def test_controlled_run_errors_and_full_storage(kbe):
     assert e.value.status == kbe.KBE_EINVAL
     with pytest.raises(kbe.KBEError) as e:
         ctx.run_controlled(rho, 1e-6, 1e-8, 0.01, 1.0, q_max=13)
-    assert e.value.status == kbe.KBE_ERANGE
+    assert e.value.status == kbe.KBE_EINVAL
     g = ctx.run_controlled(rho, 1e-8, 1e-10, 0.01, 5.0)  # 12 rows cannot reach t = 5
     assert g["status"] == kbe.KBE_ERANGE and g["n"] == 12 and g["t"][-1] < 5.0
     o = oracle.run_controlled(h, np.ones(M), W.site_potential(M), None, rho, 1e-8, 1e-10, 0.01, 5.0, 12)
