@@ -4,11 +4,12 @@ against the oracle's controlled runs.
 Decisions: the same number of steps, failures, step orders and history
 orders.  Step sizes follow from the error estimate ||y - y(0)||, a
 difference of two values that agree to about rtol, so its relative
-precision is about eps / rtol; two correct evaluations therefore place the
-points apart by up to ~1e-11 of t (checked at 1e-9), and the rows differ by
-the solution's change over that distance (checked at 1e-8).  Arithmetic:
-the oracle replaying the device's accepted points and orders gives the
-device's rows within 1e-12."""
+precision is about eps / rtol; each step factor inherits that, and the
+deviations add up along the run.  Two correct evaluations therefore place
+the points apart by up to about n eps / rtol of t after n steps; the test
+allows 10 n eps / rtol (``_t_tol``), and the rows the solution's change
+over that distance.  Arithmetic: the oracle replaying the device's accepted
+points and orders gives the device's rows within 1e-12."""
 import numpy as np
 import pytest
 
@@ -32,6 +33,11 @@ def kbe():
 
 def _rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _t_tol(n, rtol):
+    """Relative bound on the drift of the accepted points after n steps."""
+    return 10.0 * n * np.finfo(float).eps / rtol
 
 
 CASES = {  # name: (M, kind, U, dense, pulse, rtol, t_end, K_sel)
@@ -71,13 +77,14 @@ def test_controlled_run_matches_oracle(kbe, name):
     assert o["status"] == 0 and g["status"] == kbe.KBE_OK
     assert g["n"] == o["n"] and g["stats"] == o["stats"], (g["stats"], o["stats"])
     assert np.array_equal(g["q"], o["q"]) and np.array_equal(g["korder"], o["korder"])
-    assert np.abs(g["t"] - o["t"]).max() <= 1e-9 * o["t"][-1]
+    M, kind, U, dense, pulse_on, rtol, t_end, K_sel = CASES[name]
+    tt = _t_tol(o["n"], rtol)
+    assert np.abs(g["t"] - o["t"]).max() <= tt * o["t"][-1]
     assert g["q"].max() >= 3 and g["stats"][4] > 0
     p = W.tri_size(o["n"])
     Lg, Rg = g["L"][:p].cpu().numpy(), g["R"][:p].cpu().numpy()
-    assert _rel(Lg, o["L"]) < 1e-8 and _rel(Rg, o["R"]) < 1e-8
+    assert _rel(Lg, o["L"]) < 10 * tt and _rel(Rg, o["R"]) < 10 * tt
     # the oracle on the device's accepted points and orders: the same rows
-    M, kind, U, dense, pulse_on, rtol, t_end, K_sel = CASES[name]
     h, Uv, U4, v, pulse = _model(M, kind, U, dense, pulse_on)
     r = oracle.run_controlled(h, None if dense else Uv, v, pulse, W.half_filled_rho(h), rtol, rtol * 1e-2, 0.01,
                               t_end, 400, K_sel=K_sel, U4=U4, replay=(g["t"], g["q"]))
@@ -149,6 +156,6 @@ def test_controlled_run_errors_and_full_storage(kbe):
     g = ctx.run_controlled(rho, 1e-8, 1e-10, 0.01, 5.0)  # 12 rows cannot reach t = 5
     assert g["status"] == kbe.KBE_ERANGE and g["n"] == 12 and g["t"][-1] < 5.0
     o = oracle.run_controlled(h, np.ones(M), W.site_potential(M), None, rho, 1e-8, 1e-10, 0.01, 5.0, 12)
-    assert o["status"] == 1 and np.abs(g["t"] - o["t"]).max() < 1e-9
+    assert o["status"] == 1 and np.abs(g["t"] - o["t"]).max() <= _t_tol(12, 1e-8) * o["t"][-1]
     ctx.sync_status()
     ctx.close()
