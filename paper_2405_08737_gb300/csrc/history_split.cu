@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_main(SplitArgs a) {
 constexpr int kUnitBytes = 2 * kBigTile + 1024;                 // PL | Q | column exponents (padded)
 constexpr int kStage2Bytes = kUnitBytes + kBigTile + kSmallBytes;  // + QU | small operand
 constexpr int kEpi2 = 16;                                       // 4 lane quadrants x 2 groups x 2 column halves
-constexpr int kThreads2 = (kEpi2 + 2) * 32;                     // + MMA warp + producer warp
+constexpr int kThreads2 = (kEpi2 + 3) * 32;                     // + MMA warp, producer warp, second MMA warp
 
 // Slot of a straddling chunk kc in the QU buffer of the tile starting at
 // column c0 (the first straddling chunk is the first whose last point
@@ -611,8 +611,10 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
   const long long u0 = unit_begin(g, blockIdx.x), u1 = unit_begin(g, blockIdx.x + 1);
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], 1); mbar_init(&sm.empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 1); mbar_init(&sm.accempty[b], kEpi2 * 32); }
+    // full: the producer's transaction count; empty and accfull: one commit
+    // from each of the two MMA threads; accempty: every epilogue thread
+    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], 1); mbar_init(&sm.empty[s], 2); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 2); mbar_init(&sm.accempty[b], kEpi2 * 32); }
     sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -661,10 +663,14 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
       }
     }
     __syncwarp();
-  } else if (warp == kEpi2) {
-    // --------------------------------------------------------- MMA warp --
-    // One thread issues every MMA; descriptors are a per-stage base plus
+  } else if (warp == kEpi2 || warp == kEpi2 + 2) {
+    // -------------------------------------------------------- MMA warps --
+    // Two threads issue the MMAs, one per accumulator group (warp kEpi2:
+    // I^<, from PL and QU x NB^<; warp kEpi2 + 2: D, from Q and QU x NBD),
+    // so that issuing overlaps; each commits to the stage and accumulator
+    // barriers, which count both.  Descriptors are a per-stage base plus
     // compile-time offsets (a descriptor's start address is in 16-byte units).
+    const int mgrp = warp == kEpi2 ? 0 : 1;
     if (lane == 0) {
       const uint64_t big0 = umma_desc(smem_u32(sm.stage[0]), 2048, 128);
       const uint64_t small0 = umma_desc(smem_u32(sm.stage[0] + kUnitBytes + kBigTile), 1024, 128);
@@ -687,7 +693,10 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
         const uint64_t dPL0 = big0 + so, dQ0 = dPL0 + (kBigTile >> 4);
         const uint64_t dQU0 = cls == 1 ? dQ0 : dPL0 + (kUnitBytes >> 4);
         const uint64_t dS0 = small0 + so;
-        const uint32_t dl = tmem + b * kAccCols, dg = dl + kGroupCols;
+        // group 0: I^< += PL A1 + QU NB^<;  group 1: D += Q A1 + QU NBD
+        const uint32_t dacc = tmem + b * kAccCols + mgrp * kGroupCols;
+        const uint64_t dA = mgrp == 0 ? dPL0 : dQ0;
+        const uint64_t dSU = dS0 + (uint64_t)(((1 + mgrp) * kSmallVar) >> 4);
 #pragma unroll
         for (int i = 0; i < kSlices; ++i) {
           const uint32_t idesc = umma_idesc_bf16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
@@ -695,12 +704,8 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
           for (int kk = 0; kk < 2; ++kk) {
             const uint64_t oa = (uint64_t)((i * kBigSlice + kk * 2 * 2048) >> 4);
             const uint64_t ob = (uint64_t)((kk * 2 * 1024) >> 4);
-            umma_bf16(dl + i * kNS, dPL0 + oa, dS0 + ob, idesc, 1);
-            umma_bf16(dg + i * kNS, dQ0 + oa, dS0 + ob, idesc, 1);
-            if (cls != 0) {
-              umma_bf16(dl + i * kNS, dQU0 + oa, dS0 + ob + (kSmallVar >> 4), idesc, 1);
-              umma_bf16(dg + i * kNS, dQU0 + oa, dS0 + ob + (2 * kSmallVar >> 4), idesc, 1);
-            }
+            umma_bf16(dacc + i * kNS, dA + oa, dS0 + ob, idesc, 1);
+            if (cls != 0) umma_bf16(dacc + i * kNS, dQU0 + oa, dSU + ob, idesc, 1);
           }
         }
         umma_commit(&sm.accfull[b]);
