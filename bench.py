@@ -37,7 +37,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_SLICE_TRAFFIC = 2.077e9
 # DRAM bytes of one split contraction launch (split_main2) of the bench slice
 # (ncu capture, profiles/split_main_chain_m8_n1024.md)
-SPLIT_SLICE_TRAFFIC = 2.279e9
+SPLIT_SLICE_TRAFFIC = 2.262e9
 METRIC = "history-slice TFLOP/s and ms per KBE step vs plain FP64 GPU path at stated error"
 
 
@@ -646,6 +646,8 @@ def main():
                   "achieved": round(plane_bytes / (k_avg_s * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
                   "frac": round(plane_bytes / (k_avg_s * 1e-3) / 1e9 / hbm, 4),
                   "traffic": SPLIT_SLICE_TRAFFIC if (M, n) == (8, 1023) else None,
+                  "traffic_source": "ncu dram__bytes_read+write of the launch at n=767 (18432 units), "
+                                    "scaled by units to n=1023 (32768 units)",
                   "bytes_per_launch": plane_bytes,
                   "note": "digit planes of both triangles: 2x the FP64 history bytes of the slice"}
     split = {"precision": "split: 4-digit bf16 fixed-point slices on tcgen05, exact FP32 chunk sums, "
