@@ -393,7 +393,12 @@ kbe_status kbe_batch_bind(kbe_batch* b, int i, void* L, void* R, void* S_less, v
  * rows[i] < 1 leaves system i untouched, rows[i] >= n_t_i is KBE_ERANGE.
  * The graph of the step is captured on the first call and reused while P,
  * precision and the tile policy stay the same (KBE_SPLIT_BF16 graphs also
- * depend on the rows and are re-captured when they change).  Results agree
+ * depend on the rows and are re-captured when they change).  KBE_SPLIT_BF16
+ * steps encode each system's digit planes into one buffer held by the batch,
+ * the size of the largest active system's planes (about twice its two
+ * triangles), allocated by the first split step that needs it; if that
+ * allocation fails, the contraction converts its operands itself (slower,
+ * same results).  Results agree
  * with kbe_step to rounding (the history sum is chunked differently). */
 kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, void* stream);
 

@@ -278,6 +278,11 @@ struct kbe_batch {
   std::vector<int> g_rows;
   int g_count = 0;               // kernels in the step graph
   int last_launches = 0;
+  // split precision: digit planes of one system at a time (the largest
+  // active system's size), encoded in full for every system and sweep
+  void* d_planes = nullptr;
+  size_t planes_bytes = 0;
+  bool planes_failed = false;    // allocation failed: the contraction converts its own operands
 };
 
 namespace {
@@ -330,7 +335,11 @@ cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_hos
         SplitLaunch l{y.M, n, y.L, y.R, y.Sl, y.Sg, WeightsView{y.wbar, y.band, y.band_w}, y.I, c->d_split,
                       c->split_bytes, d.status};
         int k = 0;
-        e = launch_history_split(l, s, &k);
+        SplitPlanes lay;
+        if (b->d_planes && split_planes_layout(y.M, c->n_max, &lay) && lay.bytes <= b->planes_bytes)
+          e = launch_history_split2(l, lay, b->d_planes, 0, s, &k);  // encoder + bulk-copy-fed contraction
+        else
+          e = launch_history_split(l, s, &k);
         nl += k;
       }
     }
@@ -472,6 +481,7 @@ kbe_status kbe_batch_destroy(kbe_batch* b) {
   cudaFree(b->d_mem);
   cudaFree(b->d_order);
   cudaFree(b->d_field);
+  cudaFree(b->d_planes);
   delete b;
   return KBE_OK;
 }
@@ -538,6 +548,26 @@ kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, v
   const bool same_rows = precision == KBE_FP64 ||
                          ((int)b->g_rows.size() == b->n_sys && std::equal(b->g_rows.begin(), b->g_rows.end(), rows));
   if (precision == KBE_SPLIT_BF16 && (e = split_prepare()) != cudaSuccess) return bcuda(b, e, "kbe_batch_step: split setup");
+  if (precision == KBE_SPLIT_BF16 && !b->planes_failed) {  // plane buffer, before any capture
+    size_t need = 0;
+    for (int i = 0; i < b->n_sys; ++i) {
+      SplitPlanes lay;
+      if (rows[i] >= 1 && split_planes_layout(b->ctx[i]->M, b->ctx[i]->n_max, &lay)) need = std::max(need, lay.bytes);
+    }
+    if (need > b->planes_bytes) {
+      drop_graph(b);  // the graph holds the buffer's address
+      cudaFree(b->d_planes);
+      b->d_planes = nullptr;
+      b->planes_bytes = 0;
+      if (cudaMalloc(&b->d_planes, need) != cudaSuccess) {
+        cudaGetLastError();
+        b->d_planes = nullptr;
+        b->planes_failed = true;
+      } else {
+        b->planes_bytes = need;
+      }
+    }
+  }
   if (!b->graph || b->g_P != P || b->g_prec != precision || b->g_block != b->dev.block ||
       b->g_work != b->dev.item_work_log2 || !same_rows) {
     drop_graph(b);
