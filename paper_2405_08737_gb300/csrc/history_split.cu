@@ -494,7 +494,7 @@ struct EncodeArgs {
 
 // One CTA per (column tile, chunk): thread (arr, jrow) encodes row jrow of
 // plane arr (0: G^< from L, 1: Q from R) for the chunk's 16 K entries.
-__global__ void __launch_bounds__(256) split_encode(EncodeArgs a) {
+__global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
   const SplitGeom& g = a.g;
   const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
   const int ctile = a.ct_base + (int)(blockIdx.x / (unsigned)a.kc_count);
