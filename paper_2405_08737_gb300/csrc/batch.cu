@@ -283,6 +283,9 @@ struct kbe_batch {
   void* d_planes = nullptr;
   size_t planes_bytes = 0;
   bool planes_failed = false;    // allocation failed: the contraction converts its own operands
+  // split steps run system by system: rows vectors with one active system each
+  int* d_rows1 = nullptr;        // [n_sys][n_sys]
+  std::vector<int> rows1;
 };
 
 namespace {
@@ -305,9 +308,54 @@ void drop_graph(kbe_batch* b) {
 
 constexpr int kElemBlocks = 152 * 8;
 
+// Split precision with the plane buffer: the whole step of one system after
+// the other (plan, predictor, P x {self-energy, encoder + contraction, Fock,
+// RHS, corrector}), so that the system's digit planes stay in the buffer
+// between its sweeps and the later sweeps re-encode only the units that
+// touch its new row.
+cudaError_t enqueue_split_by_system(kbe_batch* b, int P, const int* rows_host, cudaStream_t s, int* count) {
+  int nl = 0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < b->n_sys && e == cudaSuccess; ++i) {
+    const int n = rows_host[i];
+    const kbe_ctx* c = b->ctx[i];
+    if (n < 1 || n >= c->grid.n_t) continue;
+    BatchDev d = b->dev;
+    d.rows = b->d_rows1 + (size_t)i * b->n_sys;
+    const BatchSys& y = b->sys[i];
+    SplitPlanes lay;
+    const bool planes = split_planes_layout(y.M, c->n_max, &lay) && lay.bytes <= b->planes_bytes;
+    batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
+    batch_rows<kOpPredictor><<<kElemBlocks, 256, 0, s>>>(d);
+    nl += 2;
+    e = cudaGetLastError();
+    for (int it = 0; it < P && e == cudaSuccess; ++it) {
+      batch_rows<kOpSigma><<<kElemBlocks, 256, 0, s>>>(d);
+      ++nl;
+      SplitLaunch l{y.M, n, y.L, y.R, y.Sl, y.Sg, WeightsView{y.wbar, y.band, y.band_w}, y.I, c->d_split,
+                    c->split_bytes, d.status};
+      int k = 0;
+      if (planes)  // rows < n are final after the first sweep's encoding
+        e = launch_history_split2(l, lay, b->d_planes, it == 0 ? 0 : n, s, &k);
+      else
+        e = launch_history_split(l, s, &k);
+      nl += k;
+      if (e != cudaSuccess) break;
+      batch_fock<<<b->n_sys, 256, 0, s>>>(d);
+      batch_rows<kOpRhs><<<kElemBlocks, 256, 0, s>>>(d);
+      batch_rows<kOpCorrector><<<kElemBlocks, 256, 0, s>>>(d);
+      nl += 3;
+      e = cudaGetLastError();
+    }
+  }
+  *count = nl;
+  return e;
+}
+
 // Enqueue one batched step (rows already on the device).  Split precision
 // launches each system's tensor-core slice (host rows needed).
 cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_host, cudaStream_t s, int* count) {
+  if (precision == KBE_SPLIT_BF16 && b->d_planes && b->d_rows1) return enqueue_split_by_system(b, P, rows_host, s, count);
   BatchDev d = b->dev;
   int nl = 0;
   batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
@@ -482,6 +530,7 @@ kbe_status kbe_batch_destroy(kbe_batch* b) {
   cudaFree(b->d_order);
   cudaFree(b->d_field);
   cudaFree(b->d_planes);
+  cudaFree(b->d_rows1);
   delete b;
   return KBE_OK;
 }
@@ -554,6 +603,12 @@ kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, v
       SplitPlanes lay;
       if (rows[i] >= 1 && split_planes_layout(b->ctx[i]->M, b->ctx[i]->n_max, &lay)) need = std::max(need, lay.bytes);
     }
+    if (!b->d_rows1) {
+      if (cudaMalloc(&b->d_rows1, sizeof(int) * (size_t)b->n_sys * b->n_sys) != cudaSuccess) {
+        cudaGetLastError();
+        b->d_rows1 = nullptr;
+      }
+    }
     if (need > b->planes_bytes) {
       drop_graph(b);  // the graph holds the buffer's address
       cudaFree(b->d_planes);
@@ -567,6 +622,13 @@ kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, v
         b->planes_bytes = need;
       }
     }
+  }
+  if (precision == KBE_SPLIT_BF16 && b->d_rows1) {  // one active system per rows vector
+    b->rows1.assign((size_t)b->n_sys * b->n_sys, -1);
+    for (int i = 0; i < b->n_sys; ++i) b->rows1[(size_t)i * b->n_sys + i] = rows[i];
+    if ((e = cudaMemcpyAsync(b->d_rows1, b->rows1.data(), sizeof(int) * b->rows1.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return bcuda(b, e, "kbe_batch_step: rows upload");
   }
   if (!b->graph || b->g_P != P || b->g_prec != precision || b->g_block != b->dev.block ||
       b->g_work != b->dev.item_work_log2 || !same_rows) {
