@@ -394,7 +394,8 @@ kbe_status kbe_batch_bind(kbe_batch* b, int i, void* L, void* R, void* S_less, v
  * The graph of the step is captured on the first call and reused while P,
  * precision and the tile policy stay the same (KBE_SPLIT_BF16 graphs also
  * depend on the rows and are re-captured when they change).  KBE_SPLIT_BF16
- * steps encode each system's digit planes into one buffer held by the batch,
+ * steps run system by system within the graph and encode each system's
+ * digit planes into one buffer held by the batch,
  * the size of the largest active system's planes (about twice its two
  * triangles), allocated by the first split step that needs it; if that
  * allocation fails, the contraction converts its operands itself (slower,
