@@ -863,13 +863,15 @@ __global__ void __launch_bounds__(256) split_reduce2(SplitGeom g, const double* 
       const double2* sr = reinterpret_cast<const double2*>(S) + (size_t)m * MM + aa * M;
       const double2* rr = reinterpret_cast<const double2*>(R) + tri(c, m) * MM + bb * M;
       double tr = 0.0, ti = 0.0;
-      for (int x = 0; x < M; ++x) {
+      for (int x = 0; x < M; ++x) {  // p * conj(q): four FMAs per term
         const double2 p = sr[x], q = rr[x];
-        tr += p.x * q.x + p.y * q.y;   // p * conj(q)
-        ti += p.y * q.x - p.x * q.y;
+        tr = fma(p.x, q.x, tr);
+        tr = fma(p.y, q.y, tr);
+        ti = fma(p.y, q.x, ti);
+        ti = fma(-p.x, q.y, ti);
       }
-      re += dw * tr;
-      im += dw * ti;
+      re = fma(dw, tr, re);
+      im = fma(dw, ti, im);
     }
     bad |= !(isfinite(re) && isfinite(im));
     reinterpret_cast<double2*>(out)[((size_t)s * (n + 1) + c) * MM + aa * M + bb] = make_double2(re, im);

@@ -307,8 +307,10 @@ __device__ __forceinline__ bool rhs_entry(const StepArgs& a, int64_t lin) {
     const double2 l = ldd(Lb + 2 * (x * M + ib));
     const double2 r = ldd(Rb + 2 * (x * M + ib));
     const double gr = r.x + l.x, gi = r.y + l.y;
-    sl.x += e.x * l.x - e.y * l.y; sl.y += e.x * l.y + e.y * l.x;
-    sg.x += e.x * gr - e.y * gi;   sg.y += e.x * gi + e.y * gr;
+    sl.x = fma(e.x, l.x, sl.x); sl.x = fma(-e.y, l.y, sl.x);
+    sl.y = fma(e.x, l.y, sl.y); sl.y = fma(e.y, l.x, sl.y);
+    sg.x = fma(e.x, gr, sg.x);  sg.x = fma(-e.y, gi, sg.x);
+    sg.y = fma(e.x, gi, sg.y);  sg.y = fma(e.y, gr, sg.y);
   }
   // -i (x + i y) = y - i x
   const double2 fl = make_double2(sl.y, -sl.x), fg = make_double2(sg.y, -sg.x);
