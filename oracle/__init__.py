@@ -392,3 +392,45 @@ def adams_error_integrals(t, n, q):
 def _tri_size(n):
     return n * (n + 1) // 2
 
+
+
+def run_thermal(t, order, h0, U, v, pulse, P, beta, N, ktau, GM, L0, R0, U4=None, nthreads=1):
+    """Stepper runs with the thermal branch (Sec. 2, Eq. KBE3): rows 1..n_t-1
+    from row 0 (L0, R0 blocks) and G^M on the uniform tau grid of N points
+    (GM [N, M, M], tau_0 = 0+, tau_{N-1} = beta-).  Returns (L, R, Gm) with
+    the mixed rows Gm [n_t, N, M, M]."""
+    t, order = _f64(t), _i32(order)
+    h0, v = _c128(h0), _f64(v)
+    M = h0.shape[0]
+    n_t = len(t)
+    L = np.zeros((_tri_size(n_t), M, M), np.complex128)
+    R = np.zeros_like(L)
+    L[0], R[0] = _c128(L0), _c128(R0)
+    Gm = np.zeros((n_t, N, M, M), np.complex128)
+    Uv = _f64(U if U is not None else np.zeros(M))
+    U4p = _p(_f64(U4)) if U4 is not None else None
+    _check(lib().orc_run_thermal(ctypes.c_int(M), ctypes.c_int(n_t), _p(t), _p(order), _p(h0), _p(Uv), U4p, _p(v),
+                                 _p(_pulse4(pulse)), ctypes.c_int(P), ctypes.c_double(beta), ctypes.c_int(N),
+                                 ctypes.c_int(ktau), _p(_c128(GM)), _p(L), _p(R), _p(Gm), ctypes.c_int(nthreads)),
+           "run_thermal")
+    return L, R, Gm
+
+
+def matsubara_conv(beta, ktau, S, GM):
+    """int_0^beta S(s) G^M(s - tau_j) ds on the uniform tau grid (split at s = tau_j)."""
+    S, GM = _c128(S), _c128(GM)
+    N, M = S.shape[0], S.shape[-1]
+    out = np.zeros_like(S)
+    _check(lib().orc_matsubara_conv(ctypes.c_int(M), ctypes.c_int(N), ctypes.c_double(beta), ctypes.c_int(ktau),
+                                    _p(S), _p(GM), _p(out)), "matsubara_conv")
+    return out
+
+
+def sigma_mixed(U4, n, Gm):
+    """Sigma^|(t_n, tau_k) of Eq. (SE) from mixed rows Gm [rows, N, M, M]."""
+    U4, Gm = _f64(U4), _c128(Gm)
+    N, M = Gm.shape[1], Gm.shape[-1]
+    out = np.zeros((N, M, M), np.complex128)
+    _check(lib().orc_sigma_mixed(ctypes.c_int(M), ctypes.c_int(N), ctypes.c_int(n), _p(U4), _p(Gm), _p(out)),
+           "sigma_mixed")
+    return out

@@ -16,6 +16,8 @@
 //   * self-energy -- Sec. 2, Eq. (SE), summed over the non-zero entries of
 //     the four-index Coulomb tensor.
 //   * Fock matrix -- Eq. (eps), for the local tensor or a general real one.
+//   * thermal branch -- Sec. 2, Eq. (KBE3) and the tau terms of Eq. (KBE2) on
+//     a uniform tau grid with the same kind of composite weights.
 //   * history integrals -- Sec. 2, Eq. (KBE2), and Eq. (KBE1) for the adjoint
 //     identity, with theta(0) = 1 and G(t,t') = -G(t',t)^+.
 //   * stepper -- integral-form Adams-Moulton on the same kind of weights with
@@ -876,6 +878,207 @@ int run_controlled(const Model<double>& md, const double* U4, const CtlOpts& o, 
   return finish(n, n_err, n_conv, 0);
 }
 
+
+// ------------------------------------------------------- thermal branch --
+// Sec. 2: with a thermal branch the mixed component G^|(t,tau) joins the
+// state (Eq. KBE3) and Eq. (KBE2) gains the term -i int_0^beta dtau
+// Sigma^|(t,tau) G^|-(tau,t').  Conventions (fermions):
+//   G^M(tau), tau in (0, beta), antiperiodic: G^M(tau - beta) = -G^M(tau);
+//   G^|-(tau, t) = [G^|(t, beta - tau)]^+;   G^|(0, tau) = -i G^M(beta - tau);
+//   Sigma^|(t,tau)_ij = U_ifde UEx_jabc G^|_fb(t,tau) G^|_ea(t,tau) G^|-_cd(tau,t)  (Eq. SE);
+//   i d/dt G^|(t,tau) = eps(t) G^|(t,tau) + int_0^t Sigma^R(t,s) G^|(s,tau) ds
+//                       + int_0^beta Sigma^|(t,s) G^M(s - tau) ds          (Eq. KBE3).
+// tau grid: tau_k = k beta / (N-1).  An integral over [0, tau_j] sums, per
+// interval [tau_{l-1}, tau_l], the integral of the interpolant of degree
+// kap = min(ktau, j) (Eq. weights) through kap+1 consecutive nodes that
+// contain the interval, centred on it where possible and kept inside
+// [0, tau_j] (all tau points exist at once, unlike the past-only stencils in
+// t); integrals over [tau_j, beta] use the mirrored rule.  The Matsubara
+// convolution is split at s = tau_j, where G^M(s - tau) jumps.
+struct TauGrid {
+  int N, ktau;
+  double beta;
+  std::vector<double> tau;
+  std::vector<std::vector<double>> left;  // [j][k], k <= j: int_0^{tau_j}
+  void build() {
+    tau.resize(N);
+    for (int k = 0; k < N; ++k) tau[k] = beta * k / (N - 1);
+    left.resize(N);
+    double w[64];
+    for (int j = 0; j < N; ++j) {
+      left[j].assign(j + 1, 0.0);
+      const int kap = ktau < j ? ktau : j;
+      for (int l = 1; l <= j; ++l) {
+        int s0 = l - 1 - (kap - 1) / 2;
+        if (s0 > j - kap) s0 = j - kap;
+        if (s0 < 0) s0 = 0;
+        lagrange_weights(tau.data() + s0, kap, tau[l - 1], tau[l], w);
+        for (int i = 0; i <= kap; ++i) left[j][s0 + i] += w[i];
+      }
+    }
+  }
+  double full(int k) const { return left[N - 1][k]; }                 // int_0^beta
+  double right(int j, int k) const { return left[N - 1 - j][N - 1 - k]; }  // int_{tau_j}^beta, k >= j
+};
+
+struct Mixed {
+  int M, N;
+  C64* G;  // [rows][N][M][M]
+  C64 at(int r, int k, int a, int b) const { return G[(((int64_t)r * N + k) * M + a) * M + b]; }
+  C64 adj(int k, int r, int a, int b) const { return conj(at(r, N - 1 - k, b, a)); }  // G^|-(tau_k, t_r)
+};
+
+// Sigma^|(t_n, tau_k), k = 0..N-1, for the tensor U4; out [N][M][M].
+void sigma_mixed(const Mixed& X, const double* U4, int n, C64* out) {
+  const int M = X.M, N = X.N;
+  auto at = [M](int a, int b, int c, int d) { return ((a * M + b) * M + c) * M + d; };
+  struct E { int i, f, d, e; double u; };
+  std::vector<E> nzU, nzX;
+  for (int i = 0; i < M; ++i)
+    for (int f = 0; f < M; ++f)
+      for (int d = 0; d < M; ++d)
+        for (int e = 0; e < M; ++e) {
+          const double u = U4[at(i, f, d, e)];
+          const double ux = 2.0 * U4[at(i, d, f, e)] - U4[at(i, f, d, e)];
+          if (u != 0.0) nzU.push_back({i, f, d, e, u});
+          if (ux != 0.0) nzX.push_back({i, f, d, e, ux});
+        }
+  for (int k = 0; k < N; ++k) {
+    C64* o = out + (size_t)k * M * M;
+    for (int q = 0; q < M * M; ++q) o[q] = C64();
+    for (const E& p : nzU)
+      for (const E& q : nzX) {
+        const C64 g = X.at(n, k, p.f, q.d) * X.at(n, k, p.e, q.f) * X.adj(k, n, q.e, p.d);
+        o[p.i * M + q.i] = o[p.i * M + q.i] + scale(p.u * q.u, g);
+      }
+  }
+}
+
+// Right-hand side of Eq. (KBE3) for row n: F^|(n, j) = -i (eps G^|(n,j) + I^|(n,j)); out [N][M][M].
+void rhs_mixed(const Model<double>& md, const Plane<double>& G, const Mixed& X, const TauGrid& tg,
+               const double* t, const int* order, const SigmaRow<double>& S, const C64* Smix, const C64* GM, int n,
+               C64* out) {
+  const int M = md.M, N = tg.N, MM = M * M;
+  std::vector<double> wn(n + 1);
+  composite_row(t, order, n, wn.data());
+  std::vector<C64> eps(MM);
+  fock(md, t[n], G.L + tri(n, n) * MM, eps.data());
+  for (int j = 0; j < N; ++j)
+    for (int a = 0; a < M; ++a)
+      for (int b = 0; b < M; ++b) {
+        Acc<double> acc;
+        for (int m = 0; m <= n; ++m)
+          for (int x = 0; x < M; ++x) acc.add(scale(wn[m], S.ret_nm(m, a, x) * X.at(m, j, x, b)));
+        for (int k = 0; k <= j; ++k)  // G^M(tau_k - tau_j) = -G^M(beta + tau_k - tau_j)
+          for (int x = 0; x < M; ++x)
+            acc.add(scale(-tg.left[j][k], Smix[(size_t)k * MM + a * M + x] * GM[(size_t)(N - 1 + k - j) * MM + x * M + b]));
+        for (int k = j; k < N; ++k)
+          for (int x = 0; x < M; ++x)
+            acc.add(scale(tg.right(j, k), Smix[(size_t)k * MM + a * M + x] * GM[(size_t)(k - j) * MM + x * M + b]));
+        C64 v = acc.get();
+        for (int x = 0; x < M; ++x) v = v + eps[a * M + x] * X.at(n, j, x, b);
+        out[((size_t)j * M + a) * M + b] = mul_mi(v);
+      }
+}
+
+// The KBE2 mixed term of row n, -i sum_k w_k Sigma^|(n,k) G^|-(tau_k, t_c), added to both
+// history integrals I^s(n,c), c = 0..n (layout [s][c][a][b]).
+void add_mixed_term(const Mixed& X, const TauGrid& tg, const C64* Smix, int n, C64* I) {
+  const int M = X.M, MM = M * M, N = tg.N;
+  for (int c = 0; c <= n; ++c)
+    for (int a = 0; a < M; ++a)
+      for (int b = 0; b < M; ++b) {
+        Acc<double> acc;
+        for (int k = 0; k < N; ++k)
+          for (int x = 0; x < M; ++x) acc.add(scale(tg.full(k), Smix[(size_t)k * MM + a * M + x] * X.adj(k, c, x, b)));
+        const C64 v = mul_mi(acc.get());
+        for (int s = 0; s < 2; ++s) {
+          C64& o = I[(((size_t)s * (n + 1) + c) * M + a) * M + b];
+          o = o + v;
+        }
+      }
+}
+
+// Right-hand sides of row j with the thermal terms: F [2][j+1][M][M], Fmix [N][M][M].
+void thermal_rhs(const Model<double>& md, const double* U4, const Plane<double>& G, const Mixed& X,
+                 const TauGrid& tg, const C64* GM, const double* t, const int* order, int j, C64* F, C64* Fmix,
+                 int nthreads) {
+  const int M = md.M, MM = M * M;
+  std::vector<C64> Sl((j + 1) * MM), Sg((j + 1) * MM), I(2 * (j + 1) * MM), Smix((size_t)tg.N * MM);
+  sigma_row(G, U4, j, Sl.data(), Sg.data());
+  sigma_mixed(X, U4, j, Smix.data());
+  SigmaRow<double> S{M, Sl.data(), Sg.data()};
+  history_slice(G, S, t, order, j, I.data(), nthreads);
+  add_mixed_term(X, tg, Smix.data(), j, I.data());
+  rhs_row(md, G, t, I.data(), j, F);
+  rhs_mixed(md, G, X, tg, t, order, S, Smix.data(), GM, j, Fmix);
+}
+
+// Integral-form Adams stepper (the structure of kbe_step, P sweeps) with the
+// thermal branch: rows n = 1 .. n_t-1 of L, R and G^|.  Row 0 and G^|(0, .)
+// are set by the caller.
+void run_thermal(const Model<double>& md, const double* U4, const TauGrid& tg, const C64* GM, const double* t,
+                 const int* order, int n_t, int P, C64* L, C64* R, C64* Gm, int nthreads) {
+  const int M = md.M, MM = M * M, N = tg.N;
+  Plane<double> G{M, L, R};
+  Mixed X{M, N, Gm};
+  std::vector<std::vector<C64>> F(n_t), Fm(n_t);
+  F[0].resize(2 * MM);
+  Fm[0].resize((size_t)N * MM);
+  thermal_rhs(md, U4, G, X, tg, GM, t, order, 0, F[0].data(), Fm[0].data(), nthreads);
+  auto Fat = [&](int j, int s, int c, int k) { return F[j][((size_t)s * (j + 1) + c) * MM + k]; };
+  auto D = [&](int j, int a, int b) { return Fat(j, 0, j, a * M + b) - conj(Fat(j, 0, j, b * M + a)); };
+  double w[64];
+  for (int n = 1; n < n_t; ++n) {
+    const int kn = order[n];
+    std::vector<C64> Gl((n + 1) * MM), Gg((n + 1) * MM), Gx((size_t)N * MM);
+    auto step_rows = [&](bool corr) {
+      for (int c = 0; c < n; ++c) {
+        const int q = std::min(kn, n - c);
+        if (corr) span_weights(t, n - q, n, n, w); else span_weights(t, n - q, n - 1, n, w);
+        const int cnt = corr ? q + 1 : q;
+        for (int k = 0; k < MM; ++k) {
+          C64 al = L[tri(n - 1, c) * MM + k], ag = R[tri(n - 1, c) * MM + k] + L[tri(n - 1, c) * MM + k];
+          for (int p = 0; p < cnt; ++p) {
+            al = al + scale(w[p], Fat(n - q + p, 0, c, k));
+            ag = ag + scale(w[p], Fat(n - q + p, 1, c, k));
+          }
+          Gl[c * MM + k] = al; Gg[c * MM + k] = ag;
+        }
+      }
+      const int q = std::min(kn, n);
+      if (corr) span_weights(t, n - q, n, n, w); else span_weights(t, n - q, n - 1, n, w);
+      const int cnt = corr ? q + 1 : q;
+      for (int k = 0; k < MM; ++k) {
+        C64 al = L[tri(n - 1, n - 1) * MM + k];
+        for (int p = 0; p < cnt; ++p) al = al + scale(w[p], D(n - q + p, k / M, k % M));
+        Gl[n * MM + k] = al;
+      }
+      for (size_t k = 0; k < (size_t)N * MM; ++k) {  // mixed row: the full history in t
+        C64 x = Gm[(size_t)(n - 1) * N * MM + k];
+        for (int p = 0; p < cnt; ++p) x = x + scale(w[p], Fm[n - q + p][k]);
+        Gx[k] = x;
+      }
+      for (int c = 0; c < n; ++c)
+        for (int k = 0; k < MM; ++k) {
+          L[tri(n, c) * MM + k] = Gl[c * MM + k];
+          R[tri(n, c) * MM + k] = Gg[c * MM + k] - Gl[c * MM + k];
+        }
+      for (int k = 0; k < MM; ++k) {
+        L[tri(n, n) * MM + k] = Gl[n * MM + k];
+        R[tri(n, n) * MM + k] = (k / M == k % M) ? C64(0.0, -1.0) : C64();
+      }
+      for (size_t k = 0; k < (size_t)N * MM; ++k) Gm[(size_t)n * N * MM + k] = Gx[k];
+    };
+    step_rows(false);
+    F[n].resize(2 * (n + 1) * MM);
+    Fm[n].resize((size_t)N * MM);
+    for (int sweep = 0; sweep < P; ++sweep) {
+      thermal_rhs(md, U4, G, X, tg, GM, t, order, n, F[n].data(), Fm[n].data(), nthreads);
+      step_rows(true);
+    }
+  }
+}
 }  // namespace
 
 // =================================================================== C ABI ==
@@ -1180,6 +1383,65 @@ int orc_adams_error_integrals(const double* t, int n, int q, double* out) {
   out[0] = node_poly_integral(t, n, np, q);
   out[1] = node_poly_integral(t, n, nc, q);
   out[2] = milne_constant(t, n, q);
+  return 0;
+}
+
+// Thermal branch (Sec. 2, Eq. KBE3): run rows 1..n_t-1 from row 0 with the
+// mixed component.  tau grid of N points on [0, beta], composite weights of
+// order ktau; GM [N][M][M] = G^M(tau_k) (tau_0 = 0+, tau_{N-1} = beta-);
+// Gm [n_t][N][M][M] receives G^|(t_r, tau_k) (row 0 is set here to
+// -i G^M(beta - tau)); L, R hold row 0 on entry.  U4 = NULL: the local U.
+int orc_run_thermal(int M, int n_t, const double* t, const int* order, const double* h0, const double* U,
+                    const double* U4, const double* v, const double* pulse4, int P, double beta, int N, int ktau,
+                    const void* GM, void* L, void* R, void* Gm, int nthreads) {
+  if (M < 1 || n_t < 1 || P < 1 || N < 2 || ktau < 1 || ktau > 12 || !(beta > 0.0)) return 1;
+  std::vector<double> U4loc;
+  Model<double> md{M, (const C64*)h0, U, v, pulse4[0], pulse4[1], pulse4[2], pulse4[3]};
+  if (!U4) { U4loc = local_U4(M, U); U4 = U4loc.data(); } else md.U4d = U4;
+  TauGrid tg{N, ktau, beta};
+  tg.build();
+  const C64* gm = (const C64*)GM;
+  C64* X = (C64*)Gm;
+  const int MM = M * M;
+  for (int j = 0; j < N; ++j)
+    for (int k = 0; k < MM; ++k) {
+      const C64 g = gm[(size_t)(N - 1 - j) * MM + k];
+      X[(size_t)j * MM + k] = C64(g.im, -g.re);  // -i G^M(beta - tau_j)
+    }
+  run_thermal(md, U4, tg, gm, t, order, n_t, P, (C64*)L, (C64*)R, X, nthreads);
+  return 0;
+}
+
+// The split Matsubara convolution of Eq. (KBE3) alone:
+// out(tau_j) = int_0^beta S(s) G^M(s - tau_j) ds on the tau grid; S, GM, out [N][M][M].
+int orc_matsubara_conv(int M, int N, double beta, int ktau, const void* S, const void* GM, void* out) {
+  if (M < 1 || N < 2 || ktau < 1 || ktau > 12) return 1;
+  TauGrid tg{N, ktau, beta};
+  tg.build();
+  const C64* s = (const C64*)S;
+  const C64* g = (const C64*)GM;
+  C64* o = (C64*)out;
+  const int MM = M * M;
+  for (int j = 0; j < N; ++j)
+    for (int a = 0; a < M; ++a)
+      for (int b = 0; b < M; ++b) {
+        Acc<double> acc;
+        for (int k = 0; k <= j; ++k)
+          for (int x = 0; x < M; ++x)
+            acc.add(scale(-tg.left[j][k], s[(size_t)k * MM + a * M + x] * g[(size_t)(N - 1 + k - j) * MM + x * M + b]));
+        for (int k = j; k < N; ++k)
+          for (int x = 0; x < M; ++x)
+            acc.add(scale(tg.right(j, k), s[(size_t)k * MM + a * M + x] * g[(size_t)(k - j) * MM + x * M + b]));
+        o[((size_t)j * M + a) * M + b] = acc.get();
+      }
+  return 0;
+}
+
+// Sigma^|(t_n, tau_k) for the tensor U4 from the mixed rows Gm [rows][N][M][M].
+int orc_sigma_mixed(int M, int N, int n, const double* U4, const void* Gm, void* out) {
+  if (M < 1 || N < 2 || n < 0) return 1;
+  Mixed X{M, N, (C64*)Gm};
+  sigma_mixed(X, U4, n, (C64*)out);
   return 0;
 }
 

@@ -92,6 +92,28 @@ def coulomb_tensor(M, seed, U=1.0, rank=None):
     return T * (U / d)
 
 
+def thermal_free(h, beta, N, t=None):
+    """Non-interacting equilibrium at inverse temperature beta (chemical
+    potential 0) on the uniform tau grid tau_k = k beta / (N - 1):
+    G^M(tau_k) = -V diag(e^{-e tau} (1 - f(e))) V^+ (tau_0 = 0+, tau_{N-1} =
+    beta-), the density f(h), and, for times t, the mixed function
+    G^|(t, tau) = i V diag(e^{-i e t} f(e) e^{e tau}) V^+ [len(t), N, M, M]."""
+    e, V = np.linalg.eigh(h)
+    tau = beta * np.arange(N) / (N - 1)
+    f = 0.5 * (1.0 - np.tanh(0.5 * beta * e))
+    # e^{-e tau}(1 - f) and f e^{e tau}, written to stay finite for large |e| beta
+    one_m_f = 0.5 * (1.0 + np.tanh(0.5 * beta * e))
+    gm_diag = -np.exp(-np.outer(tau, e)) * one_m_f
+    GM = np.einsum("ak,tk,bk->tab", V, gm_diag, V.conj())
+    rho = (V * f) @ V.conj().T
+    mix = None
+    if t is not None:
+        fe = f[None, :] * np.exp(np.outer(tau, e))  # [N, k]
+        ph = np.exp(-1j * np.outer(t, e))            # [T, k]
+        mix = 1j * np.einsum("ak,rk,jk,bk->rjab", V, ph, fe, V.conj())
+    return GM.astype(np.complex128), rho.astype(np.complex128), mix
+
+
 def half_filled_rho(h):
     M = h.shape[0]
     _, V = np.linalg.eigh(h)
