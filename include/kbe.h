@@ -127,6 +127,37 @@ kbe_status kbe_local_weights(const double* tau, int k, double lo, double hi, dou
 kbe_status kbe_set_model(kbe_ctx* ctx, const double* h0, const double* U, const double* v,
                          const double* pulse);
 
+/* Thermal branch (Sec. 2, Eq. KBE3 and the tau terms of Eq. KBE1/KBE2): the
+ * mixed component G^|(t, tau) joins the state, on the uniform grid
+ * tau_k = k beta / (n_tau - 1) (the paper represents tau functions in the
+ * DLR basis, which this library does not have).  GM: host, complex
+ * [n_tau][M][M], the Matsubara function G^M(tau_k) supplied as the initial
+ * condition (tau_0 = 0+, tau_{n_tau-1} = beta-); the call sets
+ * G^|(0, tau) = -i G^M(beta - tau), and the caller sets L(0,0) = i rho
+ * consistently (rho = -G^M(beta-)).  Conventions: G^|-(tau, t) =
+ * [G^|(t, beta - tau)]^+, G^M antiperiodic.  Every kbe_step (and
+ * kbe_rhs_row) then, in FP64 for the local interaction:
+ *   Sigma^|_ab(t_n, tau) = U_a U_b G^|_ab(t_n, tau)^2 G^|-_ba(tau, t_n),
+ *   adds -i int_0^beta Sigma^|(t_n, tau) G^|-(tau, t_c) dtau to I^<(n,c), I^>(n,c),
+ *   F^|(n, tau) = -i [eps G^| + int_0^{t_n} Sigma^R G^|(., tau) + int_0^beta
+ *                Sigma^|(t_n, s) G^M(s - tau) ds]        (Eq. KBE3),
+ * and steps the mixed row with the weights of the diagonal.  tau integrals
+ * over [0, tau_j] take, per interval, the interpolatory rule of order k_tau
+ * (Eq. weights) through nodes centred on the interval inside the range;
+ * [tau_j, beta] the mirrored rule (odd k_tau gives mirror-symmetric weights,
+ * which keep the particle number exactly).  The context holds
+ * (2 + 2 KBE_RING_ROWS + 2 n_max) n_tau M^2 complex entries plus n_tau^2
+ * weights.  GM = NULL turns the branch off.  KBE_EINVAL for a dense
+ * interaction, beta <= 0, n_tau outside [2, 4096], k_tau outside [1, 12],
+ * non-finite G^M.  Batches, the reverse mode, kbe_step_rows and
+ * kbe_run_controlled do not take a thermal branch (KBE_EINVAL / KBE_ESTATE). */
+kbe_status kbe_set_thermal(kbe_ctx* ctx, double beta, int n_tau, int k_tau, const double* GM);
+
+/* Copies rows 0..n_rows-1 of the mixed component [n_rows][n_tau][M][M]
+ * (device buffer buf) out of the context (to_context = 0) or into it
+ * (to_context = 1, e.g. to restart from a stored history), on stream. */
+kbe_status kbe_copy_mixed(kbe_ctx* ctx, int n_rows, void* buf, int to_context, void* stream);
+
 /* General four-index interaction (Sec. 2, Eq. SE and Eq. eps) in place of
  * the model's local U.  U4: host, M^4 real doubles, row-major
  * U4[((i*M + f)*M + d)*M + e] = U_ifde (chemists' order for Coulomb

@@ -54,6 +54,8 @@ def lib():
         L.kbe_set_model.argtypes = [vp, vp, vp, vp, vp]
         L.kbe_set_interaction.argtypes = [vp, vp]
         L.kbe_run_controlled.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_set_thermal.argtypes = [vp, d, i, i, vp]
+        L.kbe_copy_mixed.argtypes = [vp, i, vp, i, vp]
         L.kbe_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_selfenergy_all.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_history_slice.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
@@ -221,6 +223,30 @@ class Context:
         if U4.shape != (self.M,) * 4:
             raise ValueError("U4 must have shape (M, M, M, M)")
         self._check(lib().kbe_set_interaction(self._h, _np_ptr(U4)))
+
+    def set_thermal(self, beta, GM, k_tau=5):
+        """Thermal branch (Sec. 2, Eq. KBE3) with the Matsubara function
+        GM [n_tau, M, M] on the uniform tau grid of [0, beta]; None turns it
+        off.  Sets the mixed row of t = 0 from G^M."""
+        if GM is None:
+            self._check(lib().kbe_set_thermal(self._h, ctypes.c_double(0.0), 0, 0, None))
+            return
+        GM = np.ascontiguousarray(GM, np.complex128)
+        if GM.ndim != 3 or GM.shape[1:] != (self.M, self.M):
+            raise ValueError("GM must have shape (n_tau, M, M)")
+        self.n_tau = GM.shape[0]
+        self._check(lib().kbe_set_thermal(self._h, ctypes.c_double(beta), self.n_tau, k_tau, _np_ptr(GM)))
+
+    def mixed_rows(self, n_rows, stream=None):
+        """Copy of the mixed rows G^|(t_r, tau_k), r < n_rows: [n_rows, n_tau, M, M]."""
+        import torch
+        out = torch.empty((n_rows, self.n_tau, self.M, self.M), dtype=torch.complex128, device="cuda")
+        self._check(lib().kbe_copy_mixed(self._h, n_rows, self._dev(out), 0, self._stream(stream)))
+        return out
+
+    def set_mixed_rows(self, rows, stream=None):
+        """Load mixed rows [n_rows, n_tau, M, M] (device) into the context."""
+        self._check(lib().kbe_copy_mixed(self._h, rows.shape[0], self._dev(rows), 1, self._stream(stream)))
 
     def selfenergy_slice(self, n, L, R, Sl, Sg, stream=None):
         self._check(lib().kbe_selfenergy_slice(self._h, n, self._dev(L), self._dev(R), self._dev(Sl),

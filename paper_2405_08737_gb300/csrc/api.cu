@@ -47,6 +47,9 @@ void release(kbe_ctx* ctx) {
   cudaFree(ctx->d_ctl);
   ctx->d_ctl = nullptr;
   ctx->ctl_bytes = 0;
+  cudaFree(ctx->d_th);
+  ctx->d_th = nullptr;
+  ctx->thermal = false;
   ctx->dense = false;
   ctx->d_hist = nullptr;
   ctx->d_korder = nullptr;
@@ -175,6 +178,77 @@ StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F
   return a;
 }
 
+
+// ------------------------------------------------------- thermal branch --
+struct ThermalLayout {
+  double *GM, *left, *Smix, *Fx, *Gx;
+};
+
+ThermalLayout thermal_layout(kbe_ctx* ctx) {
+  const size_t MM = (size_t)ctx->M * ctx->M, N = ctx->th_N;
+  double* w = ctx->d_th;
+  ThermalLayout t;
+  t.GM = w;    w += N * MM * 2;
+  t.left = w;  w += N * N;
+  t.Smix = w;  w += N * MM * 2;
+  t.Fx = w;    w += (size_t)kRing * N * MM * 2;
+  t.Gx = w;
+  return t;
+}
+
+ThermalArgs thermal_args(kbe_ctx* ctx, const StepArgs& a, const void* Sl, const void* Sg, void* I) {
+  const ThermalLayout t = thermal_layout(ctx);
+  ThermalArgs x;
+  x.M = ctx->M;
+  x.N = ctx->th_N;
+  x.n = a.n;
+  x.kn = a.kn;
+  x.U = ctx->d_U;
+  x.Sl = (const double*)Sl;
+  x.Sg = (const double*)Sg;
+  x.w = weights_view(ctx);
+  x.eps = ctx->d_eps;
+  x.GM = t.GM;
+  x.left = t.left;
+  x.Gx = t.Gx;
+  x.Smix = t.Smix;
+  x.Fx = t.Fx;
+  x.I = (double*)I;
+  x.corr = a.corr;
+  x.pred = a.pred;
+  x.status = ctx->d_status;
+  return x;
+}
+
+// tau weights of the thermal branch: row j integrates over [0, tau_j]; each
+// interval takes the interpolatory rule (Eq. weights, LU-solved) through
+// kap + 1 = min(k, j) + 1 consecutive nodes containing it, centred where
+// possible and kept inside [0, tau_j]
+kbe_status thermal_weights(int N, double beta, int k, std::vector<double>* left, std::string* err) {
+  std::vector<double> tau(N);
+  for (int i = 0; i < N; ++i) tau[i] = beta * i / (N - 1);
+  left->assign((size_t)N * N, 0.0);
+  double w[kWTab];
+  for (int j = 1; j < N; ++j) {
+    const int kap = std::min(k, j);
+    for (int l = 1; l <= j; ++l) {
+      const int s0 = std::max(0, std::min(l - 1 - (kap - 1) / 2, j - kap));
+      kbe_status st = local_weights(tau.data() + s0, kap, tau[l - 1], tau[l], w, err);
+      if (st != KBE_OK) return st;
+      for (int i = 0; i <= kap; ++i) (*left)[(size_t)j * N + s0 + i] += w[i];
+    }
+  }
+  return KBE_OK;
+}
+
+// the thermal kernels of one sweep after the history slice (Sigma^|, mixed
+// term into I), and the mixed right-hand side after the Fock matrix
+cudaError_t thermal_sweep_a(kbe_ctx* ctx, const ThermalArgs& x, cudaStream_t s) {
+  cudaError_t e = launch_th_sigma(x, s);
+  if (e == cudaSuccess) e = launch_th_mixed(x, s);
+  return e;
+}
+
 // One KBE step (predictor, then P rounds of self-energy, history slice,
 // Fock matrix, right-hand side and corrector).  F rows are addressed as
 // slot (j - f_base) % f_rows.  With save != nullptr, row n of L and R is
@@ -200,6 +274,10 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
   int count = 0, nl = 0;
   cudaError_t e = launch_predictor(a, s);
   ++count;
+  if (e == cudaSuccess && ctx->thermal) {
+    e = launch_th_adams(thermal_args(ctx, a, Sl, Sg, I_work), false, s);
+    ++count;
+  }
   *count_out = count;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: predictor");
   for (int it = 0; it < P; ++it) {
@@ -218,6 +296,17 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
     kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl, true);
     *count_out = (count += nl);
     if (st != KBE_OK) return st;
+    if (ctx->thermal) {
+      const ThermalArgs x = thermal_args(ctx, a, Sl, Sg, I_work);
+      if ((e = thermal_sweep_a(ctx, x, s)) != cudaSuccess || (e = launch_fock(a, s)) != cudaSuccess ||
+          (e = launch_rhs_corrector(a, s)) != cudaSuccess || (e = launch_th_rhs(x, s)) != cudaSuccess ||
+          (e = launch_th_adams(x, true, s)) != cudaSuccess) {
+        *count_out = count + 7;
+        return cuda_fail(ctx, e, "kbe_step: thermal corrector");
+      }
+      *count_out = (count += 7);
+      continue;
+    }
     if ((e = launch_fock(a, s)) != cudaSuccess || (e = launch_rhs_corrector(a, s)) != cudaSuccess) {
       *count_out = count + 3;
       return cuda_fail(ctx, e, "kbe_step: corrector");
@@ -559,6 +648,69 @@ kbe_status kbe_set_model(kbe_ctx* ctx, const double* h0, const double* U, const 
   return KBE_OK;
 }
 
+kbe_status kbe_set_thermal(kbe_ctx* ctx, double beta, int n_tau, int k_tau, const double* GM) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!GM) {
+    ctx->thermal = false;
+    return KBE_OK;
+  }
+  if (ctx->dense) return fail(ctx, KBE_EINVAL, "kbe_set_thermal: the thermal branch needs the local interaction");
+  if (!(beta > 0.0) || !std::isfinite(beta) || n_tau < 2 || n_tau > 4096 || k_tau < 1 || k_tau > kMaxOrder)
+    return fail(ctx, KBE_EINVAL, "kbe_set_thermal: need beta > 0, 2 <= n_tau <= 4096, 1 <= k_tau <= 12");
+  const int M = ctx->M;
+  const size_t MM = (size_t)M * M, N = n_tau;
+  for (size_t i = 0; i < 2 * N * MM; ++i)
+    if (!std::isfinite(GM[i])) return fail(ctx, KBE_EINVAL, "kbe_set_thermal: non-finite G^M");
+  std::vector<double> left;
+  kbe_status st = thermal_weights(n_tau, beta, k_tau, &left, &ctx->err);
+  if (st != KBE_OK) return st;
+  if ((st = use_device(ctx)) != KBE_OK) return st;
+  const size_t doubles = 2 * N * MM + N * N + 2 * N * MM + 2 * (size_t)kRing * N * MM + 2 * (size_t)ctx->n_max * N * MM;
+  cudaFree(ctx->d_th);
+  ctx->d_th = nullptr;
+  ctx->thermal = false;
+  cudaError_t e = dev_alloc(&ctx->d_th, doubles);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->d_th = nullptr;
+    return fail(ctx, e == cudaErrorMemoryAllocation ? KBE_ENOMEM : KBE_ECUDA, "kbe_set_thermal: allocation");
+  }
+  ctx->th_N = n_tau;
+  ctx->th_k = k_tau;
+  ctx->th_beta = beta;
+  const ThermalLayout t = thermal_layout(ctx);
+  // initial mixed row G^|(0, tau_j) = -i G^M(beta - tau_j)
+  std::vector<double> row0(2 * N * MM);
+  for (size_t j = 0; j < N; ++j)
+    for (size_t k = 0; k < MM; ++k) {
+      const double* g = GM + 2 * ((N - 1 - j) * MM + k);
+      row0[2 * (j * MM + k)] = g[1];
+      row0[2 * (j * MM + k) + 1] = -g[0];
+    }
+  if ((e = cudaMemcpy(t.GM, GM, 2 * N * MM * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(t.left, left.data(), N * N * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(t.Gx, row0.data(), row0.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_set_thermal: upload");
+  ctx->thermal = true;
+  return KBE_OK;
+}
+
+kbe_status kbe_copy_mixed(kbe_ctx* ctx, int n_rows, void* buf, int to_context, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!ctx->thermal) return fail(ctx, KBE_ESTATE, "kbe_copy_mixed: no thermal branch (kbe_set_thermal)");
+  if (n_rows < 1 || n_rows > ctx->n_max) return fail(ctx, KBE_EINVAL, "kbe_copy_mixed: n_rows outside [1, n_max]");
+  if (!aligned16(buf)) return fail(ctx, KBE_EINVAL, "kbe_copy_mixed: NULL or misaligned pointer");
+  kbe_status st = use_device(ctx);
+  if (st != KBE_OK) return st;
+  const size_t bytes = (size_t)n_rows * ctx->th_N * ctx->M * ctx->M * 16;
+  double* Gx = thermal_layout(ctx).Gx;
+  cudaError_t e = to_context ? cudaMemcpyAsync(Gx, buf, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream)
+                             : cudaMemcpyAsync(buf, Gx, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_copy_mixed");
+}
+
 kbe_status kbe_set_interaction(kbe_ctx* ctx, const double* U4) {
   if (!ctx) return KBE_EINVAL;
   ctx->last_launches = 0;
@@ -567,6 +719,7 @@ kbe_status kbe_set_interaction(kbe_ctx* ctx, const double* U4) {
     return KBE_OK;
   }
   const int M = ctx->M;
+  if (ctx->thermal) return fail(ctx, KBE_EINVAL, "kbe_set_interaction: the thermal branch needs the local interaction");
   if (M > kDenseMaxM) return fail(ctx, KBE_ERANGE, "kbe_set_interaction: norb above KBE_DENSE_MAX_NORB");
   const size_t M4 = (size_t)M * M * M * M;
   for (size_t k = 0; k < M4; ++k)
@@ -668,6 +821,16 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
   count += nl;
   if (st != KBE_OK) { ctx->last_launches = count; return st; }
   StepArgs a = step_args(ctx, j, (void*)L, (void*)R, I_work, F_ring);
+  if (ctx->thermal) {  // Sigma^| and the mixed term, the row's F, then the mixed right-hand side
+    const ThermalArgs x = thermal_args(ctx, a, Sl, Sg, I_work);
+    if ((e = thermal_sweep_a(ctx, x, s)) != cudaSuccess || (e = launch_fock(a, s)) != cudaSuccess ||
+        (e = launch_rhs(a, s)) != cudaSuccess || (e = launch_th_rhs(x, s)) != cudaSuccess) {
+      ctx->last_launches = count + 5;
+      return cuda_fail(ctx, e, "kbe_rhs_row: thermal right-hand side");
+    }
+    ctx->last_launches = count + 5;
+    return KBE_OK;
+  }
   if ((e = launch_fock(a, s)) != cudaSuccess || (e = launch_rhs(a, s)) != cudaSuccess) {
     ctx->last_launches = count + 2;
     return cuda_fail(ctx, e, "kbe_rhs_row: right-hand side");
@@ -692,6 +855,7 @@ kbe_status kbe_step_rows(kbe_ctx* ctx, int n, int P, int precision, void* L, voi
                          void* I_work, void* F_rows, int j0, int n_rows, void* stream) {
   if (!ctx) return KBE_EINVAL;
   ctx->last_launches = 0;
+  if (ctx->thermal) return fail(ctx, KBE_ESTATE, "kbe_step_rows: the thermal branch steps with kbe_step");
   kbe_status st = check_step_call(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_rows);
   if (st != KBE_OK) return st;
   if ((st = check_row_store(ctx, n, j0, n_rows)) != KBE_OK) return st;
@@ -732,7 +896,8 @@ kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, cons
   kbe_status st = check_row_call(ctx, n);
   if (st != KBE_OK) return st;
   if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
-  if (ctx->dense) return fail(ctx, KBE_ESTATE, "kbe_adjoint_selfenergy_slice: needs the local interaction");
+  if (ctx->dense || ctx->thermal)
+    return fail(ctx, KBE_ESTATE, "kbe_adjoint_selfenergy_slice: needs the local interaction and no thermal branch");
   if (!aligned16(L) || !aligned16(R) || !aligned16(dS_less) || !aligned16(dS_great) || !aligned16(dL_row) ||
       !aligned16(dR_row) || !dU || (reinterpret_cast<uintptr_t>(dU) & 7u))
     return fail(ctx, KBE_EINVAL, "kbe_adjoint_selfenergy_slice: NULL or misaligned pointer");
@@ -755,7 +920,8 @@ kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* 
       (reinterpret_cast<uintptr_t>(dU) & 7u) || (reinterpret_cast<uintptr_t>(dE0) & 7u))
     return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: NULL or misaligned pointer");
   if (!ctx->grid_set) return fail(ctx, KBE_ESTATE, "no grid: call kbe_set_grid first");
-  if (ctx->dense) return fail(ctx, KBE_ESTATE, "kbe_step_adjoint: needs the local interaction");
+  if (ctx->dense || ctx->thermal)
+    return fail(ctx, KBE_ESTATE, "kbe_step_adjoint: needs the local interaction and no thermal branch");
   if (n < 1 || n >= ctx->grid.n_t) return fail(ctx, KBE_ERANGE, "kbe_step_adjoint: n outside [1, n_t)");
   if (row_lo < 0 || row_lo > n) return fail(ctx, KBE_ERANGE, "kbe_step_adjoint: row_lo outside [0, n]");
   if (P < 1 || P > 16) return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: P outside [1, 16]");
@@ -972,6 +1138,7 @@ kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts
   if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_work) || !aligned16(F_ring))
     return fail(ctx, KBE_EINVAL, "kbe_run_controlled: NULL or misaligned device pointer");
   if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
+  if (ctx->thermal) return fail(ctx, KBE_ESTATE, "kbe_run_controlled: runs without the thermal branch");
   const double rtol = opts[0], atol = opts[1], h0 = opts[2], h_max = opts[3], t_end = opts[4];
   const int q_max = iopts[0], k_hist = iopts[1], K_sel = iopts[2], precision = iopts[3];
   for (int i = 0; i < 5; ++i)

@@ -430,6 +430,8 @@ kbe_status kbe_batch_create(kbe_ctx* const* ctxs, int n_sys, kbe_batch** out) {
       return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: batched steps use the grids' history orders");
     if (c->dense)
       return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: batched steps use the local interaction");
+    if (c->thermal)
+      return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: batched steps have no thermal branch");
     if (dev0 < 0) dev0 = c->device;
     if (c->device != dev0) return bfail(nullptr, KBE_EINVAL, "kbe_batch_create: contexts on different devices");
   }

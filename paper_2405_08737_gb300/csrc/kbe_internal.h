@@ -126,6 +126,11 @@ struct kbe_ctx {
   // adaptive time stepping: self-energy and Fock rings, iterates, sums
   double* d_ctl = nullptr;
   size_t ctl_bytes = 0;
+  // thermal branch (Eq. KBE3): tau grid of th_N points on [0, th_beta]
+  bool thermal = false;
+  int th_N = 0, th_k = 0;
+  double th_beta = 0.0;
+  double* d_th = nullptr;     // GM [N][MM] | left [N][N] | Smix [N][MM] | Fx [kRing][N][MM] | Gx [n_max][N][MM]
   // measurement: event pairs around each contraction kernel
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -276,6 +281,29 @@ cudaError_t launch_ctl_predict(const CtlArgs& a, cudaStream_t s);
 cudaError_t launch_ctl_correct(const CtlArgs& a, double* out, cudaStream_t s);
 cudaError_t launch_ctl_divdiff(const CtlArgs& a, double* out, cudaStream_t s);
 cudaError_t launch_ctl_reconstruct(const ReconArgs& r, cudaStream_t s);
+
+// ---- thermal branch (thermal.cu) ----------------------------------------
+struct ThermalArgs {
+  int M, N, n, kn;
+  const double* U;       // local interaction
+  const double* Sl;      // self-energy row n
+  const double* Sg;
+  WeightsView w;
+  const double* eps;     // eps(t_n)
+  const double* GM;      // [N][M][M]
+  const double* left;    // tau weights [N][N]
+  double* Gx;            // mixed rows [n_max][N][M][M]
+  double* Smix;          // Sigma^| row n [N][M][M]
+  double* Fx;            // mixed right-hand sides, ring [kRing][N][M][M]
+  double* I;             // history slice [2][n+1][M][M]
+  const double* corr;    // stepper weights of interval n
+  const double* pred;
+  int* status;
+};
+cudaError_t launch_th_sigma(const ThermalArgs& a, cudaStream_t s);
+cudaError_t launch_th_mixed(const ThermalArgs& a, cudaStream_t s);
+cudaError_t launch_th_rhs(const ThermalArgs& a, cudaStream_t s);
+cudaError_t launch_th_adams(const ThermalArgs& a, bool corrector, cudaStream_t s);
 
 // ---- reverse mode (adjoint.cu) ------------------------------------------
 // Cotangent convention: for a real loss, zbar = dF/dRe z + i dF/dIm z.

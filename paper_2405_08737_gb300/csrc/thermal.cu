@@ -1,0 +1,160 @@
+// thermal.cu -- the thermal branch of the KBE step (Sec. 2, Eq. KBE3 and the
+// tau terms of Eq. KBE2), FP64, local interaction.
+//
+// State: the mixed rows G^|(t_r, tau_k), [n_max][N][M][M], on a uniform tau
+// grid tau_k = k beta / (N-1).  Conventions (fermions):
+//   G^|-(tau, t) = [G^|(t, beta - tau)]^+,  G^M(s - tau) = -G^M(beta + s - tau) for s < tau,
+//   Sigma^|_ab(t,tau) = U_a U_b G^|_ab(t,tau)^2 G^|-_ba(tau,t)           (Eq. SE, local U).
+// Kernels for row n:
+//   th_sigma   Sigma^|(t_n, tau_k), elementwise;
+//   th_mixed   adds -i sum_k w_k Sigma^|(n,k) G^|-(tau_k, t_c) to both history
+//              integrals I^<>(n,c), c = 0..n (one thread per output entry);
+//   th_rhs     F^|(n,j) = -i [eps G^|(n,j) + sum_m w_{n,m} Sigma^R(n,m) G^|(m,j)
+//              + int_0^beta Sigma^|(n,s) G^M(s - tau_j) ds], the Matsubara
+//              convolution split at s = tau_j (one warp per output entry,
+//              lanes over the history and tau points);
+//   th_adams   predictor or corrector of the mixed row with the weights of
+//              the diagonal (q = min(k_n, n) points).
+// tau weights: left[j][k], k <= j, integrate over [0, tau_j]; [tau_j, beta]
+// uses the mirrored row left[N-1-j][N-1-k]; the full interval is row N-1.
+
+#include "kbe_internal.h"
+
+namespace kbe {
+namespace {
+
+constexpr int kThThreads = 256;
+
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
+
+__device__ __forceinline__ void cfma(double2& acc, double w, double2 x, double2 y) {  // acc += w x y
+  const double xr = w * x.x, xi = w * x.y;
+  acc.x = fma(xr, y.x, acc.x);
+  acc.x = fma(-xi, y.y, acc.x);
+  acc.y = fma(xr, y.y, acc.y);
+  acc.y = fma(xi, y.x, acc.y);
+}
+
+__global__ void __launch_bounds__(kThThreads) th_sigma(ThermalArgs a) {
+  const int M = a.M, MM = M * M, N = a.N;
+  const int64_t e = (int64_t)blockIdx.x * kThThreads + threadIdx.x;
+  if (e >= (int64_t)N * MM) return;
+  const int k = (int)(e / MM), ab = (int)(e - (int64_t)k * MM), ia = ab / M, ib = ab - ia * M;
+  const double* row = a.Gx + (int64_t)a.n * N * MM * 2;
+  const double2 g = ld2(row + ((int64_t)k * MM + ab) * 2);
+  const double2 h = ld2(row + ((int64_t)(N - 1 - k) * MM + ab) * 2);  // G^|-_ba(tau_k, t_n) = conj(h)
+  const double uu = a.U[ia] * a.U[ib];
+  const double g2r = g.x * g.x - g.y * g.y, g2i = 2.0 * g.x * g.y;
+  const double2 s = make_double2(uu * (g2r * h.x + g2i * h.y), uu * (g2i * h.x - g2r * h.y));
+  st2(a.Smix + e * 2, s);
+  if (!(isfinite(s.x) && isfinite(s.y))) atomicOr(a.status, kStatusNumeric);
+}
+
+__global__ void __launch_bounds__(kThThreads) th_mixed(ThermalArgs a) {
+  const int M = a.M, MM = M * M, N = a.N, n = a.n;
+  const int64_t e = (int64_t)blockIdx.x * kThThreads + threadIdx.x;
+  if (e >= (int64_t)(n + 1) * MM) return;
+  const int c = (int)(e / MM), ab = (int)(e - (int64_t)c * MM), ia = ab / M, ib = ab - ia * M;
+  const double* wfull = a.left + (int64_t)(N - 1) * N;
+  const double* gc = a.Gx + (int64_t)c * N * MM * 2;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = 0; k < N; ++k) {
+    const double w = wfull[k];
+    const double* sk = a.Smix + ((int64_t)k * MM + ia * M) * 2;
+    const double* gk = gc + ((int64_t)(N - 1 - k) * MM + ib * M) * 2;  // G^|-(tau_k,t_c)_xb = conj(G^|(t_c,beta-tau_k)_bx)
+    for (int x = 0; x < M; ++x) {
+      const double2 g = ld2(gk + 2 * x);
+      cfma(acc, w, ld2(sk + 2 * x), make_double2(g.x, -g.y));
+    }
+  }
+  // -i (x + i y) = y - i x, added to I^< and I^>
+  for (int s = 0; s < 2; ++s) {
+    double* o = a.I + (((int64_t)s * (n + 1) + c) * MM + ab) * 2;
+    const double2 v = ld2(o);
+    st2(o, make_double2(v.x + acc.y, v.y - acc.x));
+  }
+}
+
+__global__ void __launch_bounds__(kThThreads) th_rhs(ThermalArgs a) {
+  const int M = a.M, MM = M * M, N = a.N, n = a.n;
+  const int lane = threadIdx.x & 31;
+  const int64_t item = ((int64_t)blockIdx.x * kThThreads + threadIdx.x) >> 5;
+  if (item >= (int64_t)N * MM) return;  // whole warps leave together
+  const int j = (int)(item / MM), ab = (int)(item - (int64_t)j * MM), ia = ab / M, ib = ab - ia * M;
+  double2 acc = make_double2(0.0, 0.0);
+  // history term: sum_m w_{n,m} Sigma^R(n,m)_ax G^|(m,j)_xb
+  for (int m = lane; m <= n; m += 32) {
+    const double w = a.w.at(n, m);
+    const double* sg = a.Sg + ((int64_t)m * MM + ia * M) * 2;
+    const double* sl = a.Sl + ((int64_t)m * MM + ia * M) * 2;
+    const double* gx = a.Gx + (((int64_t)m * N + j) * MM) * 2;
+    for (int x = 0; x < M; ++x) {
+      const double2 p = ld2(sg + 2 * x), q = ld2(sl + 2 * x);
+      cfma(acc, w, make_double2(p.x - q.x, p.y - q.y), ld2(gx + 2 * (x * M + ib)));
+    }
+  }
+  // Matsubara convolution, split at s = tau_j
+  for (int k = lane; k < N; k += 32) {
+    const double* sk = a.Smix + ((int64_t)k * MM + ia * M) * 2;
+    if (k <= j) {  // G^M(tau_k - tau_j) = -G^M(tau_{N-1+k-j})
+      const double w = -a.left[(int64_t)j * N + k];
+      const double* gm = a.GM + (int64_t)(N - 1 + k - j) * MM * 2;
+      for (int x = 0; x < M; ++x) cfma(acc, w, ld2(sk + 2 * x), ld2(gm + 2 * (x * M + ib)));
+    }
+    if (k >= j) {
+      const double w = a.left[(int64_t)(N - 1 - j) * N + (N - 1 - k)];
+      const double* gm = a.GM + (int64_t)(k - j) * MM * 2;
+      for (int x = 0; x < M; ++x) cfma(acc, w, ld2(sk + 2 * x), ld2(gm + 2 * (x * M + ib)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane != 0) return;
+  const double* gn = a.Gx + (((int64_t)n * N + j) * MM) * 2;
+  for (int x = 0; x < M; ++x) cfma(acc, 1.0, ld2(a.eps + 2 * (ia * M + x)), ld2(gn + 2 * (x * M + ib)));
+  double* out = a.Fx + (((int64_t)(n % kRing) * N + j) * MM + ab) * 2;
+  st2(out, make_double2(acc.y, -acc.x));  // -i (...)
+  if (!(isfinite(acc.x) && isfinite(acc.y))) atomicOr(a.status, kStatusNumeric);
+}
+
+__global__ void __launch_bounds__(kThThreads) th_adams(ThermalArgs a, int corrector) {
+  const int M = a.M, MM = M * M, N = a.N, n = a.n;
+  const int64_t e = (int64_t)blockIdx.x * kThThreads + threadIdx.x;
+  if (e >= (int64_t)N * MM) return;
+  const int q = a.kn < n ? a.kn : n;
+  const double* w = (corrector ? a.corr : a.pred) + (q - 1) * kWTab;
+  double2 g = ld2(a.Gx + ((int64_t)(n - 1) * N * MM + e) * 2);
+  for (int p = 0; p < q + corrector; ++p) {
+    const int jr = n - q + p;
+    const double2 f = ld2(a.Fx + ((int64_t)(jr % kRing) * N * MM + e) * 2);
+    g.x = fma(w[p], f.x, g.x);
+    g.y = fma(w[p], f.y, g.y);
+  }
+  st2(a.Gx + ((int64_t)n * N * MM + e) * 2, g);
+}
+
+unsigned blocks_for(int64_t threads) { return (unsigned)((threads + kThThreads - 1) / kThThreads); }
+
+}  // namespace
+
+cudaError_t launch_th_sigma(const ThermalArgs& a, cudaStream_t s) {
+  th_sigma<<<blocks_for((int64_t)a.N * a.M * a.M), kThThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_th_mixed(const ThermalArgs& a, cudaStream_t s) {
+  th_mixed<<<blocks_for((int64_t)(a.n + 1) * a.M * a.M), kThThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_th_rhs(const ThermalArgs& a, cudaStream_t s) {
+  th_rhs<<<blocks_for((int64_t)a.N * a.M * a.M * 32), kThThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_th_adams(const ThermalArgs& a, bool corrector, cudaStream_t s) {
+  th_adams<<<blocks_for((int64_t)a.N * a.M * a.M), kThThreads, 0, s>>>(a, corrector ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace kbe
