@@ -184,12 +184,16 @@ struct ThermalLayout {
   double *GM, *left, *Smix, *Fx, *Gx;
 };
 
+// doubles of the tau-weight table, padded so that the complex arrays after
+// it start on 256-byte boundaries (the kernels load them as double2)
+size_t thermal_left_doubles(size_t N) { return (N * N + 31) / 32 * 32; }
+
 ThermalLayout thermal_layout(kbe_ctx* ctx) {
   const size_t MM = (size_t)ctx->M * ctx->M, N = ctx->th_N;
   double* w = ctx->d_th;
   ThermalLayout t;
   t.GM = w;    w += N * MM * 2;
-  t.left = w;  w += N * N;
+  t.left = w;  w += thermal_left_doubles(N);
   t.Smix = w;  w += N * MM * 2;
   t.Fx = w;    w += (size_t)kRing * N * MM * 2;
   t.Gx = w;
@@ -666,7 +670,8 @@ kbe_status kbe_set_thermal(kbe_ctx* ctx, double beta, int n_tau, int k_tau, cons
   kbe_status st = thermal_weights(n_tau, beta, k_tau, &left, &ctx->err);
   if (st != KBE_OK) return st;
   if ((st = use_device(ctx)) != KBE_OK) return st;
-  const size_t doubles = 2 * N * MM + N * N + 2 * N * MM + 2 * (size_t)kRing * N * MM + 2 * (size_t)ctx->n_max * N * MM;
+  const size_t doubles = 2 * N * MM + thermal_left_doubles(N) + 2 * N * MM + 2 * (size_t)kRing * N * MM +
+                         2 * (size_t)ctx->n_max * N * MM;
   cudaFree(ctx->d_th);
   ctx->d_th = nullptr;
   ctx->thermal = false;
