@@ -240,7 +240,8 @@ class Context:
     def mixed_rows(self, n_rows, stream=None):
         """Copy of the mixed rows G^|(t_r, tau_k), r < n_rows: [n_rows, n_tau, M, M]."""
         import torch
-        out = torch.empty((n_rows, self.n_tau, self.M, self.M), dtype=torch.complex128, device="cuda")
+        n_tau = max(getattr(self, "n_tau", 0), 1)  # without a thermal branch the call reports KBE_ESTATE
+        out = torch.empty((n_rows, n_tau, self.M, self.M), dtype=torch.complex128, device="cuda")
         self._check(lib().kbe_copy_mixed(self._h, n_rows, self._dev(out), 0, self._stream(stream)))
         return out
 
