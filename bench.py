@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-adaptive", action="store_true", help="skip the adaptive history-order run")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-interaction self-energy and step")
     ap.add_argument("--no-controller", action="store_true", help="skip the adaptive time-stepping runs")
+    ap.add_argument("--no-thermal", action="store_true", help="skip the thermal-branch step")
     ap.add_argument("--dense-norb", default="2,8,16,32",
                     help="comma-separated orbital counts of the dense self-energy rows")
     return ap.parse_args()
@@ -480,6 +481,33 @@ def controller_bench(kbe, seed, stream, t_end=8.0, n_max=2048):
     return out
 
 
+def thermal_bench(kbe, ctx, run, n, P, stream, t, h, steps, beta=10.0, n_tau=128):
+    """The KBE step of the main workload with the thermal branch (Eq. KBE3):
+    mixed rows of the non-interacting state at inverse temperature beta on
+    n_tau tau points, the mixed right-hand sides of the last rows rebuilt,
+    then the same timed steps.  Algorithmic FP64 work of the thermal terms
+    per sweep: the KBE2 mixed term (n+1) M^2 n_tau M and the KBE3 right-hand
+    side n_tau M^2 (n+1+n_tau) M complex multiply-adds (8 flops each)."""
+    import torch
+    import workloads as W
+    M = ctx.M
+    GM, _, mix = W.thermal_free(h, beta, n_tau, t[:n + 1])
+    ctx.set_thermal(beta, GM, k_tau=5)
+    ctx.set_mixed_rows(torch.as_tensor(mix, device="cuda"))
+    del mix
+    for j in range(max(0, n - 6), n):
+        ctx.rhs_row(j, run.L, run.R, run.Sl, run.Sg, run.I, run.F, stream=stream)
+    out = {"workload": "%s step of row n=%d with a thermal branch: beta=%.1f, %d tau points, tau order 5"
+                       % (WORKLOAD, n, beta, n_tau), "n_tau": n_tau}
+    for precision in ("fp64", "split"):
+        ms, launches, _, _ = time_steps(ctx, run, n, P, steps, 2, stream, precision)
+        out[precision + "_ms_per_step"] = round(ms / steps, 4)
+        out[precision + "_gpu_launches"] = launches
+    ctx.set_thermal(beta, None)
+    out["thermal_flops_per_step"] = 8.0 * P * (M ** 3 * n_tau * (n + 1) + M ** 3 * n_tau * (n + 1 + n_tau))
+    return out
+
+
 def hbm_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -686,6 +714,13 @@ def main():
         line["differentiation_form"] = window_bench(kbe, args.seed, stream)
     if rank == 0 and not args.no_adaptive:
         line["adaptive_orders"] = adaptive_bench(kbe, args.seed, stream)
+    if rank == 0 and not args.no_thermal:
+        th = thermal_bench(kbe, ctx, run, n, args.P, stream, t, h, max(3, args.steps // 4))
+        th["fp64_step_without_thermal_ms"] = round(ms_step, 4)
+        d_ms = th["fp64_ms_per_step"] - ms_step
+        th["thermal_terms_tflops_from_step_difference"] = (round(th["thermal_flops_per_step"] / (d_ms * 1e-3) / 1e12, 4)
+                                                           if d_ms > 0 else None)
+        line["thermal_branch"] = th
     if rank == 0 and not args.no_controller:
         line["adaptive_time_stepping"] = controller_bench(kbe, args.seed, stream)
     if rank == 0 and not args.no_dense:

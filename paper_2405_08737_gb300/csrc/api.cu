@@ -684,6 +684,8 @@ kbe_status kbe_set_thermal(kbe_ctx* ctx, double beta, int n_tau, int k_tau, cons
   ctx->th_N = n_tau;
   ctx->th_k = k_tau;
   ctx->th_beta = beta;
+  if ((e = cudaMemset(ctx->d_th, 0, doubles * sizeof(double))) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_set_thermal: clear");
   const ThermalLayout t = thermal_layout(ctx);
   // initial mixed row G^|(0, tau_j) = -i G^M(beta - tau_j)
   std::vector<double> row0(2 * N * MM);
