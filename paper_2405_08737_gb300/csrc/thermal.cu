@@ -8,7 +8,8 @@
 // Kernels for row n:
 //   th_sigma   Sigma^|(t_n, tau_k), elementwise;
 //   th_mixed   adds -i sum_k w_k Sigma^|(n,k) G^|-(tau_k, t_c) to both history
-//              integrals I^<>(n,c), c = 0..n (one thread per output entry);
+//              integrals I^<>(n,c), c = 0..n (8 lanes per output entry, each
+//              taking every 8th tau point, then a shuffle sum);
 //   th_rhs     F^|(n,j) = -i [eps G^|(n,j) + sum_m w_{n,m} Sigma^R(n,m) G^|(m,j)
 //              + int_0^beta Sigma^|(n,s) G^M(s - tau_j) ds], the Matsubara
 //              convolution split at s = tau_j (one warp per output entry,
@@ -51,15 +52,21 @@ __global__ void __launch_bounds__(kThThreads) th_sigma(ThermalArgs a) {
   if (!(isfinite(s.x) && isfinite(s.y))) atomicOr(a.status, kStatusNumeric);
 }
 
+// kMixLanes consecutive lanes share an output entry and split the tau points.
+constexpr int kMixLanes = 8;
+
 __global__ void __launch_bounds__(kThThreads) th_mixed(ThermalArgs a) {
   const int M = a.M, MM = M * M, N = a.N, n = a.n;
-  const int64_t e = (int64_t)blockIdx.x * kThThreads + threadIdx.x;
-  if (e >= (int64_t)(n + 1) * MM) return;
-  const int c = (int)(e / MM), ab = (int)(e - (int64_t)c * MM), ia = ab / M, ib = ab - ia * M;
+  const int64_t tid = (int64_t)blockIdx.x * kThThreads + threadIdx.x;
+  const int64_t e = tid / kMixLanes;           // output entry (groups of lanes never straddle a warp)
+  const int part = (int)(tid % kMixLanes);
+  const bool live = e < (int64_t)(n + 1) * MM;
+  const int64_t ee = live ? e : 0;
+  const int c = (int)(ee / MM), ab = (int)(ee - (int64_t)c * MM), ia = ab / M, ib = ab - ia * M;
   const double* wfull = a.left + (int64_t)(N - 1) * N;
   const double* gc = a.Gx + (int64_t)c * N * MM * 2;
   double2 acc = make_double2(0.0, 0.0);
-  for (int k = 0; k < N; ++k) {
+  for (int k = live ? part : N; k < N; k += kMixLanes) {
     const double w = wfull[k];
     const double* sk = a.Smix + ((int64_t)k * MM + ia * M) * 2;
     const double* gk = gc + ((int64_t)(N - 1 - k) * MM + ib * M) * 2;  // G^|-(tau_k,t_c)_xb = conj(G^|(t_c,beta-tau_k)_bx)
@@ -68,6 +75,11 @@ __global__ void __launch_bounds__(kThThreads) th_mixed(ThermalArgs a) {
       cfma(acc, w, ld2(sk + 2 * x), make_double2(g.x, -g.y));
     }
   }
+  for (int o = kMixLanes / 2; o > 0; o >>= 1) {  // the group's lanes are consecutive within the warp
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (!live || part != 0) return;
   // -i (x + i y) = y - i x, added to I^< and I^>
   for (int s = 0; s < 2; ++s) {
     double* o = a.I + (((int64_t)s * (n + 1) + c) * MM + ab) * 2;
@@ -145,7 +157,7 @@ cudaError_t launch_th_sigma(const ThermalArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_th_mixed(const ThermalArgs& a, cudaStream_t s) {
-  th_mixed<<<blocks_for((int64_t)(a.n + 1) * a.M * a.M), kThThreads, 0, s>>>(a);
+  th_mixed<<<blocks_for((int64_t)(a.n + 1) * a.M * a.M * kMixLanes), kThThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_th_rhs(const ThermalArgs& a, cudaStream_t s) {
