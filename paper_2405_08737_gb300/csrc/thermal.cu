@@ -8,12 +8,10 @@
 // Kernels for row n:
 //   th_sigma   Sigma^|(t_n, tau_k), elementwise;
 //   th_mixed   adds -i sum_k w_k Sigma^|(n,k) G^|-(tau_k, t_c) to both history
-//              integrals I^<>(n,c), c = 0..n (8 lanes per output entry, each
-//              taking every 8th tau point, then a shuffle sum);
+//              integrals I^<>(n,c), c = 0..n;
 //   th_rhs     F^|(n,j) = -i [eps G^|(n,j) + sum_m w_{n,m} Sigma^R(n,m) G^|(m,j)
 //              + int_0^beta Sigma^|(n,s) G^M(s - tau_j) ds], the Matsubara
-//              convolution split at s = tau_j (one warp per output entry,
-//              lanes over the history and tau points);
+//              convolution split at s = tau_j;
 //   th_adams   predictor or corrector of the mixed row with the weights of
 //              the diagonal (q = min(k_n, n) points).
 // tau weights: left[j][k], k <= j, integrate over [0, tau_j]; [tau_j, beta]
@@ -52,21 +50,37 @@ __global__ void __launch_bounds__(kThThreads) th_sigma(ThermalArgs a) {
   if (!(isfinite(s.x) && isfinite(s.y))) atomicOr(a.status, kStatusNumeric);
 }
 
-// kMixLanes consecutive lanes share an output entry and split the tau points.
-constexpr int kMixLanes = 8;
+// th_mixed and th_rhs: a block serves 32 consecutive output entries (one per
+// lane, so that the lanes of a warp read neighbouring entries) and its warps
+// split the long sum (warp w takes every kParts-th point); the warps' sums
+// are added in a fixed order through shared memory.
+constexpr int kParts = 8;
+constexpr int kPartThreads = 32 * kParts;
 
-__global__ void __launch_bounds__(kThThreads) th_mixed(ThermalArgs a) {
+__device__ __forceinline__ bool reduce_parts(double2& acc) {
+  __shared__ double2 red[kParts][32];
+  red[threadIdx.x >> 5][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (threadIdx.x >= 32) return false;
+  acc = red[0][threadIdx.x];
+  for (int w = 1; w < kParts; ++w) {
+    acc.x += red[w][threadIdx.x].x;
+    acc.y += red[w][threadIdx.x].y;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kPartThreads) th_mixed(ThermalArgs a) {
   const int M = a.M, MM = M * M, N = a.N, n = a.n;
-  const int64_t tid = (int64_t)blockIdx.x * kThThreads + threadIdx.x;
-  const int64_t e = tid / kMixLanes;           // output entry (groups of lanes never straddle a warp)
-  const int part = (int)(tid % kMixLanes);
+  const int part = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
   const bool live = e < (int64_t)(n + 1) * MM;
   const int64_t ee = live ? e : 0;
   const int c = (int)(ee / MM), ab = (int)(ee - (int64_t)c * MM), ia = ab / M, ib = ab - ia * M;
   const double* wfull = a.left + (int64_t)(N - 1) * N;
   const double* gc = a.Gx + (int64_t)c * N * MM * 2;
   double2 acc = make_double2(0.0, 0.0);
-  for (int k = live ? part : N; k < N; k += kMixLanes) {
+  for (int k = live ? part : N; k < N; k += kParts) {
     const double w = wfull[k];
     const double* sk = a.Smix + ((int64_t)k * MM + ia * M) * 2;
     const double* gk = gc + ((int64_t)(N - 1 - k) * MM + ib * M) * 2;  // G^|-(tau_k,t_c)_xb = conj(G^|(t_c,beta-tau_k)_bx)
@@ -75,11 +89,7 @@ __global__ void __launch_bounds__(kThThreads) th_mixed(ThermalArgs a) {
       cfma(acc, w, ld2(sk + 2 * x), make_double2(g.x, -g.y));
     }
   }
-  for (int o = kMixLanes / 2; o > 0; o >>= 1) {  // the group's lanes are consecutive within the warp
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-  }
-  if (!live || part != 0) return;
+  if (!reduce_parts(acc) || !live) return;
   // -i (x + i y) = y - i x, added to I^< and I^>
   for (int s = 0; s < 2; ++s) {
     double* o = a.I + (((int64_t)s * (n + 1) + c) * MM + ab) * 2;
@@ -88,15 +98,16 @@ __global__ void __launch_bounds__(kThThreads) th_mixed(ThermalArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kThThreads) th_rhs(ThermalArgs a) {
+__global__ void __launch_bounds__(kPartThreads) th_rhs(ThermalArgs a) {
   const int M = a.M, MM = M * M, N = a.N, n = a.n;
-  const int lane = threadIdx.x & 31;
-  const int64_t item = ((int64_t)blockIdx.x * kThThreads + threadIdx.x) >> 5;
-  if (item >= (int64_t)N * MM) return;  // whole warps leave together
-  const int j = (int)(item / MM), ab = (int)(item - (int64_t)j * MM), ia = ab / M, ib = ab - ia * M;
+  const int part = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+  const bool live = e < (int64_t)N * MM;
+  const int64_t ee = live ? e : 0;
+  const int j = (int)(ee / MM), ab = (int)(ee - (int64_t)j * MM), ia = ab / M, ib = ab - ia * M;
   double2 acc = make_double2(0.0, 0.0);
   // history term: sum_m w_{n,m} Sigma^R(n,m)_ax G^|(m,j)_xb
-  for (int m = lane; m <= n; m += 32) {
+  for (int m = live ? part : n + 1; m <= n; m += kParts) {
     const double w = a.w.at(n, m);
     const double* sg = a.Sg + ((int64_t)m * MM + ia * M) * 2;
     const double* sl = a.Sl + ((int64_t)m * MM + ia * M) * 2;
@@ -107,7 +118,7 @@ __global__ void __launch_bounds__(kThThreads) th_rhs(ThermalArgs a) {
     }
   }
   // Matsubara convolution, split at s = tau_j
-  for (int k = lane; k < N; k += 32) {
+  for (int k = live ? part : N; k < N; k += kParts) {
     const double* sk = a.Smix + ((int64_t)k * MM + ia * M) * 2;
     if (k <= j) {  // G^M(tau_k - tau_j) = -G^M(tau_{N-1+k-j})
       const double w = -a.left[(int64_t)j * N + k];
@@ -120,11 +131,7 @@ __global__ void __launch_bounds__(kThThreads) th_rhs(ThermalArgs a) {
       for (int x = 0; x < M; ++x) cfma(acc, w, ld2(sk + 2 * x), ld2(gm + 2 * (x * M + ib)));
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
-  }
-  if (lane != 0) return;
+  if (!reduce_parts(acc) || !live) return;
   const double* gn = a.Gx + (((int64_t)n * N + j) * MM) * 2;
   for (int x = 0; x < M; ++x) cfma(acc, 1.0, ld2(a.eps + 2 * (ia * M + x)), ld2(gn + 2 * (x * M + ib)));
   double* out = a.Fx + (((int64_t)(n % kRing) * N + j) * MM + ab) * 2;
@@ -157,11 +164,11 @@ cudaError_t launch_th_sigma(const ThermalArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_th_mixed(const ThermalArgs& a, cudaStream_t s) {
-  th_mixed<<<blocks_for((int64_t)(a.n + 1) * a.M * a.M * kMixLanes), kThThreads, 0, s>>>(a);
+  th_mixed<<<(unsigned)(((int64_t)(a.n + 1) * a.M * a.M + 31) / 32), kPartThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_th_rhs(const ThermalArgs& a, cudaStream_t s) {
-  th_rhs<<<blocks_for((int64_t)a.N * a.M * a.M * 32), kThThreads, 0, s>>>(a);
+  th_rhs<<<(unsigned)(((int64_t)a.N * a.M * a.M + 31) / 32), kPartThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_th_adams(const ThermalArgs& a, bool corrector, cudaStream_t s) {
