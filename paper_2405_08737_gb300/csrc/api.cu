@@ -181,7 +181,7 @@ StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F
 
 // ------------------------------------------------------- thermal branch --
 struct ThermalLayout {
-  double *GM, *left, *Smix, *Fx, *Gx;
+  double *GM, *left, *Smix, *Smw, *Aw, *Fx, *Gx;
 };
 
 // doubles of the tau-weight table, padded so that the complex arrays after
@@ -195,6 +195,8 @@ ThermalLayout thermal_layout(kbe_ctx* ctx) {
   t.GM = w;    w += N * MM * 2;
   t.left = w;  w += thermal_left_doubles(N);
   t.Smix = w;  w += N * MM * 2;
+  t.Smw = w;   w += N * MM * 2;
+  t.Aw = w;    w += (size_t)ctx->n_max * MM * 2;
   t.Fx = w;    w += (size_t)kRing * N * MM * 2;
   t.Gx = w;
   return t;
@@ -216,6 +218,8 @@ ThermalArgs thermal_args(kbe_ctx* ctx, const StepArgs& a, const void* Sl, const 
   x.left = t.left;
   x.Gx = t.Gx;
   x.Smix = t.Smix;
+  x.Smw = t.Smw;
+  x.Aw = t.Aw;
   x.Fx = t.Fx;
   x.I = (double*)I;
   x.corr = a.corr;
@@ -670,8 +674,8 @@ kbe_status kbe_set_thermal(kbe_ctx* ctx, double beta, int n_tau, int k_tau, cons
   kbe_status st = thermal_weights(n_tau, beta, k_tau, &left, &ctx->err);
   if (st != KBE_OK) return st;
   if ((st = use_device(ctx)) != KBE_OK) return st;
-  const size_t doubles = 2 * N * MM + thermal_left_doubles(N) + 2 * N * MM + 2 * (size_t)kRing * N * MM +
-                         2 * (size_t)ctx->n_max * N * MM;
+  const size_t doubles = 2 * N * MM + thermal_left_doubles(N) + 4 * N * MM + 2 * (size_t)ctx->n_max * MM +
+                         2 * (size_t)kRing * N * MM + 2 * (size_t)ctx->n_max * N * MM;
   cudaFree(ctx->d_th);
   ctx->d_th = nullptr;
   ctx->thermal = false;

@@ -130,7 +130,7 @@ struct kbe_ctx {
   bool thermal = false;
   int th_N = 0, th_k = 0;
   double th_beta = 0.0;
-  double* d_th = nullptr;     // GM [N][MM] | left [N][N] | Smix [N][MM] | Fx [kRing][N][MM] | Gx [n_max][N][MM]
+  double* d_th = nullptr;     // GM | left | Smix | Smw | Aw [n_max][MM] | Fx [kRing][N][MM] | Gx [n_max][N][MM]
   // measurement: event pairs around each contraction kernel
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -294,13 +294,15 @@ struct ThermalArgs {
   const double* left;    // tau weights [N][N]
   double* Gx;            // mixed rows [n_max][N][M][M]
   double* Smix;          // Sigma^| row n [N][M][M]
+  double* Smw;           // w_k Sigma^|(n, k) with the full-interval tau weights [N][M][M]
+  double* Aw;            // w_{n,m} Sigma^R(n, m), m <= n [n_max][M][M]
   double* Fx;            // mixed right-hand sides, ring [kRing][N][M][M]
   double* I;             // history slice [2][n+1][M][M]
   const double* corr;    // stepper weights of interval n
   const double* pred;
   int* status;
 };
-cudaError_t launch_th_sigma(const ThermalArgs& a, cudaStream_t s);
+cudaError_t launch_th_sigma(const ThermalArgs& a, cudaStream_t s);  // also Smw and Aw
 cudaError_t launch_th_mixed(const ThermalArgs& a, cudaStream_t s);
 cudaError_t launch_th_rhs(const ThermalArgs& a, cudaStream_t s);
 cudaError_t launch_th_adams(const ThermalArgs& a, bool corrector, cudaStream_t s);
