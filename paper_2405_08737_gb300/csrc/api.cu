@@ -297,8 +297,10 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
       SelectArgs sa{ctx->M, n, ctx->adaptive_K, (const double*)L, (const double*)R, (const double*)Sl,
                     (const double*)Sg, ctx->d_hist + (size_t)n * kMaxOrder * kWTab, ctx->d_band, ctx->d_wbar,
                     ctx->band_w, ctx->d_korder};
-      e = launch_select_order(sa, s);
-      *count_out = ++count;
+      sa.u = ctx->d_hist + (size_t)ctx->n_max * kMaxOrder * kWTab;
+      int ns = 0;
+      e = launch_select_order(sa, s, &ns);
+      *count_out = (count += ns);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: history order selection");
     }
     kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl, true);
@@ -441,8 +443,10 @@ kbe_status ctl_feval(CtlRun& r, int n) {
     SelectArgs sa{ctx->M, n, r.K_sel, (const double*)r.L, (const double*)r.R, (const double*)r.Sl,
                   (const double*)r.Sg, ctx->d_hist + (size_t)n * kMaxOrder * kWTab, ctx->d_band, ctx->d_wbar,
                   ctx->band_w, ctx->d_korder};
-    if ((e = launch_select_order(sa, r.s)) != cudaSuccess) return cuda_fail(ctx, e, "kbe_run_controlled: order");
-    ++r.launches;
+    sa.u = ctx->d_hist + (size_t)ctx->n_max * kMaxOrder * kWTab;
+    int ns = 0;
+    if ((e = launch_select_order(sa, r.s, &ns)) != cudaSuccess) return cuda_fail(ctx, e, "kbe_run_controlled: order");
+    r.launches += ns;
   }
   int nl = 0;
   kbe_status st = history(ctx, n, r.precision, r.L, r.R, r.Sl, r.Sg, r.I, r.s, &nl, true);
@@ -1065,7 +1069,7 @@ kbe_status kbe_set_adaptive_orders(kbe_ctx* ctx, int K) {
     return KBE_OK;
   }
   const size_t tab = (size_t)ctx->n_max * kMaxOrder * kWTab;
-  if (!ctx->d_hist && (e = cudaMalloc(&ctx->d_hist, tab * sizeof(double))) != cudaSuccess)
+  if (!ctx->d_hist && (e = cudaMalloc(&ctx->d_hist, hist_doubles(ctx->n_max, ctx->M) * sizeof(double))) != cudaSuccess)
     return cuda_fail(ctx, e, "kbe_set_adaptive_orders: allocation");
   if (!ctx->d_korder && (e = cudaMalloc(&ctx->d_korder, ctx->n_max * sizeof(int))) != cudaSuccess)
     return cuda_fail(ctx, e, "kbe_set_adaptive_orders: allocation");
@@ -1168,7 +1172,7 @@ kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts
   cudaError_t e = cudaSuccess;
   if (K_sel > 0) {
     const size_t tab = (size_t)n_max * kMaxOrder * kWTab;
-    if (!ctx->d_hist && (e = cudaMalloc(&ctx->d_hist, tab * sizeof(double))) != cudaSuccess)
+    if (!ctx->d_hist && (e = cudaMalloc(&ctx->d_hist, hist_doubles(ctx->n_max, ctx->M) * sizeof(double))) != cudaSuccess)
       return cuda_fail(ctx, e, "kbe_run_controlled: allocation");
     if (!ctx->d_korder && (e = cudaMalloc(&ctx->d_korder, n_max * sizeof(int))) != cudaSuccess)
       return cuda_fail(ctx, e, "kbe_run_controlled: allocation");

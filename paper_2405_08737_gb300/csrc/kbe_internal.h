@@ -248,8 +248,13 @@ struct SelectArgs {
   double* wbar;        // settled weights (entry n - band_w written)
   int band_w;
   int* korder;         // chosen order per interval (entry n written)
+  double* u = nullptr; // scratch: test integrand [kMaxOrder+1][M][M] complex
 };
-cudaError_t launch_select_order(const SelectArgs& a, cudaStream_t s);
+cudaError_t launch_select_order(const SelectArgs& a, cudaStream_t s, int* launches);
+// d_hist holds the local weights [n_max][kMaxOrder][kWTab], then the scratch u
+inline size_t hist_doubles(int n_max, int M) {
+  return (size_t)n_max * kMaxOrder * kWTab + 2 * (size_t)(kMaxOrder + 1) * M * M;
+}
 
 // ---- adaptive time stepping (controller.cu) -----------------------------
 struct CtlArgs {
