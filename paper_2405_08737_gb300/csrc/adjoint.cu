@@ -66,12 +66,26 @@ __device__ __forceinline__ void mac_ca(Cz& acc, Cz a, Cz b) {
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// Rows the slice adjoints read in their inner loops, formed once:
+// Js = Ibar^< + Ibar^>, A1 = w_{n,m} (S^> - S^<)(n,m); both [n+1][M][M].
+__global__ void __launch_bounds__(256) adj_prep(int M, int n, const double* __restrict__ Ib,
+                                                const double* __restrict__ Sl, const double* __restrict__ Sg,
+                                                WeightsView w, double* __restrict__ Js, double* __restrict__ A1) {
+  const int MM = M * M;
+  const int64_t srow = (int64_t)(n + 1) * MM;
+  const int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (lin >= srow) return;
+  stz(Js + lin * 2, ldz(Ib + lin * 2) + ldz(Ib + (srow + lin) * 2));
+  stz(A1 + lin * 2, sc(w.at(n, (int)(lin / MM)), ldz(Sg + lin * 2) - ldz(Sl + lin * 2)));
+}
+
 // ------------------------------------------------ history slice: Sigma ---
 // Partial sums over a chunk of output columns c of A1bar[m] and Bbar^s[m]
 // for every (m, a, x): part[chunk][3][n+1][M][M].
 __global__ void __launch_bounds__(256) adj_hist_small(int M, int n, int chunk_len, const double* __restrict__ L,
                                                       const double* __restrict__ R, const double* __restrict__ Ib,
-                                                      WeightsView w, double* __restrict__ part) {
+                                                      const double* __restrict__ Js, WeightsView w,
+                                                      double* __restrict__ part) {
   const int MM = M * M;
   const int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (lin >= (int64_t)(n + 1) * MM) return;
@@ -83,22 +97,21 @@ __global__ void __launch_bounds__(256) adj_hist_small(int M, int n, int chunk_le
   for (int c = c0; c < c1; ++c) {
     const double* il = Ib + ((int64_t)c * MM + a * M) * 2;
     const double* ig = Ib + (srow + (int64_t)c * MM + a * M) * 2;
+    const double* is = Js + ((int64_t)c * MM + a * M) * 2;  // Ibar^< + Ibar^>
+    // jl conj(G^<) + jg conj(G^>) = (jl + jg) conj(L) + jg conj(R), as G^> = R + L
     if (c <= m) {  // G^<(m,c) = L(m,c), G^> = (R+L)(m,c): conj(G(m,c)[x][b])
       const double* lb = L + (tri(m, c) * MM + x * M) * 2;
       const double* rb = R + (tri(m, c) * MM + x * M) * 2;
       for (int b = 0; b < M; ++b) {
-        const Cz l = ldz(lb + 2 * b), r = ldz(rb + 2 * b);
-        const Cz jl = ldz(il + 2 * b), jg = ldz(ig + 2 * b);
-        mac_cj(A, jl, l);
-        mac_cj(A, jg, l + r);
+        mac_cj(A, ldz(is + 2 * b), ldz(lb + 2 * b));
+        mac_cj(A, ldz(ig + 2 * b), ldz(rb + 2 * b));
       }
     } else {       // G(m,c)[x][b] = -conj(X(c,m)[b][x]): conj -> -X(c,m)[b][x]
       const int64_t blk = tri(c, m) * MM;
       for (int b = 0; b < M; ++b) {
         const Cz l = ldz(L + (blk + b * M + x) * 2), r = ldz(R + (blk + b * M + x) * 2);
-        const Cz jl = ldz(il + 2 * b), jg = ldz(ig + 2 * b);
-        mac(A, jl, Cz{-l.re, -l.im});
-        mac(A, jg, Cz{-(l.re + r.re), -(l.im + r.im)});
+        mac(A, ldz(is + 2 * b), Cz{-l.re, -l.im});
+        mac(A, ldz(ig + 2 * b), Cz{-r.re, -r.im});
       }
     }
     if (c >= m) {  // term 2: w_{c,m} Ibar^s(c)[a][b] R(c,m)[b][x]
@@ -145,7 +158,8 @@ __global__ void __launch_bounds__(256) adj_hist_small_reduce(int M, int n, int n
 // Cotangents of the stored blocks (r,q) of rows r in [row_lo, n]: rows r < n
 // accumulate into dL, dR (triangles); row n goes to gL, gR (row buffers of
 // the current iterate, [n+1][M][M]).
-__global__ void __launch_bounds__(256) adj_hist_rows(int M, int n, int row_lo, const double* __restrict__ Sl,
+__global__ void __launch_bounds__(256) adj_hist_rows(int M, int n, int row_lo, const double* __restrict__ Js,
+                                                     const double* __restrict__ A1, const double* __restrict__ Sl,
                                                      const double* __restrict__ Sg, const double* __restrict__ Ib,
                                                      WeightsView w, double* __restrict__ dL, double* __restrict__ dR,
                                                      double* __restrict__ gL, double* __restrict__ gR) {
@@ -164,28 +178,22 @@ __global__ void __launch_bounds__(256) adj_hist_rows(int M, int n, int row_lo, c
   while ((int64_t)r * (r + 1) / 2 > p) --r;
   while ((int64_t)(r + 1) * (r + 2) / 2 <= p) ++r;
   const int q = (int)(p - (int64_t)r * (r + 1) / 2);
-  const double wr = w.at(n, r), wq = w.at(n, q);
-  Cz dl{0, 0}, dr{0, 0};
+  // A1[m][a][x] = w_{n,m} (Sg - Sl)[m][a][x] and Js = Ibar^< + Ibar^> are precomputed rows
+  Cz dl{0, 0}, dr{0, 0}, t2{0, 0};
   for (int a = 0; a < M; ++a) {
-    // A1[r][a][x] = w_{n,r} (Sg - Sl)[r][a][x]
-    const Cz a1r = sc(wr, ldz(Sg + ((int64_t)r * MM + a * M + x) * 2) - ldz(Sl + ((int64_t)r * MM + a * M + x) * 2));
-    const Cz jlq = ldz(Ib + ((int64_t)q * MM + a * M + y) * 2);
-    const Cz jgq = ldz(Ib + (srow + (int64_t)q * MM + a * M + y) * 2);
-    mac_ca(dl, a1r, jlq + jgq);
-    mac_ca(dr, a1r, jgq);
+    const Cz a1r = ldz(A1 + ((int64_t)r * MM + a * M + x) * 2);
+    mac_ca(dl, a1r, ldz(Js + ((int64_t)q * MM + a * M + y) * 2));
+    mac_ca(dr, a1r, ldz(Ib + (srow + (int64_t)q * MM + a * M + y) * 2));
     if (q < r) {
-      const Cz a1q = sc(wq, ldz(Sg + ((int64_t)q * MM + a * M + y) * 2) - ldz(Sl + ((int64_t)q * MM + a * M + y) * 2));
-      const Cz jlr = ldz(Ib + ((int64_t)r * MM + a * M + x) * 2);
+      const Cz na1q = sc(-1.0, ldz(A1 + ((int64_t)q * MM + a * M + y) * 2));
       const Cz jgr = ldz(Ib + (srow + (int64_t)r * MM + a * M + x) * 2);
-      Cz t{0, 0}, tg{0, 0}, t2{0, 0};
-      mac_ca(t, jlr + jgr, a1q);
-      mac_ca(tg, jgr, a1q);
-      mac_ca(t2, jlr, ldz(Sl + ((int64_t)q * MM + a * M + y) * 2));
+      mac_ca(dl, ldz(Js + ((int64_t)r * MM + a * M + x) * 2), na1q);
+      mac_ca(dr, jgr, na1q);
+      mac_ca(t2, ldz(Ib + ((int64_t)r * MM + a * M + x) * 2), ldz(Sl + ((int64_t)q * MM + a * M + y) * 2));
       mac_ca(t2, jgr, ldz(Sg + ((int64_t)q * MM + a * M + y) * 2));
-      dl = dl - t;
-      dr = dr - tg + sc(w.at(r, q), t2);
     }
   }
+  if (q < r) dr = dr + sc(w.at(r, q), t2);
   if (r < n) {
     addz(dL + ((p - base) * MM + xy) * 2, dl);
     if (q < r) addz(dR + ((p - base) * MM + xy) * 2, dr);
@@ -414,18 +422,23 @@ cudaError_t launch_adjoint_history(const AdjHistArgs& h, cudaStream_t s, int* la
   int64_t want = (152LL * 2048 + srow - 1) / srow;
   int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
   if (nchunk > n + 1) nchunk = n + 1;
-  while (nchunk > 1 && (size_t)nchunk * 3 * srow * 16 > h.work_bytes) --nchunk;
-  if ((size_t)nchunk * 3 * srow * 16 > h.work_bytes) return cudaErrorInvalidValue;
+  // the workspace holds the chunk partials [nchunk][3][srow], then the rows Js and A1
+  while (nchunk > 1 && (size_t)(nchunk * 3 + 2) * srow * 16 > h.work_bytes) --nchunk;
+  if ((size_t)(nchunk * 3 + 2) * srow * 16 > h.work_bytes) return cudaErrorInvalidValue;
   const int chunk_len = (n + 1 + nchunk - 1) / nchunk;
   nchunk = (n + 1 + chunk_len - 1) / chunk_len;
-  adj_hist_small<<<dim3(blocks_for(srow), nchunk), 256, 0, s>>>(M, n, chunk_len, h.L, h.R, h.Ib, h.w, h.work);
+  double* Js = h.work + (size_t)nchunk * 3 * srow * 2;
+  double* A1 = Js + srow * 2;
+  adj_prep<<<blocks_for(srow), 256, 0, s>>>(M, n, h.Ib, h.Sl, h.Sg, h.w, Js, A1);
+  adj_hist_small<<<dim3(blocks_for(srow), nchunk), 256, 0, s>>>(M, n, chunk_len, h.L, h.R, h.Ib, Js, h.w, h.work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adj_hist_small_reduce<<<blocks_for(srow), 256, 0, s>>>(M, n, nchunk, h.work, h.w, h.dSl, h.dSg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int64_t rows_total = (tri(n + 1, 0) - tri(h.row_lo, 0)) * MM;
-  adj_hist_rows<<<blocks_for(rows_total), 256, 0, s>>>(M, n, h.row_lo, h.Sl, h.Sg, h.Ib, h.w, h.dL, h.dR, h.gL, h.gR);
-  *launches = 3;
+  adj_hist_rows<<<blocks_for(rows_total), 256, 0, s>>>(M, n, h.row_lo, Js, A1, h.Sl, h.Sg, h.Ib, h.w, h.dL, h.dR,
+                                                       h.gL, h.gR);
+  *launches = 4;
   return cudaGetLastError();
 }
 
