@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-m32", action="store_true", help="skip the 32-orbital precision-form measurement")
     ap.add_argument("--n-t", type=int, default=None,
                     help="truncate the grid to this many points (smaller profiling case)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batching form")
@@ -131,10 +132,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def setup_workload(kbe, seed, n_t_override=None):
+def setup_workload(kbe, seed, n_t_override=None, name=None):
     import torch
     import workloads as W
-    cfg = W.CONFIGS[WORKLOAD]
+    cfg = W.CONFIGS[name or WORKLOAD]
     M, n_t = cfg["M"], cfg["n_t"]
     t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], seed)
     if n_t_override:
@@ -614,6 +615,48 @@ def window_bench(kbe, seed, stream):
             "dF_dE0": gE, "dF_dE0_fd": fdE, "rel_err_E0": abs(gE - fdE) / abs(fdE)}
 
 
+def precision_m32_bench(kbe, seed, stream, steps):
+    """The precision form on its own workload: the 32-orbital GOE model
+    (U = 1.5, N_t = 1024, orders 1..5), one KBE step of row n = 1023 (P = 2)
+    restarted from the non-interacting history, FP64 and split paths.
+    Reports ms per step, the split contraction against HBM (its digit planes
+    are streamed once per 8-orbital part) and the deviation of the split
+    step's new row and last slice from the FP64 step's (max-norm relative;
+    the FP64 path matches the oracle to 1e-12)."""
+    import torch
+    cfg, t, order, h, U, v, pulse, ctx, run, n = setup_workload(kbe, seed, name="goe_m32_n1024")
+    M, P = cfg["M"], 2
+    ms, launches, _, _ = time_steps(ctx, run, n, P, 1, 1, stream)
+    ref = step_rows(run, n)
+    ms_s, launches_s, kc_s, kms_s = time_steps(ctx, run, n, P, steps, 2, stream, "split")
+    got = step_rows(run, n)
+    ctx.sync_status()
+    ctx.close()
+    del run
+    torch.cuda.empty_cache()
+    dev = {}
+    for name, a, b in (("new_row", np.concatenate([got[0], got[1]]), np.concatenate([ref[0], ref[1]])),
+                       ("slice", got[2], ref[2])):
+        dev[name] = float(np.abs(a - b).max() / np.abs(b).max())
+    ct = 128 // M
+    cpt = ((n + 1) * M + 15) // 16
+    plane_bytes = ((n + 1 + ct - 1) // ct) * cpt * ((M + 7) // 8) * 66560
+    k_avg = kms_s / max(kc_s, 1)
+    hbm = hbm_peak_gbs()
+    flops = P * slice_flops(M, n)
+    return {"workload": "goe_m32_n1024: GOE one-body h (M=32), local U=1.5, N_t=1024 nonuniform, orders 1..5; "
+                        "KBE step of row n=%d with P=%d" % (n, P),
+            "fp64_ms_per_step": round(ms, 3), "fp64_tflops": round(flops / (ms * 1e-3) / 1e12, 4),
+            "split_ms_per_step": round(ms_s / steps, 3),
+            "split_tflops_fp64_equivalent": round(flops / (ms_s / steps * 1e-3) / 1e12, 4),
+            "speedup_vs_fp64_step": round(ms / (ms_s / steps), 3),
+            "split_contraction": {"kernel": "split_main2", "avg_ms": round(k_avg, 4), "bytes_per_launch": plane_bytes,
+                                  "achieved_gbs": round(plane_bytes / (k_avg * 1e-3) / 1e9, 1), "peak_gbs": hbm,
+                                  "frac": round(plane_bytes / (k_avg * 1e-3) / 1e9 / hbm, 4)},
+            "split_deviation_from_fp64_step": dev, "stated_error_bound": 1e-8,
+            "gpu_launches": {"fp64": launches, "split": launches_s}}
+
+
 def step_rows(run, n):
     p = W_tri(n)
     return (run.L[p:p + n + 1].cpu().numpy(), run.R[p:p + n + 1].cpu().numpy(),
@@ -740,6 +783,8 @@ def main():
     ctx.close()
     del run
     torch.cuda.empty_cache()
+    if rank == 0 and not args.no_m32:
+        line["precision_form_goe_m32"] = precision_m32_bench(kbe, args.seed, stream, 3)
     if not args.no_batch:
         line["batching_form"] = batch_bench(kbe, args.seed, args.P, stream, rank, world)
     if rank == 0:

@@ -23,8 +23,8 @@
 // entries (m,x), the big operands are the plane tiles PL, Q and the masked
 // QU = Q [m <= c]; the small operands A1, NB^<, NBD (prepared once per
 // slice) are the "B" matrices of the MMA.  Term 2 for the band m > c - K,
-// where w_{c,m} still differs from wbar_m, is left out of QU and added in
-// FP64 with the exact weights by the reduction kernel.
+// where w_{c,m} still differs from wbar_m, is left out of QU and added with
+// the exact weights in double-float by the reduction kernel.
 //
 // Roles in one CTA (1 CTA per SM, persistent over a contiguous range of
 // (tile, chunk) units): 8 converter warps load the FP64 blocks, find the
@@ -37,6 +37,7 @@
 #include <atomic>
 #include <cstdio>
 
+#include "dfloat.cuh"
 #include "kbe_internal.h"
 #include "split_common.cuh"
 
@@ -805,19 +806,57 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
 // ---------------------------------------------------------------- reduce -
 // I_out[s][c][a][b] = sum of the partials of every CTA that covered the
 // tile of (c, a), in CTA order (I^< from group 0; I^> from groups 0 and 1),
-// plus the band of term 2 in FP64 with the exact composite weights:
+// plus the band of term 2 with the exact composite weights,
 //   sum_{m = c-K..c} w_{c,m} S^s(n,m)_ax conj(R(c,m)_bx).
-// Same sums with one block per (tile, chunk of its outputs): the CTAs that
-// covered the tile and the tile's segment in each are found once per block.
-__global__ void __launch_bounds__(256) split_reduce2(SplitGeom g, const double* __restrict__ part,
-                                                     const double* __restrict__ Sl, const double* __restrict__ Sg,
-                                                     const double* __restrict__ R, WeightsView w,
-                                                     double* __restrict__ out, int* status) {
+// Reduction of one output column c and one 8-orbital part (block (c, part)):
+// the per-CTA partials of the column's tile in CTA order (FP64), plus the
+// band of term 2, sum_{m in (c - band_w, c]} w_{c,m} Sigma^s(n,m) G^A(m,c),
+// with the exact weights.  The band runs in double-float on the FP32 pipe:
+// per band point m the block stages R(c,m) (transposed, [x][b]) and
+// w_{c,m} Sigma^s(n,m) for its rows a as double-float pairs in shared memory,
+// and each thread accumulates its outputs' products with Ogita-Rump-Oishi's
+// compensated dot product (TwoSum of the leading products, the product
+// errors and the TwoSum errors in a float tail), about 2^-47 of the
+// products' sizes, far below the slice's 1e-8 bound.  In FP64 the band's
+// band_w M^3 complex products per column and sign set this kernel's time
+// (the FP64 pipe issues 1/64 of the FP32 rate on this part).
+constexpr int kRedThreads = 128;
+constexpr int kRedOut = 2 * kNA * 32 / kRedThreads;  // outputs per thread at M = 32
+
+struct DotAcc {
+  float s, c;
+};
+// a += p q (p, q double-float)
+__device__ __forceinline__ void dot_acc(DotAcc& a, float ph, float pl, float qh, float ql) {
+  const float h = ph * qh;
+  float e = fmaf(ph, qh, -h);
+  e = fmaf(ph, ql, e);
+  e = fmaf(pl, qh, e);
+  const float s = a.s + h;
+  const float v = s - a.s;
+  a.c += ((a.s - (s - v)) + (h - v)) + e;
+  a.s = s;
+}
+__device__ __forceinline__ float4 c2_of(double2 v) {
+  const df::F2 re = df::from_double_fast(v.x), im = df::from_double_fast(v.y);
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+__global__ void __launch_bounds__(kRedThreads) split_reduce2(SplitGeom g, const double* __restrict__ part,
+                                                             const double* __restrict__ Sl,
+                                                             const double* __restrict__ Sg,
+                                                             const double* __restrict__ R, WeightsView w,
+                                                             double* __restrict__ out, int* status) {
   const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
-  const int tile = blockIdx.x;
-  const int ctile = tile / g.parts, pt = tile % g.parts;
+  const int c = blockIdx.x, pt = blockIdx.y;
+  const int ctile = c / CT, cl = c - ctile * CT;
+  const int tile = ctile * g.parts + pt;
+  const int na = min(kNA, M - pt * kNA);
+  const int nout = 2 * na * M;
   __shared__ int s_i0, s_k;
-  __shared__ int s_seg[160];  // G <= 152 CTAs
+  __shared__ int s_seg[160];                   // G <= 152 CTAs
+  __shared__ float4 s_r[32 * 32];              // R(c,m) transposed: [x][b]
+  __shared__ float4 s_s[2 * kNA * 32];         // w_{c,m} Sigma^s(n,m): [s][al][x]
   if (threadIdx.x == 0) {
     const long long ulo = (long long)tile * g.cpt, uhi = ulo + g.cpt;
     int i = (int)((ulo * g.G) / g.U);
@@ -833,20 +872,55 @@ __global__ void __launch_bounds__(256) split_reduce2(SplitGeom g, const double* 
     s_i0 = i0;
     s_k = k;
   }
+  DotAcc acc[kRedOut][2];
+#pragma unroll
+  for (int q = 0; q < kRedOut; ++q) acc[q][0] = acc[q][1] = DotAcc{0.f, 0.f};
+  // band of term 2 (block-uniform loop: c and m are the block's)
+  for (int m = max(0, c - w.band_w + 1); m <= c; ++m) {
+    const double dw = w.at(c, m);
+    if (dw == 0.0) continue;
+    __syncthreads();
+    const double2* rb = reinterpret_cast<const double2*>(R) + tri(c, m) * MM;
+    for (int i = threadIdx.x; i < MM; i += kRedThreads) {
+      const int b = i / M, x = i - b * M;
+      s_r[x * M + b] = c2_of(rb[i]);
+    }
+    for (int i = threadIdx.x; i < nout; i += kRedThreads) {
+      const int s = i / (na * M), r = i - s * (na * M);
+      const double2 v = reinterpret_cast<const double2*>(s ? Sg : Sl)[(size_t)m * MM + pt * kNA * M + r];
+      s_s[i] = c2_of(make_double2(dw * v.x, dw * v.y));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kRedOut; ++q) {
+      const int o = threadIdx.x + q * kRedThreads;
+      if (o >= nout) break;
+      const int row = o / M, bb = o - row * M;  // row = s * na + al
+      const float4* sp = s_s + row * M;
+      for (int x = 0; x < M; ++x) {  // p conj(r): (p.re r.re + p.im r.im) + i (p.im r.re - p.re r.im)
+        const float4 p = sp[x], r = s_r[x * M + bb];
+        dot_acc(acc[q][0], p.x, p.y, r.x, r.y);
+        dot_acc(acc[q][0], p.z, p.w, r.z, r.w);
+        dot_acc(acc[q][1], p.z, p.w, r.x, r.y);
+        dot_acc(acc[q][1], -p.x, -p.y, r.z, r.w);
+      }
+    }
+  }
   __syncthreads();
   const int i0 = s_i0, nk = s_k;
-  const int per_s = CT * kNA * M;
   bool bad = false;
-  for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < 2 * per_s; idx += gridDim.y * blockDim.x) {
-    const int s = idx / per_s;
-    const int rem = idx - s * per_s;
-    const int cl = rem / (kNA * M);
-    const int r2 = rem - cl * (kNA * M);
-    const int al = r2 / M, bb = r2 - al * M;
-    const int c = ctile * CT + cl, aa = pt * kNA + al;
-    if (c > n || aa >= M) continue;
+#pragma unroll
+  for (int q = 0; q < kRedOut; ++q) {
+    const int o = threadIdx.x + q * kRedThreads;
+    if (o >= nout || c > n) break;
+    const int s = o / (na * M), r = o - s * (na * M);
+    const int al = r / M, bb = r - al * M;
     // group 0 holds I^<, group 1 holds D = I^> - I^<
-    double re = 0.0, im = 0.0;
+    // a non-finite float word is reported (to_double needs finite words)
+    bad |= !(df::finite_bits(acc[q][0].s) && df::finite_bits(acc[q][0].c) && df::finite_bits(acc[q][1].s) &&
+             df::finite_bits(acc[q][1].c));
+    double re = df::to_double(df::F2{acc[q][0].s, acc[q][0].c});
+    double im = df::to_double(df::F2{acc[q][1].s, acc[q][1].c});
     for (int grp = 0; grp <= s; ++grp)
       for (int k = 0; k < nk; ++k) {
         const int seg = s_seg[k];
@@ -856,33 +930,13 @@ __global__ void __launch_bounds__(256) split_reduce2(SplitGeom g, const double* 
         re += v.x;
         im += v.y;
       }
-    const double* S = s == 0 ? Sl : Sg;
-    for (int m = max(0, c - w.band_w + 1); m <= c; ++m) {
-      const double dw = w.at(c, m);
-      if (dw == 0.0) continue;
-      const double2* sr = reinterpret_cast<const double2*>(S) + (size_t)m * MM + aa * M;
-      const double2* rr = reinterpret_cast<const double2*>(R) + tri(c, m) * MM + bb * M;
-      double tr = 0.0, ti = 0.0;
-      for (int x = 0; x < M; ++x) {  // p * conj(q): four FMAs per term
-        const double2 p = sr[x], q = rr[x];
-        tr = fma(p.x, q.x, tr);
-        tr = fma(p.y, q.y, tr);
-        ti = fma(p.y, q.x, ti);
-        ti = fma(-p.x, q.y, ti);
-      }
-      re = fma(dw, tr, re);
-      im = fma(dw, ti, im);
-    }
     bad |= !(isfinite(re) && isfinite(im));
-    reinterpret_cast<double2*>(out)[((size_t)s * (n + 1) + c) * MM + aa * M + bb] = make_double2(re, im);
+    reinterpret_cast<double2*>(out)[((size_t)s * (n + 1) + c) * MM + (pt * kNA + al) * M + bb] = make_double2(re, im);
   }
   if (bad) atomicOr(status, kStatusNumeric);
 }
 
-inline dim3 reduce2_grid(const SplitGeomHost& h) {
-  const int per_tile = 2 * h.CT * kNA * h.M;
-  return dim3((unsigned)h.tiles, (unsigned)((per_tile + 255) / 256));
-}
+inline dim3 reduce2_grid(const SplitGeomHost& h) { return dim3((unsigned)(h.n + 1), (unsigned)h.parts); }
 
 }  // namespace
 
@@ -991,7 +1045,7 @@ cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& pl_la
   if (l.ev_end) cudaEventRecord(l.ev_end, s);
   ++*launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  split_reduce2<<<reduce2_grid(h), 256, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
+  split_reduce2<<<reduce2_grid(h), kRedThreads, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
   ++*launches;
   return cudaGetLastError();
 }
@@ -1021,7 +1075,7 @@ cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* laun
   if (l.ev_end) cudaEventRecord(l.ev_end, s);
   ++*launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  split_reduce2<<<reduce2_grid(h), 256, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
+  split_reduce2<<<reduce2_grid(h), kRedThreads, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
   ++*launches;
   return cudaGetLastError();
 }
