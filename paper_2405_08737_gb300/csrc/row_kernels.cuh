@@ -65,10 +65,12 @@ __device__ __forceinline__ df::F2 sigma_uu(int M, int ab, const double* __restri
   return df::from_double_fast(U[a] * U[b]);
 }
 
-__device__ __forceinline__ bool sigma_entry(int M, int64_t e, int ab, bool diag, df::F2 uu,
-                                            const double2* __restrict__ L, const double2* __restrict__ R,
-                                            double2* __restrict__ Sl, double2* __restrict__ Sg) {
-  const double2 l64 = L[e], r64 = R[e];
+// The same with the entry's L and R values already loaded (l64, r64), so
+// that a caller can have the next entry's loads in flight meanwhile.
+__device__ __forceinline__ bool sigma_entry_v(int M, int64_t e, int ab, bool diag, df::F2 uu, double2 l64,
+                                              double2 r64, const double2* __restrict__ L,
+                                              const double2* __restrict__ R, double2* __restrict__ Sl,
+                                              double2* __restrict__ Sg) {
   const df::C2 l = ld_c2(l64);
   const df::C2 g = ld_c2(make_double2(r64.x + l64.x, r64.y + l64.y));
   df::C2 sg, sl;
@@ -90,6 +92,11 @@ __device__ __forceinline__ bool sigma_entry(int M, int64_t e, int ab, bool diag,
   // hi + lo is finite exactly when hi is: x - x is 0 for finite x, nan otherwise
   const float z = (sg.re.hi - sg.re.hi) + (sg.im.hi - sg.im.hi) + (sl.re.hi - sl.re.hi) + (sl.im.hi - sl.im.hi);
   return z == 0.0f;
+}
+__device__ __forceinline__ bool sigma_entry(int M, int64_t e, int ab, bool diag, df::F2 uu,
+                                            const double2* __restrict__ L, const double2* __restrict__ R,
+                                            double2* __restrict__ Sl, double2* __restrict__ Sg) {
+  return sigma_entry_v(M, e, ab, diag, uu, L[e], R[e], L, R, Sl, Sg);
 }
 
 // ---------------------------------------------------------- history slice --

@@ -31,8 +31,10 @@ __device__ __forceinline__ int64_t tri_row(int64_t p) {
 // launch covers whole rows of a triangle (the diagonal blocks are found
 // from the triangle index).  Each CTA streams one contiguous range of
 // entries, blockDim at a time; a thread keeps (block, ab) and, for whole
-// triangles, the index of the next diagonal block by increments.
-__global__ void __launch_bounds__(256) sigma_kernel(int MM, int M, int64_t n_elem, int64_t first_block,
+// triangles, the index of the next diagonal block by increments.  Five CTAs
+// per SM (at most 51 registers), each thread with the next entry's loads in
+// flight, keep enough bytes moving for HBM.
+__global__ void __launch_bounds__(256, 5) sigma_kernel(int MM, int M, int64_t n_elem, int64_t first_block,
                                                     int64_t diag_block, const double2* __restrict__ L,
                                                     const double2* __restrict__ R,
                                                     const double* __restrict__ U,
@@ -56,7 +58,15 @@ __global__ void __launch_bounds__(256) sigma_kernel(int MM, int M, int64_t n_ele
   bool ok = true;
   int uu_ab = ab;
   df::F2 uu = rk::sigma_uu(M, ab, U);
+  // the next entry's loads are issued before this entry's arithmetic: two
+  // entries' 32 bytes in flight per thread
+  double2 l_next = L[e], r_next = R[e];
   for (; e < e_end; e += blockDim.x) {
+    const double2 l64 = l_next, r64 = r_next;
+    if (e + blockDim.x < e_end) {
+      l_next = L[e + blockDim.x];
+      r_next = R[e + blockDim.x];
+    }
     if (ab != uu_ab) {  // never for M dividing 16: blockDim is a multiple of M^2
       uu = rk::sigma_uu(M, ab, U);
       uu_ab = ab;
@@ -72,7 +82,7 @@ __global__ void __launch_bounds__(256) sigma_kernel(int MM, int M, int64_t n_ele
       }
       diag = p == next_diag;
     }
-    ok &= rk::sigma_entry(M, e, ab, diag, uu, L, R, Sl, Sg);
+    ok &= rk::sigma_entry_v(M, e, ab, diag, uu, l64, r64, L, R, Sl, Sg);
     blk += sblk;
     ab += sab;
     if (ab >= MM) {
