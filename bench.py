@@ -183,28 +183,23 @@ def time_steps(ctx, run, n, P, steps, warmup, stream, precision="fp64"):
 
 
 def e2e_steps(ctx, run, n, P, steps, warmup, stream):
-    """The same step through the public API with host buffers: every step
-    copies the history and stored right-hand sides from pinned host memory,
-    runs the step and reads the new row back."""
+    """The same step through the public API with host buffers
+    (kbe_step_host): every step copies the history rows 0..n-1 and the
+    stored right-hand sides from pinned host memory, runs the step (the
+    first history slice contracts each chunk of columns as its rows arrive)
+    and reads the new row back."""
     import torch
     L_h = run.L.cpu().pin_memory()
     R_h = run.R.cpu().pin_memory()
     F_h = run.F.cpu().pin_memory()
     M = ctx.M
-    p0 = n * (n + 1) // 2
     out_L = torch.empty((n + 1, M, M), dtype=torch.complex128).pin_memory()
     out_R = torch.empty_like(out_L).pin_memory()
-    h2d = (L_h.numel() + R_h.numel() + F_h.numel()) * 16
+    h2d = 2 * W_tri(n) * M * M * 16 + F_h.numel() * 16
     d2h = 2 * (n + 1) * M * M * 16
 
     def one():
-        with torch.cuda.stream(stream):
-            run.L.copy_(L_h, non_blocking=True)
-            run.R.copy_(R_h, non_blocking=True)
-            run.F.copy_(F_h, non_blocking=True)
-            run.step(n, P=P, stream=stream)
-            out_L.copy_(run.L[p0:p0 + n + 1], non_blocking=True)
-            out_R.copy_(run.R[p0:p0 + n + 1], non_blocking=True)
+        run.step_host(n, L_h, R_h, F_h, out_L, out_R, P=P, stream=stream)
 
     for _ in range(warmup):
         one()

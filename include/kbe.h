@@ -236,6 +236,28 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
 kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* S_less,
                     void* S_great, void* I_work, void* F_ring, void* stream);
 
+/* kbe_step with its inputs in host memory, for callers that keep the run on
+ * the host: rows 0..n-1 of both triangles (L_host, R_host: the same packed
+ * layout as L, R, at least tri(n) blocks) and the right-hand-side ring
+ * (F_host: the image of F_ring) are copied into the device buffers L, R,
+ * F_ring, and the new row n of L and R is copied back to L_row_host and
+ * R_row_host ((n+1) M^2 complex each).  The rows are copied from row n-1
+ * down in up to 4 chunks of about equal size on a copy stream of the
+ * context; with KBE_FP64 (and no adaptive orders or thermal branch) the
+ * first sweep's history slice contracts the output columns of each chunk as
+ * soon as it has arrived (column c reads rows c..n only), so the copies
+ * overlap the contraction; the results are bitwise those of kbe_step on the
+ * same data.  Otherwise the step starts once all rows are in.  Host buffers
+ * should be page-locked (cudaHostAlloc or registered) for the copies to be
+ * asynchronous; none of them may be changed or freed before the stream has
+ * passed the step.  The copies start after the work already queued on
+ * `stream` and never touch row n or above.  Digit planes cached by
+ * KBE_SPLIT_BF16 steps are dropped (the rows are rewritten).  Errors as
+ * kbe_step, plus KBE_EINVAL for a NULL host pointer. */
+kbe_status kbe_step_host(kbe_ctx* ctx, int n, int P, int precision, const void* L_host, const void* R_host,
+                         const void* F_host, void* L, void* R, void* S_less, void* S_great, void* I_work,
+                         void* F_ring, void* L_row_host, void* R_row_host, void* stream);
+
 /* kbe_step with the right-hand-side rows in a row store instead of the
  * ring: row j lives in slot j - j0 of F_rows, device
  * [n_rows][2][n_max][M][M].  Step n reads rows n-k_n .. n-1 and writes row

@@ -62,6 +62,7 @@ def lib():
         L.kbe_rhs_row.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
+        L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_adjoint_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, vp]
         L.kbe_adjoint_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_adjoint.argtypes = [vp, i, i, vp, vp, vp, i, i, vp, vp, i, vp, vp, vp, vp]
@@ -158,6 +159,18 @@ class Context:
         import torch
         s = torch.cuda.current_stream() if stream is None else stream
         return ctypes.c_void_p(s.cuda_stream)
+
+    @staticmethod
+    def _host(x, nbytes):
+        """Pointer to a contiguous complex128 host tensor of at least nbytes."""
+        import torch
+        if not isinstance(x, torch.Tensor) or x.is_cuda:
+            raise TypeError("expected a host (CPU) tensor")
+        if x.dtype != torch.complex128 or not x.is_contiguous():
+            raise TypeError("expected a contiguous complex128 tensor")
+        if x.numel() * 16 < nbytes:
+            raise ValueError("host tensor of %d bytes, %d needed" % (x.numel() * 16, nbytes))
+        return ctypes.c_void_p(x.data_ptr())
 
     def _dev(self, x, shape=None):
         import torch
@@ -270,6 +283,21 @@ class Context:
         self._check(lib().kbe_step(self._h, n, P, PRECISIONS[precision], self._dev(L), self._dev(R),
                                    self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_ring),
                                    self._stream(stream)))
+
+    def step_host(self, n, L_host, R_host, F_host, L, R, Sl, Sg, I_work, F_ring, L_row_host, R_row_host, P=2,
+                  precision="fp64", stream=None):
+        """kbe_step_host: rows 0..n-1 of L, R and the ring F come from host
+        tensors (page-locked for asynchronous copies) and row n of L, R is
+        copied back to L_row_host, R_row_host; the upload overlaps the first
+        history slice."""
+        blk = self.M * self.M * 16
+        row = (n + 1) * blk
+        self._check(lib().kbe_step_host(self._h, n, P, PRECISIONS[precision],
+                                        self._host(L_host, tri_size(n) * blk), self._host(R_host, tri_size(n) * blk),
+                                        self._host(F_host, KBE_RING_ROWS * 2 * self.n_max * blk),
+                                        self._dev(L), self._dev(R), self._dev(Sl), self._dev(Sg), self._dev(I_work),
+                                        self._dev(F_ring), self._host(L_row_host, row), self._host(R_row_host, row),
+                                        self._stream(stream)))
 
     def step_rows(self, n, L, R, Sl, Sg, I_work, F_rows, j0, P=2, precision="fp64", stream=None):
         """kbe_step with right-hand-side row j in slot j - j0 of the row store F_rows."""
@@ -395,6 +423,12 @@ class Run:
     def step(self, n, P=2, precision="fp64", stream=None):
         self.ctx.step(n, self.L, self.R, self.Sl, self.Sg, self.I, self.F, P=P, precision=precision,
                       stream=stream)
+
+    def step_host(self, n, L_host, R_host, F_host, L_row_host, R_row_host, P=2, precision="fp64", stream=None):
+        """One step with the history and ring uploaded from host tensors and
+        the new row downloaded (Context.step_host on this run's buffers)."""
+        self.ctx.step_host(n, L_host, R_host, F_host, self.L, self.R, self.Sl, self.Sg, self.I, self.F,
+                           L_row_host, R_row_host, P=P, precision=precision, stream=stream)
 
 
 # ---------------------------------------------------------------- batching

@@ -36,6 +36,14 @@ template <class T> cudaError_t dev_alloc(T** p, size_t count) {
 void release(kbe_ctx* ctx) {
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
   ctx->ev_pool.clear();
+  for (cudaEvent_t& ev : ctx->up_ev) {
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  }
+  if (ctx->up_start) cudaEventDestroy(ctx->up_start);
+  if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+  ctx->up_start = nullptr;
+  ctx->up_stream = nullptr;
   cudaFree(ctx->d_wbar); cudaFree(ctx->d_band); cudaFree(ctx->d_corr); cudaFree(ctx->d_pred);
   cudaFree(ctx->d_h0); cudaFree(ctx->d_U); cudaFree(ctx->d_v); cudaFree(ctx->d_eps);
   cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split); cudaFree(ctx->d_adj);
@@ -96,8 +104,23 @@ bool next_events(kbe_ctx* ctx, cudaEvent_t* b, cudaEvent_t* e) {
 // of L, R are then final, so digit planes encoded for them by earlier slices
 // of the same arrays are reused (the split path re-encodes only units that
 // involve rows >= the cached row count).
+struct Staged;
 kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void* R, const void* Sl,
-                   const void* Sg, void* I_out, cudaStream_t s, int* launches, bool stepping = false) {
+                   const void* Sg, void* I_out, cudaStream_t s, int* launches, bool stepping = false,
+                   const Staged* staged = nullptr);
+
+// Rows arriving in chunks (kbe_step_host): chunk k is complete once ev[k]
+// has fired, and the output columns [c_lo[k], c_hi[k]) read only rows of
+// chunks 0..k.
+struct Staged {
+  int k = 0;
+  int c_lo[16], c_hi[16];
+  cudaEvent_t ev[16];
+};
+
+kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void* R, const void* Sl,
+                   const void* Sg, void* I_out, cudaStream_t s, int* launches, bool stepping,
+                   const Staged* staged) {
   if (precision == KBE_SPLIT_BF16) {
     if (!ctx->d_split) return fail(ctx, KBE_EINVAL, "split precision needs 1 <= norb <= 32");
     SplitLaunch l{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
@@ -136,8 +159,13 @@ kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void
   if (precision != KBE_FP64) return fail(ctx, KBE_EINVAL, "unknown precision");
   HistoryArgs a{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
                 weights_view(ctx), (double*)I_out, ctx->d_part, ctx->part_bytes, ctx->d_status};
+  cudaError_t e;
+  if (staged) {  // the column ranges contract as their rows arrive (no timing events: they would hold the waits)
+    e = launch_history_f64_ranges(a, staged->k, staged->c_lo, staged->c_hi, staged->ev, s, launches);
+    return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "history slice launch");
+  }
   if (!next_events(ctx, &a.ev_begin, &a.ev_end)) return fail(ctx, KBE_ECUDA, "profiling: cudaEventCreate");
-  cudaError_t e = launch_history_f64(a, s, launches);
+  e = launch_history_f64(a, s, launches);
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "history slice launch");
 }
 
@@ -262,8 +290,12 @@ cudaError_t thermal_sweep_a(kbe_ctx* ctx, const ThermalArgs& x, cudaStream_t s) 
 // slot (j - f_base) % f_rows.  With save != nullptr, row n of L and R is
 // copied to save[p] before round p and to save[P] at the end
 // (save[p] = [2][n+1][M][M]: L row, then R row).
+// With staged != nullptr the history rows and F arrive in chunks (kbe_step_host):
+// the predictor waits for chunk 0 (F and the rows next to n), and the first
+// FP64 history slice contracts its column ranges as their rows arrive.
 kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* Sl, void* Sg, void* I_work,
-                     void* F, int f_base, int f_rows, cudaStream_t s, double* save, int* count_out) {
+                     void* F, int f_base, int f_rows, cudaStream_t s, double* save, int* count_out,
+                     const Staged* staged = nullptr) {
   StepArgs a = step_args(ctx, n, L, R, I_work, F);
   a.f_base = f_base;
   a.f_rows = f_rows;
@@ -280,7 +312,13 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
     return e;
   };
   int count = 0, nl = 0;
-  cudaError_t e = launch_predictor(a, s);
+  cudaError_t e = cudaSuccess;
+  if (staged && (e = cudaStreamWaitEvent(s, staged->ev[0], 0)) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_step: wait for the uploaded rows");
+  const bool pipelined = staged && precision == KBE_FP64 && ctx->adaptive_K == 0 && !ctx->thermal;
+  if (staged && !pipelined && (e = cudaStreamWaitEvent(s, staged->ev[staged->k - 1], 0)) != cudaSuccess)
+    return cuda_fail(ctx, e, "kbe_step: wait for the uploaded rows");
+  e = launch_predictor(a, s);
   ++count;
   if (e == cudaSuccess && ctx->thermal) {
     e = launch_th_adams(thermal_args(ctx, a, Sl, Sg, I_work), false, s);
@@ -303,7 +341,8 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
       *count_out = (count += ns);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step: history order selection");
     }
-    kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl, true);
+    kbe_status st = history(ctx, n, precision, L, R, Sl, Sg, I_work, s, &nl, true,
+                            pipelined && it == 0 ? staged : nullptr);
     *count_out = (count += nl);
     if (st != KBE_OK) return st;
     if (ctx->thermal) {
@@ -866,6 +905,77 @@ kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R,
   return st;
 }
 
+kbe_status kbe_step_host(kbe_ctx* ctx, int n, int P, int precision, const void* L_host, const void* R_host,
+                         const void* F_host, void* L, void* R, void* Sl, void* Sg, void* I_work, void* F_ring,
+                         void* L_row_host, void* R_row_host, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  kbe_status st = check_step_call(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_ring);
+  if (st != KBE_OK) return st;
+  if (!L_host || !R_host || !F_host || !L_row_host || !R_row_host)
+    return fail(ctx, KBE_EINVAL, "kbe_step_host: NULL host pointer");
+  cudaError_t e = cudaSuccess;
+  if (!ctx->up_stream) {
+    e = cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->up_start, cudaEventDisableTiming);
+    for (cudaEvent_t& ev : ctx->up_ev)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step_host: copy stream");
+  }
+  // one copy stream: two concurrent host-to-device copies (L and R) were
+  // measured slower (e2e step 26.0 ms instead of 23.9 ms)
+  const cudaStream_t s = (cudaStream_t)stream, cs = ctx->up_stream;
+  const size_t blk = (size_t)ctx->M * ctx->M * 16;  // bytes of one block
+  // rows n-1 down to 0 in chunks of about equal bytes (row r holds r + 1
+  // blocks); the columns of each chunk are contracted while the next ones
+  // are copied.  Every column reads a block of each row above it, so the
+  // longest rows come first and the step waits for the first chunk.  Four
+  // chunks measured best (e2e step of chain_m8_n1024: 23.3 ms with 4,
+  // 23.6 ms with 8, 23.9 ms with 16, 27.0 ms with the upload before the
+  // step): each column range is one more launch of the contraction.
+  Staged sg;
+  sg.k = std::min(4, n);
+  int hi = n;
+  for (int k = 0; k < sg.k; ++k) {
+    const double target = (double)tri(n, 0) * (double)(sg.k - k - 1) / sg.k;  // blocks left below the chunk
+    int lo = k + 1 == sg.k ? 0 : (int)std::floor((std::sqrt(8.0 * target + 1.0) - 1.0) / 2.0);
+    lo = std::max(0, std::min(lo, hi - 1));
+    sg.c_lo[k] = lo;
+    sg.c_hi[k] = k == 0 ? n + 1 : hi;
+    hi = lo;
+  }
+  sg.c_lo[sg.k - 1] = 0;
+  // the copies start after the work already queued on the stream (the
+  // buffers may still be in use) and never overwrite row n
+  if ((e = cudaEventRecord(ctx->up_start, s)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ctx->up_start, 0)))
+    return cuda_fail(ctx, e, "kbe_step_host: copy stream");
+  const size_t ring_bytes = (size_t)kRing * 2 * ctx->n_max * blk;
+  e = cudaMemcpyAsync(F_ring, F_host, ring_bytes, cudaMemcpyHostToDevice, cs);
+  for (int k = 0; k < sg.k && e == cudaSuccess; ++k) {
+    const int r_lo = sg.c_lo[k], r_hi = k == 0 ? n : sg.c_hi[k];
+    const size_t off = (size_t)tri(r_lo, 0) * blk, bytes = (size_t)(tri(r_hi, 0) - tri(r_lo, 0)) * blk;
+    if (bytes > 0) {
+      e = cudaMemcpyAsync((char*)L + off, (const char*)L_host + off, bytes, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char*)R + off, (const char*)R_host + off, bytes, cudaMemcpyHostToDevice, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sg.ev[k] = ctx->up_ev[k], cs);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_step_host: upload");
+  // rows 0..n-1 were rewritten: digit planes cached from earlier steps are stale
+  ctx->planes_L = ctx->planes_R = nullptr;
+  ctx->planes_rows = 0;
+  int count = 0;
+  st = step_impl(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_ring, 0, kRing, s, nullptr, &count, &sg);
+  ctx->last_launches = count;
+  if (st != KBE_OK) return st;
+  const size_t row_bytes = (size_t)(n + 1) * blk;
+  e = cudaMemcpyAsync(L_row_host, (const char*)L + (size_t)tri(n, 0) * blk, row_bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(R_row_host, (const char*)R + (size_t)tri(n, 0) * blk, row_bytes, cudaMemcpyDeviceToHost, s);
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_step_host: row download");
+}
+
 kbe_status kbe_step_rows(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* Sl, void* Sg,
                          void* I_work, void* F_rows, int j0, int n_rows, void* stream) {
   if (!ctx) return KBE_EINVAL;
@@ -1171,7 +1281,6 @@ kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts
   const int M = ctx->M, MM = M * M, n_max = ctx->n_max;
   cudaError_t e = cudaSuccess;
   if (K_sel > 0) {
-    const size_t tab = (size_t)n_max * kMaxOrder * kWTab;
     if (!ctx->d_hist && (e = cudaMalloc(&ctx->d_hist, hist_doubles(ctx->n_max, ctx->M) * sizeof(double))) != cudaSuccess)
       return cuda_fail(ctx, e, "kbe_run_controlled: allocation");
     if (!ctx->d_korder && (e = cudaMalloc(&ctx->d_korder, n_max * sizeof(int))) != cudaSuccess)

@@ -48,9 +48,10 @@ __global__ void __launch_bounds__(256) history_prep(int MM, int n, const double*
     rk::history_prep_entry(MM, n, e, Sl, Sg, w, A1, Bl, Bg);
 }
 
-__global__ void __launch_bounds__(256) history_partial(PartialArgs p) {
-  const int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (lin >= (int64_t)(p.n + 1) * p.MM) return;
+// Output entries lin in [lin0, lin_end) (whole columns: lin = c M^2 + a M + b).
+__global__ void __launch_bounds__(256) history_partial(PartialArgs p, int64_t lin0, int64_t lin_end) {
+  const int64_t lin = lin0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (lin >= lin_end) return;
   rk::history_partial_entry(p, lin, blockIdx.y);
 }
 
@@ -81,8 +82,13 @@ inline unsigned grid_for(int64_t n, int64_t cap) {
 }  // namespace
 
 // Workspace layout (doubles): A1, Bl, Bg: 3 x (n+1) MM complex; then the
-// split partials nchunk x 2 x (n+1) MM complex.
-cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches) {
+// split partials nchunk x 2 x (n+1) MM complex.  The output columns may be
+// contracted in several launches (column ranges, each after an optional
+// event, e.g. the arrival of the history rows it reads); every entry is
+// computed by the same thread arithmetic whatever the ranges, so the
+// results are bitwise those of one launch.
+cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const int* c_lo, const int* c_hi,
+                                      const cudaEvent_t* wait, cudaStream_t s, int* launches) {
   const int M = a.M, MM = M * M, n = a.n;
   const int64_t row = (int64_t)(n + 1) * MM;       // complex entries per s
   const int64_t outputs = row;                     // threads of one chunk
@@ -113,12 +119,18 @@ cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launch
   if (e != cudaSuccess) { *launches = nl; return e; }
   PartialArgs p{M, MM, n, chunk_len, a.L, a.R, a.Sl, a.Sg, A1, Bl, Bg, a.w,
                 nchunk == 1 ? a.out : partials};
-  dim3 grid((unsigned)((outputs + kHistBlock - 1) / kHistBlock), (unsigned)nchunk);
   if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
-  history_partial<<<grid, kHistBlock, 0, s>>>(p);
+  for (int k = 0; k < nranges; ++k) {
+    const int lo = std::max(0, c_lo[k]), hi = std::min(n + 1, c_hi[k]);
+    if (wait && wait[k] && (e = cudaStreamWaitEvent(s, wait[k], 0)) != cudaSuccess) break;
+    if (hi <= lo) continue;
+    const int64_t lin0 = (int64_t)lo * MM, lin_end = (int64_t)hi * MM;
+    dim3 grid((unsigned)((lin_end - lin0 + kHistBlock - 1) / kHistBlock), (unsigned)nchunk);
+    history_partial<<<grid, kHistBlock, 0, s>>>(p, lin0, lin_end);
+    ++nl;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+  }
   if (a.ev_end) cudaEventRecord(a.ev_end, s);
-  ++nl;
-  e = cudaGetLastError();
   if (e != cudaSuccess) { *launches = nl; return e; }
   if (nchunk > 1) {
     history_reduce<<<grid_for(2 * row, 152 * 8), 256, 0, s>>>(2 * row, nchunk, (const double2*)partials,
@@ -129,6 +141,11 @@ cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launch
   ++nl;
   *launches = nl;
   return cudaGetLastError();
+}
+
+cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches) {
+  const int lo = 0, hi = a.n + 1;
+  return launch_history_f64_ranges(a, 1, &lo, &hi, nullptr, s, launches);
 }
 
 }  // namespace kbe

@@ -135,6 +135,10 @@ struct kbe_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
+  // kbe_step_host: copy stream for the history upload and its events
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_start = nullptr;
+  cudaEvent_t up_ev[16] = {};
 };
 
 namespace kbe {
@@ -179,6 +183,11 @@ struct HistoryArgs {
 };
 // FP64 history slice; sets *launches to the number of kernels enqueued.
 cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches);
+// The same with the output columns contracted in nranges launches, range k
+// (columns [c_lo[k], c_hi[k])) after the stream waits for wait[k] (if wait
+// and wait[k] are set); bitwise the same results as one launch.
+cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const int* c_lo, const int* c_hi,
+                                      const cudaEvent_t* wait, cudaStream_t s, int* launches);
 
 // Split-precision history slice (history_split.cu).
 struct SplitGeomHost {
