@@ -2,7 +2,20 @@
 
 The systems of a batched step are independent, so N GPUs share a batch by
 taking disjoint sets of systems: no collective touches the data path, and
-only the step time is reduced (the maximum over ranks).  The split balances
+only the step time is reduced (the maximum over ranks).
+
+One system can be split too (not run by this build, whose calls each use one
+GPU; the host logic below is tested with gloo ranks on the CPU): the stored
+triangle is cut into contiguous bands of rows, one per rank, with about equal
+numbers of stored blocks.  A stored block (r, c), r >= c, enters the history
+slice of row n (Eq. KBE2) three times: term 1 of output column c (history
+point m = r), term 1 of output column r through G(c, r) = -G(r, c)^+ (m = c,
+r != c) and term 2 of output column r through G^A(c, r) = R(r, c)^+ (m = c).
+So each rank adds the contributions of its own blocks to all n + 1 output
+columns, and one all-reduce of the 2 (n+1) M^2 complex partials gives every
+rank the slice; the self-energy row n and the new row n itself are O(n M^2)
+and every rank computes them from the reduced slice.  Communication is
+O(n M^2) per slice against O(n^2 M^3 / N) work per rank.  The split balances
 the history-slice work, which dominates a step: a system of M orbitals at
 row n costs 8 M^3 (n+1)(3n+2) flops per slice (Eq. KBE2 over the 2n+1
 required output blocks).  Systems are dealt largest first to the least
@@ -42,3 +55,48 @@ def max_over_ranks(value):
     t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def tri(n):
+    """Stored blocks of rows 0..n-1 of a lower triangle: n (n+1) / 2."""
+    return n * (n + 1) // 2
+
+
+def row_bands(n_rows, world):
+    """Contiguous bands [lo, hi) of the rows 0..n_rows-1, one per rank, each
+    holding about tri(n_rows) / world stored blocks (row r holds r + 1
+    blocks); deterministic, so every rank derives the same bands."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    total = tri(n_rows)
+    bounds = [0]
+    for k in range(1, world):
+        target = total * k / world
+        r = bounds[-1]
+        while r < n_rows and tri(r + 1) <= target:
+            r += 1
+        # the nearer of r and r + 1 to the target, never before the last bound
+        if r < n_rows and abs(tri(r + 1) - target) < abs(tri(r) - target):
+            r += 1
+        bounds.append(max(bounds[-1], r))
+    bounds.append(n_rows)
+    return [(bounds[k], bounds[k + 1]) for k in range(world)]
+
+
+def band_owner(bands, r):
+    """The rank whose band holds row r."""
+    for k, (lo, hi) in enumerate(bands):
+        if lo <= r < hi:
+            return k
+    raise ValueError("row %d is in no band" % r)
+
+
+def sharded_slice(partial, group=None):
+    """Sum the ranks' partial history slices in place (all-reduce over
+    ``group``); every rank ends with the whole slice.  ``partial`` holds this
+    rank's contributions [2][n+1][M][M] (complex128, on the rank's device)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(partial, op=dist.ReduceOp.SUM, group=group)
+    return partial
+
