@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-interaction self-energy and step")
     ap.add_argument("--no-controller", action="store_true", help="skip the adaptive time-stepping runs")
     ap.add_argument("--no-thermal", action="store_true", help="skip the thermal-branch step")
+    ap.add_argument("--no-seeds", action="store_true", help="skip the main step at the other input seeds")
     ap.add_argument("--dense-norb", default="2,8,16,32",
                     help="comma-separated orbital counts of the dense self-energy rows")
     return ap.parse_args()
@@ -652,6 +653,26 @@ def precision_m32_bench(kbe, seed, stream, steps):
             "gpu_launches": {"fp64": launches, "split": launches_s}}
 
 
+def seed_spread(kbe, seeds, n_t, P, stream):
+    """The main KBE step (FP64 and split) on the inputs of each seed (grid
+    and pulse drawn from it): ms per step per seed and their medians."""
+    import torch
+    out = {"seeds": list(seeds), "fp64_ms_per_step": [], "split_ms_per_step": []}
+    for sd in seeds:
+        cfg, t, order, h, U, v, pulse, ctx, run, n = setup_workload(kbe, sd, n_t)
+        ms, _, _, _ = time_steps(ctx, run, n, P, 4, 3, stream)
+        ms_s, _, _, _ = time_steps(ctx, run, n, P, 4, 3, stream, "split")
+        ctx.sync_status()
+        ctx.close()
+        del run
+        torch.cuda.empty_cache()
+        out["fp64_ms_per_step"].append(round(ms / 4, 4))
+        out["split_ms_per_step"].append(round(ms_s / 4, 4))
+    out["median_fp64_ms_per_step"] = float(np.median(out["fp64_ms_per_step"]))
+    out["median_split_ms_per_step"] = float(np.median(out["split_ms_per_step"]))
+    return out
+
+
 def step_rows(run, n):
     p = W_tri(n)
     return (run.L[p:p + n + 1].cpu().numpy(), run.R[p:p + n + 1].cpu().numpy(),
@@ -778,6 +799,8 @@ def main():
     ctx.close()
     del run
     torch.cuda.empty_cache()
+    if rank == 0 and not args.no_seeds:
+        line["seed_spread"] = seed_spread(kbe, sorted({args.seed, 1, 2} | {0}), args.n_t, args.P, stream)
     if rank == 0 and not args.no_m32:
         line["precision_form_goe_m32"] = precision_m32_bench(kbe, args.seed, stream, 3)
     if not args.no_batch:
