@@ -702,12 +702,15 @@ def main():
     # the precision form: the same step with the contraction on the tensor cores
     ms_s, launches_s, kc_s, kms_s = time_steps(ctx, run, n, args.P, args.steps, args.warmup, stream, "split")
     rows["split"] = step_rows(run, n)
+    # the double-float contraction on the FP32 pipe (KBE_DF64)
+    ms_d, launches_d, kc_d, kms_d = time_steps(ctx, run, n, args.P, args.steps, args.warmup, stream, "df64")
+    rows["df64"] = step_rows(run, n)
     clk = clocks.stop()
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([ms, ms_s], device="cuda", dtype=torch.float64)
+        tt = torch.tensor([ms, ms_s, ms_d], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, ms_s = float(tt[0].item()), float(tt[1].item())
+        ms, ms_s, ms_d = float(tt[0].item()), float(tt[1].item()), float(tt[2].item())
         dist.barrier()
     ms_step = ms / args.steps
     flops_step = args.P * slice_flops(M, n)
@@ -743,6 +746,16 @@ def main():
              "value": round(world * flops_step / (ms_step_s * 1e-3) / 1e12, 4), "unit": "TFLOP/s (FP64-equivalent)",
              "speedup_vs_fp64_step": round(ms_step / ms_step_s, 3), "stated_error_bound": 1e-8,
              "contraction_kernel_ms": round(kms_s / max(kc_s, 1), 4), "gpu_launches": launches_s}
+    ms_step_d = ms_d / args.steps
+    k_avg_d = kms_d / max(kc_d, 1)
+    df64 = {"precision": "double-float contraction on the FP32 pipe (KBE_DF64): hi + lo floats, compensated sums",
+            "ms_per_step": round(ms_step_d, 4),
+            "value": round(world * flops_step / (ms_step_d * 1e-3) / 1e12, 4), "unit": "TFLOP/s (FP64-equivalent)",
+            "speedup_vs_fp64_step": round(ms_step / ms_step_d, 3),
+            "contraction_kernel_ms": round(k_avg_d, 4),
+            "contraction_tflops_fp64_equivalent": round(slice_flops(M, n) / (k_avg_d * 1e-3) / 1e12, 4),
+            "contraction_vs_fp64_peak": round(slice_flops(M, n) / (k_avg_d * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3),
+            "gpu_launches": launches_d}
     e2e = None
     if not args.no_e2e:
         e2e_ms, h2d, d2h = e2e_steps(ctx, run, n, args.P, max(3, args.steps // 4), 1, stream)
@@ -757,7 +770,7 @@ def main():
                        "norb": M, "n_t": n + 1, "n": n, "P": args.P, "precision": "fp64",
                        "l2": "inputs larger than L2 (history %.2f GB per step)" % (2 * (n + 1) * (n + 2) / 2 * M * M * 16 / 1e9),
                        "parallelism": "independent replicas" if world > 1 else "single GPU"},
-            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "precision_form": split}
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "precision_form": split, "df64_form": df64}
     if clk:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -767,6 +780,7 @@ def main():
         line["error_vs_oracle"] = dict(errs["fp64"], where="new row n and last history slice of the timed KBE "
                                                            "step, max-norm relative")
         line["precision_form"]["error_vs_oracle"] = errs["split"]
+        line["df64_form"]["error_vs_oracle"] = errs["df64"]
     if rank == 0 and not args.no_selfenergy:
         line["selfenergy"] = sigma_bench(kbe, ctx, run, n + 1, stream)
     if rank == 0 and not args.no_window:

@@ -74,6 +74,11 @@ typedef int kbe_status;
                           /* in FP32 and combined in double-float; about 1e-9 */
                           /* relative to the slice maximum.  norb <= 32.      */
                           /* Deterministic.  Requires R(r,r) = -i*1 exactly. */
+#define KBE_DF64 2        /* the contraction in double-float arithmetic on    */
+                          /* the FP32 pipe (hi + lo floats, about 2^-47 per   */
+                          /* product, compensated sums): about 1e-14 of the   */
+                          /* terms' sizes, several times the FP64 pipe's      */
+                          /* rate on this part.  Deterministic.               */
 
 /* ---------------------------------------------------------- lifecycle -- */
 
@@ -199,7 +204,8 @@ kbe_status kbe_selfenergy_all(kbe_ctx* ctx, int n_rows, const void* L, const voi
 /* History slice of row n, Eq. (KBE2) (formula at the top of this file):
  * I_out [2][n+1][M][M] device, written.  L, R: device triangles holding
  * rows 0..n; S_less, S_great: device self-energy row n.  precision:
- * KBE_FP64.  Deterministic for KBE_FP64 (fixed split and reduction order).
+ * KBE_FP64, KBE_SPLIT_BF16 or KBE_DF64.  Deterministic (fixed split and
+ * reduction order).
  * Requires a grid with n < n_t.  Uses the context's workspace: calls on
  * one context must not overlap on different streams. */
 kbe_status kbe_history_slice(kbe_ctx* ctx, int n, int precision, const void* L, const void* R,

@@ -23,7 +23,8 @@ KBE_MAX_ORDER = 12
 KBE_RING_ROWS = 13
 KBE_FP64 = 0
 KBE_SPLIT_BF16 = 1
-PRECISIONS = {"fp64": KBE_FP64, "split": KBE_SPLIT_BF16}
+KBE_DF64 = 2
+PRECISIONS = {"fp64": KBE_FP64, "split": KBE_SPLIT_BF16, "df64": KBE_DF64}
 
 _lib = None
 

@@ -156,10 +156,15 @@ kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void
     }
     return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "split history slice launch");
   }
-  if (precision != KBE_FP64) return fail(ctx, KBE_EINVAL, "unknown precision");
+  if (precision != KBE_FP64 && precision != KBE_DF64) return fail(ctx, KBE_EINVAL, "unknown precision");
   HistoryArgs a{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
                 weights_view(ctx), (double*)I_out, ctx->d_part, ctx->part_bytes, ctx->d_status};
   cudaError_t e;
+  if (precision == KBE_DF64) {
+    if (!next_events(ctx, &a.ev_begin, &a.ev_end)) return fail(ctx, KBE_ECUDA, "profiling: cudaEventCreate");
+    e = launch_history_df(a, s, launches);
+    return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "history slice launch");
+  }
   if (staged) {  // the column ranges contract as their rows arrive (no timing events: they would hold the waits)
     e = launch_history_f64_ranges(a, staged->k, staged->c_lo, staged->c_hi, staged->ev, s, launches);
     return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "history slice launch");
@@ -375,7 +380,8 @@ kbe_status check_step_call(kbe_ctx* ctx, int n, int P, int precision, const void
   if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
   if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_work) || !aligned16(F))
     return fail(ctx, KBE_EINVAL, "kbe_step: NULL or misaligned pointer");
-  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16) return fail(ctx, KBE_EINVAL, "kbe_step: unknown precision");
+  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16 && precision != KBE_DF64)
+    return fail(ctx, KBE_EINVAL, "kbe_step: unknown precision");
   if (ctx->adaptive_K > 0) {
     if (n > ctx->adaptive_rows)
       return fail(ctx, KBE_ESTATE, "kbe_step: adaptive history orders need the steps in order (row " +
@@ -1272,7 +1278,7 @@ kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts
     return fail(ctx, KBE_EINVAL, "kbe_run_controlled: need rtol >= 0, atol > 0, h0 > 0, h_max >= 0, t_end > 0");
   if (q_max < 1 || q_max > kMaxOrder || k_hist < 1 || k_hist > kMaxOrder || K_sel < 0 || K_sel > kMaxOrder)
     return fail(ctx, KBE_EINVAL, "kbe_run_controlled: q_max, k_hist in [1, 12], K_sel in [0, 12]");
-  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16)
+  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16 && precision != KBE_DF64)
     return fail(ctx, KBE_EINVAL, "kbe_run_controlled: unknown precision");
   if (ctx->n_max < 2) return fail(ctx, KBE_EINVAL, "kbe_run_controlled: n_max < 2");
   kbe_status st = use_device(ctx);

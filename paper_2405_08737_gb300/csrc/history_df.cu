@@ -1,0 +1,242 @@
+// history_df.cu -- history slice of Eq. (KBE2) (Sec. 2) in double-float
+// arithmetic on the FP32 pipe (precision KBE_DF64).
+//
+// The same sums as history_f64.cu,
+//   I^<(n,c) = sum_m A1[m] G^<(m,c) + sum_{m<=c} B^<[m] G^A(m,c),
+//   I^>(n,c) = sum_m A1[m] G^>(m,c) + sum_{m<=c} B^>[m] G^A(m,c),
+// with A1[m] = w_{n,m} (S^> - S^<)[m], B^s[m] = wbar_m S^s[m] (w_{c,m} S^s[m]
+// in the band m > c - K - 1), G^> = G^< + R below and on the diagonal, and
+// the symmetries G^s(m,c) = -G^s(c,m)^+ (m < c), G^A(m,c) = R(c,m)^+.
+//
+// GB300 issues 64 FP32 operations per FP64 operation, so a complex
+// multiply-add done as four double-float products (each hi*hi, its FMA
+// error and the two cross terms, about 2^-47 relative) with Ogita-Rump-Oishi
+// compensated accumulation (a TwoSum per term, the errors in a float tail)
+// costs about 48 FP32 operations where FP64 needs 4 DFMA: at the two pipes'
+// rates the slice runs about four times faster than on the FP64 pipe, with
+// an error of order 1e-14 of the terms' sizes (Sec. 3.2's quadrature and
+// the history are FP64 inputs, converted once per use to hi + lo floats).
+//
+// Layout.  A prep kernel forms A1, B^<, B^> in FP64 (as history_prep) and
+// stores them as double-float (float4: re.hi, re.lo, im.hi, im.lo) rows.
+// One thread owns one output column entry (c, b) for a group of 2 values of
+// a and both s: each history entry it loads is converted once and used for
+// its 2 values of a; the self-energy operands are shared by the warp
+// (broadcast loads).  The history index m is split into chunks across
+// grid.y; per-chunk partials go to the workspace as FP64 and the FP64
+// reduction adds them in chunk order (deterministic).
+
+#include <algorithm>
+
+#include "dfloat.cuh"
+#include "row_kernels.cuh"
+
+namespace kbe {
+namespace {
+
+constexpr int kNA = 2;          // values of a per thread
+constexpr int kDfBlock = 128;   // threads per block
+
+struct DfArgs {
+  int M, MM, n, AG;             // AG = ceil(M / kNA) groups of a
+  int chunk_len;
+  const double* L;
+  const double* R;
+  const double* Sl;             // raw row n (band points of term 2)
+  const double* Sg;
+  const float4* A1;             // double-float rows [n+1][M][M]
+  const float4* Bl;
+  const float4* Bg;
+  WeightsView w;
+  double* dst;                  // partials [chunk][2][n+1][MM] or the output
+};
+
+__device__ __forceinline__ float4 c2f(double2 v) {
+  const df::F2 r = df::from_double_fast(v.x), i = df::from_double_fast(v.y);
+  return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+
+__global__ void __launch_bounds__(256) history_df_prep(int MM, int n, const double* __restrict__ Sl,
+                                                       const double* __restrict__ Sg, WeightsView w,
+                                                       float4* __restrict__ A1, float4* __restrict__ Bl,
+                                                       float4* __restrict__ Bg) {
+  const int64_t total = (int64_t)(n + 1) * MM;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e / MM);
+    const double wn = w.at(n, m), wb = w.wbar[m];
+    const double2 l = reinterpret_cast<const double2*>(Sl)[e];
+    const double2 g = reinterpret_cast<const double2*>(Sg)[e];
+    A1[e] = c2f(make_double2(wn * (g.x - l.x), wn * (g.y - l.y)));
+    Bl[e] = c2f(make_double2(wb * l.x, wb * l.y));
+    Bg[e] = c2f(make_double2(wb * g.x, wb * g.y));
+  }
+}
+
+// compensated accumulator of one real sum: s + c
+struct Acc {
+  float s, c;
+};
+// a += x y (x, y double-float: hi, lo)
+__device__ __forceinline__ void acc_prod(Acc& a, float xh, float xl, float yh, float yl) {
+  const float h = xh * yh;
+  float e = fmaf(xh, yh, -h);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float s = a.s + h;
+  const float v = s - a.s;
+  a.c += ((a.s - (s - v)) + (h - v)) + e;
+  a.s = s;
+}
+// complex: (re, im) += p q, p, q as float4 (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ void cmac(Acc& re, Acc& im, float4 p, float4 q) {
+  acc_prod(re, p.x, p.y, q.x, q.y);
+  acc_prod(re, -p.z, -p.w, q.z, q.w);
+  acc_prod(im, p.x, p.y, q.z, q.w);
+  acc_prod(im, p.z, p.w, q.x, q.y);
+}
+__device__ __forceinline__ float4 cneg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+__device__ __forceinline__ float4 cconj(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
+// double-float sum (error of order 2^-47 of |a| + |b|)
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
+  const df::F2 r = df::add(df::F2{a.x, a.y}, df::F2{b.x, b.y});
+  const df::F2 i = df::add(df::F2{a.z, a.w}, df::F2{b.z, b.w});
+  return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+
+__global__ void __launch_bounds__(kDfBlock) history_df_partial(DfArgs p) {
+  const int M = p.M, MM = p.MM, n = p.n, AG = p.AG;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)(n + 1) * AG * M) return;
+  const int c = (int)(t / ((int64_t)AG * M));
+  const int r = (int)(t - (int64_t)c * AG * M);
+  const int ag = r / M, b = r - ag * M;
+  const int a0 = ag * kNA;
+  const int na = min(kNA, M - a0);
+  const int chunk = blockIdx.y;
+  const int m0 = chunk * p.chunk_len;
+  const int m1 = min(n + 1, m0 + p.chunk_len);
+  const int band_lo = c - p.w.band_w + 1;  // m >= band_lo: w_{c,m} from the band
+
+  Acc lr[kNA], li[kNA], gr[kNA], gi[kNA];  // I^< and I^> (re, im)
+#pragma unroll
+  for (int k = 0; k < kNA; ++k) lr[k] = li[k] = gr[k] = gi[k] = Acc{0.f, 0.f};
+  const double2* L = reinterpret_cast<const double2*>(p.L);
+  const double2* R = reinterpret_cast<const double2*>(p.R);
+
+  for (int m = m0; m < m1; ++m) {
+    const bool below = m > c, diag = m == c;
+    const bool band = !below && m >= band_lo;
+    const double wcm = band ? p.w.at(c, m) : 0.0;
+    // this thread's column b of G(m,c): block (m,c) row x for m >= c; block
+    // (c,m) row b, transposed and conjugated, for m < c
+    const int64_t blk = below || diag ? tri(m, c) * MM : tri(c, m) * MM;
+    for (int x = 0; x < M; ++x) {
+      float4 gl, gs, ga;
+      if (below || diag) {
+        gl = c2f(L[blk + x * M + b]);
+        const float4 rr = c2f(R[blk + x * M + b]);
+        gs = cadd(gl, rr);                                 // G^>(m,c) = L + R
+        ga = diag ? cconj(c2f(R[blk + b * M + x])) : rr;   // G^A(c,c)_xb = conj(R(c,c)_bx)
+      } else {
+        const float4 l = c2f(L[blk + b * M + x]), rr = c2f(R[blk + b * M + x]);
+        gl = cneg(cconj(l));                               // G^<(m,c)_xb = -conj(L(c,m)_bx)
+        gs = cneg(cconj(cadd(l, rr)));                     // G^>(m,c)_xb = -conj((L+R)(c,m)_bx)
+        ga = cconj(rr);                                    // G^A(m,c)_xb = conj(R(c,m)_bx)
+      }
+      const float4* a1 = p.A1 + ((int64_t)m * M + a0) * M + x;
+#pragma unroll
+      for (int k = 0; k < kNA; ++k) {
+        if (k < na) {
+          const float4 s1 = a1[(int64_t)k * M];
+          cmac(lr[k], li[k], s1, gl);
+          cmac(gr[k], gi[k], s1, gs);
+        }
+      }
+      if (below) continue;
+      if (!band) {
+        const float4* bl = p.Bl + ((int64_t)m * M + a0) * M + x;
+        const float4* bg = p.Bg + ((int64_t)m * M + a0) * M + x;
+#pragma unroll
+        for (int k = 0; k < kNA; ++k) {
+          if (k < na) {
+            cmac(lr[k], li[k], bl[(int64_t)k * M], ga);
+            cmac(gr[k], gi[k], bg[(int64_t)k * M], ga);
+          }
+        }
+      } else {
+        const double2* sl = reinterpret_cast<const double2*>(p.Sl) + ((int64_t)m * M + a0) * M + x;
+        const double2* sg = reinterpret_cast<const double2*>(p.Sg) + ((int64_t)m * M + a0) * M + x;
+#pragma unroll
+        for (int k = 0; k < kNA; ++k) {
+          if (k < na) {
+            const double2 vl = sl[(int64_t)k * M], vg = sg[(int64_t)k * M];
+            cmac(lr[k], li[k], c2f(make_double2(wcm * vl.x, wcm * vl.y)), ga);
+            cmac(gr[k], gi[k], c2f(make_double2(wcm * vg.x, wcm * vg.y)), ga);
+          }
+        }
+      }
+    }
+  }
+  double2* d = reinterpret_cast<double2*>(p.dst);
+  const int64_t stride_s = (int64_t)(n + 1) * MM;
+  const int64_t base = (int64_t)chunk * 2 * stride_s + (int64_t)c * MM + b;
+#pragma unroll
+  for (int k = 0; k < kNA; ++k) {
+    if (k < na) {
+      const int64_t e = base + (int64_t)(a0 + k) * M;
+      d[e] = make_double2((double)lr[k].s + (double)lr[k].c, (double)li[k].s + (double)li[k].c);
+      d[e + stride_s] = make_double2((double)gr[k].s + (double)gr[k].c, (double)gi[k].s + (double)gi[k].c);
+    }
+  }
+}
+
+inline unsigned grid_for(int64_t n, int64_t cap) {
+  int64_t b = (n + 255) / 256;
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+// Workspace as launch_history_f64: the three double-float operand rows take
+// the places of A1, Bl, Bg (16 bytes per complex either way), then the
+// per-chunk partials.
+cudaError_t launch_history_df(const HistoryArgs& a, cudaStream_t s, int* launches) {
+  const int M = a.M, MM = M * M, n = a.n;
+  const int AG = (M + kNA - 1) / kNA;
+  const int64_t row = (int64_t)(n + 1) * MM;
+  const int64_t threads = (int64_t)(n + 1) * AG * M;
+  // enough threads for full occupancy, and chunks of at most ~32 history
+  // points so that a block's work stays short
+  int64_t want = std::max<int64_t>((152LL * 2048 + threads - 1) / threads, (n + 1 + 31) / 32);
+  int nchunk = (int)std::min<int64_t>(std::max<int64_t>(want, 1), kMaxSplit);
+  if (nchunk > n + 1) nchunk = n + 1;
+  const size_t prep_bytes = (size_t)3 * row * 16;
+  while (nchunk > 1 && prep_bytes + (size_t)nchunk * 2 * row * 16 > a.part_bytes) --nchunk;
+  if (prep_bytes + (nchunk > 1 ? (size_t)nchunk * 2 * row * 16 : 0) > a.part_bytes) return cudaErrorInvalidValue;
+  const int chunk_len = (n + 1 + nchunk - 1) / nchunk;
+  nchunk = (n + 1 + chunk_len - 1) / chunk_len;
+
+  float4* A1 = reinterpret_cast<float4*>(a.part);
+  float4* Bl = A1 + row;
+  float4* Bg = Bl + row;
+  double* partials = a.part + 6 * row;
+  int nl = 0;
+  history_df_prep<<<grid_for(row, 152 * 8), 256, 0, s>>>(MM, n, a.Sl, a.Sg, a.w, A1, Bl, Bg);
+  ++nl;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { *launches = nl; return e; }
+  DfArgs p{M, MM, n, AG, chunk_len, a.L, a.R, a.Sl, a.Sg, A1, Bl, Bg, a.w, nchunk == 1 ? a.out : partials};
+  dim3 grid((unsigned)((threads + kDfBlock - 1) / kDfBlock), (unsigned)nchunk);
+  if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
+  history_df_partial<<<grid, kDfBlock, 0, s>>>(p);
+  if (a.ev_end) cudaEventRecord(a.ev_end, s);
+  ++nl;
+  if ((e = cudaGetLastError()) != cudaSuccess) { *launches = nl; return e; }
+  int nr = 0;
+  e = launch_history_finish(nchunk, row, partials, a.out, a.status, s, &nr);
+  *launches = nl + nr;
+  return e;
+}
+
+}  // namespace kbe

@@ -143,6 +143,20 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
   return cudaGetLastError();
 }
 
+// The last kernel of a split slice: partials [nchunk][2][row] summed in
+// chunk order into out (or, for one chunk, out checked for finite values).
+cudaError_t launch_history_finish(int nchunk, int64_t row, const double* partials, double* out, int* status,
+                                  cudaStream_t s, int* launches) {
+  if (nchunk > 1) {
+    history_reduce<<<grid_for(2 * row, 152 * 8), 256, 0, s>>>(2 * row, nchunk, (const double2*)partials,
+                                                              (double2*)out, status);
+  } else {
+    finite_check<<<grid_for(2 * row, 152 * 8), 256, 0, s>>>(2 * row, (const double2*)out, status);
+  }
+  *launches = 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches) {
   const int lo = 0, hi = a.n + 1;
   return launch_history_f64_ranges(a, 1, &lo, &hi, nullptr, s, launches);

@@ -183,6 +183,12 @@ struct HistoryArgs {
 };
 // FP64 history slice; sets *launches to the number of kernels enqueued.
 cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches);
+// The history slice in double-float on the FP32 pipe (KBE_DF64), same
+// workspace and outputs as launch_history_f64.
+cudaError_t launch_history_df(const HistoryArgs& a, cudaStream_t s, int* launches);
+// Chunk partials [nchunk][2][row] summed in order into out (one launch).
+cudaError_t launch_history_finish(int nchunk, int64_t row, const double* partials, double* out, int* status,
+                                  cudaStream_t s, int* launches);
 // The same with the output columns contracted in nranges launches, range k
 // (columns [c_lo[k], c_hi[k])) after the stream waits for wait[k] (if wait
 // and wait[k] are set); bitwise the same results as one launch.
