@@ -215,6 +215,7 @@ StepArgs step_args(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F
 // ------------------------------------------------------- thermal branch --
 struct ThermalLayout {
   double *GM, *left, *Smix, *Smw, *Aw, *Fx, *Gx;
+  float4 *Smwf, *Awf;
 };
 
 // doubles of the tau-weight table, padded so that the complex arrays after
@@ -231,7 +232,9 @@ ThermalLayout thermal_layout(kbe_ctx* ctx) {
   t.Smw = w;   w += N * MM * 2;
   t.Aw = w;    w += (size_t)ctx->n_max * MM * 2;
   t.Fx = w;    w += (size_t)kRing * N * MM * 2;
-  t.Gx = w;
+  t.Gx = w;    w += (size_t)ctx->n_max * N * MM * 2;
+  t.Smwf = reinterpret_cast<float4*>(w);  w += N * MM * 2;
+  t.Awf = reinterpret_cast<float4*>(w);
   return t;
 }
 
@@ -253,6 +256,9 @@ ThermalArgs thermal_args(kbe_ctx* ctx, const StepArgs& a, const void* Sl, const 
   x.Smix = t.Smix;
   x.Smw = t.Smw;
   x.Aw = t.Aw;
+  x.Smwf = t.Smwf;
+  x.Awf = t.Awf;
+  x.df = 0;
   x.Fx = t.Fx;
   x.I = (double*)I;
   x.corr = a.corr;
@@ -351,7 +357,8 @@ kbe_status step_impl(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R
     *count_out = (count += nl);
     if (st != KBE_OK) return st;
     if (ctx->thermal) {
-      const ThermalArgs x = thermal_args(ctx, a, Sl, Sg, I_work);
+      ThermalArgs x = thermal_args(ctx, a, Sl, Sg, I_work);
+      x.df = precision != KBE_FP64;  // the thermal sums in double-float with the faster contractions
       if ((e = thermal_sweep_a(ctx, x, s)) != cudaSuccess || (e = launch_fock(a, s)) != cudaSuccess ||
           (e = launch_rhs_corrector(a, s)) != cudaSuccess || (e = launch_th_rhs(x, s)) != cudaSuccess ||
           (e = launch_th_adams(x, true, s)) != cudaSuccess) {
@@ -724,7 +731,8 @@ kbe_status kbe_set_thermal(kbe_ctx* ctx, double beta, int n_tau, int k_tau, cons
   if (st != KBE_OK) return st;
   if ((st = use_device(ctx)) != KBE_OK) return st;
   const size_t doubles = 2 * N * MM + thermal_left_doubles(N) + 4 * N * MM + 2 * (size_t)ctx->n_max * MM +
-                         2 * (size_t)kRing * N * MM + 2 * (size_t)ctx->n_max * N * MM;
+                         2 * (size_t)kRing * N * MM + 2 * (size_t)ctx->n_max * N * MM + 2 * N * MM +
+                         2 * (size_t)ctx->n_max * MM;  // + the double-float copies of Smw and Aw
   cudaFree(ctx->d_th);
   ctx->d_th = nullptr;
   ctx->thermal = false;
@@ -882,7 +890,8 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
   if (st != KBE_OK) { ctx->last_launches = count; return st; }
   StepArgs a = step_args(ctx, j, (void*)L, (void*)R, I_work, F_ring);
   if (ctx->thermal) {  // Sigma^| and the mixed term, the row's F, then the mixed right-hand side
-    const ThermalArgs x = thermal_args(ctx, a, Sl, Sg, I_work);
+    ThermalArgs x = thermal_args(ctx, a, Sl, Sg, I_work);
+    x.df = precision != KBE_FP64;
     if ((e = thermal_sweep_a(ctx, x, s)) != cudaSuccess || (e = launch_fock(a, s)) != cudaSuccess ||
         (e = launch_rhs(a, s)) != cudaSuccess || (e = launch_th_rhs(x, s)) != cudaSuccess) {
       ctx->last_launches = count + 5;

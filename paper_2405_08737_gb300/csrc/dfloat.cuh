@@ -226,5 +226,45 @@ __host__ __device__ __forceinline__ C2 cmul_cj(C2 a, C2 b) {
 // real scale
 __host__ __device__ __forceinline__ C2 cscale(F2 s, C2 a) { return C2{mul(s, a.re), mul(s, a.im)}; }
 
+// ------------------------------------------------ compensated dot products --
+// Complex double-float values as float4 (re.hi, re.lo, im.hi, im.lo), and
+// real sums kept as Ogita-Rump-Oishi pairs: the leading sum s (a TwoSum per
+// term) and a float tail c collecting the TwoSum and product errors.
+struct Acc {
+  float s, c;
+};
+// a += x y (x, y double-float: hi, lo; the lo*lo term is below 2^-48)
+__device__ __forceinline__ void acc_prod(Acc& a, float xh, float xl, float yh, float yl) {
+  const float h = xh * yh;
+  float e = fmaf(xh, yh, -h);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float s = a.s + h;
+  const float v = s - a.s;
+  a.c += ((a.s - (s - v)) + (h - v)) + e;
+  a.s = s;
+}
+// (re, im) += p q
+__device__ __forceinline__ void cmac(Acc& re, Acc& im, float4 p, float4 q) {
+  acc_prod(re, p.x, p.y, q.x, q.y);
+  acc_prod(re, -p.z, -p.w, q.z, q.w);
+  acc_prod(im, p.x, p.y, q.z, q.w);
+  acc_prod(im, p.z, p.w, q.x, q.y);
+}
+__device__ __forceinline__ float4 c2f(double2 v) {
+  const F2 r = from_double_fast(v.x), i = from_double_fast(v.y);
+  return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+__device__ __forceinline__ float4 cneg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+__device__ __forceinline__ float4 cconj(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
+// double-float complex sum (error of order 2^-47 of |a| + |b|)
+__device__ __forceinline__ float4 cadd4(float4 a, float4 b) {
+  const F2 r = add(F2{a.x, a.y}, F2{b.x, b.y});
+  const F2 i = add(F2{a.z, a.w}, F2{b.z, b.w});
+  return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+// the pair's value in FP64
+__device__ __forceinline__ double acc_value(Acc a) { return (double)a.s + (double)a.c; }
+
 }  // namespace df
 }  // namespace kbe

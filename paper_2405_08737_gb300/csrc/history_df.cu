@@ -55,10 +55,12 @@ struct DfArgs {
   double* dst;                  // partials [chunk][2][n+1][MM] or the output
 };
 
-__device__ __forceinline__ float4 c2f(double2 v) {
-  const df::F2 r = df::from_double_fast(v.x), i = df::from_double_fast(v.y);
-  return make_float4(r.hi, r.lo, i.hi, i.lo);
-}
+using df::Acc;
+using df::c2f;
+using df::cconj;
+using df::cmac;
+using df::cneg;
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) { return df::cadd4(a, b); }
 
 __global__ void __launch_bounds__(256) history_df_prep(int MM, int n, const double* __restrict__ Sl,
                                                        const double* __restrict__ Sg, WeightsView w,
@@ -75,37 +77,6 @@ __global__ void __launch_bounds__(256) history_df_prep(int MM, int n, const doub
     Bl[e] = c2f(make_double2(wb * l.x, wb * l.y));
     Bg[e] = c2f(make_double2(wb * g.x, wb * g.y));
   }
-}
-
-// compensated accumulator of one real sum: s + c
-struct Acc {
-  float s, c;
-};
-// a += x y (x, y double-float: hi, lo)
-__device__ __forceinline__ void acc_prod(Acc& a, float xh, float xl, float yh, float yl) {
-  const float h = xh * yh;
-  float e = fmaf(xh, yh, -h);
-  e = fmaf(xh, yl, e);
-  e = fmaf(xl, yh, e);
-  const float s = a.s + h;
-  const float v = s - a.s;
-  a.c += ((a.s - (s - v)) + (h - v)) + e;
-  a.s = s;
-}
-// complex: (re, im) += p q, p, q as float4 (re.hi, re.lo, im.hi, im.lo)
-__device__ __forceinline__ void cmac(Acc& re, Acc& im, float4 p, float4 q) {
-  acc_prod(re, p.x, p.y, q.x, q.y);
-  acc_prod(re, -p.z, -p.w, q.z, q.w);
-  acc_prod(im, p.x, p.y, q.z, q.w);
-  acc_prod(im, p.z, p.w, q.x, q.y);
-}
-__device__ __forceinline__ float4 cneg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
-__device__ __forceinline__ float4 cconj(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
-// double-float sum (error of order 2^-47 of |a| + |b|)
-__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
-  const df::F2 r = df::add(df::F2{a.x, a.y}, df::F2{b.x, b.y});
-  const df::F2 i = df::add(df::F2{a.z, a.w}, df::F2{b.z, b.w});
-  return make_float4(r.hi, r.lo, i.hi, i.lo);
 }
 
 __global__ void __launch_bounds__(kDfBlock) history_df_partial(DfArgs p) {

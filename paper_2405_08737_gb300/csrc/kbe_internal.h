@@ -316,6 +316,9 @@ struct ThermalArgs {
   double* Smix;          // Sigma^| row n [N][M][M]
   double* Smw;           // w_k Sigma^|(n, k) with the full-interval tau weights [N][M][M]
   double* Aw;            // w_{n,m} Sigma^R(n, m), m <= n [n_max][M][M]
+  float4* Smwf;          // Smw and Aw as double-float (re.hi, re.lo, im.hi, im.lo)
+  float4* Awf;
+  int df;                // 1: the two long sums in double-float on the FP32 pipe
   double* Fx;            // mixed right-hand sides, ring [kRing][N][M][M]
   double* I;             // history slice [2][n+1][M][M]
   const double* corr;    // stepper weights of interval n

@@ -16,9 +16,15 @@
 //              convolution split at s = tau_j;
 //   th_adams   predictor or corrector of the mixed row with the weights of
 //              the diagonal (q = min(k_n, n) points).
+// With a.df set (the split and double-float precisions of the step) the two
+// long sums, the mixed term of th_mixed and the history term of th_rhs, run
+// in double-float on the FP32 pipe (dfloat.cuh: operands as hi + lo floats,
+// compensated sums, about 2^-47 of the terms' sizes); the Matsubara
+// convolution and everything else stay FP64.
 // tau weights: left[j][k], k <= j, integrate over [0, tau_j]; [tau_j, beta]
 // uses the mirrored row left[N-1-j][N-1-k]; the full interval is row N-1.
 
+#include "dfloat.cuh"
 #include "kbe_internal.h"
 
 namespace kbe {
@@ -56,7 +62,9 @@ __global__ void __launch_bounds__(kThThreads) th_sigma(ThermalArgs a) {
     const int m = (int)(r / MM);
     const double w = a.w.at(a.n, m);
     const double2 g = ld2(a.Sg + r * 2), l = ld2(a.Sl + r * 2);
-    st2(a.Aw + r * 2, make_double2(w * (g.x - l.x), w * (g.y - l.y)));
+    const double2 v = make_double2(w * (g.x - l.x), w * (g.y - l.y));
+    st2(a.Aw + r * 2, v);
+    a.Awf[r] = df::c2f(v);
     return;
   }
   const int k = (int)(e / MM), ab = (int)(e - (int64_t)k * MM), ia = ab / M, ib = ab - ia * M;
@@ -68,7 +76,9 @@ __global__ void __launch_bounds__(kThThreads) th_sigma(ThermalArgs a) {
   const double2 s = make_double2(uu * (g2r * h.x + g2i * h.y), uu * (g2i * h.x - g2r * h.y));
   st2(a.Smix + e * 2, s);
   const double wk = a.left[(int64_t)(N - 1) * N + k];
-  st2(a.Smw + e * 2, make_double2(wk * s.x, wk * s.y));
+  const double2 sw = make_double2(wk * s.x, wk * s.y);
+  st2(a.Smw + e * 2, sw);
+  a.Smwf[e] = df::c2f(sw);
   if (!(isfinite(s.x) && isfinite(s.y))) atomicOr(a.status, kStatusNumeric);
 }
 
@@ -78,21 +88,47 @@ __global__ void __launch_bounds__(kThThreads) th_sigma(ThermalArgs a) {
 // are added in a fixed order through shared memory.
 constexpr int kParts = 8;
 constexpr int kPartThreads = 32 * kParts;
+// th_rhs in double-float: 16 parts (more warps per SM for its 256 blocks)
+constexpr int kPartsDf = 16;
 
+template <int NP>
 __device__ __forceinline__ bool reduce_parts(double2& acc) {
-  __shared__ double2 red[kParts][32];
+  __shared__ double2 red[NP][32];
   red[threadIdx.x >> 5][threadIdx.x & 31] = acc;
   __syncthreads();
   if (threadIdx.x >= 32) return false;
   acc = red[0][threadIdx.x];
-  for (int w = 1; w < kParts; ++w) {
+  for (int w = 1; w < NP; ++w) {
     acc.x += red[w][threadIdx.x].x;
     acc.y += red[w][threadIdx.x].y;
   }
   return true;
 }
 
+// Double-float sums with kChains independent accumulator pairs (term x goes
+// to chain x mod kChains, unrolled so the chains stay in registers), so that consecutive products do not wait on one
+// another's TwoSum; the chains are added in FP64 in a fixed order.
+constexpr int kChains = 4;
+struct DfSum {
+  df::Acc re[kChains], im[kChains];
+  __device__ __forceinline__ DfSum() {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) re[i] = im[i] = df::Acc{0.f, 0.f};
+  }
+  __device__ __forceinline__ double2 value() const {
+    double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+      v.x += df::acc_value(re[i]);
+      v.y += df::acc_value(im[i]);
+    }
+    return v;
+  }
+};
+
+template <bool DF>
 __global__ void __launch_bounds__(kPartThreads) th_mixed(ThermalArgs a) {
+  constexpr int kParts = 8;
   const int M = a.M, MM = M * M, N = a.N, n = a.n;
   const int part = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
@@ -101,15 +137,28 @@ __global__ void __launch_bounds__(kPartThreads) th_mixed(ThermalArgs a) {
   const int c = (int)(ee / MM), ab = (int)(ee - (int64_t)c * MM), ia = ab / M, ib = ab - ia * M;
   const double* gc = a.Gx + (int64_t)c * N * MM * 2;
   double2 acc = make_double2(0.0, 0.0);
-  for (int k = live ? part : N; k < N; k += kParts) {
-    const double* sk = a.Smw + ((int64_t)k * MM + ia * M) * 2;         // w_k Sigma^|(n,k)
-    const double* gk = gc + ((int64_t)(N - 1 - k) * MM + ib * M) * 2;  // G^|-(tau_k,t_c)_xb = conj(G^|(t_c,beta-tau_k)_bx)
-    for (int x = 0; x < M; ++x) {
-      const double2 g = ld2(gk + 2 * x);
-      cfma4(acc, ld2(sk + 2 * x), make_double2(g.x, -g.y));
+  if (DF) {
+    DfSum sum;
+    for (int k = live ? part : N; k < N; k += kParts) {
+      const float4* sk = a.Smwf + (int64_t)k * MM + ia * M;
+      const double* gk = gc + ((int64_t)(N - 1 - k) * MM + ib * M) * 2;
+      for (int x0 = 0; x0 < M; x0 += kChains)
+#pragma unroll
+        for (int i = 0; i < kChains; ++i)
+          if (x0 + i < M) df::cmac(sum.re[i], sum.im[i], sk[x0 + i], df::cconj(df::c2f(ld2(gk + 2 * (x0 + i)))));
+    }
+    acc = sum.value();
+  } else {
+    for (int k = live ? part : N; k < N; k += kParts) {
+      const double* sk = a.Smw + ((int64_t)k * MM + ia * M) * 2;         // w_k Sigma^|(n,k)
+      const double* gk = gc + ((int64_t)(N - 1 - k) * MM + ib * M) * 2;  // G^|-(tau_k,t_c)_xb = conj(G^|(t_c,beta-tau_k)_bx)
+      for (int x = 0; x < M; ++x) {
+        const double2 g = ld2(gk + 2 * x);
+        cfma4(acc, ld2(sk + 2 * x), make_double2(g.x, -g.y));
+      }
     }
   }
-  if (!reduce_parts(acc) || !live) return;
+  if (!reduce_parts<kParts>(acc) || !live) return;
   // -i (x + i y) = y - i x, added to I^< and I^>
   for (int s = 0; s < 2; ++s) {
     double* o = a.I + (((int64_t)s * (n + 1) + c) * MM + ab) * 2;
@@ -118,7 +167,9 @@ __global__ void __launch_bounds__(kPartThreads) th_mixed(ThermalArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kPartThreads) th_rhs(ThermalArgs a) {
+template <bool DF>
+__global__ void __launch_bounds__(32 * (DF ? kPartsDf : kParts)) th_rhs(ThermalArgs a) {
+  constexpr int kParts = DF ? kPartsDf : ::kbe::kParts;
   const int M = a.M, MM = M * M, N = a.N, n = a.n;
   const int part = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
@@ -127,10 +178,23 @@ __global__ void __launch_bounds__(kPartThreads) th_rhs(ThermalArgs a) {
   const int j = (int)(ee / MM), ab = (int)(ee - (int64_t)j * MM), ia = ab / M, ib = ab - ia * M;
   double2 acc = make_double2(0.0, 0.0);
   // history term: sum_m w_{n,m} Sigma^R(n,m)_ax G^|(m,j)_xb
-  for (int m = live ? part : n + 1; m <= n; m += kParts) {
-    const double* aw = a.Aw + ((int64_t)m * MM + ia * M) * 2;  // w_{n,m} Sigma^R(n,m)
-    const double* gx = a.Gx + (((int64_t)m * N + j) * MM) * 2;
-    for (int x = 0; x < M; ++x) cfma4(acc, ld2(aw + 2 * x), ld2(gx + 2 * (x * M + ib)));
+  if (DF) {
+    DfSum sum;
+    for (int m = live ? part : n + 1; m <= n; m += kParts) {
+      const float4* aw = a.Awf + (int64_t)m * MM + ia * M;
+      const double* gx = a.Gx + (((int64_t)m * N + j) * MM) * 2;
+      for (int x0 = 0; x0 < M; x0 += kChains)
+#pragma unroll
+        for (int i = 0; i < kChains; ++i)
+          if (x0 + i < M) df::cmac(sum.re[i], sum.im[i], aw[x0 + i], df::c2f(ld2(gx + 2 * ((x0 + i) * M + ib))));
+    }
+    acc = sum.value();
+  } else {
+    for (int m = live ? part : n + 1; m <= n; m += kParts) {
+      const double* aw = a.Aw + ((int64_t)m * MM + ia * M) * 2;  // w_{n,m} Sigma^R(n,m)
+      const double* gx = a.Gx + (((int64_t)m * N + j) * MM) * 2;
+      for (int x = 0; x < M; ++x) cfma4(acc, ld2(aw + 2 * x), ld2(gx + 2 * (x * M + ib)));
+    }
   }
   // Matsubara convolution, split at s = tau_j
   for (int k = live ? part : N; k < N; k += kParts) {
@@ -146,7 +210,7 @@ __global__ void __launch_bounds__(kPartThreads) th_rhs(ThermalArgs a) {
       for (int x = 0; x < M; ++x) cfma(acc, w, ld2(sk + 2 * x), ld2(gm + 2 * (x * M + ib)));
     }
   }
-  if (!reduce_parts(acc) || !live) return;
+  if (!reduce_parts<kParts>(acc) || !live) return;
   const double* gn = a.Gx + (((int64_t)n * N + j) * MM) * 2;
   for (int x = 0; x < M; ++x) cfma(acc, 1.0, ld2(a.eps + 2 * (ia * M + x)), ld2(gn + 2 * (x * M + ib)));
   double* out = a.Fx + (((int64_t)(n % kRing) * N + j) * MM + ab) * 2;
@@ -179,11 +243,19 @@ cudaError_t launch_th_sigma(const ThermalArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_th_mixed(const ThermalArgs& a, cudaStream_t s) {
-  th_mixed<<<(unsigned)(((int64_t)(a.n + 1) * a.M * a.M + 31) / 32), kPartThreads, 0, s>>>(a);
+  const unsigned blocks = (unsigned)(((int64_t)(a.n + 1) * a.M * a.M + 31) / 32);
+  if (a.df)
+    th_mixed<true><<<blocks, kPartThreads, 0, s>>>(a);
+  else
+    th_mixed<false><<<blocks, kPartThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_th_rhs(const ThermalArgs& a, cudaStream_t s) {
-  th_rhs<<<(unsigned)(((int64_t)a.N * a.M * a.M + 31) / 32), kPartThreads, 0, s>>>(a);
+  const unsigned blocks = (unsigned)(((int64_t)a.N * a.M * a.M + 31) / 32);
+  if (a.df)
+    th_rhs<true><<<blocks, 32 * kPartsDf, 0, s>>>(a);
+  else
+    th_rhs<false><<<blocks, kPartThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_th_adams(const ThermalArgs& a, bool corrector, cudaStream_t s) {

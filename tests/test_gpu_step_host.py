@@ -131,3 +131,30 @@ def test_step_host_null_host_pointer_is_einval(kbe):
                                  vp(0))
     assert st == kbe.KBE_EINVAL
     ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["df64", "dense"])
+def test_step_host_other_paths_equal_step(kbe, mode):
+    """A step that contracts with another kernel (KBE_DF64, which waits for
+    the whole upload before the first sweep) or forms another self-energy
+    (dense U, pipelined): kbe_step_host still gives kbe_step's rows."""
+    import torch
+    ctx, _, (L, R, rows, Fr) = _restart(kbe, "chain_m8_n1024", 50, 7)
+    n, M = 49, ctx.M
+    precision = "df64" if mode == "df64" else "fp64"
+    if mode == "dense":
+        ctx.set_interaction(W.coulomb_tensor(M, 7, U=1.0))
+    run = kbe.Run(ctx)
+    _load(kbe, run, L, R, rows, Fr)
+    L_h, R_h, F_h = run.L.cpu().pin_memory(), run.R.cpu().pin_memory(), run.F.cpu().pin_memory()
+    run.step(n, P=2, precision=precision)
+    ctx.sync_status()
+    p = W.tri_index(n, 0)
+    ref_L, ref_R = run.L[p:p + n + 1].cpu().numpy(), run.R[p:p + n + 1].cpu().numpy()
+    run2 = kbe.Run(ctx)
+    out_L = torch.empty((n + 1, M, M), dtype=torch.complex128).pin_memory()
+    out_R = torch.empty_like(out_L).pin_memory()
+    run2.step_host(n, L_h, R_h, F_h, out_L, out_R, P=2, precision=precision)
+    ctx.sync_status()
+    assert np.array_equal(out_L.numpy(), ref_L) and np.array_equal(out_R.numpy(), ref_R)
+    ctx.close()

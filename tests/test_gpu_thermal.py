@@ -85,6 +85,22 @@ def test_thermal_split_precision(kbe):
     ctx.close()
 
 
+@pytest.mark.parametrize("name", ["dimer_pulse", "goe4"])
+def test_thermal_double_float(kbe, name):
+    """KBE_DF64 steps: the history slice and the two long thermal sums
+    (mixed term, KBE3 history term) in double-float (about 2^-47 of the terms'
+    sizes); the runs' rows stay within 1e-11 of the oracle's."""
+    M, h, t, order, Uv, v, pulse, beta, N, kt, GM, rho = _setup(name)
+    Lo, Ro, Go = oracle.run_thermal(t, order, h, Uv, v, pulse, 2, beta, N, kt, GM, 1j * rho, -1j * np.eye(M),
+                                    nthreads=4)
+    ctx, run = _gpu(kbe, name, precision="df64")
+    p = W.tri_size(len(t))
+    assert _rel(run.L[:p].cpu().numpy(), Lo) < 1e-11
+    assert _rel(run.R[:p].cpu().numpy(), Ro) < 1e-11
+    assert _rel(ctx.mixed_rows(len(t)).cpu().numpy(), Go) < 1e-11
+    ctx.close()
+
+
 def test_thermal_errors(kbe):
     import torch
     M, h, t, order, Uv, v, pulse, beta, N, kt, GM, rho = _setup("goe4")
