@@ -593,6 +593,21 @@ def window_bench(kbe, seed, stream):
     dens = lambda u, e: 2.0 * float(win.forward(u, e)[0, 0].imag.cpu())
     fdU = (dens(U + hh, pulse["E0"]) - dens(U - hh, pulse["E0"])) / (2 * hh)
     fdE = (dens(U, pulse["E0"] + hh) - dens(U, pulse["E0"] - hh)) / (2 * hh)
+    # the same window with the double-float contraction (forward and recompute)
+    win_d = kbe.Window(ctx, L, R, F, n_start, nt, h, v, pulse, P=2, precision="df64")
+    Ud = torch.tensor(U, dtype=torch.float64, requires_grad=True)
+    Ed = torch.tensor(pulse["E0"], dtype=torch.float64, requires_grad=True)
+    kbe.window_final_block(Ud, Ed, win_d)  # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    blk_d = kbe.window_final_block(Ud, Ed, win_d)
+    e1.record(stream)
+    (2.0 * blk_d[0, 0].imag).backward()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    fwd_d, bwd_d = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    gUd, gEd = float(Ud.grad.sum()), float(Ed.grad)
     ctx.close()
     # FP64 work: the forward window is 2 slices per step; the reverse sweep recomputes them and
     # runs 2 adjoint slices per step (Sigma-row cotangent, 24 M^3 (n+1)^2 flops each; the
@@ -608,7 +623,10 @@ def window_bench(kbe, seed, stream):
             "backward_tflops": round(bwd_flops / (bwd * 1e-3) / 1e12, 4),
             "backward_frac_of_fp64_peak": round(bwd_flops / (bwd * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
             "dF_dU": gU, "dF_dU_fd": fdU, "rel_err_U": abs(gU - fdU) / abs(fdU),
-            "dF_dE0": gE, "dF_dE0_fd": fdE, "rel_err_E0": abs(gE - fdE) / abs(fdE)}
+            "dF_dE0": gE, "dF_dE0_fd": fdE, "rel_err_E0": abs(gE - fdE) / abs(fdE),
+            "df64": {"forward_ms": round(fwd_d, 2), "backward_ms": round(bwd_d, 2),
+                     "rel_diff_from_fp64_gradient_U": abs(gUd - gU) / abs(gU),
+                     "rel_diff_from_fp64_gradient_E0": abs(gEd - gE) / abs(gE)}}
 
 
 def precision_m32_bench(kbe, seed, stream, steps):

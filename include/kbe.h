@@ -306,8 +306,9 @@ kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, cons
                                         const void* dS_great, void* dL_row, void* dR_row, double* dU,
                                         void* stream);
 
-/* Reverse sweep of one KBE step n taken by kbe_step_rows with precision
- * KBE_FP64 (same P, same store F_rows, j0, n_rows).  On entry L, R hold rows
+/* Reverse sweep of one KBE step n taken by kbe_step_rows with the same
+ * precision (KBE_FP64 or KBE_DF64; KBE_EINVAL otherwise), the same P and
+ * the same store F_rows, j0, n_rows.  On entry L, R hold rows
  * 0..n and F_rows rows j0..n as the forward run left them (later steps do
  * not touch them); the call recomputes step n from rows 0..n-1, keeping
  * its P iterates on the device, then runs the adjoints of the corrector,
@@ -326,8 +327,8 @@ kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, cons
  * of any function of the rows through the window [n_start, n_end).  The
  * first call allocates a reverse-mode workspace of (13 + 2 (P+1)) n_max M^2
  * complex entries held by the context (KBE_ENOMEM if that fails). */
-kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* F_rows, int j0, int n_rows,
-                            void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0,
+kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* F_rows, int j0,
+                            int n_rows, void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0,
                             void* stream);
 
 /* Adaptive history orders (Sec. 3.2).  With K in 1..12, every fixed-point

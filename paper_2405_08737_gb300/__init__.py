@@ -66,7 +66,7 @@ def lib():
         L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_adjoint_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, vp]
         L.kbe_adjoint_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
-        L.kbe_step_adjoint.argtypes = [vp, i, i, vp, vp, vp, i, i, vp, vp, i, vp, vp, vp, vp]
+        L.kbe_step_adjoint.argtypes = [vp, i, i, i, vp, vp, vp, i, i, vp, vp, i, vp, vp, vp, vp]
         L.kbe_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
         L.kbe_batch_destroy.argtypes = [vp]
         L.kbe_batch_last_error.argtypes = [vp]
@@ -321,9 +321,12 @@ class Context:
                                                        self._dev(dSg), self._dev(dL_row), self._dev(dR_row),
                                                        self._real_dev(dU), self._stream(stream)))
 
-    def step_adjoint(self, n, P, L, R, F_rows, j0, dL, dR, row_lo, dF_rows, dU, dE0, stream=None):
-        """Reverse sweep of the FP64 step n taken by step_rows (see kbe.h)."""
-        self._check(lib().kbe_step_adjoint(self._h, n, P, self._dev(L), self._dev(R), self._dev(F_rows), int(j0),
+    def step_adjoint(self, n, P, L, R, F_rows, j0, dL, dR, row_lo, dF_rows, dU, dE0, precision="fp64",
+                     stream=None):
+        """Reverse sweep of the step n taken by step_rows with the same
+        precision ("fp64" or "df64"; see kbe.h)."""
+        self._check(lib().kbe_step_adjoint(self._h, n, P, PRECISIONS[precision], self._dev(L), self._dev(R),
+                                           self._dev(F_rows), int(j0),
                                            int(F_rows.shape[0]), self._dev(dL), self._dev(dR), int(row_lo),
                                            self._dev(dF_rows), self._real_dev(dU), self._real_dev(dE0),
                                            self._stream(stream)))
@@ -507,15 +510,18 @@ class Window:
     Rows 0..n_start-1 of ``L``/``R`` (CUDA triangles of at least n_end
     rows) and the right-hand-side rows j0..n_start-1 in ``F_frozen``
     (mapping j -> [2, j+1, M, M]) are constants.  ``forward`` runs the
-    window through the library's FP64 stepper keeping every right-hand-side
-    row (the checkpoints), and returns the final diagonal block
-    L(n_end-1, n_end-1); ``backward`` sweeps kbe_step_adjoint from the last
-    step down and returns (dU, dE0) for a cotangent of that block.
+    window through the library's stepper (``precision`` "fp64" or "df64")
+    keeping every right-hand-side row (the checkpoints), and returns the
+    final diagonal block L(n_end-1, n_end-1); ``backward`` sweeps
+    kbe_step_adjoint from the last step down and returns (dU, dE0) for a
+    cotangent of that block.
     """
 
-    def __init__(self, ctx, L, R, F_frozen, n_start, n_end, h0, v, pulse, P=2):
+    def __init__(self, ctx, L, R, F_frozen, n_start, n_end, h0, v, pulse, P=2, precision="fp64"):
         import torch
-        self.ctx, self.P = ctx, int(P)
+        if precision not in ("fp64", "df64"):
+            raise ValueError("precision must be 'fp64' or 'df64'")
+        self.ctx, self.P, self.precision = ctx, int(P), precision
         self.n_start, self.n_end = int(n_start), int(n_end)
         self.h0 = np.ascontiguousarray(h0, np.complex128)
         self.v = np.ascontiguousarray(v, np.float64)
@@ -537,7 +543,7 @@ class Window:
         self._set_params(U, E0)
         for n in range(self.n_start, self.n_end):
             self.ctx.step_rows(n, self.L, self.R, self.Sl, self.Sg, self.I, self.F, self.j0, P=self.P,
-                               stream=stream)
+                               precision=self.precision, stream=stream)
         self._state = (U.tobytes(), float(E0))
         p = tri_size(self.n_end) - 1
         return self.L[p].clone()
@@ -559,7 +565,7 @@ class Window:
         dE0 = torch.zeros(1, dtype=torch.float64, device="cuda")
         for n in range(self.n_end - 1, self.n_start - 1, -1):
             self.ctx.step_adjoint(n, self.P, self.L, self.R, self.F, self.j0, dL, dR, lo, dF, dU, dE0,
-                                  stream=stream)
+                                  precision=self.precision, stream=stream)
         return dU, dE0[0]
 
 

@@ -1052,10 +1052,13 @@ kbe_status kbe_adjoint_selfenergy_slice(kbe_ctx* ctx, int n, const void* L, cons
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_adjoint_selfenergy_slice");
 }
 
-kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* F_rows, int j0, int n_rows,
-                            void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0, void* stream) {
+kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* F_rows, int j0,
+                            int n_rows, void* dL, void* dR, int row_lo, void* dF_rows, double* dU, double* dE0,
+                            void* stream) {
   if (!ctx) return KBE_EINVAL;
   ctx->last_launches = 0;
+  if (precision != KBE_FP64 && precision != KBE_DF64)
+    return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: precision must be KBE_FP64 or KBE_DF64");
   if (!aligned16(dL) || !aligned16(dR) || !aligned16(dF_rows) || !dU || !dE0 ||
       (reinterpret_cast<uintptr_t>(dU) & 7u) || (reinterpret_cast<uintptr_t>(dE0) & 7u))
     return fail(ctx, KBE_EINVAL, "kbe_step_adjoint: NULL or misaligned pointer");
@@ -1079,13 +1082,14 @@ kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, void* L, void* R, void* 
   double* Fs = w + 10 * rowd; // [2][n_max][M][M]
   double* epsb = w + 12 * rowd;
   double* save = w + kAdjFixedRows * rowd;
-  st = check_step_call(ctx, n, P, KBE_FP64, L, R, Sl, Sg, Iw, F_rows);
+  st = check_step_call(ctx, n, P, precision, L, R, Sl, Sg, Iw, F_rows);
   if (st != KBE_OK) return st;
   if ((st = check_row_store(ctx, n, j0, n_rows)) != KBE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   int count = 0, nl = 0;
-  // forward again from the stored rows, keeping the iterates of row n
-  st = step_impl(ctx, n, P, KBE_FP64, L, R, Sl, Sg, Iw, F_rows, j0, n_rows, s, save, &count);
+  // forward again from the stored rows, keeping the iterates of row n (the
+  // same kernels as the forward step, so the same iterates)
+  st = step_impl(ctx, n, P, precision, L, R, Sl, Sg, Iw, F_rows, j0, n_rows, s, save, &count);
   if (st != KBE_OK) { ctx->last_launches = count; return st; }
   const size_t row_bytes = (size_t)(n + 1) * MM * 16;
   const int64_t base = tri(row_lo, 0);

@@ -253,3 +253,43 @@ def test_window_gradient_full_size_vs_finite_differences(kbe, pulse_in_window):
     else:
         assert abs(gE - fd) <= 1e-9, (gE, fd)
     ctx.close()
+
+
+def test_window_gradient_double_float(kbe):
+    """A window run with the double-float contraction (KBE_DF64 forward and
+    recompute, FP64 adjoint kernels): its gradient against the oracle's
+    forward-mode derivative (1e-8: the forward differs from the FP64 one by
+    the contraction's ~2^-47 of the terms), and kbe_step_adjoint rejects the
+    split precision."""
+    import torch
+    M, n_t, W_, P = 3, 24, 6, 2
+    n_start = n_t - W_
+    t, order, h, U, v, pulse, L, R, F = _window_case(M, n_t, n_start, 11, True)
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    win = kbe.Window(ctx, _dev(L), _dev(R), F, n_start, n_t, h, v, pulse, P=P, precision="df64")
+    Ut = torch.tensor(U, dtype=torch.float64, requires_grad=True)
+    E0 = torch.tensor(pulse["E0"], dtype=torch.float64, requires_grad=True)
+    blk = kbe.window_final_block(Ut, E0, win)
+    (2.0 * blk[0, 0].imag).backward()
+    ctx.sync_status()
+    gU, gE = Ut.grad.numpy(), float(E0.grad)
+    for a in range(M):
+        e = np.zeros(M)
+        e[a] = 1.0
+        _, Ld = oracle.run_tangent(t, order, h, U, e, v, pulse, 0.0, P, L, R, F, n_start, n_t, nthreads=4)
+        ref = 2.0 * Ld[0, 0].imag
+        assert abs(gU[a] - ref) <= 1e-8 * max(abs(ref), 1e-3), (a, gU[a], ref)
+    _, Ld = oracle.run_tangent(t, order, h, U, np.zeros(M), v, pulse, 1.0, P, L, R, F, n_start, n_t, nthreads=4)
+    ref = 2.0 * Ld[0, 0].imag
+    assert abs(gE - ref) <= 1e-8 * max(abs(ref), 1e-3), (gE, ref)
+    with pytest.raises(ValueError):
+        kbe.Window(ctx, _dev(L), _dev(R), F, n_start, n_t, h, v, pulse, P=P, precision="split")
+    dL = torch.zeros((W.tri_size(n_t), M, M), dtype=torch.complex128, device="cuda")
+    dU = torch.zeros(M, dtype=torch.float64, device="cuda")
+    dE = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(kbe.KBEError) as err:
+        ctx.step_adjoint(n_t - 1, P, win.L, win.R, win.F, win.j0, dL, dL.clone(), 0, torch.zeros_like(win.F), dU, dE,
+                         precision="split")
+    assert err.value.status == kbe.KBE_EINVAL
+    ctx.close()
