@@ -258,6 +258,25 @@ def cpu_baseline(run, t, order, h, U, v, pulse, n, M, P, gpu_rows):
     return tflops, threads, sample, errs, dt
 
 
+def cpu_thread_scaling(run, t, order, U, n_s=255):
+    """The oracle's history slice of row n_s (bounded sample) on one thread
+    and on all host threads: seconds and FP64 GFLOP/s each."""
+    import oracle
+    threads = oracle.threads_available()
+    L = run.L[: W_tri(n_s + 1)].cpu().numpy()
+    R = run.R[: W_tri(n_s + 1)].cpu().numpy()
+    Sl, Sg = oracle.sigma_row(oracle.local_U4(U), n_s, L, R)
+    M = L.shape[-1]
+    out = {"sample": "oracle history slice of row n=%d, M=%d" % (n_s, M), "threads": threads}
+    for key, nt in (("one_thread", 1), ("all_threads", threads)):
+        t0 = time.perf_counter()
+        oracle.history_slice(t, order, n_s, L, R, Sl, Sg, nthreads=nt)
+        dt = time.perf_counter() - t0
+        out[key + "_s"] = round(dt, 3)
+        out[key + "_gflops"] = round(slice_flops(M, n_s) / dt / 1e9, 3)
+    return out
+
+
 def batch_bench(kbe, seed, P, stream, rank=0, world=1):
     """The batching form on 64 independent chains (M in {4,8,12,16,24},
     N_t in [256,1536], U in [0.5,3]): one batched KBE step advances every
@@ -795,6 +814,7 @@ def main():
         tf, threads, sample, errs, _ = cpu_baseline(run, t, order, h, U, v, pulse, n, M, args.P, rows)
         line["cpu_baseline"] = {"value": round(tf, 6), "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                                 "sample": sample}
+        line["cpu_thread_scaling"] = cpu_thread_scaling(run, t, order, U)
         line["error_vs_oracle"] = dict(errs["fp64"], where="new row n and last history slice of the timed KBE "
                                                            "step, max-norm relative")
         line["precision_form"]["error_vs_oracle"] = errs["split"]
