@@ -16,6 +16,7 @@
 //   Rbar(r,q) += A1[r]^+ Ibar^>(q) - [q<r] Ibar^>(r)^+ A1[q] + [q<r] w_{r,q} sum_s Ibar^s(r)^+ S^s[q].
 // (R(r,r) = -i*1 is a constant of the method and carries no cotangent.)
 
+#include "dfloat.cuh"
 #include "kbe_internal.h"
 
 namespace kbe {
@@ -131,6 +132,72 @@ __global__ void __launch_bounds__(256) adj_hist_small(int M, int n, int chunk_le
   stz(out, A);
   stz(out + srow * 2, Bl);
   stz(out + 2 * srow * 2, Bg);
+}
+
+// The same partial sums in double-float on the FP32 pipe (the reverse sweep
+// of KBE_DF64 steps): the cotangent rows Ibar^<, Ibar^> and Js come as
+// double-float rows (Ibf [2][n+1][MM], Jsf [n+1][MM]), the history entries
+// are converted where they are read, every sum is a compensated pair.
+__global__ void __launch_bounds__(256) adj_prep_df(int64_t n2, const double* __restrict__ Ib,
+                                                   const double* __restrict__ Js, float4* __restrict__ Ibf,
+                                                   float4* __restrict__ Jsf, int64_t srow) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n2) return;
+  Ibf[e] = df::c2f(reinterpret_cast<const double2*>(Ib)[e]);
+  if (e < srow) Jsf[e] = df::c2f(reinterpret_cast<const double2*>(Js)[e]);
+}
+
+__global__ void __launch_bounds__(256) adj_hist_small_df(int M, int n, int chunk_len, const double* __restrict__ L,
+                                                         const double* __restrict__ R,
+                                                         const float4* __restrict__ Ibf,
+                                                         const float4* __restrict__ Jsf, WeightsView w,
+                                                         double* __restrict__ part) {
+  const int MM = M * M;
+  const int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (lin >= (int64_t)(n + 1) * MM) return;
+  const int m = (int)(lin / MM), ax = (int)(lin - (int64_t)m * MM);
+  const int a = ax / M, x = ax - a * M;
+  const int c0 = blockIdx.y * chunk_len, c1 = min(n + 1, c0 + chunk_len);
+  const int64_t srow = (int64_t)(n + 1) * MM;
+  const double2* L2 = reinterpret_cast<const double2*>(L);
+  const double2* R2 = reinterpret_cast<const double2*>(R);
+  df::Acc Ar{0.f, 0.f}, Ai{0.f, 0.f}, Blr{0.f, 0.f}, Bli{0.f, 0.f}, Bgr{0.f, 0.f}, Bgi{0.f, 0.f};
+  for (int c = c0; c < c1; ++c) {
+    const float4* il = Ibf + (int64_t)c * MM + a * M;
+    const float4* ig = Ibf + srow + (int64_t)c * MM + a * M;
+    const float4* is = Jsf + (int64_t)c * MM + a * M;
+    if (c <= m) {  // conj(G(m,c)[x][b]): conj(L), conj(R) of block (m,c) row x
+      const int64_t blk = tri(m, c) * MM + x * M;
+      for (int b = 0; b < M; ++b) {
+        df::cmac(Ar, Ai, is[b], df::cconj(df::c2f(L2[blk + b])));
+        df::cmac(Ar, Ai, ig[b], df::cconj(df::c2f(R2[blk + b])));
+      }
+    } else {       // -X(c,m)[b][x]
+      const int64_t blk = tri(c, m) * MM;
+      for (int b = 0; b < M; ++b) {
+        df::cmac(Ar, Ai, is[b], df::cneg(df::c2f(L2[blk + b * M + x])));
+        df::cmac(Ar, Ai, ig[b], df::cneg(df::c2f(R2[blk + b * M + x])));
+      }
+    }
+    if (c >= m) {  // term 2: w_{c,m} sum_b Ibar^s(c)[a][b] R(c,m)[b][x]
+      const df::F2 wf = df::from_double_fast(w.at(c, m));
+      const int64_t blk = tri(c, m) * MM;
+      df::Acc tlr{0.f, 0.f}, tli{0.f, 0.f}, tgr{0.f, 0.f}, tgi{0.f, 0.f};
+      for (int b = 0; b < M; ++b) {
+        const float4 r = df::c2f(R2[blk + b * M + x]);
+        df::cmac(tlr, tli, il[b], r);
+        df::cmac(tgr, tgi, ig[b], r);
+      }
+      df::acc_prod(Blr, wf.hi, wf.lo, tlr.s, tlr.c);
+      df::acc_prod(Bli, wf.hi, wf.lo, tli.s, tli.c);
+      df::acc_prod(Bgr, wf.hi, wf.lo, tgr.s, tgr.c);
+      df::acc_prod(Bgi, wf.hi, wf.lo, tgi.s, tgi.c);
+    }
+  }
+  double* out = part + ((int64_t)blockIdx.y * 3 * srow + lin) * 2;
+  stz(out, Cz{df::acc_value(Ar), df::acc_value(Ai)});
+  stz(out + srow * 2, Cz{df::acc_value(Blr), df::acc_value(Bli)});
+  stz(out + 2 * srow * 2, Cz{df::acc_value(Bgr), df::acc_value(Bgi)});
 }
 
 // Sl_bar, Sg_bar from the ordered sum of the chunk partials.
@@ -422,15 +489,29 @@ cudaError_t launch_adjoint_history(const AdjHistArgs& h, cudaStream_t s, int* la
   int64_t want = (152LL * 2048 + srow - 1) / srow;
   int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
   if (nchunk > n + 1) nchunk = n + 1;
-  // the workspace holds the chunk partials [nchunk][3][srow], then the rows Js and A1
-  while (nchunk > 1 && (size_t)(nchunk * 3 + 2) * srow * 16 > h.work_bytes) --nchunk;
-  if ((size_t)(nchunk * 3 + 2) * srow * 16 > h.work_bytes) return cudaErrorInvalidValue;
+  // the workspace holds the chunk partials [nchunk][3][srow], then the rows Js
+  // and A1 (and, for the double-float sums, Ibar^<, Ibar^> and Js as
+  // double-float rows)
+  const int extra = h.df ? 5 : 2;
+  while (nchunk > 1 && (size_t)(nchunk * 3 + extra) * srow * 16 > h.work_bytes) --nchunk;
+  if ((size_t)(nchunk * 3 + extra) * srow * 16 > h.work_bytes) return cudaErrorInvalidValue;
   const int chunk_len = (n + 1 + nchunk - 1) / nchunk;
   nchunk = (n + 1 + chunk_len - 1) / chunk_len;
   double* Js = h.work + (size_t)nchunk * 3 * srow * 2;
   double* A1 = Js + srow * 2;
   adj_prep<<<blocks_for(srow), 256, 0, s>>>(M, n, h.Ib, h.Sl, h.Sg, h.w, Js, A1);
-  adj_hist_small<<<dim3(blocks_for(srow), nchunk), 256, 0, s>>>(M, n, chunk_len, h.L, h.R, h.Ib, Js, h.w, h.work);
+  int nl = 3;
+  if (h.df) {
+    float4* Ibf = reinterpret_cast<float4*>(A1 + srow * 2);
+    float4* Jsf = Ibf + 2 * srow;
+    adj_prep_df<<<blocks_for(2 * srow), 256, 0, s>>>(2 * srow, h.Ib, Js, Ibf, Jsf, srow);
+    adj_hist_small_df<<<dim3(blocks_for(srow), nchunk), 256, 0, s>>>(M, n, chunk_len, h.L, h.R, Ibf, Jsf, h.w,
+                                                                     h.work);
+    ++nl;
+  } else {
+    adj_hist_small<<<dim3(blocks_for(srow), nchunk), 256, 0, s>>>(M, n, chunk_len, h.L, h.R, h.Ib, Js, h.w,
+                                                                  h.work);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adj_hist_small_reduce<<<blocks_for(srow), 256, 0, s>>>(M, n, nchunk, h.work, h.w, h.dSl, h.dSg);
@@ -438,7 +519,7 @@ cudaError_t launch_adjoint_history(const AdjHistArgs& h, cudaStream_t s, int* la
   const int64_t rows_total = (tri(n + 1, 0) - tri(h.row_lo, 0)) * MM;
   adj_hist_rows<<<blocks_for(rows_total), 256, 0, s>>>(M, n, h.row_lo, Js, A1, h.Sl, h.Sg, h.Ib, h.w, h.dL, h.dR,
                                                        h.gL, h.gR);
-  *launches = 4;
+  *launches = nl + 1;
   return cudaGetLastError();
 }
 

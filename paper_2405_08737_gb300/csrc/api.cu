@@ -1151,6 +1151,7 @@ kbe_status kbe_step_adjoint(kbe_ctx* ctx, int n, int P, int precision, void* L, 
     // history slice -> Sigma row, rows row_lo..n-1, row n
     AdjHistArgs h{ctx->M, n, row_lo, (const double*)L, (const double*)R, Sl, Sg, Ib, weights_view(ctx), dSl, dSg,
                   (double*)dL, (double*)dR, gL, gR, ctx->d_part, ctx->part_bytes};
+    h.df = precision == KBE_DF64;  // the step's own arithmetic for its longest reverse sum
     e = launch_adjoint_history(h, s, &nl);
     count += nl;
     if ((st = check("kbe_step_adjoint: history slice")) != KBE_OK) return st;

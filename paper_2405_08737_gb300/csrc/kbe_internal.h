@@ -348,6 +348,7 @@ struct AdjHistArgs {
   double* gR;
   double* work;
   size_t work_bytes;
+  int df = 0;           // 1: the Sigma-row cotangent sums in double-float (KBE_DF64 steps)
 };
 cudaError_t launch_adjoint_history(const AdjHistArgs& a, cudaStream_t s, int* launches);
 
