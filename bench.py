@@ -353,7 +353,7 @@ def batch_bench(kbe, seed, P, stream, rank=0, world=1):
            "plain_fp64_launches": plain_launches,
            "autotune": {"block": blk, "item_work_log2": work, "history_ms_at_quarter_rows": round(tune_ms, 3),
                         "seconds": round(tune_s, 2)}}
-    for prec in ("fp64", "split"):
+    for prec in ("fp64", "split", "df64"):
         batch.step(rows, P=P, precision=prec, stream=stream)  # warm-up (graph capture)
         torch.cuda.synchronize()
         e0.record(stream)

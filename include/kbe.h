@@ -461,7 +461,9 @@ kbe_status kbe_batch_bind(kbe_batch* b, int i, void* L, void* R, void* S_less, v
  * allocation fails, the contraction converts its operands itself (slower,
  * same results).  Results agree
  * with kbe_step to rounding (the history sum is chunked differently).
- * precision: KBE_FP64 or KBE_SPLIT_BF16 (KBE_DF64 is KBE_EINVAL here). */
+ * precision: KBE_FP64, KBE_SPLIT_BF16 or KBE_DF64 (each system's
+ * double-float slice in its own context's workspace, graph re-captured
+ * when the rows change, like KBE_SPLIT_BF16). */
 kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, void* stream);
 
 /* Tile policy of the persistent FP64 history kernel: `block` output entries

@@ -374,6 +374,18 @@ cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_hos
         batch_history<256><<<b->hist_blocks[1], 256, 0, s>>>(d);
       batch_rows<kOpReduce><<<kElemBlocks, 256, 0, s>>>(d);
       nl += 3;
+    } else if (precision == KBE_DF64) {  // each system's double-float slice in its context's workspace
+      for (int i = 0; i < b->n_sys && e == cudaSuccess; ++i) {
+        const int n = rows_host[i];
+        const kbe_ctx* c = b->ctx[i];
+        if (n < 1 || n >= c->grid.n_t) continue;
+        const BatchSys& y = b->sys[i];
+        HistoryArgs a{y.M, n, y.L, y.R, y.Sl, y.Sg, WeightsView{y.wbar, y.band, y.band_w}, y.I, c->d_part,
+                      c->part_bytes, d.status};
+        int k = 0;
+        e = launch_history_df(a, s, &k);
+        nl += k;
+      }
     } else {
       for (int i = 0; i < b->n_sys && e == cudaSuccess; ++i) {
         const int n = rows_host[i];
@@ -581,7 +593,8 @@ kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, v
   b->last_launches = 0;
   if (!rows) return bfail(b, KBE_EINVAL, "kbe_batch_step: rows is NULL");
   if (P < 1 || P > 16) return bfail(b, KBE_EINVAL, "kbe_batch_step: P outside [1, 16]");
-  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16) return bfail(b, KBE_EINVAL, "kbe_batch_step: unknown precision");
+  if (precision != KBE_FP64 && precision != KBE_SPLIT_BF16 && precision != KBE_DF64)
+    return bfail(b, KBE_EINVAL, "kbe_batch_step: unknown precision");
   for (int i = 0; i < b->n_sys; ++i) {
     const kbe_ctx* c = b->ctx[i];
     if (rows[i] >= c->grid.n_t) return bfail(b, KBE_ERANGE, "kbe_batch_step: row beyond a system's grid");

@@ -364,8 +364,11 @@ cudaError_t launch_history_df(const HistoryArgs& a, cudaStream_t s, int* launche
   TileGeom tg;
   size_t smem = 0;
   const bool tiled = tile_geom(M, n, kTileSmem, &tg, &smem);
-  if (tiled && (e = cudaFuncSetAttribute(history_df_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTileSmem)) != cudaSuccess) {
+  // (no attribute call at or below the default 48 KB, so that the launch can
+  // be recorded in a graph capture)
+  if (tiled && kTileSmem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(history_df_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTileSmem)) != cudaSuccess) {
     *launches = nl;
     return e;
   }

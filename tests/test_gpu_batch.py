@@ -131,6 +131,27 @@ def test_batch_split_precision(kbe):
     batch.close()
 
 
+def test_batch_double_float(kbe):
+    """Batched KBE_DF64 steps run each system's double-float slice in the
+    graph: whole runs match the single-system KBE_DF64 stepper (1e-13) and
+    the oracle (1e-11)."""
+    runs = _runs(kbe)
+    batch = kbe.Batch(runs)
+    _advance(batch, SYSTEMS, precision="df64")
+    single = _runs(kbe)
+    for run, s in zip(single, SYSTEMS):
+        for n in range(1, s[1]):
+            run.step(n, P=2, precision="df64")
+        run.ctx.sync_status()
+    for a, b, s in zip(runs, single, SYSTEMS):
+        p = W.tri_size(s[1])
+        La = a.L[:p].cpu().numpy()
+        assert _rel(La, b.L[:p].cpu().numpy()) < 1e-13, s
+        Lo, _ = _oracle(*s)
+        assert _rel(La, Lo) < 1e-11, (s, _rel(La, Lo))
+    batch.close()
+
+
 def test_batch_inactive_systems_untouched_and_graph_reused(kbe):
     import torch
     runs = _runs(kbe)
