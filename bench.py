@@ -468,7 +468,7 @@ def controller_bench(kbe, seed, stream, t_end=8.0, n_max=2048):
     out = {"workload": "%s model, t = 0 .. %.1f, grid chosen by the run (atol = 1e-2 rtol)" % (WORKLOAD, t_end),
            "runs": []}
     finals = {}
-    for rtol, precision in ((1e-6, "fp64"), (1e-8, "fp64"), (1e-6, "split")):
+    for rtol, precision in ((1e-6, "fp64"), (1e-8, "fp64"), (1e-6, "split"), (1e-8, "df64")):
         ctx = kbe.Context(M, n_max)
         ctx.set_model(h, U, v, pulse)
         torch.cuda.synchronize()
@@ -494,6 +494,7 @@ def controller_bench(kbe, seed, stream, t_end=8.0, n_max=2048):
     ref = finals[(1e-8, "fp64")]
     out["final_density_diff_rtol1e-6_vs_1e-8"] = float(np.abs(finals[(1e-6, "fp64")] - ref).max())
     out["final_density_diff_split_vs_fp64_1e-8"] = float(np.abs(finals[(1e-6, "split")] - ref).max())
+    out["final_density_diff_df64_vs_fp64_at_1e-8"] = float(np.abs(finals[(1e-8, "df64")] - ref).max())
     return out
 
 

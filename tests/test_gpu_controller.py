@@ -138,6 +138,25 @@ def test_split_precision_controlled_run(kbe):
     ctx.close()
 
 
+def test_double_float_controlled_run(kbe):
+    """With the double-float contraction (its rounding about 2^6 times
+    FP64's) the controller takes the oracle's decisions: the same step count,
+    statistics and orders, the accepted points within 64 times the FP64
+    drift bound, and the oracle replaying the device's points and orders
+    gives the same rows to 1e-11."""
+    o, g, ctx = _both(kbe, "goe3", precision="df64")
+    M, kind, U, dense, pulse_on, rtol, t_end, K_sel = CASES["goe3"]
+    assert g["status"] == kbe.KBE_OK and g["n"] == o["n"] and g["stats"] == o["stats"]
+    assert np.array_equal(g["q"], o["q"])
+    assert np.abs(g["t"] - o["t"]).max() <= 64 * _t_tol(o["n"], rtol) * o["t"][-1]
+    h, Uv, U4, v, pulse = _model(M, kind, U, dense, pulse_on)
+    r = oracle.run_controlled(h, Uv, v, pulse, W.half_filled_rho(h), rtol, rtol * 1e-2, 0.01, t_end, 400,
+                              K_sel=K_sel, replay=(g["t"], g["q"]))
+    p = W.tri_size(g["n"])
+    assert _rel(g["L"][:p].cpu().numpy(), r["L"]) < 1e-11 and _rel(g["R"][:p].cpu().numpy(), r["R"]) < 1e-11
+    ctx.close()
+
+
 def test_controlled_run_errors_and_full_storage(kbe):
     M = 2
     h = W.chain_h(M)
