@@ -20,6 +20,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -87,13 +88,17 @@ def dist_setup(args):
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples during the timed region, written to the CSV file
+    named by KBE_CLOCKS_CSV (a temporary file when unset)."""
 
     def __init__(self, idx):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = os.environ.get("KBE_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                     "kbe_clocks_%d.csv" % os.getpid())
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            d = os.path.dirname(self.path)
+            if d:
+                os.makedirs(d, exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(idx),
