@@ -669,6 +669,8 @@ def precision_m32_bench(kbe, seed, stream, steps):
     ref = step_rows(run, n)
     ms_s, launches_s, kc_s, kms_s = time_steps(ctx, run, n, P, steps, 2, stream, "split")
     got = step_rows(run, n)
+    ms_d, _, _, _ = time_steps(ctx, run, n, P, 1, 1, stream, "df64")
+    got_d = step_rows(run, n)
     ctx.sync_status()
     ctx.close()
     del run
@@ -677,6 +679,10 @@ def precision_m32_bench(kbe, seed, stream, steps):
     for name, a, b in (("new_row", np.concatenate([got[0], got[1]]), np.concatenate([ref[0], ref[1]])),
                        ("slice", got[2], ref[2])):
         dev[name] = float(np.abs(a - b).max() / np.abs(b).max())
+    dev_d = {}
+    for name, a, b in (("new_row", np.concatenate([got_d[0], got_d[1]]), np.concatenate([ref[0], ref[1]])),
+                       ("slice", got_d[2], ref[2])):
+        dev_d[name] = float(np.abs(a - b).max() / np.abs(b).max())
     ct = 128 // M
     cpt = ((n + 1) * M + 15) // 16
     plane_bytes = ((n + 1 + ct - 1) // ct) * cpt * ((M + 7) // 8) * 66560
@@ -693,6 +699,8 @@ def precision_m32_bench(kbe, seed, stream, steps):
                                   "achieved_gbs": round(plane_bytes / (k_avg * 1e-3) / 1e9, 1), "peak_gbs": hbm,
                                   "frac": round(plane_bytes / (k_avg * 1e-3) / 1e9 / hbm, 4)},
             "split_deviation_from_fp64_step": dev, "stated_error_bound": 1e-8,
+            "df64_ms_per_step": round(ms_d, 3), "df64_speedup_vs_fp64_step": round(ms / ms_d, 3),
+            "df64_deviation_from_fp64_step": dev_d,
             "gpu_launches": {"fp64": launches, "split": launches_s}}
 
 
