@@ -383,6 +383,39 @@ def batch_bench(kbe, seed, P, stream, rank=0, world=1):
     return out
 
 
+def slice_sweep(kbe, ctx, run, M, stream, rows=(255, 511, 767, 1023), reps=3):
+    """The history slice alone at several rows n of the main workload's
+    history, each precision's contraction kernel timed by the library's
+    events: FP64 against the FP64 peak, split against HBM (its digit planes),
+    double-float as FP64-equivalent TFLOP/s."""
+    import torch
+    out = {}
+    I = torch.empty_like(run.I)
+    hbm = hbm_peak_gbs()
+    for n in rows:
+        ctx.selfenergy_slice(n, run.L, run.R, run.Sl, run.Sg, stream=stream)
+        res = {}
+        for prec in ("fp64", "split", "df64"):
+            ctx.history_slice(n, run.L, run.R, run.Sl, run.Sg, I, precision=prec, stream=stream)  # warm-up
+            torch.cuda.synchronize()
+            ctx.set_profiling(True)
+            for _ in range(reps):
+                ctx.history_slice(n, run.L, run.R, run.Sl, run.Sg, I, precision=prec, stream=stream)
+            torch.cuda.synchronize()
+            k, ms = ctx.read_profiling()
+            ctx.set_profiling(False)
+            res[prec + "_contraction_ms"] = round(ms / max(k, 1), 4)
+        f = slice_flops(M, n)
+        ct = 128 // M
+        planes = ((n + 1 + ct - 1) // ct) * (((n + 1) * M + 15) // 16) * ((M + 7) // 8) * 66560
+        res["fp64_frac_of_fp64_peak"] = round(f / (res["fp64_contraction_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4)
+        res["split_frac_of_hbm"] = round(planes / (res["split_contraction_ms"] * 1e-3) / 1e9 / hbm, 4)
+        res["df64_tflops_fp64_equivalent"] = round(f / (res["df64_contraction_ms"] * 1e-3) / 1e12, 4)
+        out[str(n)] = res
+    ctx.sync_status()
+    return out
+
+
 def sigma_bench(kbe, ctx, run, n_t, stream, reps=10):
     """The self-energy kernel over the whole stored triangle (kbe_selfenergy_all):
     32 B read and 32 B written per complex entry, 2.15 GB for the chain
@@ -835,6 +868,8 @@ def main():
         line["df64_form"]["error_vs_oracle"] = errs["df64"]
     if rank == 0 and not args.no_selfenergy:
         line["selfenergy"] = sigma_bench(kbe, ctx, run, n + 1, stream)
+        line["slice_sweep"] = slice_sweep(kbe, ctx, run, M, stream,
+                                          rows=tuple(r for r in (255, 511, 767, 1023) if r <= n))
     if rank == 0 and not args.no_window:
         line["differentiation_form"] = window_bench(kbe, args.seed, stream)
     if rank == 0 and not args.no_adaptive:
