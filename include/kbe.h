@@ -211,6 +211,21 @@ kbe_status kbe_selfenergy_all(kbe_ctx* ctx, int n_rows, const void* L, const voi
 kbe_status kbe_history_slice(kbe_ctx* ctx, int n, int precision, const void* L, const void* R,
                              const void* S_less, const void* S_great, void* I_out, void* stream);
 
+/* One device's share of a history slice split across devices (the slice
+ * of Eq. KBE2 by bands of stored rows): the contributions of the stored
+ * blocks (r, c), row_lo <= r < row_hi, r <= n, of L and R to I(n, c) for
+ * every c = 0..n -- term 1 of column c through G(r, c) (history point
+ * m = r), term 1 of column r through G(c, r) = -G(r, c)^+ (m = c < r) and
+ * term 2 of column r through G^A(c, r) = R(r, c)^+ (m = c).  I_out
+ * [2][n+1][M][M] device, written with the band's partial sums; the sum of
+ * the partials of bands that partition the rows 0..n is the slice of
+ * kbe_history_slice (KBE_FP64) to rounding.  A device needs only its own
+ * rows of L and R, row n (for its Sigma row) and the Sigma row itself.
+ * KBE_EINVAL for row_lo < 0, row_hi < row_lo or a bad pointer; otherwise
+ * as kbe_history_slice. */
+kbe_status kbe_history_slice_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, const void* L, const void* R,
+                                  const void* S_less, const void* S_great, void* I_out, void* stream);
+
 /* ----------------------------------------------------------- stepper --- */
 
 /* Right-hand-side row j of Eq. (KBE2), the t-derivative along row j:

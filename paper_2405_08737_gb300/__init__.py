@@ -64,6 +64,7 @@ def lib():
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
         L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_history_slice_band.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp]
         L.kbe_adjoint_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, vp]
         L.kbe_adjoint_selfenergy_slice.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_adjoint.argtypes = [vp, i, i, i, vp, vp, vp, i, i, vp, vp, i, vp, vp, vp, vp]
@@ -274,6 +275,12 @@ class Context:
     def history_slice(self, n, L, R, Sl, Sg, out, precision="fp64", stream=None):
         self._check(lib().kbe_history_slice(self._h, n, PRECISIONS[precision], self._dev(L), self._dev(R),
                                             self._dev(Sl), self._dev(Sg), self._dev(out), self._stream(stream)))
+
+    def history_slice_band(self, n, row_lo, row_hi, L, R, Sl, Sg, out, stream=None):
+        """One device's share of the FP64 slice of row n: the contributions
+        of the stored rows [row_lo, row_hi) (kbe_history_slice_band)."""
+        self._check(lib().kbe_history_slice_band(self._h, n, int(row_lo), int(row_hi), self._dev(L), self._dev(R),
+                                                 self._dev(Sl), self._dev(Sg), self._dev(out), self._stream(stream)))
 
     def rhs_row(self, j, L, R, Sl, Sg, I_work, F_ring, precision="fp64", stream=None):
         self._check(lib().kbe_rhs_row(self._h, j, PRECISIONS[precision], self._dev(L), self._dev(R),

@@ -870,6 +870,26 @@ kbe_status kbe_history_slice(kbe_ctx* ctx, int n, int precision, const void* L, 
   return st;
 }
 
+kbe_status kbe_history_slice_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, const void* L, const void* R,
+                                  const void* Sl, const void* Sg, void* I_out, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  kbe_status st = check_row_call(ctx, n);
+  if (st != KBE_OK) return st;
+  if (row_lo < 0 || row_hi < row_lo) return fail(ctx, KBE_EINVAL, "kbe_history_slice_band: need 0 <= row_lo <= row_hi");
+  if (!aligned16(L) || !aligned16(R) || !aligned16(Sl) || !aligned16(Sg) || !aligned16(I_out))
+    return fail(ctx, KBE_EINVAL, "kbe_history_slice_band: NULL or misaligned pointer");
+  if ((st = use_device(ctx)) != KBE_OK) return st;
+  HistoryArgs a{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
+                weights_view(ctx), (double*)I_out, ctx->d_part, ctx->part_bytes, ctx->d_status};
+  a.band_lo = row_lo;
+  a.band_hi = row_hi;
+  int nl = 0;
+  cudaError_t e = launch_history_f64(a, (cudaStream_t)stream, &nl);
+  ctx->last_launches = nl;
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_history_slice_band: launch");
+}
+
 kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const void* R, void* Sl, void* Sg,
                        void* I_work, void* F_ring, void* stream) {
   if (!ctx) return KBE_EINVAL;

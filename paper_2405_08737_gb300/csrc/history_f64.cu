@@ -119,6 +119,8 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
   if (e != cudaSuccess) { *launches = nl; return e; }
   PartialArgs p{M, MM, n, chunk_len, a.L, a.R, a.Sl, a.Sg, A1, Bl, Bg, a.w,
                 nchunk == 1 ? a.out : partials};
+  p.band_lo = a.band_lo;
+  p.band_hi = a.band_hi;
   if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
   for (int k = 0; k < nranges; ++k) {
     const int lo = std::max(0, c_lo[k]), hi = std::min(n + 1, c_hi[k]);

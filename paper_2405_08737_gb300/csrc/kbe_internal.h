@@ -180,6 +180,8 @@ struct HistoryArgs {
   int* status;
   cudaEvent_t ev_begin = nullptr;  // optional timing of the contraction kernel
   cudaEvent_t ev_end = nullptr;
+  int band_lo = 0;                 // contributions of the stored rows [band_lo, band_hi) only
+  int band_hi = 0x7fffffff;
 };
 // FP64 history slice; sets *launches to the number of kernels enqueued.
 cudaError_t launch_history_f64(const HistoryArgs& a, cudaStream_t s, int* launches);

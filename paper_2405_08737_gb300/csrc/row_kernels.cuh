@@ -126,6 +126,10 @@ struct PartialArgs {
   const double* Bg;
   WeightsView w;
   double* dst;        // partials [chunk][2][n+1][MM] or the output when one chunk
+  // stored rows whose blocks contribute (a band of the triangle, one rank's
+  // share of a slice split across devices); all rows by default
+  int band_lo = 0;
+  int band_hi = 0x7fffffff;
 };
 
 // Output entry lin = (c, a, b) of the history slice over history points
@@ -140,9 +144,12 @@ __device__ __forceinline__ void history_partial_entry(const PartialArgs& p, int6
 
   Cd P{0, 0}, Q{0, 0}, Tl{0, 0}, Tg{0, 0};  // A1 G^<, A1 G^R, term-2 <, term-2 >
   const int band_lo = c - p.w.band_w + 1;    // m >= band_lo: w_{c,m} from the band
+  // blocks of row c (m <= c) count when row c is in the stored-row band;
+  // blocks of rows m > c when row m is
+  const bool row_c = c >= p.band_lo && c < p.band_hi;
 
   // region m < c: stored block (c, m), read transposed
-  const int mA1 = min(m1, c);
+  const int mA1 = row_c ? min(m1, c) : m0;
   for (int m = m0; m < mA1; ++m) {
     const double* lc = p.L + (tri(c, m) * MM + b * M) * 2;
     const double* rc = p.R + (tri(c, m) * MM + b * M) * 2;
@@ -176,7 +183,7 @@ __device__ __forceinline__ void history_partial_entry(const PartialArgs& p, int6
     }
   }
   // diagonal m == c
-  if (c >= m0 && c < m1) {
+  if (row_c && c >= m0 && c < m1) {
     const int m = c;
     const double wcc = p.w.at(c, c);
     const double* lb = p.L + tri(c, c) * MM * 2;
@@ -196,7 +203,7 @@ __device__ __forceinline__ void history_partial_entry(const PartialArgs& p, int6
     }
   }
   // region m > c: stored block (m, c), read directly
-  for (int m = max(m0, c + 1); m < m1; ++m) {
+  for (int m = max(max(m0, c + 1), p.band_lo); m < min(m1, p.band_hi); ++m) {
     const double* lm = p.L + (tri(m, c) * MM + b) * 2;
     const double* rm = p.R + (tri(m, c) * MM + b) * 2;
     const double* a1 = p.A1 + ((int64_t)m * MM + a * M) * 2;

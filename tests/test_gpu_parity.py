@@ -292,3 +292,38 @@ def test_errors_are_reported_not_raised_on_device(kbe):
     ctx.selfenergy_slice(3, Ld, Rd, Sl, Sg)  # the context stays usable
     ctx.history_slice(3, Ld, Rd, Sl, Sg, out)
     ctx.sync_status()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5])
+def test_row_band_partials_sum_to_the_slice(kbe, world):
+    """The per-device share of the one-system split (kbe_history_slice_band):
+    the partial slices of the row bands of parallel.row_bands, computed one
+    after another on this GPU and summed (the all-reduce of the plan), give
+    kbe_history_slice's slice (1e-14) and the oracle's (1e-12); an empty band
+    contributes nothing."""
+    import torch
+    from paper_2405_08737_gb300 import parallel
+    M, n_t = 5, 45
+    t, order, h, rho0, U, L, R = _case(M, n_t, 17, "free")
+    ctx = _ctx(kbe, M, n_t, t, order, h, U)
+    Ld, Rd = _dev(L), _dev(R)
+    n = n_t - 1
+    Sl, Sg = oracle.sigma_row(oracle.local_U4(U), n, L, R)
+    Sld, Sgd = _dev(Sl), _dev(Sg)
+    full = torch.zeros((2, n + 1, M, M), dtype=torch.complex128, device="cuda")
+    ctx.history_slice(n, Ld, Rd, Sld, Sgd, full)
+    total = torch.zeros_like(full)
+    part = torch.empty_like(full)
+    for lo, hi in parallel.row_bands(n + 1, world):
+        ctx.history_slice_band(n, lo, hi, Ld, Rd, Sld, Sgd, part)
+        total += part
+    ctx.history_slice_band(n, 7, 7, Ld, Rd, Sld, Sgd, part)
+    ctx.sync_status()
+    assert not part.abs().any()
+    ref = oracle.history_slice(t, order, n, L, R, Sl, Sg, nthreads=8)
+    f, tot = full.cpu().numpy(), total.cpu().numpy()
+    assert _rel(tot, f) < 1e-14 and _rel(tot, ref) < TOL
+    with pytest.raises(kbe.KBEError) as e:
+        ctx.history_slice_band(n, 5, 4, Ld, Rd, Sld, Sgd, part)
+    assert e.value.status == kbe.KBE_EINVAL
+    ctx.close()
