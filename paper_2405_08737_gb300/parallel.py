@@ -4,10 +4,13 @@ The systems of a batched step are independent, so N GPUs share a batch by
 taking disjoint sets of systems: no collective touches the data path, and
 only the step time is reduced (the maximum over ranks).
 
-One system can be split too (not run by this build, whose calls each use one
-GPU; the host logic below is tested with gloo ranks on the CPU): the stored
-triangle is cut into contiguous bands of rows, one per rank, with about equal
-numbers of stored blocks.  A stored block (r, c), r >= c, enters the history
+One system can be split too: the stored triangle is cut into contiguous
+bands of rows, one per rank, with about equal numbers of stored blocks
+(row_bands); each rank's device computes its band's contributions with
+Context.history_slice_band (kbe_history_slice_band), and sharded_slice sums
+them.  The host logic is tested with gloo ranks on the CPU and the per-band
+kernel on one GPU (the bands one after another); no call here drives more
+than one GPU.  A stored block (r, c), r >= c, enters the history
 slice of row n (Eq. KBE2) three times: term 1 of output column c (history
 point m = r), term 1 of output column r through G(c, r) = -G(r, c)^+ (m = c,
 r != c) and term 2 of output column r through G^A(c, r) = R(r, c)^+ (m = c).
