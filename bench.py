@@ -416,6 +416,40 @@ def slice_sweep(kbe, ctx, run, M, stream, rows=(255, 511, 767, 1023), reps=3):
     return out
 
 
+def band_split(kbe, ctx, run, n, stream, worlds=(2, 4, 8), reps=2):
+    """The one-system split by row bands (parallel.row_bands): each band's
+    partial slice of row n timed on this GPU (CUDA events), against the whole
+    slice divided by the band count -- the compute each of N devices would
+    do, without the all-reduce of the 2 (n+1) M^2 partials."""
+    import torch
+    from paper_2405_08737_gb300 import parallel
+    out = {}
+    part = torch.empty_like(run.I)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ctx.selfenergy_slice(n, run.L, run.R, run.Sl, run.Sg, stream=stream)
+    full = timed(lambda: ctx.history_slice(n, run.L, run.R, run.Sl, run.Sg, part, stream=stream))
+    out["whole_slice_ms"] = round(full, 4)
+    for w in worlds:
+        ms = [round(timed(lambda lo=lo, hi=hi: ctx.history_slice_band(n, lo, hi, run.L, run.R, run.Sl, run.Sg, part,
+                                                                      stream=stream)), 4)
+              for lo, hi in parallel.row_bands(n + 1, w)]
+        out[str(w)] = {"band_ms": ms, "max_over_ideal": round(max(ms) / (full / w), 3)}
+    ctx.sync_status()
+    return out
+
+
 def sigma_bench(kbe, ctx, run, n_t, stream, reps=10):
     """The self-energy kernel over the whole stored triangle (kbe_selfenergy_all):
     32 B read and 32 B written per complex entry, 2.15 GB for the chain
@@ -870,6 +904,7 @@ def main():
         line["selfenergy"] = sigma_bench(kbe, ctx, run, n + 1, stream)
         line["slice_sweep"] = slice_sweep(kbe, ctx, run, M, stream,
                                           rows=tuple(r for r in (255, 511, 767, 1023) if r <= n))
+        line["band_split"] = band_split(kbe, ctx, run, n, stream)
     if rank == 0 and not args.no_window:
         line["differentiation_form"] = window_bench(kbe, args.seed, stream)
     if rank == 0 and not args.no_adaptive:
