@@ -263,8 +263,8 @@ kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R,
  * (F_host: the image of F_ring) are copied into the device buffers L, R,
  * F_ring, and the new row n of L and R is copied back to L_row_host and
  * R_row_host ((n+1) M^2 complex each).  The rows are copied from row n-1
- * down in up to 4 chunks of about equal size on a copy stream of the
- * context; with KBE_FP64 (and no adaptive orders or thermal branch) the
+ * down in up to 5 chunks whose sizes grow geometrically (ratio 1.8, the
+ * first the smallest) on a copy stream of the context; with KBE_FP64 (and no adaptive orders or thermal branch) the
  * first sweep's history slice contracts the output columns of each chunk as
  * soon as it has arrived (column c reads rows c..n only), so the copies
  * overlap the contraction; the results are bitwise those of kbe_step on the

@@ -961,18 +961,27 @@ kbe_status kbe_step_host(kbe_ctx* ctx, int n, int P, int precision, const void* 
   // measured slower (e2e step 26.0 ms instead of 23.9 ms)
   const cudaStream_t s = (cudaStream_t)stream, cs = ctx->up_stream;
   const size_t blk = (size_t)ctx->M * ctx->M * 16;  // bytes of one block
-  // rows n-1 down to 0 in chunks of about equal bytes (row r holds r + 1
-  // blocks); the columns of each chunk are contracted while the next ones
-  // are copied.  Every column reads a block of each row above it, so the
-  // longest rows come first and the step waits for the first chunk.  Four
-  // chunks measured best (e2e step of chain_m8_n1024: 23.3 ms with 4,
-  // 23.6 ms with 8, 23.9 ms with 16, 27.0 ms with the upload before the
-  // step): each column range is one more launch of the contraction.
+  // rows n-1 down to 0 in chunks (row r holds r + 1 blocks); the columns of
+  // each chunk are contracted while the next ones are copied.  Every column
+  // reads a block of each row above it, so the longest rows come first and
+  // the step waits for the first chunk alone.  The chunks' bytes grow
+  // geometrically (shares 1 : q : q^2 ...), so that the first is small and
+  // each later one arrives while the columns before it are contracted.
+  // Measured on the e2e step of chain_m8_n1024 (row 1023, M = 8): 5 chunks
+  // with q = 1.8 22.7 ms; 4 or 6 chunks with q = 1.5-2.0 22.8-23.1 ms; 4
+  // equal chunks 23.6 ms; the upload before the step 27.0 ms.  Each column
+  // range is one more launch of the contraction.
   Staged sg;
-  sg.k = std::min(4, n);
+  sg.k = std::min(5, n);
+  const double q = 1.8;
+  double share_sum = 0.0, share = 1.0;
+  for (int k = 0; k < sg.k; ++k, share *= q) share_sum += share;
+  double share_acc = 0.0;
+  share = 1.0;
   int hi = n;
-  for (int k = 0; k < sg.k; ++k) {
-    const double target = (double)tri(n, 0) * (double)(sg.k - k - 1) / sg.k;  // blocks left below the chunk
+  for (int k = 0; k < sg.k; ++k, share *= q) {
+    share_acc += share;
+    const double target = (double)tri(n, 0) * std::max(0.0, 1.0 - share_acc / share_sum);  // blocks below the chunk
     int lo = k + 1 == sg.k ? 0 : (int)std::floor((std::sqrt(8.0 * target + 1.0) - 1.0) / 2.0);
     lo = std::max(0, std::min(lo, hi - 1));
     sg.c_lo[k] = lo;
