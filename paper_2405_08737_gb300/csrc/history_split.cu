@@ -490,11 +490,14 @@ struct EncodeArgs {
   uint8_t* qu;         // [column tile][qu_slots][kBigTile]
   int cpt_stride, qu_slots;
   int ct_base, kc_base, kc_count;  // units: ct_base + i / kc_count, kc_base + i % kc_count
+  int c_min;                       // only the columns c >= c_min are encoded
   int* status;
 };
 
 // One CTA per (column tile, chunk): thread (arr, jrow) encodes row jrow of
 // plane arr (0: G^< from L, 1: Q from R) for the chunk's 16 K entries.
+// Every column has its own exponent, so the rows of the columns below c_min
+// are left as they are.
 __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
   const SplitGeom& g = a.g;
   const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
@@ -511,7 +514,8 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
   __syncthreads();
   const double2* base = reinterpret_cast<const double2*>(arr == 0 ? a.L : a.R);
   const int c = c0 + cl;
-  const bool col_live = row_live && c <= n;
+  const bool enc = row_live && c >= a.c_min;
+  const bool col_live = enc && c <= n;
   double er[kKC], ei[kKC];
   unsigned keep = 0;
   int ef = 0;
@@ -536,7 +540,7 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
 #pragma unroll
     for (int k = 0; k < kKC; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
   }
-  if (row_live && ef > 0) atomicMax(&ecol[cl], ef);
+  if (enc && ef > 0) atomicMax(&ecol[cl], ef);
   __syncthreads();
   uint8_t* unit = a.planes + ((size_t)ctile * a.cpt_stride + kc) * kUnitBytes;
   uint8_t* dst = unit + arr * kBigTile;
@@ -548,7 +552,7 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
   }
   const int e = scale_from_field(ecol[cl]);
 #pragma unroll
-  for (int kg = 0; kg < 4; ++kg) {
+  for (int kg = 0; kg < 4 && enc; ++kg) {
     uint32_t w[kSlices][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -570,7 +574,8 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
       }
     }
   }
-  if (ct < 128) reinterpret_cast<int*>(unit + 2 * kBigTile)[ct] = ecol[ct];
+  // exponents of the encoded columns (and the padding beyond the tile's CT)
+  if (ct < 128 && c0 + ct >= a.c_min) reinterpret_cast<int*>(unit + 2 * kBigTile)[ct] = ecol[ct];
 }
 
 struct Smem2 {
@@ -1022,20 +1027,23 @@ cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& pl_la
   if (e != cudaSuccess) return e;
   split_prep<<<dim3(h.cpt, h.parts), 256, 0, s>>>(l.M, l.n, h.parts, l.Sl, l.Sg, l.w, small, e_small);
   ++*launches;
-  // units whose data involve rows >= r0: every chunk of the column tiles
-  // from the one holding column r0, and the chunks from the one holding
-  // row r0 onwards in the tiles before it
+  // entries involving rows >= r0: every chunk of the columns c >= r0 (the
+  // column tiles from the one holding column r0, those columns only), and
+  // the chunks from the one holding row r0 onwards in the tiles up to that
+  // one (all their columns; the columns >= r0 of the tile holding r0 get
+  // the same values twice)
   if (r0 < 0) r0 = 0;
   const int ct_lo = r0 > h.n ? col_tiles : r0 / h.CT;
   const int kc_lo = (int)(((long long)r0 * h.M) / kKC);
   if (ct_lo < col_tiles) {
-    EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, ct_lo, 0, h.cpt, l.status};
+    EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, ct_lo, 0, h.cpt, r0, l.status};
     split_encode<<<(unsigned)((size_t)(col_tiles - ct_lo) * h.cpt), 256, 0, s>>>(ea);
     ++*launches;
   }
-  if (ct_lo > 0 && kc_lo < h.cpt) {
-    EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, 0, kc_lo, h.cpt - kc_lo, l.status};
-    split_encode<<<(unsigned)((size_t)ct_lo * (h.cpt - kc_lo)), 256, 0, s>>>(ea);
+  const int ct_hi = std::min(col_tiles, ct_lo + 1);
+  if (r0 > 0 && kc_lo < h.cpt) {
+    EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, 0, kc_lo, h.cpt - kc_lo, 0, l.status};
+    split_encode<<<(unsigned)((size_t)ct_hi * (h.cpt - kc_lo)), 256, 0, s>>>(ea);
     ++*launches;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

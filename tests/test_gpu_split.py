@@ -181,12 +181,14 @@ def test_split_stepper_tracks_oracle(kbe):
         ctx.close()
 
 
-def test_split_plane_cache_is_exact(kbe):
+@pytest.mark.parametrize("name,n_t", [("chain_m8_n1024", 40), ("goe_m32_n1024", 24)])
+def test_split_plane_cache_is_exact(kbe, name, n_t):
     """KBE steps that reuse the digit planes of earlier rows give bitwise the
     rows of steps that encode every row again (kbe_reset_cache before each
-    step), including a repeated step of the same row."""
+    step), including a repeated step of the same row.  A step re-encodes
+    only the entries of the rows it changed; with 16 (M = 8) and 4 (M = 32)
+    columns per tile the changed rows fall at every position of a tile."""
     import torch
-    name, n_t = "chain_m8_n1024", 40
     cfg = W.CONFIGS[name]
     t, order = W.grid(cfg["n_t"], cfg["dt0"], cfg["sig"], 6)
     t, order = t[:n_t], order[:n_t]
