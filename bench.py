@@ -35,7 +35,7 @@ WORKLOAD = "chain_m8_n1024"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes of one FP64 contraction launch of the bench slice (ncu capture,
 # profiles/history_partial_fp64_chain_m8_n1024.md)
-FP64_SLICE_TRAFFIC = 2.077e9
+FP64_SLICE_TRAFFIC = 2.056e9
 # DRAM bytes of one split contraction launch (split_main2) of the bench slice
 # (ncu capture, profiles/split_main_chain_m8_n1024.md)
 SPLIT_SLICE_TRAFFIC = 2.262e9
