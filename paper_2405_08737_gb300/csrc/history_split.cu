@@ -827,6 +827,8 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
 // (the FP64 pipe issues 1/64 of the FP32 rate on this part).
 constexpr int kRedThreads = 128;
 constexpr int kRedOut = 2 * kNA * 32 / kRedThreads;  // outputs per thread at M = 32
+constexpr int kRedStage = 1792;  // float4 of staged operands: one point at M = 32 (1024 + 512)
+constexpr int kRedGroup = 16;    // band points staged together at most (band_w <= 13)
 
 struct DotAcc {
   float s, c;
@@ -847,7 +849,9 @@ __device__ __forceinline__ float4 c2_of(double2 v) {
   return make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
-__global__ void __launch_bounds__(kRedThreads) split_reduce2(SplitGeom g, const double* __restrict__ part,
+// Seven CTAs per SM (at most 73 registers, 29 KB of shared memory each):
+// one wave for the 1024 (c, part) blocks of an 8-orbital slice of row 1023.
+__global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, const double* __restrict__ part,
                                                              const double* __restrict__ Sl,
                                                              const double* __restrict__ Sg,
                                                              const double* __restrict__ R, WeightsView w,
@@ -858,10 +862,12 @@ __global__ void __launch_bounds__(kRedThreads) split_reduce2(SplitGeom g, const 
   const int tile = ctile * g.parts + pt;
   const int na = min(kNA, M - pt * kNA);
   const int nout = 2 * na * M;
-  __shared__ int s_i0, s_k;
+  __shared__ int s_i0, s_k, s_cnt, s_mnext;
   __shared__ int s_seg[160];                   // G <= 152 CTAs
-  __shared__ float4 s_r[32 * 32];              // R(c,m) transposed: [x][b]
-  __shared__ float4 s_s[2 * kNA * 32];         // w_{c,m} Sigma^s(n,m): [s][al][x]
+  __shared__ float4 s_stage[kRedStage];        // the group's R(c,m) (transposed, [x][b]), then its
+                                               // w_{c,m} Sigma^s(n,m) ([s][al][x]), per point
+  __shared__ int s_m[kRedGroup];
+  __shared__ double s_dw[kRedGroup], s_wt[kRedGroup];
   if (threadIdx.x == 0) {
     const long long ulo = (long long)tile * g.cpt, uhi = ulo + g.cpt;
     int i = (int)((ulo * g.G) / g.U);
@@ -880,34 +886,62 @@ __global__ void __launch_bounds__(kRedThreads) split_reduce2(SplitGeom g, const 
   DotAcc acc[kRedOut][2];
 #pragma unroll
   for (int q = 0; q < kRedOut; ++q) acc[q][0] = acc[q][1] = DotAcc{0.f, 0.f};
-  // band of term 2 (block-uniform loop: c and m are the block's)
-  for (int m = max(0, c - w.band_w + 1); m <= c; ++m) {
-    const double dw = w.at(c, m);
-    if (dw == 0.0) continue;
+  // band of term 2: the points m = c - band_w + 1 .. c with w_{c,m} != 0,
+  // in increasing m.  As many points as the shared arrays hold are staged
+  // together (all of them at M <= 8), so that their loads are in flight at
+  // once; the sums take the points in the same order either way.
+  const int per = min(kRedGroup, kRedStage / (MM + nout));
+  float4* s_r = s_stage;
+  float4* s_s = s_stage + per * MM;
+  for (int m_next = max(0, c - w.band_w + 1); m_next <= c;) {
+    __syncthreads();  // the previous group's operands are consumed
+    if (threadIdx.x < kRedGroup) {  // the next candidates' weights, loaded in parallel
+      const int m = m_next + (int)threadIdx.x;
+      s_wt[threadIdx.x] = m <= c ? w.at(c, m) : 0.0;
+    }
     __syncthreads();
-    const double2* rb = reinterpret_cast<const double2*>(R) + tri(c, m) * MM;
-    for (int i = threadIdx.x; i < MM; i += kRedThreads) {
+    if (threadIdx.x == 0) {
+      int cnt = 0, k = 0;
+      for (; k < kRedGroup && m_next + k <= c && cnt < per; ++k) {
+        const double dw = s_wt[k];
+        if (dw != 0.0) { s_m[cnt] = m_next + k; s_dw[cnt] = dw; ++cnt; }
+      }
+      s_cnt = cnt;
+      s_mnext = m_next + k;
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    m_next = s_mnext;
+#pragma unroll 4
+    for (int f = threadIdx.x; f < cnt * MM; f += kRedThreads) {
+      const int j = f / MM, i = f - j * MM;
       const int b = i / M, x = i - b * M;
-      s_r[x * M + b] = c2_of(rb[i]);
+      s_r[j * MM + x * M + b] = c2_of(reinterpret_cast<const double2*>(R)[tri(c, s_m[j]) * MM + i]);
     }
-    for (int i = threadIdx.x; i < nout; i += kRedThreads) {
+#pragma unroll 4
+    for (int f = threadIdx.x; f < cnt * nout; f += kRedThreads) {
+      const int j = f / nout, i = f - j * nout;
       const int s = i / (na * M), r = i - s * (na * M);
-      const double2 v = reinterpret_cast<const double2*>(s ? Sg : Sl)[(size_t)m * MM + pt * kNA * M + r];
-      s_s[i] = c2_of(make_double2(dw * v.x, dw * v.y));
+      const double2 v = reinterpret_cast<const double2*>(s ? Sg : Sl)[(size_t)s_m[j] * MM + pt * kNA * M + r];
+      const double dw = s_dw[j];
+      s_s[f] = c2_of(make_double2(dw * v.x, dw * v.y));
     }
     __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const float4* sr = s_r + j * MM;
 #pragma unroll
-    for (int q = 0; q < kRedOut; ++q) {
-      const int o = threadIdx.x + q * kRedThreads;
-      if (o >= nout) break;
-      const int row = o / M, bb = o - row * M;  // row = s * na + al
-      const float4* sp = s_s + row * M;
-      for (int x = 0; x < M; ++x) {  // p conj(r): (p.re r.re + p.im r.im) + i (p.im r.re - p.re r.im)
-        const float4 p = sp[x], r = s_r[x * M + bb];
-        dot_acc(acc[q][0], p.x, p.y, r.x, r.y);
-        dot_acc(acc[q][0], p.z, p.w, r.z, r.w);
-        dot_acc(acc[q][1], p.z, p.w, r.x, r.y);
-        dot_acc(acc[q][1], -p.x, -p.y, r.z, r.w);
+      for (int q = 0; q < kRedOut; ++q) {
+        const int o = threadIdx.x + q * kRedThreads;
+        if (o >= nout) break;
+        const int row = o / M, bb = o - row * M;  // row = s * na + al
+        const float4* sp = s_s + j * nout + row * M;
+        for (int x = 0; x < M; ++x) {  // p conj(r): (p.re r.re + p.im r.im) + i (p.im r.re - p.re r.im)
+          const float4 p = sp[x], r = sr[x * M + bb];
+          dot_acc(acc[q][0], p.x, p.y, r.x, r.y);
+          dot_acc(acc[q][0], p.z, p.w, r.z, r.w);
+          dot_acc(acc[q][1], p.z, p.w, r.x, r.y);
+          dot_acc(acc[q][1], -p.x, -p.y, r.z, r.w);
+        }
       }
     }
   }
