@@ -39,6 +39,18 @@ FP64_SLICE_TRAFFIC = 2.056e9
 # DRAM bytes of one split contraction launch (split_main2) of the bench slice
 # (ncu capture, profiles/split_main_chain_m8_n1024.md)
 SPLIT_SLICE_TRAFFIC = 2.262e9
+SPLIT_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of the launch at n=767 (18432 units), scaled by units to "
+                        "n=1023 (32768 units)")
+SPLIT_KERNEL = "split_main2 (tcgen05 contraction fed by bulk copies of bf16 digit planes)"
+
+
+def split_stream_bytes(M, n):
+    """Bytes the split contraction streams for slice n: per (column tile of
+    128/M columns, chunk of 16 complex history entries, 8-orbital part) one
+    66560-byte unit of digit planes (PL, Q, column exponents)."""
+    ct = 128 // M
+    cpt = ((n + 1) * M + 15) // 16
+    return ((n + 1 + ct - 1) // ct) * cpt * ((M + 7) // 8) * 66560
 METRIC = "history-slice TFLOP/s and ms per KBE step vs plain FP64 GPU path at stated error"
 
 
@@ -383,6 +395,35 @@ def batch_bench(kbe, seed, P, stream, rank=0, world=1):
     return out
 
 
+def split_roofline(M, n, k_avg_ms):
+    """Roofline of the split contraction of slice n.  Bound: the larger of
+    the HBM time of the algorithmic bytes (the FP64 L and R triangles read
+    once, 16 M^2 (n+1)(n+2) B) and the tensor time of the digit products
+    (13 digit pairs x 4 real products x 2 flops per complex multiply-add,
+    (n+1)(3n+2) M^3 of them) at the sustained bf16 peak.  achieved/frac are
+    on the binding one; the bytes the kernel actually streams are reported
+    beside it."""
+    hbm = hbm_peak_gbs()
+    alg_bytes = 16.0 * M * M * (n + 1) * (n + 2)
+    digit_flops = 13 * 4 * 2 * (n + 1) * (3 * n + 2) * M ** 3
+    tc = bf16_peak_tflops(sustained=True)
+    t_hbm = alg_bytes / (hbm * 1e9)
+    t_tc = digit_flops / (tc * 1e12)
+    sec = k_avg_ms * 1e-3
+    out = {"kernel": SPLIT_KERNEL, "avg_ms": round(k_avg_ms, 4), "algorithmic_bytes": alg_bytes,
+           "digit_product_flops": digit_flops, "streamed_bytes": split_stream_bytes(M, n),
+           "hbm_frac_on_algorithmic_bytes": round(alg_bytes / sec / 1e9 / hbm, 4),
+           "tensor_frac_on_digit_flops": round(digit_flops / sec / 1e12 / tc, 4)}
+    if t_hbm >= t_tc:
+        out.update({"bound": "hbm", "achieved": round(alg_bytes / sec / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": out["hbm_frac_on_algorithmic_bytes"], "peak_source": "MEASURED_PEAKS.json hbm_gbs"})
+    else:
+        out.update({"bound": "tensor", "achieved": round(digit_flops / sec / 1e12, 2), "peak": tc,
+                    "unit": "TFLOP/s", "frac": out["tensor_frac_on_digit_flops"],
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"})
+    return out
+
+
 def slice_sweep(kbe, ctx, run, M, stream, rows=(255, 511, 767, 1023), reps=3):
     """The history slice alone at several rows n of the main workload's
     history, each precision's contraction kernel timed by the library's
@@ -406,10 +447,10 @@ def slice_sweep(kbe, ctx, run, M, stream, rows=(255, 511, 767, 1023), reps=3):
             ctx.set_profiling(False)
             res[prec + "_contraction_ms"] = round(ms / max(k, 1), 4)
         f = slice_flops(M, n)
-        ct = 128 // M
-        planes = ((n + 1 + ct - 1) // ct) * (((n + 1) * M + 15) // 16) * ((M + 7) // 8) * 66560
         res["fp64_frac_of_fp64_peak"] = round(f / (res["fp64_contraction_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4)
-        res["split_frac_of_hbm"] = round(planes / (res["split_contraction_ms"] * 1e-3) / 1e9 / hbm, 4)
+        sr = split_roofline(M, n, res["split_contraction_ms"])
+        res["split_bound"] = sr["bound"]
+        res["split_frac"] = sr["frac"]
         res["df64_tflops_fp64_equivalent"] = round(f / (res["df64_contraction_ms"] * 1e-3) / 1e12, 4)
         out[str(n)] = res
     ctx.sync_status()
@@ -473,6 +514,9 @@ def sigma_bench(kbe, ctx, run, n_t, stream, reps=10):
     del Sl, Sg
     gbs = nbytes / (ms * 1e-3) / 1e9
     return {"kernel": "sigma_kernel over the whole triangle (kbe_selfenergy_all)", "bound": "hbm",
+            "arithmetic": "double-float (hi + lo FP32 pairs, about 2^-47 per operation) for the products of "
+                          "Eq. SE; G^> = R + L and the final hi + lo sums in FP64; rows within 1e-13 of the "
+                          "FP64 oracle",
             "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
             "avg_ms": round(ms, 4), "bytes_per_launch": nbytes,
             "note": "algorithmic bytes: L, R read and S^<, S^> written once (64 B per complex entry)"}
@@ -595,6 +639,17 @@ def thermal_bench(kbe, ctx, run, n, P, stream, t, h, steps, beta=10.0, n_tau=128
     ctx.set_thermal(beta, None)
     out["thermal_flops_per_step"] = 8.0 * P * (M ** 3 * n_tau * (n + 1) + M ** 3 * n_tau * (n + 1 + n_tau))
     return out
+
+
+def bf16_peak_tflops(sustained=True):
+    """Measured dense bf16 peak (MEASURED_PEAKS.json): the sustained figure
+    for kernels timed inside a long step, else the burst figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained" if sustained else "bf16_tflops"])
+    except Exception:
+        return 1700.0 if sustained else 1900.0
 
 
 def hbm_peak_gbs():
@@ -750,11 +805,7 @@ def precision_m32_bench(kbe, seed, stream, steps):
     for name, a, b in (("new_row", np.concatenate([got_d[0], got_d[1]]), np.concatenate([ref[0], ref[1]])),
                        ("slice", got_d[2], ref[2])):
         dev_d[name] = float(np.abs(a - b).max() / np.abs(b).max())
-    ct = 128 // M
-    cpt = ((n + 1) * M + 15) // 16
-    plane_bytes = ((n + 1 + ct - 1) // ct) * cpt * ((M + 7) // 8) * 66560
     k_avg = kms_s / max(kc_s, 1)
-    hbm = hbm_peak_gbs()
     flops = P * slice_flops(M, n)
     return {"workload": "goe_m32_n1024: GOE one-body h (M=32), local U=1.5, N_t=1024 nonuniform, orders 1..5; "
                         "KBE step of row n=%d with P=%d" % (n, P),
@@ -762,9 +813,7 @@ def precision_m32_bench(kbe, seed, stream, steps):
             "split_ms_per_step": round(ms_s / steps, 3),
             "split_tflops_fp64_equivalent": round(flops / (ms_s / steps * 1e-3) / 1e12, 4),
             "speedup_vs_fp64_step": round(ms / (ms_s / steps), 3),
-            "split_contraction": {"kernel": "split_main2", "avg_ms": round(k_avg, 4), "bytes_per_launch": plane_bytes,
-                                  "achieved_gbs": round(plane_bytes / (k_avg * 1e-3) / 1e9, 1), "peak_gbs": hbm,
-                                  "frac": round(plane_bytes / (k_avg * 1e-3) / 1e9 / hbm, 4)},
+            "split_contraction": split_roofline(M, n, k_avg),
             "split_deviation_from_fp64_step": dev, "stated_error_bound": 1e-8,
             "df64_ms_per_step": round(ms_d, 3), "df64_speedup_vs_fp64_step": round(ms / ms_d, 3),
             "df64_deviation_from_fp64_step": dev_d,
@@ -843,21 +892,10 @@ def main():
             "avg_ms": round(k_avg, 4), "peak_source": "unit counts x clock: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz "
                               "(FP64 is not in MEASURED_PEAKS.json)"}
     ms_step_s = ms_s / args.steps
-    # the split contraction streams the digit planes of the history: per (column tile of 128/M
-    # columns, chunk of 16 complex history entries) 66560 bytes (PL, Q, column exponents)
-    ct = 128 // M
-    cpt = ((n + 1) * M + 15) // 16
-    plane_bytes = ((n + 1 + ct - 1) // ct) * cpt * ((M + 7) // 8) * 66560
     k_avg_s = kms_s / max(kc_s, 1)
-    hbm = hbm_peak_gbs()
-    split_roof = {"bound": "hbm", "kernel": "split_main2 (tcgen05 contraction fed by bulk copies)",
-                  "achieved": round(plane_bytes / (k_avg_s * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
-                  "frac": round(plane_bytes / (k_avg_s * 1e-3) / 1e9 / hbm, 4),
-                  "traffic": SPLIT_SLICE_TRAFFIC if (M, n) == (8, 1023) else None,
-                  "traffic_source": "ncu dram__bytes_read+write of the launch at n=767 (18432 units), "
-                                    "scaled by units to n=1023 (32768 units)",
-                  "bytes_per_launch": plane_bytes,
-                  "note": "digit planes of both triangles: 2x the FP64 history bytes of the slice"}
+    split_roof = split_roofline(M, n, k_avg_s)
+    split_roof["traffic"] = SPLIT_SLICE_TRAFFIC if (M, n) == (8, 1023) else None
+    split_roof["traffic_source"] = SPLIT_TRAFFIC_SOURCE
     split = {"precision": "split: 4-digit bf16 fixed-point slices on tcgen05, exact FP32 chunk sums, "
                           "double-float accumulation (KBE_SPLIT_BF16)", "roofline": split_roof,
              "ms_per_step": round(ms_step_s, 4),

@@ -93,7 +93,9 @@ kbe_status kbe_create(int norb, int n_max, kbe_ctx** out);
 kbe_status kbe_destroy(kbe_ctx* ctx);
 
 /* Text of the last error on this context (static storage of the context;
- * "" when none).  A NULL ctx gives the last kbe_create error. */
+ * "" when none).  A NULL ctx gives the last context-free error (kbe_create,
+ * kbe_history_slice_noalloc, kbe_batch_create) of the calling host thread;
+ * each thread keeps its own. */
 const char* kbe_last_error(const kbe_ctx* ctx);
 
 /* ------------------------------------------------------------- grid ---- */
@@ -227,6 +229,15 @@ kbe_status kbe_history_slice_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, c
                                   const void* S_less, const void* S_great, void* I_out, void* stream);
 
 /* ----------------------------------------------------------- stepper --- */
+
+/* Row 0 of a run that starts from an uncorrelated state (Sec. 2: the
+ * initial density matrix enters as G^<(0,0) = i rho, and Eq. BC with
+ * theta(0) = 1 fixes G^R(0,0) = -i 1): writes block p(0,0) of L (= i rho0)
+ * and of R (= -i 1) on `stream`.  rho0: host complex MxM matrix (the
+ * one-body density matrix per spin), read during the call.  L, R: device
+ * triangles.  KBE_EINVAL for NULL or misaligned pointers or non-finite
+ * entries.  Follow it with kbe_rhs_row(ctx, 0, ...) for the ring. */
+kbe_status kbe_init_uncorrelated(kbe_ctx* ctx, const double* rho0, void* L, void* R, void* stream);
 
 /* Right-hand-side row j of Eq. (KBE2), the t-derivative along row j:
  *   F^s(j,c) = -i ( eps(t_j) G^s(j,c) + I^s(j,c) ),  c = 0..j,
@@ -505,9 +516,9 @@ kbe_status kbe_batch_sync_status(kbe_batch* b, void* stream);
 /* History slice of row n (the same Eq. KBE2 contraction and kernels as
  * kbe_history_slice, KBE_FP64) for callers that cannot allocate device
  * memory: code that runs inside another framework's memory pool or
- * allocator hooks, graph builders that may not allocate while recording,
- * or hosts that only hand over fixed buffers.  The paper has no
- * counterpart; this entry exists for those callers.
+ * allocator hooks (a nested cudaMalloc there would re-enter the allocator
+ * or escape its accounting), or hosts that only hand over fixed buffers.
+ * The paper has no counterpart; this entry exists for those callers.
  *
  * No context: the grid t[0..n_t-1], order[1..n_t-1] is passed on the host
  * (same validation as kbe_set_grid) and its weights are recomputed on each
@@ -515,7 +526,8 @@ kbe_status kbe_batch_sync_status(kbe_batch* b, void* stream);
  * the layouts of kbe_history_slice.  All scratch lives in one static
  * device array of 64 MiB that every GPU loading the library reserves until
  * the process exits: n_t <= 8192 and (n+1)*norb^2 <= about 1.37e6 complex
- * entries, else KBE_EINVAL with a message in kbe_last_error(NULL).  The
+ * entries, else KBE_EINVAL with a message in kbe_last_error(NULL) (the
+ * last context-free error of the calling host thread).  The
  * call allocates no device memory (no cudaMalloc, cudaFree or allocating
  * library routine).  Its first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make

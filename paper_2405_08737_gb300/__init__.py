@@ -61,6 +61,7 @@ def lib():
         L.kbe_selfenergy_all.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_history_slice.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
         L.kbe_rhs_row.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_init_uncorrelated.argtypes = [vp, vp, vp, vp, vp]
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
         L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -282,6 +283,12 @@ class Context:
         self._check(lib().kbe_history_slice_band(self._h, n, int(row_lo), int(row_hi), self._dev(L), self._dev(R),
                                                  self._dev(Sl), self._dev(Sg), self._dev(out), self._stream(stream)))
 
+    def init_uncorrelated(self, rho0, L, R, stream=None):
+        """kbe_init_uncorrelated: block (0,0) of L = i rho0, of R = -i 1."""
+        rho = np.ascontiguousarray(np.asarray(rho0, np.complex128).reshape(self.M, self.M))
+        self._check(lib().kbe_init_uncorrelated(self._h, _np_ptr(rho), self._dev(L), self._dev(R),
+                                                self._stream(stream)))
+
     def rhs_row(self, j, L, R, Sl, Sg, I_work, F_ring, precision="fp64", stream=None):
         self._check(lib().kbe_rhs_row(self._h, j, PRECISIONS[precision], self._dev(L), self._dev(R),
                                       self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_ring),
@@ -423,12 +430,9 @@ class Run:
         self.F = ctx.empty_ring()
 
     def init_uncorrelated(self, rho0, stream=None):
-        """Row 0 from G^<(0,0) = i rho0, G^R(0,0) = -i, and its right-hand side."""
-        import torch
-        M = self.ctx.M
-        rho = torch.as_tensor(np.asarray(rho0, np.complex128), device="cuda")
-        self.L[0].copy_(1j * rho)
-        self.R[0].copy_(-1j * torch.eye(M, dtype=torch.complex128, device="cuda"))
+        """Row 0 from G^<(0,0) = i rho0, G^R(0,0) = -i (kbe_init_uncorrelated),
+        and its right-hand side."""
+        self.ctx.init_uncorrelated(rho0, self.L, self.R, stream=stream)
         self.ctx.rhs_row(0, self.L, self.R, self.Sl, self.Sg, self.I, self.F, stream=stream)
 
     def step(self, n, P=2, precision="fp64", stream=None):

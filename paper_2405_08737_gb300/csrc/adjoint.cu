@@ -486,7 +486,7 @@ cudaError_t launch_adjoint_history(const AdjHistArgs& h, cudaStream_t s, int* la
   *launches = 0;
   const int M = h.M, MM = M * M, n = h.n;
   const int64_t srow = (int64_t)(n + 1) * MM;
-  int64_t want = (152LL * 2048 + srow - 1) / srow;
+  int64_t want = ((int64_t)sm_count() * 2048 + srow - 1) / srow;
   int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
   if (nchunk > n + 1) nchunk = n + 1;
   // the workspace holds the chunk partials [nchunk][3][srow], then the rows Js

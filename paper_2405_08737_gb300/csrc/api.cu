@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libkbe (declared in include/kbe.h): argument
 // validation, device workspace, and the launch sequences of each call.
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -578,6 +579,24 @@ kbe_status ctl_interval_weights(CtlRun& r, int n) {
 
 void kbe::set_global_error(const char* msg) { g_create_err = msg; }
 
+int kbe::sm_count() {
+  constexpr int kDevs = 64;
+  static std::atomic<int> cached[kDevs] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) {
+    cudaGetLastError();
+    return 1;
+  }
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  cached[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 extern "C" {
 
 kbe_status kbe_create(int norb, int n_max, kbe_ctx** out) {
@@ -888,6 +907,25 @@ kbe_status kbe_history_slice_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, c
   cudaError_t e = launch_history_f64(a, (cudaStream_t)stream, &nl);
   ctx->last_launches = nl;
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_history_slice_band: launch");
+}
+
+kbe_status kbe_init_uncorrelated(kbe_ctx* ctx, const double* rho0, void* L, void* R, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (!rho0) return fail(ctx, KBE_EINVAL, "kbe_init_uncorrelated: NULL rho0");
+  if (!aligned16(L) || !aligned16(R)) return fail(ctx, KBE_EINVAL, "kbe_init_uncorrelated: NULL or misaligned pointer");
+  const int MM = ctx->M * ctx->M;
+  for (int i = 0; i < 2 * MM; ++i)
+    if (!std::isfinite(rho0[i])) return fail(ctx, KBE_EINVAL, "kbe_init_uncorrelated: non-finite rho0");
+  kbe_status st = use_device(ctx);
+  if (st != KBE_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // rho0 is staged in the Fock-matrix buffer, which the next right-hand side overwrites
+  cudaError_t e = cudaMemcpyAsync(ctx->d_eps, rho0, (size_t)MM * 16, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_init_row0(ctx->M, ctx->d_eps, (double*)L, (double*)R, s);
+  ctx->last_launches = 1;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kbe_init_uncorrelated");
+  return KBE_OK;
 }
 
 kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const void* R, void* Sl, void* Sg,

@@ -306,7 +306,6 @@ void drop_graph(kbe_batch* b) {
   b->g_prec = -1;
 }
 
-constexpr int kElemBlocks = 152 * 8;
 
 // Split precision with the plane buffer: the whole step of one system after
 // the other (plan, predictor, P x {self-energy, encoder + contraction, Fock,
@@ -326,11 +325,11 @@ cudaError_t enqueue_split_by_system(kbe_batch* b, int P, const int* rows_host, c
     SplitPlanes lay;
     const bool planes = split_planes_layout(y.M, c->n_max, &lay) && lay.bytes <= b->planes_bytes;
     batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
-    batch_rows<kOpPredictor><<<kElemBlocks, 256, 0, s>>>(d);
+    batch_rows<kOpPredictor><<<sm_count() * 8, 256, 0, s>>>(d);
     nl += 2;
     e = cudaGetLastError();
     for (int it = 0; it < P && e == cudaSuccess; ++it) {
-      batch_rows<kOpSigma><<<kElemBlocks, 256, 0, s>>>(d);
+      batch_rows<kOpSigma><<<sm_count() * 8, 256, 0, s>>>(d);
       ++nl;
       SplitLaunch l{y.M, n, y.L, y.R, y.Sl, y.Sg, WeightsView{y.wbar, y.band, y.band_w}, y.I, c->d_split,
                     c->split_bytes, d.status};
@@ -342,8 +341,8 @@ cudaError_t enqueue_split_by_system(kbe_batch* b, int P, const int* rows_host, c
       nl += k;
       if (e != cudaSuccess) break;
       batch_fock<<<b->n_sys, 256, 0, s>>>(d);
-      batch_rows<kOpRhs><<<kElemBlocks, 256, 0, s>>>(d);
-      batch_rows<kOpCorrector><<<kElemBlocks, 256, 0, s>>>(d);
+      batch_rows<kOpRhs><<<sm_count() * 8, 256, 0, s>>>(d);
+      batch_rows<kOpCorrector><<<sm_count() * 8, 256, 0, s>>>(d);
       nl += 3;
       e = cudaGetLastError();
     }
@@ -360,19 +359,19 @@ cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_hos
   int nl = 0;
   batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
   ++nl;
-  batch_rows<kOpPredictor><<<kElemBlocks, 256, 0, s>>>(d);
+  batch_rows<kOpPredictor><<<sm_count() * 8, 256, 0, s>>>(d);
   ++nl;
   cudaError_t e = cudaGetLastError();
   for (int it = 0; it < P && e == cudaSuccess; ++it) {
-    batch_rows<kOpSigma><<<kElemBlocks, 256, 0, s>>>(d);
+    batch_rows<kOpSigma><<<sm_count() * 8, 256, 0, s>>>(d);
     ++nl;
     if (precision == KBE_FP64) {  // prep also clears the work counter
-      batch_rows<kOpPrep><<<kElemBlocks, 256, 0, s>>>(d);
+      batch_rows<kOpPrep><<<sm_count() * 8, 256, 0, s>>>(d);
       if (d.block == 128)
         batch_history<128><<<b->hist_blocks[0], 128, 0, s>>>(d);
       else
         batch_history<256><<<b->hist_blocks[1], 256, 0, s>>>(d);
-      batch_rows<kOpReduce><<<kElemBlocks, 256, 0, s>>>(d);
+      batch_rows<kOpReduce><<<sm_count() * 8, 256, 0, s>>>(d);
       nl += 3;
     } else if (precision == KBE_DF64) {  // each system's double-float slice in its context's workspace
       for (int i = 0; i < b->n_sys && e == cudaSuccess; ++i) {
@@ -405,8 +404,8 @@ cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_hos
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     batch_fock<<<b->n_sys, 256, 0, s>>>(d);
-    batch_rows<kOpRhs><<<kElemBlocks, 256, 0, s>>>(d);
-    batch_rows<kOpCorrector><<<kElemBlocks, 256, 0, s>>>(d);
+    batch_rows<kOpRhs><<<sm_count() * 8, 256, 0, s>>>(d);
+    batch_rows<kOpCorrector><<<sm_count() * 8, 256, 0, s>>>(d);
     nl += 3;
     if (e == cudaSuccess) e = cudaGetLastError();
   }
@@ -525,8 +524,8 @@ kbe_status kbe_batch_create(kbe_ctx* const* ctxs, int n_sys, kbe_batch** out) {
     delete b;
     return st;
   }
-  int sms = 152, occ128 = 1, occ256 = 1;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev0);
+  const int sms = sm_count();
+  int occ128 = 1, occ256 = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ128, batch_history<128>, 128, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ256, batch_history<256>, 256, 0);
   b->hist_blocks[0] = sms * std::max(1, occ128);
@@ -694,7 +693,7 @@ kbe_status kbe_batch_autotune(kbe_batch* b, const int* rows, int reps, void* str
   // the slice of the current state: self-energy rows, then timed history slices
   BatchDev d = b->dev;
   batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
-  batch_rows<kOpSigma><<<kElemBlocks, 256, 0, s>>>(d);
+  batch_rows<kOpSigma><<<sm_count() * 8, 256, 0, s>>>(d);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -708,7 +707,7 @@ kbe_status kbe_batch_autotune(kbe_batch* b, const int* rows, int reps, void* str
       double tot = 0.0;
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // r = 0 warms up
         batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
-        batch_rows<kOpPrep><<<kElemBlocks, 256, 0, s>>>(d);
+        batch_rows<kOpPrep><<<sm_count() * 8, 256, 0, s>>>(d);
         cudaEventRecord(e0, s);
         if (d.block == 128) batch_history<128><<<b->hist_blocks[0], 128, 0, s>>>(d);
         else batch_history<256><<<b->hist_blocks[1], 256, 0, s>>>(d);

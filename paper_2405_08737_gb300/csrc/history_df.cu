@@ -342,7 +342,7 @@ cudaError_t launch_history_df(const HistoryArgs& a, cudaStream_t s, int* launche
   const int64_t threads = (int64_t)(n + 1) * AG * M;
   // enough threads for full occupancy, and chunks of at most ~32 history
   // points so that a block's work stays short
-  int64_t want = std::max<int64_t>((152LL * 2048 + threads - 1) / threads, (n + 1 + 31) / 32);
+  int64_t want = std::max<int64_t>(((int64_t)sm_count() * 2048 + threads - 1) / threads, (n + 1 + 31) / 32);
   int nchunk = (int)std::min<int64_t>(std::max<int64_t>(want, 1), kMaxSplit);
   if (nchunk > n + 1) nchunk = n + 1;
   const size_t prep_bytes = (size_t)3 * row * 16;
@@ -356,7 +356,7 @@ cudaError_t launch_history_df(const HistoryArgs& a, cudaStream_t s, int* launche
   float4* Bg = Bl + row;
   double* partials = a.part + 6 * row;
   int nl = 0;
-  history_df_prep<<<grid_for(row, 152 * 8), 256, 0, s>>>(MM, n, a.Sl, a.Sg, a.w, A1, Bl, Bg);
+  history_df_prep<<<grid_for(row, sm_count() * 8), 256, 0, s>>>(MM, n, a.Sl, a.Sg, a.w, A1, Bl, Bg);
   ++nl;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { *launches = nl; return e; }

@@ -93,10 +93,10 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
   const int64_t row = (int64_t)(n + 1) * MM;       // complex entries per s
   const int64_t outputs = row;                     // threads of one chunk
   // Split of the history index m: at least enough threads for full
-  // occupancy (152 SMs x 2048 threads), and chunks short enough that one
+  // occupancy (every SM x 2048 threads), and chunks short enough that one
   // 128-thread block does about 2^16 complex multiply-adds (3M per point and
   // output), which keeps the tail of the launch short.
-  int64_t want = (152LL * 2048 + outputs - 1) / outputs;
+  int64_t want = ((int64_t)sm_count() * 2048 + outputs - 1) / outputs;
   const int64_t len_target = std::max<int64_t>(1, (1 << 16) / (kHistBlock * 3 * M));
   want = std::max<int64_t>(want, (n + 1 + len_target - 1) / len_target);
   int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
@@ -113,7 +113,7 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
   double* Bg = Bl + 2 * row;
   double* partials = Bg + 2 * row;
   int nl = 0;
-  history_prep<<<grid_for(row, 152 * 8), 256, 0, s>>>(MM, n, a.Sl, a.Sg, a.w, A1, Bl, Bg);
+  history_prep<<<grid_for(row, sm_count() * 8), 256, 0, s>>>(MM, n, a.Sl, a.Sg, a.w, A1, Bl, Bg);
   ++nl;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { *launches = nl; return e; }
@@ -135,10 +135,10 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
   if (a.ev_end) cudaEventRecord(a.ev_end, s);
   if (e != cudaSuccess) { *launches = nl; return e; }
   if (nchunk > 1) {
-    history_reduce<<<grid_for(2 * row, 152 * 8), 256, 0, s>>>(2 * row, nchunk, (const double2*)partials,
+    history_reduce<<<grid_for(2 * row, sm_count() * 8), 256, 0, s>>>(2 * row, nchunk, (const double2*)partials,
                                                               (double2*)a.out, a.status);
   } else {
-    finite_check<<<grid_for(2 * row, 152 * 8), 256, 0, s>>>(2 * row, (const double2*)a.out, a.status);
+    finite_check<<<grid_for(2 * row, sm_count() * 8), 256, 0, s>>>(2 * row, (const double2*)a.out, a.status);
   }
   ++nl;
   *launches = nl;
@@ -150,10 +150,10 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
 cudaError_t launch_history_finish(int nchunk, int64_t row, const double* partials, double* out, int* status,
                                   cudaStream_t s, int* launches) {
   if (nchunk > 1) {
-    history_reduce<<<grid_for(2 * row, 152 * 8), 256, 0, s>>>(2 * row, nchunk, (const double2*)partials,
+    history_reduce<<<grid_for(2 * row, sm_count() * 8), 256, 0, s>>>(2 * row, nchunk, (const double2*)partials,
                                                               (double2*)out, status);
   } else {
-    finite_check<<<grid_for(2 * row, 152 * 8), 256, 0, s>>>(2 * row, (const double2*)out, status);
+    finite_check<<<grid_for(2 * row, sm_count() * 8), 256, 0, s>>>(2 * row, (const double2*)out, status);
   }
   *launches = 1;
   return cudaGetLastError();

@@ -63,6 +63,7 @@ constexpr int kGroupCols = kLevels * kNS;   // 5 levels x 16 columns
 constexpr int kAccCols = 2 * kGroupCols;    // groups I^< and I^>: 160 columns
 constexpr int kTmemCols = 512;              // two accumulator buffers (320 used)
 constexpr long long kSpinLimit = 1ll << 26; // bounded waits
+constexpr int kMaxSplitCtas = 160;          // persistent CTAs of a contraction, at most
 
 struct SplitGeom {
   int M, MM, n;
@@ -370,6 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_main(SplitArgs a) {
         const int it = (int)(last - u0);
         long long spins = 0;
         while (!mbar_try(&sm.empty[it % kStages], (it / kStages) & 1) && ++spins < kSpinLimit) __nanosleep(64);
+        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);  // copies or MMAs may still be in flight
       }
     }
     __syncwarp();
@@ -666,6 +668,7 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
         const int it = (int)(u - u0);
         long long spins = 0;
         while (!mbar_try(&sm.full[it % kStages], (it / kStages) & 1) && ++spins < kSpinLimit) __nanosleep(64);
+        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);  // copies or MMAs may still be in flight
       }
     }
     __syncwarp();
@@ -722,6 +725,7 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
         const int it = (int)(last - u0);
         long long spins = 0;
         while (!mbar_try(&sm.empty[it % kStages], (it / kStages) & 1) && ++spins < kSpinLimit) __nanosleep(64);
+        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);  // copies or MMAs may still be in flight
       }
     }
     __syncwarp();
@@ -863,7 +867,7 @@ __global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, con
   const int na = min(kNA, M - pt * kNA);
   const int nout = 2 * na * M;
   __shared__ int s_i0, s_k, s_cnt, s_mnext;
-  __shared__ int s_seg[160];                   // G <= 152 CTAs
+  __shared__ int s_seg[kMaxSplitCtas];
   __shared__ float4 s_stage[kRedStage];        // the group's R(c,m) (transposed, [x][b]), then its
                                                // w_{c,m} Sigma^s(n,m) ([s][al][x]), per point
   __shared__ int s_m[kRedGroup];
@@ -875,7 +879,7 @@ __global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, con
     while (i + 1 < g.G && g.U * (i + 1) / g.G <= ulo) ++i;
     const int i0 = i;
     int k = 0;
-    for (; i < g.G && k < 160; ++i) {
+    for (; i < g.G && k < kMaxSplitCtas; ++i) {
       const long long b0 = g.U * i / g.G, b1 = g.U * (i + 1) / g.G;
       if (b0 >= uhi) break;
       s_seg[k++] = b1 <= b0 ? -1 : (int)(tile - b0 / g.cpt);
@@ -990,7 +994,8 @@ bool split_geometry(int M, int n, SplitGeomHost* h) {
   const int col_tiles = (n + 1 + h->CT - 1) / h->CT;
   h->tiles = col_tiles * h->parts;
   h->U = (long long)h->tiles * h->cpt;
-  h->G = (int)(h->U < 152 ? h->U : 152);
+  const int ctas = std::min(sm_count(), kMaxSplitCtas);
+  h->G = (int)(h->U < ctas ? h->U : ctas);
   // tiles touched by one CTA range: at most ceil(range / cpt) + 1
   const long long range = (h->U + h->G - 1) / h->G;
   h->S = (int)((range + h->cpt - 1) / h->cpt + 1);

@@ -62,8 +62,13 @@ struct SplitPlanes {
   size_t bytes = 0;
 };
 
-// Record a context-free error message (returned by kbe_last_error(NULL)).
+// Record a context-free error message (returned by kbe_last_error(NULL) on
+// the calling host thread).
 void set_global_error(const char* msg);
+
+// Streaming multiprocessors of the current device (queried once per device;
+// launch heuristics size their grids from it).
+int sm_count();
 
 struct Model {
   bool set = false;
@@ -249,6 +254,8 @@ struct StepArgs {
   int* status;
 };
 cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s);
+// L(0,0) = i rho, R(0,0) = -i 1 from the device matrix rho (complex MxM).
+cudaError_t launch_init_row0(int M, const double* rho, double* L, double* R, cudaStream_t s);
 cudaError_t launch_fock(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rhs(const StepArgs& a, cudaStream_t s);          // F row n only
 cudaError_t launch_rhs_corrector(const StepArgs& a, cudaStream_t s);  // F row n, then new row n

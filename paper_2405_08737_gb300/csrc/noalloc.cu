@@ -1,13 +1,13 @@
 // noalloc.cu -- a history slice that allocates no device memory.
 //
 // Some callers cannot call cudaMalloc: code running inside another
-// framework's memory pool or allocator hooks, CUDA-graph builders that may
-// not allocate while they record, or embedded hosts that hand over fixed
-// buffers only.  kbe_history_slice_noalloc() serves them: it needs no
-// context, takes the grid on the host and the two-time data on the device,
-// and keeps all of its scratch (weight tables, folded self-energy rows,
-// split partials, status word) in one file-scope __device__ array of fixed
-// size.  Every GPU that loads the library reserves that array until the
+// framework's memory pool or allocator hooks (where a nested allocation
+// would re-enter the allocator or break its accounting), or embedded hosts
+// that hand over fixed buffers only.  kbe_history_slice_noalloc() serves
+// them: it needs no context, takes the grid on the host and the two-time
+// data on the device, and keeps all of its scratch (weight tables, folded
+// self-energy rows, split partials, status word) in one file-scope
+// __device__ array of fixed size.  Every GPU that loads the library reserves that array until the
 // process exits.
 //
 // The array is shared by every call on a device and keeps the last call's

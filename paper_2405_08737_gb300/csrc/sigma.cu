@@ -104,7 +104,7 @@ cudaError_t launch_sigma(int M, int64_t first_block, int64_t n_blocks, int64_t d
   const int64_t off = first_block * MM;
   if (n_elem == 0) return cudaSuccess;
   int64_t blocks = (n_elem + 255) / 256;
-  const int64_t cap = 152 * 16;  // a grid-stride loop beyond ~16 CTAs per SM
+  const int64_t cap = (int64_t)sm_count() * 16;  // a grid-stride loop beyond ~16 CTAs per SM
   if (blocks > cap) blocks = cap;
   sigma_kernel<<<(unsigned)blocks, 256, 0, s>>>(MM, M, n_elem, first_block, diag_rel, (const double2*)L + off,
                                                 (const double2*)R + off, U, (double2*)Sl, (double2*)Sg, status);

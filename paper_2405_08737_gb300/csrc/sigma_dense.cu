@@ -220,7 +220,7 @@ cudaError_t launch_sigma_dense(int M, int64_t first_block, int64_t n_blocks, int
   a.g = t.g;
   a.g3 = t.g3;
   int64_t blocks = 2 * n_blocks;
-  const int64_t cap = 152 * 16;
+  const int64_t cap = (int64_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
   sigma_dense_kernel<<<(unsigned)blocks, kThreads, t.smem, s>>>(a);
   return cudaGetLastError();

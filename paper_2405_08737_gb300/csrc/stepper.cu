@@ -41,7 +41,23 @@ __global__ void __launch_bounds__(256) corrector_kernel(StepArgs a) {
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// Row 0 of an uncorrelated start: G^<(0,0) = i rho0 and G^R(0,0) = -i 1
+// (Eq. BC with theta(0) = 1).
+__global__ void init_row0_kernel(int M, const double2* __restrict__ rho, double2* __restrict__ L,
+                                 double2* __restrict__ R) {
+  for (int ab = threadIdx.x; ab < M * M; ab += blockDim.x) {
+    const double2 p = rho[ab];
+    L[ab] = make_double2(-p.y, p.x);
+    R[ab] = make_double2(0.0, ab / M == ab % M ? -1.0 : 0.0);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_init_row0(int M, const double* rho, double* L, double* R, cudaStream_t s) {
+  init_row0_kernel<<<1, 256, 0, s>>>(M, (const double2*)rho, (double2*)L, (double2*)R);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fock(const StepArgs& a, cudaStream_t s) {
   fock_kernel<<<1, 256, 0, s>>>(a);

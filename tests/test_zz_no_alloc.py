@@ -1,12 +1,15 @@
 """The allocation-free history slice against the context entry point.
 
 kbe_history_slice_noalloc serves callers that cannot allocate device memory
-(code inside another framework's memory pool or allocator hooks, graph
-builders that may not allocate while recording, hosts that only hand over
-fixed buffers).  It keeps its scratch in a static device array, so this
-test checks that two calls in a row, the second reusing the array left by
-the first, both match the context path (kbe_history_slice) through the
-C ABI, and that sizes beyond the array are rejected on the host.
+(code inside another framework's memory pool or allocator hooks, where a
+nested cudaMalloc would re-enter the allocator or escape its accounting,
+and hosts that only hand over fixed buffers).  It keeps its scratch in a
+static device array, so this test checks that calls in a row, each reusing
+the array left by the one before (a larger row on another grid after a
+smaller one included), match the context path (kbe_history_slice) through
+the C ABI; that the device's free memory does not change across the calls
+that follow the first; and that sizes beyond the array are rejected on the
+host.
 
 The file name sorts last so that a run stopping at the first failure has
 already run every other test."""
@@ -52,23 +55,33 @@ def _case(M, n_t, seed):
     return t, order.astype(np.int32), h, U, L, R, torch
 
 
-def _context_slice(kbe, ctx, n, L, R, Sl, Sg):
-    import torch
-    out = torch.zeros((2, n + 1, ctx.M, ctx.M), dtype=torch.complex128, device="cuda")
-    ctx.history_slice(n, L, R, Sl[: n + 1].contiguous(), Sg[: n + 1].contiguous(), out)
+def _prepare(kbe, M, n_t, seed, n):
+    """Inputs of row n on a seeded grid and the context path's slice."""
+    t, order, h, U, L, R, torch = _case(M, n_t, seed)
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, U, W.site_potential(M), None)
+    Sl = torch.zeros((n_t, M, M), dtype=torch.complex128, device="cuda")
+    Sg = torch.zeros_like(Sl)
+    ctx.selfenergy_slice(n, L, R, Sl, Sg)
+    Sl_n, Sg_n = Sl[: n + 1].contiguous(), Sg[: n + 1].contiguous()
+    ref = torch.zeros((2, n + 1, M, M), dtype=torch.complex128, device="cuda")
+    ctx.history_slice(n, L, R, Sl_n, Sg_n, ref)
     ctx.sync_status()
-    return out
-
-
-def _noalloc_slice(kbe, M, n, t, order, L, R, Sl, Sg):
-    import torch
+    ctx.close()
     out = torch.full((2, n + 1, M, M), float("nan"), dtype=torch.complex128, device="cuda")
-    st = kbe.lib().kbe_history_slice_noalloc(M, n, _np(t), _np(order), len(t), _ptr(L), _ptr(R),
-                                             _ptr(Sl), _ptr(Sg), _ptr(out),
+    return dict(M=M, n=n, t=t, order=order, L=L, R=R, Sl=Sl_n, Sg=Sg_n, ref=ref, out=out)
+
+
+def _noalloc(kbe, c):
+    """One allocation-free call into the preallocated output (no torch work)."""
+    import torch
+    st = kbe.lib().kbe_history_slice_noalloc(c["M"], c["n"], _np(c["t"]), _np(c["order"]), len(c["t"]),
+                                             _ptr(c["L"]), _ptr(c["R"]), _ptr(c["Sl"]), _ptr(c["Sg"]),
+                                             _ptr(c["out"]),
                                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == kbe.KBE_OK, kbe.lib().kbe_last_error(None)
     torch.cuda.synchronize()
-    return out
 
 
 def _rel(a, b):
@@ -78,18 +91,30 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("M,n_t,rows", [(8, 300, (299, 150)), (3, 50, (49, 0))])
 def test_noalloc_matches_context_path_twice(kbe, M, n_t, rows):
-    t, order, h, U, L, R, torch = _case(M, n_t, 11 + M)
-    ctx = kbe.Context(M, n_t)
-    ctx.set_grid(t, order)
-    ctx.set_model(h, U, W.site_potential(M), None)
-    Sl = torch.zeros((n_t, M, M), dtype=torch.complex128, device="cuda")
-    Sg = torch.zeros_like(Sl)
-    for n in rows:  # two calls in a row share the static scratch
-        ctx.selfenergy_slice(n, L, R, Sl, Sg)
-        ref = _context_slice(kbe, ctx, n, L, R, Sl, Sg)
-        got = _noalloc_slice(kbe, M, n, t, order, L, R, Sl[: n + 1].contiguous(), Sg[: n + 1].contiguous())
-        assert _rel(got, ref) < TOL, (M, n, _rel(got, ref))
-    ctx.close()
+    cases = [_prepare(kbe, M, n_t, 11 + M, n) for n in rows]
+    for c in cases:  # two calls in a row share the static scratch
+        _noalloc(kbe, c)
+        assert _rel(c["out"], c["ref"]) < TOL, (M, c["n"], _rel(c["out"], c["ref"]))
+
+
+def test_noalloc_larger_row_on_another_grid_after_a_smaller_one(kbe):
+    """A small row, then a larger row on a different seeded grid and orbital
+    count, then the small one again: each result matches the context path,
+    whatever the earlier call left in the shared array.  The device's free
+    memory is the same after every call that follows the first."""
+    import torch
+    cases = [_prepare(kbe, 4, 120, 3, 40), _prepare(kbe, 6, 400, 7, 399), _prepare(kbe, 4, 120, 3, 40)]
+    torch.cuda.synchronize()
+    _noalloc(kbe, cases[0])  # the first call may look up the array's device address
+    free0 = torch.cuda.mem_get_info()[0]
+    for c in cases:
+        c["out"].fill_(float("nan"))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for c in cases:
+        _noalloc(kbe, c)
+        assert torch.cuda.mem_get_info()[0] == free0, "the call changed the device's free memory"
+        assert _rel(c["out"], c["ref"]) < TOL, (c["M"], c["n"], _rel(c["out"], c["ref"]))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(kbe):
