@@ -436,6 +436,21 @@ kbe_status kbe_reset_cache(kbe_ctx* ctx);
  * the last call (then cleared): KBE_OK, KBE_ENUMERIC or KBE_ETIMEOUT. */
 kbe_status kbe_sync_status(kbe_ctx* ctx, void* stream);
 
+/* Test support for the device-side failure path (no fault is involved):
+ * the next split-precision contraction launched on this context (by
+ * kbe_history_slice, kbe_step, ... with KBE_SPLIT_BF16) issues no copy for
+ * its work unit `unit` (a unit is one column tile of 128 / norb output
+ * columns times one chunk of 16 history entries; the persistent CTA that
+ * owns it stops producing there), and every wait of its pipeline gives up
+ * after spin_limit polls (instead of about 2^26).  The consumers' bounded
+ * waits run out, every CTA of the launch finishes the copies and MMAs it
+ * had already issued, frees its tensor memory and returns, and
+ * kbe_sync_status reports KBE_ETIMEOUT; the slice's output is then
+ * undefined.  Later calls are unaffected (the setting applies to one launch
+ * and clears itself).  A unit beyond the launch's last unit withholds
+ * nothing.  KBE_EINVAL for unit < 0 or spin_limit < 1. */
+kbe_status kbe_debug_withhold_split(kbe_ctx* ctx, long long unit, long long spin_limit);
+
 /* Number of kernels the last kbe_* call on this context enqueued. */
 int kbe_last_launch_count(const kbe_ctx* ctx);
 

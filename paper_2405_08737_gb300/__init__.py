@@ -62,6 +62,7 @@ def lib():
         L.kbe_history_slice.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
         L.kbe_rhs_row.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_init_uncorrelated.argtypes = [vp, vp, vp, vp, vp]
+        L.kbe_debug_withhold_split.argtypes = [vp, ctypes.c_longlong, ctypes.c_longlong]
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
         L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -399,6 +400,10 @@ class Context:
         n = n_rows.value
         return {"t": t[:n], "q": q[:n], "korder": ko[:n], "n": n, "stats": tuple(int(x) for x in stats),
                 "L": L, "R": R, "status": int(st)}
+
+    def debug_withhold_split(self, unit, spin_limit):
+        """Failure-path test of the next split contraction (kbe_debug_withhold_split)."""
+        self._check(lib().kbe_debug_withhold_split(self._h, int(unit), int(spin_limit)))
 
     def set_profiling(self, enable):
         """Record CUDA events around each contraction kernel (clears old records)."""

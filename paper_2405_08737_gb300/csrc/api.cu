@@ -139,6 +139,10 @@ kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void
         ctx->planes_L = ctx->planes_R = nullptr;
       }
     }
+    l.withhold = ctx->dbg_withhold;
+    l.spin_limit = ctx->dbg_spin;
+    ctx->dbg_withhold = -1;  // one launch only
+    ctx->dbg_spin = 0;
     cudaError_t e;
     if (ctx->d_planes) {
       int r0 = 0;
@@ -907,6 +911,14 @@ kbe_status kbe_history_slice_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, c
   cudaError_t e = launch_history_f64(a, (cudaStream_t)stream, &nl);
   ctx->last_launches = nl;
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_history_slice_band: launch");
+}
+
+kbe_status kbe_debug_withhold_split(kbe_ctx* ctx, long long unit, long long spin_limit) {
+  if (!ctx) return KBE_EINVAL;
+  if (unit < 0 || spin_limit < 1) return fail(ctx, KBE_EINVAL, "kbe_debug_withhold_split: unit < 0 or spin_limit < 1");
+  ctx->dbg_withhold = unit;
+  ctx->dbg_spin = spin_limit;
+  return KBE_OK;
 }
 
 kbe_status kbe_init_uncorrelated(kbe_ctx* ctx, const double* rho0, void* L, void* R, void* stream) {

@@ -583,6 +583,7 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
 struct Smem2 {
   uint8_t stage[kStages][kStage2Bytes];
   uint64_t full[kStages], empty[kStages], accfull[2], accempty[2];
+  uint64_t mmadone[2];  // one per MMA-issuing thread: all of its MMAs have completed
   uint32_t tmem;
   int abort;
 };
@@ -596,13 +597,18 @@ struct Split2Args {
   const int* e_small;
   double* part;
   int* status;
+  // failure-path test: the producer issues nothing for unit `withhold` (or
+  // later) and every work wait gives up after `spin` polls; the final waits
+  // for copies and MMAs already issued keep the full limit
+  long long withhold;
+  long long spin;
 };
 
-__device__ __forceinline__ bool wait_bar2(Smem2& sm, void* bar, uint32_t parity, int* status) {
+__device__ __forceinline__ bool wait_bar2(Smem2& sm, void* bar, uint32_t parity, int* status, long long limit) {
   long long it = 0;
   while (!mbar_try(bar, parity)) {
-    if (++it > kSpinLimit || *(volatile int*)&sm.abort) {
-      if (it > kSpinLimit) { atomicOr(status, kStatusTimeout); sm.abort = 1; }
+    if (++it > limit || *(volatile int*)&sm.abort) {
+      if (it > limit) { atomicOr(status, kStatusTimeout); sm.abort = 1; }
       return false;
     }
     if (it > 64) __nanosleep(64);
@@ -623,6 +629,8 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
     // from each of the two MMA threads; accempty: every epilogue thread
     for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], 1); mbar_init(&sm.empty[s], 2); }
     for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 2); mbar_init(&sm.accempty[b], kEpi2 * 32); }
+    mbar_init(&sm.mmadone[0], 1);
+    mbar_init(&sm.mmadone[1], 1);
     sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -645,7 +653,8 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
       for (long long u = u0; u < u1; ++u) {
         const int it = (int)(u - u0);
         const int s = it % kStages;
-        if (!wait_bar2(sm, &sm.empty[s], ((it / kStages) & 1) ^ 1, a.status)) break;
+        if (!wait_bar2(sm, &sm.empty[s], ((it / kStages) & 1) ^ 1, a.status, a.spin)) break;
+        if (u == a.withhold) break;  // test of the failure path: nothing issued for this stage
         const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
         const int ctile = tile / g.parts, part = tile % g.parts;
         const int c0 = ctile * CT;
@@ -687,8 +696,8 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
       for (long long u = u0; u < u1; ++u) {
         const int it = (int)(u - u0);
         const int s = it % kStages, b = it & 1;
-        if (!wait_bar2(sm, &sm.full[s], (it / kStages) & 1, a.status)) break;
-        if (!wait_bar2(sm, &sm.accempty[b], (it >> 1) & 1, a.status)) break;
+        if (!wait_bar2(sm, &sm.full[s], (it / kStages) & 1, a.status, a.spin)) break;
+        if (!wait_bar2(sm, &sm.accempty[b], (it >> 1) & 1, a.status, a.spin)) break;
         tc_fence_after();
         const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
         const int c0 = (tile / g.parts) * CT;
@@ -721,11 +730,14 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
         umma_commit(&sm.empty[s]);
         last = u;
       }
+      // before the accumulators are freed, every MMA this thread issued must
+      // have completed (its own barrier: after an abort the other thread may
+      // not have committed the same units)
       if (last >= 0) {
-        const int it = (int)(last - u0);
+        umma_commit(&sm.mmadone[mgrp]);
         long long spins = 0;
-        while (!mbar_try(&sm.empty[it % kStages], (it / kStages) & 1) && ++spins < kSpinLimit) __nanosleep(64);
-        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);  // copies or MMAs may still be in flight
+        while (!mbar_try(&sm.mmadone[mgrp], 0) && ++spins < kSpinLimit) __nanosleep(64);
+        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);  // MMAs may still be in flight
       }
     }
     __syncwarp();
@@ -762,7 +774,7 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
                                       2 * kBigTile) + cl)
                               : 0;
       const int es = __ldg(a.e_small + kc * g.parts + tile % g.parts);
-      if (!__all_sync(0xffffffffu, wait_bar2(sm, &sm.accfull[b], (it >> 1) & 1, a.status))) break;
+      if (!__all_sync(0xffffffffu, wait_bar2(sm, &sm.accfull[b], (it >> 1) & 1, a.status, a.spin))) break;
       tc_fence_after();
       const float sc = pow2f(scale_from_field(ec) + es - 14);
       const uint32_t buf = lane_addr + b * kAccCols + my_cols;
@@ -1086,7 +1098,8 @@ cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& pl_la
     ++*launches;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  Split2Args args{g, pl, qu, pl_layout.cpt_stride, qs, small, e_small, part, l.status};
+  Split2Args args{g, pl, qu, pl_layout.cpt_stride, qs, small, e_small, part, l.status,
+                  l.withhold, l.spin_limit > 0 ? l.spin_limit : kSpinLimit};
   if (l.ev_begin) cudaEventRecord(l.ev_begin, s);
   split_main2<<<h.G, kThreads2, sizeof(Smem2), s>>>(args);
   if (l.ev_end) cudaEventRecord(l.ev_end, s);

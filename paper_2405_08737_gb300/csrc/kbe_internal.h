@@ -111,6 +111,9 @@ struct kbe_ctx {
   const void* planes_L = nullptr;
   const void* planes_R = nullptr;
   int planes_rows = 0;
+  // failure-path test of the next split contraction (kbe_debug_withhold_split)
+  long long dbg_withhold = -1;
+  long long dbg_spin = 0;
   int* d_status = nullptr;
   size_t part_bytes = 0;
   // reverse-mode workspace, allocated by the first adjoint call that needs it
@@ -221,6 +224,8 @@ struct SplitLaunch {
   int* status;
   cudaEvent_t ev_begin = nullptr;
   cudaEvent_t ev_end = nullptr;
+  long long withhold = -1;   // failure-path test (kbe_debug_withhold_split): unit never supplied
+  long long spin_limit = 0;  // polls of a work wait before it gives up (0: the default)
 };
 bool split_geometry(int M, int n, SplitGeomHost* h);
 size_t split_workspace_bytes(int M, int n_max);

@@ -39,6 +39,53 @@ def _inner(a, b):
     return float(np.real(np.vdot(np.asarray(a).ravel(), np.asarray(b).ravel())))
 
 
+def _rss(a, b):
+    """Root-sum-square of the terms of Re <a, b>: the size of an inner product
+    of random directions, against which its rounding is measured."""
+    return float(np.linalg.norm(np.real(np.conj(np.asarray(a)) * np.asarray(b))))
+
+
+def _oracle_vjp(t, order, n, L, R, Sl, Sg, dI, row_lo):
+    """The exact vector-Jacobian product of the oracle's slice, written out
+    as the transpose of its real-linear maps.  The slice is linear in the
+    self-energy row at fixed G and linear in (L, R) at fixed Sigma (both
+    terms of Eq. KBE2 are products of one Sigma factor and one G factor), so
+    the image of each real basis direction e is the oracle's slice with e in
+    place of that argument and the other one kept; the cotangent of the
+    coordinate is Re <dI, slice(e)> (PyTorch convention: zbar = dF/dRe z +
+    i dF/dIm z).  R(r,r) = -i 1 is fixed and gets none."""
+    base = W.tri_size(row_lo)
+    zL, zS = np.zeros_like(L), np.zeros_like(Sl)
+
+    def pull(fn, shape, skip=()):
+        out = np.zeros(shape, np.complex128)
+        flat = out.reshape(-1)
+        per = int(np.prod(shape[1:]))
+        for j in range(flat.size):
+            if j // per in skip:
+                continue
+            for unit, to in ((1.0, 1.0), (1j, 1j)):
+                e = np.zeros(shape, np.complex128)
+                e.reshape(-1)[j] = unit
+                flat[j] += to * _inner(dI, fn(e))
+        return out
+
+    dSl = pull(lambda e: oracle.history_slice(t, order, n, L, R, e, zS), Sl.shape)
+    dSg = pull(lambda e: oracle.history_slice(t, order, n, L, R, zS, e), Sg.shape)
+
+    def rows(e_rows, which):
+        e = np.zeros_like(L)
+        e[base:] = e_rows
+        return oracle.history_slice(t, order, n, e, zL, Sl, Sg) if which == "L" else \
+            oracle.history_slice(t, order, n, zL, e, Sl, Sg)
+
+    shape = (L.shape[0] - base,) + L.shape[1:]
+    diag = {W.tri_index(r, r) - base for r in range(row_lo, n + 1)}
+    dL = pull(lambda e: rows(e, "L"), shape)
+    dR = pull(lambda e: rows(e, "R"), shape, skip=diag)
+    return dSl, dSg, dL, dR
+
+
 def _cplx(rng, shape):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 
@@ -74,9 +121,10 @@ def test_adjoint_slice_dot_products(kbe, M, n_t, n, row_lo):
     for trial in range(3):
         # self-energy direction
         eSl, eSg = _cplx(rng, Sl.shape), _cplx(rng, Sg.shape)
-        lhs = _inner(dI, oracle.history_slice(t, order, n, L, R, eSl, eSg))
+        y = oracle.history_slice(t, order, n, L, R, eSl, eSg)
+        lhs = _inner(dI, y)
         rhs = _inner(dSl, eSl) + _inner(dSg, eSg)
-        assert abs(lhs - rhs) <= 1e-12 * (np.abs(dI).sum() * np.abs(I0).max() + abs(lhs)), (trial, lhs, rhs)
+        assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + _rss(dI, y)), (trial, lhs, rhs)
         # G direction on rows row_lo..n (R(r,r) fixed)
         eL = np.zeros_like(L)
         eR = np.zeros_like(R)
@@ -84,13 +132,44 @@ def test_adjoint_slice_dot_products(kbe, M, n_t, n, row_lo):
         eR[base:] = _cplx(rng, eR[base:].shape)
         for r in range(row_lo, n + 1):
             eR[W.tri_index(r, r)] = 0
-        dIg = oracle.history_slice(t, order, n, L + eL, R + eR, Sl, Sg) - I0
+        # the slice is linear in (L, R) at fixed Sigma: evaluate the direction itself
+        dIg = oracle.history_slice(t, order, n, eL, eR, Sl, Sg)
         lhs = _inner(dI, dIg)
         rhs = _inner(dL, eL[base:]) + _inner(dR, eR[base:])
-        assert abs(lhs - rhs) <= 1e-12 * (np.abs(dI).sum() * np.abs(I0).max() + abs(lhs)), (trial, lhs, rhs)
+        assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + _rss(dI, dIg)), (trial, lhs, rhs)
     # the diagonal blocks of R get no cotangent, rows below row_lo are not formed
     for r in range(row_lo, n + 1):
         assert not np.any(dR[W.tri_index(r, r) - base])
+    ctx.close()
+
+
+@pytest.mark.parametrize("M,n,row_lo", [(1, 4, 0), (2, 5, 0), (3, 6, 2), (2, 6, 6)])
+def test_adjoint_slice_elementwise_against_oracle_transpose(kbe, M, n, row_lo):
+    """Every entry of the Sigma-row and history cotangents of
+    kbe_adjoint_slice equals the oracle's exact vector-Jacobian product
+    (the transpose of its slice, built column by column from basis
+    directions) to 1e-12 of the largest entry."""
+    import torch
+    n_t = n + 3
+    rng = np.random.default_rng(1000 + 10 * M + n)
+    t, order = W.grid(n_t, 0.05, 0.4, 50 + M + n)
+    L, R = W.random_triangles(M, n + 1, 60 + M + n)
+    Sl, Sg = W.random_rows(M, n, 70 + M + n)
+    dI = _cplx(rng, (2, n + 1, M, M))
+    ctx = _ctx(kbe, M, n_t, t, order, W.goe_h(M, 1), np.ones(M))
+    base = W.tri_size(row_lo)
+    nblk = W.tri_size(n + 1) - base
+    dSl = torch.zeros((n + 1, M, M), dtype=torch.complex128, device="cuda")
+    dSg = torch.zeros_like(dSl)
+    dL = torch.zeros((nblk, M, M), dtype=torch.complex128, device="cuda")
+    dR = torch.zeros_like(dL)
+    ctx.adjoint_slice(n, _dev(L), _dev(R), _dev(Sl), _dev(Sg), _dev(dI), dSl, dSg, dL, dR, row_lo)
+    ctx.sync_status()
+    got = [x.cpu().numpy() for x in (dSl, dSg, dL, dR)]
+    ref = _oracle_vjp(t, order, n, L, R, Sl, Sg, dI, row_lo)
+    for name, a, b in zip(("dS<", "dS>", "dL", "dR"), got, ref):
+        err = np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+        assert err < 1e-12, (name, err)
     ctx.close()
 
 

@@ -7,9 +7,13 @@ difference of two values that agree to about rtol, so its relative
 precision is about eps / rtol; each step factor inherits that, and the
 deviations add up along the run.  Two correct evaluations therefore place
 the points apart by up to about n eps / rtol of t after n steps; the test
-allows 10 n eps / rtol (``_t_tol``), and the rows the solution's change
-over that distance.  Arithmetic: the oracle replaying the device's accepted
-points and orders gives the device's rows within 1e-12."""
+allows 10 n eps / rtol (``_t_tol``).  The rows may then differ by what the
+solution changes over the measured shift of their two time arguments:
+the run's largest |dG/dt| (divided differences of the oracle's rows along
+both arguments) times the measured drift of the points, with a factor 4
+for the curvature between grid points, plus 1e-12 of the rows for the
+arithmetic (``_row_bound``).  Arithmetic: the oracle replaying the device's
+accepted points and orders gives the device's rows within 1e-12."""
 import numpy as np
 import pytest
 
@@ -38,6 +42,26 @@ def _rel(a, b):
 def _t_tol(n, rtol):
     """Relative bound on the drift of the accepted points after n steps."""
     return 10.0 * n * np.finfo(float).eps / rtol
+
+
+def _row_bound(L, t, t_other):
+    """Absolute bound on |L_gpu - L_oracle| implied by the shift of the
+    accepted points between the two runs (t: the oracle's, t_other: the
+    device's): 4 x max |dG/dt| over both time arguments x the largest shift
+    of a point, twice (both arguments of a block move), plus 1e-12 of the
+    rows."""
+    n = len(t)
+    drift = float(np.abs(np.asarray(t_other) - np.asarray(t)).max())
+    dmax = 0.0
+    for j in range(1, n):
+        p, q = W.tri_size(j), W.tri_size(j - 1)
+        dt = t[j] - t[j - 1]
+        # along the first argument: (j, c) against (j-1, c), c < j
+        dmax = max(dmax, float(np.abs(L[p:p + j] - L[q:q + j]).max()) / dt)
+        # along the second argument: (j, c) against (j, c-1), c = 1..j
+        dc = np.diff(t[: j + 1])
+        dmax = max(dmax, float((np.abs(L[p + 1:p + j + 1] - L[p:p + j]).max(axis=(1, 2)) / dc).max()))
+    return 4.0 * 2.0 * dmax * drift + 1e-12 * float(np.abs(L).max()), drift, dmax
 
 
 CASES = {  # name: (M, kind, U, dense, pulse, rtol, t_end, K_sel)
@@ -83,7 +107,10 @@ def test_controlled_run_matches_oracle(kbe, name):
     assert g["q"].max() >= 3 and g["stats"][4] > 0
     p = W.tri_size(o["n"])
     Lg, Rg = g["L"][:p].cpu().numpy(), g["R"][:p].cpu().numpy()
-    assert _rel(Lg, o["L"]) < 10 * tt and _rel(Rg, o["R"]) < 10 * tt
+    for name, a, b in (("L", Lg, o["L"]), ("R", Rg, o["R"])):
+        bound, drift, dmax = _row_bound(b, o["t"], g["t"])
+        err = float(np.abs(a - b).max())
+        assert err <= bound, (name, err, bound, drift, dmax)
     # the oracle on the device's accepted points and orders: the same rows
     h, Uv, U4, v, pulse = _model(M, kind, U, dense, pulse_on)
     r = oracle.run_controlled(h, None if dense else Uv, v, pulse, W.half_filled_rho(h), rtol, rtol * 1e-2, 0.01,

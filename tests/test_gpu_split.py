@@ -210,3 +210,34 @@ def test_split_plane_cache_is_exact(kbe, name, n_t):
     assert torch.equal(runs[0].L, runs[1].L) and torch.equal(runs[0].R, runs[1].R)
     for r in runs:
         r.ctx.close()
+
+
+def test_split_wait_timeout_is_reported_and_the_context_recovers(kbe):
+    """The device-side failure path of the contraction's pipeline, with no
+    fault: one work unit's copies are withheld (kbe_debug_withhold_split)
+    and the waits give up after 4096 polls.  The launch returns, the
+    status reads KBE_ETIMEOUT, and the next slice on the same context is
+    correct again."""
+    import torch
+    M, n_t = 8, 200
+    n = n_t - 1
+    t, order, h, L, R = _case(M, n_t, 31, "free")
+    Sl, Sg = oracle.sigma_row(oracle.local_U4(np.ones(M)), n, L, R)
+    ref = oracle.history_slice(t, order, n, L, R, Sl, Sg, nthreads=oracle.threads_available())
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, np.ones(M), W.site_potential(M), None)
+    Ld, Rd, Sld, Sgd = _dev(L), _dev(R), _dev(Sl), _dev(Sg)
+    out = torch.zeros((2, n + 1, M, M), dtype=torch.complex128, device="cuda")
+    ctx.history_slice(n, Ld, Rd, Sld, Sgd, out, precision="split")  # planes allocated, kernels loaded
+    ctx.sync_status()
+    ctx.debug_withhold_split(3, 4096)
+    ctx.history_slice(n, Ld, Rd, Sld, Sgd, out, precision="split")
+    with pytest.raises(kbe.KBEError) as e:
+        ctx.sync_status()
+    assert e.value.status == kbe.KBE_ETIMEOUT
+    out.fill_(float("nan"))
+    ctx.history_slice(n, Ld, Rd, Sld, Sgd, out, precision="split")
+    ctx.sync_status()
+    assert _rel(out.cpu().numpy(), ref) < TOL_SPLIT
+    ctx.close()
