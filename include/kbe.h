@@ -428,6 +428,20 @@ kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts
                               void* S_less, void* S_great, void* I_work, void* F_ring, double* t_out,
                               int* q_out, int* korder_out, int* n_rows, int* stats, void* stream);
 
+/* Storage of the split-precision contraction (KBE_SPLIT_BF16).  keep = 1
+ * (the default): the first split slice allocates a buffer of the history's
+ * digit planes (about twice the two triangles: 32 n_max^2 norb^2 bytes),
+ * an encoder kernel fills it and the contraction streams it; during
+ * kbe_step the planes of rows below the step's row are kept between steps
+ * and only the new rows' entries are encoded again.  keep = 0: no plane
+ * buffer (an existing one is freed, after a device synchronisation); every
+ * split slice runs one persistent contraction that converts the FP64
+ * history entries into digit planes inside the kernel, the form the batched
+ * steps use.  Both give the same results to rounding (the same digits and
+ * sums; partial sums are grouped differently).  KBE_EINVAL unless keep is 0
+ * or 1. */
+kbe_status kbe_set_split_planes(kbe_ctx* ctx, int keep);
+
 /* Forget per-history state kept between steps (the split path's digit
  * planes); the next step encodes every row again.  No GPU work. */
 kbe_status kbe_reset_cache(kbe_ctx* ctx);
@@ -494,14 +508,17 @@ kbe_status kbe_batch_bind(kbe_batch* b, int i, void* L, void* R, void* S_less, v
  * rows[i] < 1 leaves system i untouched, rows[i] >= n_t_i is KBE_ERANGE.
  * The graph of the step is captured on the first call and reused while P,
  * precision and the tile policy stay the same (KBE_SPLIT_BF16 graphs also
- * depend on the rows and are re-captured when they change).  KBE_SPLIT_BF16
- * steps run system by system within the graph and encode each system's
- * digit planes into one buffer held by the batch,
- * the size of the largest active system's planes (about twice its two
- * triangles), allocated by the first split step that needs it; if that
- * allocation fails, the contraction converts its operands itself (slower,
- * same results).  Results agree
- * with kbe_step to rounding (the history sum is chunked differently).
+ * depend on the rows and are re-captured when they change).  With
+ * KBE_SPLIT_BF16 every sweep contracts all active systems in ONE persistent
+ * tensor-core launch over a work list of (system, column tile, history
+ * chunk) units, split into contiguous ranges of about equal cost, one per
+ * SM; the kernel converts each unit's FP64 history entries into digit
+ * planes itself (no plane buffer), then a reduction launch adds the partial
+ * sums and the band term of every system's columns.  The work list (a few
+ * KB to MB) and the partial sums are held by the batch, allocated by the
+ * first split step that needs them (KBE_ENOMEM if that fails), and the work
+ * list is uploaded on `stream` when the rows change.  Results agree with
+ * kbe_step to rounding (the history sum is chunked differently).
  * precision: KBE_FP64, KBE_SPLIT_BF16 or KBE_DF64 (each system's
  * double-float slice in its own context's workspace, graph re-captured
  * when the rows change, like KBE_SPLIT_BF16). */

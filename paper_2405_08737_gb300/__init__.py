@@ -63,6 +63,7 @@ def lib():
         L.kbe_rhs_row.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_init_uncorrelated.argtypes = [vp, vp, vp, vp, vp]
         L.kbe_debug_withhold_split.argtypes = [vp, ctypes.c_longlong, ctypes.c_longlong]
+        L.kbe_set_split_planes.argtypes = [vp, i]
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
         L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -400,6 +401,10 @@ class Context:
         n = n_rows.value
         return {"t": t[:n], "q": q[:n], "korder": ko[:n], "n": n, "stats": tuple(int(x) for x in stats),
                 "L": L, "R": R, "status": int(st)}
+
+    def set_split_planes(self, keep):
+        """kbe_set_split_planes: keep (True) or drop (False) the digit-plane cache of the split path."""
+        self._check(lib().kbe_set_split_planes(self._h, 1 if keep else 0))
 
     def debug_withhold_split(self, unit, spin_limit):
         """Failure-path test of the next split contraction (kbe_debug_withhold_split)."""

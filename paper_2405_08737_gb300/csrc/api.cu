@@ -127,7 +127,7 @@ kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void
     SplitLaunch l{ctx->M, n, (const double*)L, (const double*)R, (const double*)Sl, (const double*)Sg,
                   weights_view(ctx), (double*)I_out, ctx->d_split, ctx->split_bytes, ctx->d_status};
     if (!next_events(ctx, &l.ev_begin, &l.ev_end)) return fail(ctx, KBE_ECUDA, "profiling: cudaEventCreate");
-    if (!ctx->d_planes && !ctx->planes_failed) {
+    if (ctx->split_planes && !ctx->d_planes && !ctx->planes_failed) {
       SplitPlanes lay;
       if (!split_planes_layout(ctx->M, ctx->n_max, &lay) || cudaMalloc(&ctx->d_planes, lay.bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -144,7 +144,7 @@ kbe_status history(kbe_ctx* ctx, int n, int precision, const void* L, const void
     ctx->dbg_withhold = -1;  // one launch only
     ctx->dbg_spin = 0;
     cudaError_t e;
-    if (ctx->d_planes) {
+    if (ctx->split_planes && ctx->d_planes) {
       int r0 = 0;
       if (stepping && ctx->planes_L == L && ctx->planes_R == R && ctx->planes_rows <= n) r0 = ctx->planes_rows;
       e = launch_history_split2(l, ctx->planes_layout, ctx->d_planes, r0, s, launches);
@@ -911,6 +911,23 @@ kbe_status kbe_history_slice_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, c
   cudaError_t e = launch_history_f64(a, (cudaStream_t)stream, &nl);
   ctx->last_launches = nl;
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_history_slice_band: launch");
+}
+
+kbe_status kbe_set_split_planes(kbe_ctx* ctx, int keep) {
+  if (!ctx) return KBE_EINVAL;
+  if (keep != 0 && keep != 1) return fail(ctx, KBE_EINVAL, "kbe_set_split_planes: keep must be 0 or 1");
+  ctx->split_planes = keep != 0;
+  if (!keep && ctx->d_planes) {
+    if (use_device(ctx) == KBE_OK) {
+      cudaDeviceSynchronize();  // no launch may still read the buffer
+      cudaFree(ctx->d_planes);
+    }
+    ctx->d_planes = nullptr;
+  }
+  ctx->planes_L = ctx->planes_R = nullptr;
+  ctx->planes_rows = 0;
+  ctx->planes_failed = false;
+  return KBE_OK;
 }
 
 kbe_status kbe_debug_withhold_split(kbe_ctx* ctx, long long unit, long long spin_limit) {

@@ -278,14 +278,14 @@ struct kbe_batch {
   std::vector<int> g_rows;
   int g_count = 0;               // kernels in the step graph
   int last_launches = 0;
-  // split precision: digit planes of one system at a time (the largest
-  // active system's size), encoded in full for every system and sweep
-  void* d_planes = nullptr;
-  size_t planes_bytes = 0;
-  bool planes_failed = false;    // allocation failed: the contraction converts its own operands
-  // split steps run system by system: rows vectors with one active system each
-  int* d_rows1 = nullptr;        // [n_sys][n_sys]
-  std::vector<int> rows1;
+  // split precision: the work list of the fused contraction over every
+  // active system (host plan, its device image) and the partial sums
+  FusedPlanHost fplan;
+  std::vector<unsigned char> fplan_up;   // the image on the device
+  void* d_fplan = nullptr;
+  size_t fplan_bytes = 0;
+  double* d_fpart = nullptr;
+  size_t fpart_bytes = 0;
 };
 
 namespace {
@@ -307,54 +307,10 @@ void drop_graph(kbe_batch* b) {
 }
 
 
-// Split precision with the plane buffer: the whole step of one system after
-// the other (plan, predictor, P x {self-energy, encoder + contraction, Fock,
-// RHS, corrector}), so that the system's digit planes stay in the buffer
-// between its sweeps and the later sweeps re-encode only the units that
-// touch its new row.
-cudaError_t enqueue_split_by_system(kbe_batch* b, int P, const int* rows_host, cudaStream_t s, int* count) {
-  int nl = 0;
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < b->n_sys && e == cudaSuccess; ++i) {
-    const int n = rows_host[i];
-    const kbe_ctx* c = b->ctx[i];
-    if (n < 1 || n >= c->grid.n_t) continue;
-    BatchDev d = b->dev;
-    d.rows = b->d_rows1 + (size_t)i * b->n_sys;
-    const BatchSys& y = b->sys[i];
-    SplitPlanes lay;
-    const bool planes = split_planes_layout(y.M, c->n_max, &lay) && lay.bytes <= b->planes_bytes;
-    batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
-    batch_rows<kOpPredictor><<<sm_count() * 8, 256, 0, s>>>(d);
-    nl += 2;
-    e = cudaGetLastError();
-    for (int it = 0; it < P && e == cudaSuccess; ++it) {
-      batch_rows<kOpSigma><<<sm_count() * 8, 256, 0, s>>>(d);
-      ++nl;
-      SplitLaunch l{y.M, n, y.L, y.R, y.Sl, y.Sg, WeightsView{y.wbar, y.band, y.band_w}, y.I, c->d_split,
-                    c->split_bytes, d.status};
-      int k = 0;
-      if (planes)  // rows < n are final after the first sweep's encoding
-        e = launch_history_split2(l, lay, b->d_planes, it == 0 ? 0 : n, s, &k);
-      else
-        e = launch_history_split(l, s, &k);
-      nl += k;
-      if (e != cudaSuccess) break;
-      batch_fock<<<b->n_sys, 256, 0, s>>>(d);
-      batch_rows<kOpRhs><<<sm_count() * 8, 256, 0, s>>>(d);
-      batch_rows<kOpCorrector><<<sm_count() * 8, 256, 0, s>>>(d);
-      nl += 3;
-      e = cudaGetLastError();
-    }
-  }
-  *count = nl;
-  return e;
-}
-
 // Enqueue one batched step (rows already on the device).  Split precision
-// launches each system's tensor-core slice (host rows needed).
+// runs the fused contraction over the work list built from the host rows
+// (its image already uploaded).
 cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_host, cudaStream_t s, int* count) {
-  if (precision == KBE_SPLIT_BF16 && b->d_planes && b->d_rows1) return enqueue_split_by_system(b, P, rows_host, s, count);
   BatchDev d = b->dev;
   int nl = 0;
   batch_plan<<<1, 256, (size_t)b->n_sys * 24, s>>>(d);
@@ -385,22 +341,10 @@ cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_hos
         e = launch_history_df(a, s, &k);
         nl += k;
       }
-    } else {
-      for (int i = 0; i < b->n_sys && e == cudaSuccess; ++i) {
-        const int n = rows_host[i];
-        const kbe_ctx* c = b->ctx[i];
-        if (n < 1 || n >= c->grid.n_t) continue;
-        const BatchSys& y = b->sys[i];
-        SplitLaunch l{y.M, n, y.L, y.R, y.Sl, y.Sg, WeightsView{y.wbar, y.band, y.band_w}, y.I, c->d_split,
-                      c->split_bytes, d.status};
-        int k = 0;
-        SplitPlanes lay;
-        if (b->d_planes && split_planes_layout(y.M, c->n_max, &lay) && lay.bytes <= b->planes_bytes)
-          e = launch_history_split2(l, lay, b->d_planes, 0, s, &k);  // encoder + bulk-copy-fed contraction
-        else
-          e = launch_history_split(l, s, &k);
-        nl += k;
-      }
+    } else {  // one persistent tensor-core contraction over every active system's units
+      int k = 0;
+      e = launch_history_fused(b->fplan, b->d_fplan, b->d_fpart, d.status, s, &k);
+      nl += k;
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     batch_fock<<<b->n_sys, 256, 0, s>>>(d);
@@ -542,8 +486,8 @@ kbe_status kbe_batch_destroy(kbe_batch* b) {
   cudaFree(b->d_mem);
   cudaFree(b->d_order);
   cudaFree(b->d_field);
-  cudaFree(b->d_planes);
-  cudaFree(b->d_rows1);
+  cudaFree(b->d_fplan);
+  cudaFree(b->d_fpart);
   delete b;
   return KBE_OK;
 }
@@ -565,6 +509,7 @@ kbe_status kbe_batch_bind(kbe_batch* b, int i, void* L, void* R, void* S_less, v
   b->bound[i] = 1;
   b->dirty = true;
   drop_graph(b);  // split graphs hold the pointers
+  b->g_rows.clear();  // and so does the split work list: rebuild it
   return KBE_OK;
 }
 
@@ -611,38 +556,51 @@ kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, v
   const bool same_rows = precision == KBE_FP64 ||
                          ((int)b->g_rows.size() == b->n_sys && std::equal(b->g_rows.begin(), b->g_rows.end(), rows));
   if (precision == KBE_SPLIT_BF16 && (e = split_prepare()) != cudaSuccess) return bcuda(b, e, "kbe_batch_step: split setup");
-  if (precision == KBE_SPLIT_BF16 && !b->planes_failed) {  // plane buffer, before any capture
-    size_t need = 0;
+  if (precision == KBE_SPLIT_BF16 && !same_rows) {  // the work list of these rows, before any capture
+    std::vector<FusedSystem> fs;
     for (int i = 0; i < b->n_sys; ++i) {
-      SplitPlanes lay;
-      if (rows[i] >= 1 && split_planes_layout(b->ctx[i]->M, b->ctx[i]->n_max, &lay)) need = std::max(need, lay.bytes);
+      if (rows[i] < 1) continue;
+      const BatchSys& y = b->sys[i];
+      fs.push_back(FusedSystem{y.M, rows[i], y.L, y.R, y.Sl, y.Sg, WeightsView{y.wbar, y.band, y.band_w}, y.I,
+                               b->ctx[i]->d_split});
     }
-    if (!b->d_rows1) {
-      if (cudaMalloc(&b->d_rows1, sizeof(int) * (size_t)b->n_sys * b->n_sys) != cudaSuccess) {
-        cudaGetLastError();
-        b->d_rows1 = nullptr;
+    if (fs.empty()) {
+      b->fplan = FusedPlanHost{};
+    } else {
+      if (!fused_build(fs.data(), (int)fs.size(), &b->fplan))
+        return bfail(b, KBE_EINVAL, "kbe_batch_step: split work list");
+      const size_t need_plan = b->fplan.image.size(), need_part = fused_part_bytes(b->fplan);
+      if (need_plan > b->fplan_bytes || need_part > b->fpart_bytes) {
+        drop_graph(b);  // the graph holds the buffers' addresses
+        if (need_plan > b->fplan_bytes) {
+          cudaFree(b->d_fplan);
+          b->d_fplan = nullptr;
+          b->fplan_bytes = 0;
+          b->fplan_up.clear();
+          if ((e = cudaMalloc(&b->d_fplan, need_plan)) != cudaSuccess) {
+            b->d_fplan = nullptr;
+            return bfail(b, KBE_ENOMEM, "kbe_batch_step: split work list buffer");
+          }
+          b->fplan_bytes = need_plan;
+        }
+        if (need_part > b->fpart_bytes) {
+          cudaFree(b->d_fpart);
+          b->d_fpart = nullptr;
+          b->fpart_bytes = 0;
+          if ((e = cudaMalloc(&b->d_fpart, need_part)) != cudaSuccess) {
+            b->d_fpart = nullptr;
+            return bfail(b, KBE_ENOMEM, "kbe_batch_step: split partial sums");
+          }
+          b->fpart_bytes = need_part;
+        }
+      }
+      if (b->fplan.image != b->fplan_up) {  // stream-ordered after the steps already queued
+        if ((e = cudaMemcpyAsync(b->d_fplan, b->fplan.image.data(), b->fplan.image.size(), cudaMemcpyHostToDevice,
+                                 s)) != cudaSuccess)
+          return bcuda(b, e, "kbe_batch_step: split work list upload");
+        b->fplan_up = b->fplan.image;
       }
     }
-    if (need > b->planes_bytes) {
-      drop_graph(b);  // the graph holds the buffer's address
-      cudaFree(b->d_planes);
-      b->d_planes = nullptr;
-      b->planes_bytes = 0;
-      if (cudaMalloc(&b->d_planes, need) != cudaSuccess) {
-        cudaGetLastError();
-        b->d_planes = nullptr;
-        b->planes_failed = true;
-      } else {
-        b->planes_bytes = need;
-      }
-    }
-  }
-  if (precision == KBE_SPLIT_BF16 && b->d_rows1) {  // one active system per rows vector
-    b->rows1.assign((size_t)b->n_sys * b->n_sys, -1);
-    for (int i = 0; i < b->n_sys; ++i) b->rows1[(size_t)i * b->n_sys + i] = rows[i];
-    if ((e = cudaMemcpyAsync(b->d_rows1, b->rows1.data(), sizeof(int) * b->rows1.size(), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
-      return bcuda(b, e, "kbe_batch_step: rows upload");
   }
   if (!b->graph || b->g_P != P || b->g_prec != precision || b->g_block != b->dev.block ||
       b->g_work != b->dev.item_work_log2 || !same_rows) {

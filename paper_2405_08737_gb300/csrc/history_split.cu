@@ -46,10 +46,7 @@ namespace {
 
 using namespace split;
 
-constexpr int kConvWarps = 8;
-constexpr int kEpiWarps = 4;
-constexpr int kThreads = (kEpiWarps + 1 + kConvWarps) * 32;  // 416
-constexpr int kConvThreads = kConvWarps * 32;
+constexpr int kConvThreads = 256;        // threads that convert FP64 history rows into digit planes
 constexpr int kKC = 16;                     // complex K entries per chunk (32 real)
 constexpr int kNS = 16;                     // small-operand columns per slice: 8 a x (re, im)
 constexpr int kNA = 8;                      // a values per part
@@ -57,13 +54,13 @@ constexpr int kBigSlice = 128 * 2 * kKC * 2;          // bytes of one digit plan
 constexpr int kBigTile = kSlices * kBigSlice;         // 32 KB
 constexpr int kSmallVar = 4 * kSlices * 2 * 128;      // 4 kgroups x 4 slices x 2 colgroups x 128 B = 4 KB
 constexpr int kSmallBytes = 3 * kSmallVar;            // 12 KB
-constexpr int kStageBytes = 3 * kBigTile + kSmallBytes + 512;  // + column exponents
 constexpr int kStages = 2;
 constexpr int kGroupCols = kLevels * kNS;   // 5 levels x 16 columns
 constexpr int kAccCols = 2 * kGroupCols;    // groups I^< and I^>: 160 columns
 constexpr int kTmemCols = 512;              // two accumulator buffers (320 used)
 constexpr long long kSpinLimit = 1ll << 26; // bounded waits
 constexpr int kMaxSplitCtas = 160;          // persistent CTAs of a contraction, at most
+constexpr int kSlotComplex = 2 * 128 * 8;   // one partial slot: [group][c_l][a_l < 8][b], CT M <= 128
 
 struct SplitGeom {
   int M, MM, n;
@@ -77,28 +74,17 @@ struct SplitGeom {
   int band_w;      // composite-weight band width (K+1)
 };
 
-struct SplitArgs {
-  SplitGeom g;
-  const double* L;
-  const double* R;
-  const uint8_t* small;   // [cpt][parts][12288 B]
-  const int* e_small;     // [cpt][parts]
-  double* part;           // [G][S][2][CT][8][M] complex
-  int* status;
-};
-
 // ---------------------------------------------------------------- prep ---
 // Small operands of chunk kc, part p: A1, NB^<, NBD as bf16 digit planes in
 // the shared-memory layout [variant][kgroup 4][slice 4][colgroup 2][8][8],
 // entries B[(a, q_out)][(kappa, q_in)] of the real form of P z:
 //   (re,re) = P.re, (re,im) = -P.im, (im,re) = P.im, (im,im) = P.re.
-__global__ void __launch_bounds__(256) split_prep(int M, int n, int parts, const double* __restrict__ Sl,
-                                                  const double* __restrict__ Sg, WeightsView w,
-                                                  uint8_t* __restrict__ small, int* __restrict__ e_small) {
-  const int kc = blockIdx.x, p = blockIdx.y;
+__device__ __forceinline__ void prep_chunk(int M, int n, int parts, const double* __restrict__ Sl,
+                                           const double* __restrict__ Sg, const WeightsView& w,
+                                           uint8_t* __restrict__ small, int* __restrict__ e_small, int kc, int p,
+                                           int* s_ef) {
   const int MM = M * M;
-  __shared__ int s_ef;
-  if (threadIdx.x == 0) s_ef = 0;
+  if (threadIdx.x == 0) *s_ef = 0;
   __syncthreads();
   // 3 variants x 16 kappa x 8 a: 384 complex values, 2 per thread (256 threads -> 512 slots)
   double vr[2], vi[2];
@@ -130,9 +116,9 @@ __global__ void __launch_bounds__(256) split_prep(int M, int n, int parts, const
     }
   }
   my_ef = __reduce_max_sync(0xffffffffu, my_ef);
-  if ((threadIdx.x & 31) == 0) atomicMax(&s_ef, my_ef);
+  if ((threadIdx.x & 31) == 0) atomicMax(s_ef, my_ef);
   __syncthreads();
-  const int e = scale_from_field(s_ef);
+  const int e = scale_from_field(*s_ef);
   uint8_t* out = small + ((size_t)kc * parts + p) * kSmallBytes;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -159,15 +145,14 @@ __global__ void __launch_bounds__(256) split_prep(int M, int n, int parts, const
   if (threadIdx.x == 0) e_small[kc * parts + p] = e;
 }
 
-// ---------------------------------------------------------------- main ---
-struct Smem {
-  uint8_t stage[kStages][kStageBytes];
-  uint64_t full[kStages], empty[kStages], accfull[2], accempty[2];
-  int accmeta[2][128];
-  uint32_t tmem;
-  int abort;
-};
+__global__ void __launch_bounds__(256) split_prep(int M, int n, int parts, const double* __restrict__ Sl,
+                                                  const double* __restrict__ Sg, WeightsView w,
+                                                  uint8_t* __restrict__ small, int* __restrict__ e_small) {
+  __shared__ int s_ef;
+  prep_chunk(M, n, parts, Sl, Sg, w, small, e_small, blockIdx.x, blockIdx.y, &s_ef);
+}
 
+// ---------------------------------------------------------------- main ---
 __device__ __forceinline__ long long unit_begin(const SplitGeom& g, int cta) { return g.U * cta / g.G; }
 
 // AND of a predicate over the converter warps (named barrier 1); every
@@ -182,18 +167,6 @@ __device__ __forceinline__ bool conv_all(bool ok) {
   return r != 0;
 }
 
-__device__ __forceinline__ bool wait_bar(Smem& sm, void* bar, uint32_t parity, int* status) {
-  long long it = 0;
-  while (!mbar_try(bar, parity)) {
-    if (++it > kSpinLimit || *(volatile int*)&sm.abort) {
-      if (it > kSpinLimit) { atomicOr(status, kStatusTimeout); sm.abort = 1; }
-      return false;
-    }
-    if (it > 64) __nanosleep(64);
-  }
-  return true;
-}
-
 // Chunk class relative to the tile's column range [c0, c1]: term 2 of the
 // tensor-core part covers m <= c - band_w (QU = Q there, 0 elsewhere).
 // 0: QU = 0 for every (m, c) of the chunk; 1: QU = Q for all; 2: mixed.
@@ -201,264 +174,6 @@ __device__ __forceinline__ int chunk_class(int m_lo, int m_hi, int c0, int c1, i
   if (m_lo > c1 - band_w) return 0;
   if (m_hi <= c0 - band_w) return 1;
   return 2;
-}
-
-__global__ void __launch_bounds__(kThreads, 1) split_main(SplitArgs a) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
-  const SplitGeom& g = a.g;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
-  const long long u0 = unit_begin(g, blockIdx.x), u1 = unit_begin(g, blockIdx.x + 1);
-
-  // zero the digit planes once (rows beyond CT*M are never written later)
-  for (int i = tid; i < kStages * kStageBytes / 16; i += kThreads)
-    reinterpret_cast<uint4*>(smem_raw)[i] = make_uint4(0, 0, 0, 0);
-  if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], kConvThreads); mbar_init(&sm.empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 2); mbar_init(&sm.accempty[b], kEpiWarps * 32); }
-    sm.abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == kEpiWarps) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = sm.tmem;
-
-  if (warp > kEpiWarps) {
-    // ------------------------------------------------------ converters --
-    // Thread ct owns one row j = (c_l, b) of one big operand (arr 0: the
-    // G^< plane from L, arr 1: the Q plane from R) and all 16 K entries of
-    // a chunk: 16 loads in flight, then one 16-byte store per K-group.
-    const int ct = tid - (kEpiWarps + 1) * 32;  // 0..255
-    const int arr = ct >> 7, jrow = ct & 127;
-    const bool row_live = jrow < CT * M;
-    const int cl = row_live ? jrow / M : 0, bb = jrow - cl * M;
-    const double2* base = reinterpret_cast<const double2*>(arr == 0 ? a.L : a.R);
-    for (long long u = u0; u < u1; ++u) {
-      const int it = (int)(u - u0);
-      const int s = it % kStages;
-      if (!conv_all(wait_bar(sm, &sm.empty[s], ((it / kStages) & 1) ^ 1, a.status))) break;
-      uint8_t* st = sm.stage[s];
-      int* ecol = reinterpret_cast<int*>(st + 3 * kBigTile + kSmallBytes);
-      const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
-      const int ctile = tile / g.parts, part = tile % g.parts;
-      const int c0 = ctile * CT;
-      const int kap0 = kc * kKC;
-      const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
-      {  // small operand of (kc, part): 12 KB
-        const uint4* src = reinterpret_cast<const uint4*>(a.small + ((size_t)kc * g.parts + part) * kSmallBytes);
-        uint4* dst = reinterpret_cast<uint4*>(st + 3 * kBigTile);
-        for (int i = ct; i < kSmallBytes / 16; i += kConvThreads) dst[i] = src[i];
-      }
-      if (ct < CT) ecol[ct] = 0;
-      asm volatile("bar.sync 1, %0;" ::"r"(kConvThreads) : "memory");
-      const int c = c0 + cl;
-      const bool col_live = row_live && c <= n;
-      double er[kKC], ei[kKC];
-      unsigned keep = 0;  // bit k: K entry k lies in the tensor-core part of term 2 (m <= c - band_w)
-      int ef = 0;
-      {
-        int m = kap0 / M, x = kap0 - m * M;
-#pragma unroll
-        for (int k = 0; k < kKC; ++k) {
-          double2 z = make_double2(0.0, 0.0);
-          if (col_live && m <= n) {
-            if (m >= c) {
-              z = __ldcs(base + tri(m, c) * MM + x * M + bb);
-            } else {
-              z = __ldcs(base + tri(c, m) * MM + bb * M + x);
-              z.x = -z.x;  // -conj
-            }
-          }
-          er[k] = z.x;
-          ei[k] = z.y;
-          keep |= (unsigned)(m <= c - g.band_w) << k;
-          if (++x == M) { x = 0; ++m; }
-        }
-#pragma unroll
-        for (int k = 0; k < kKC; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
-      }
-      if (row_live && ef > 0) atomicMax(&ecol[cl], ef);
-      asm volatile("bar.sync 1, %0;" ::"r"(kConvThreads) : "memory");
-      if (row_live) {
-        const int e = scale_from_field(ecol[cl]);
-        uint8_t* dst = st + arr * kBigTile;  // PL or Q
-        uint8_t* QU = st + 2 * kBigTile;
-        const bool qu = arr == 1 && cls == 2;
-#pragma unroll
-        for (int kg = 0; kg < 4; ++kg) {
-          uint32_t w[kSlices][4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            uint32_t dr[kSlices], di[kSlices];
-            digits_bf16(fixed31(er[4 * kg + q], e), dr);
-            digits_bf16(fixed31(ei[4 * kg + q], e), di);
-#pragma unroll
-            for (int sl = 0; sl < kSlices; ++sl) w[sl][q] = __byte_perm(dr[sl], di[sl], 0x5410);
-          }
-          const int off = (kg * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
-#pragma unroll
-          for (int sl = 0; sl < kSlices; ++sl) {
-            *reinterpret_cast<uint4*>(dst + sl * kBigSlice + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
-            if (qu) {
-              const unsigned kb = keep >> (4 * kg);
-              *reinterpret_cast<uint4*>(QU + sl * kBigSlice + off) =
-                  make_uint4(kb & 1u ? w[sl][0] : 0u, kb & 2u ? w[sl][1] : 0u, kb & 4u ? w[sl][2] : 0u,
-                             kb & 8u ? w[sl][3] : 0u);
-            }
-          }
-        }
-      }
-      fence_async_smem();
-      mbar_arrive(&sm.full[s]);
-    }
-  } else if (warp == kEpiWarps) {
-    // --------------------------------------------------------- MMA warp --
-    if (lane == 0) {
-      long long last = -1;
-      for (long long u = u0; u < u1; ++u) {
-        const int it = (int)(u - u0);
-        const int s = it % kStages, b = it & 1;
-        if (!wait_bar(sm, &sm.full[s], (it / kStages) & 1, a.status)) break;
-        if (!wait_bar(sm, &sm.accempty[b], (it >> 1) & 1, a.status)) break;
-        tc_fence_after();
-        uint8_t* st = sm.stage[s];
-        const int* ecol = reinterpret_cast<const int*>(st + 3 * kBigTile + kSmallBytes);
-        for (int c = 0; c < CT; ++c) sm.accmeta[b][c] = ecol[c];
-        mbar_arrive(&sm.accfull[b]);  // releases accmeta; the commit below is the second arrival
-        const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
-        const int c0 = (tile / g.parts) * CT;
-        const int kap0 = kc * kKC;
-        const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
-        const uint32_t aPL = smem_u32(st), aQ = smem_u32(st + kBigTile);
-        const uint32_t aQU = cls == 1 ? aQ : smem_u32(st + 2 * kBigTile);
-        const uint32_t bS = smem_u32(st + 3 * kBigTile);
-        const uint32_t dl = tmem + b * kAccCols, dg = dl + kGroupCols;
-        for (int i = 0; i < kSlices; ++i) {
-          // small digits j with i + j <= 4: N = 16 * min(4, 5 - i)
-          const uint32_t idesc = umma_idesc_bf16(kNS * min(kSlices, kLevels - i));
-          for (int kk = 0; kk < 2; ++kk) {
-            const uint32_t ka = (uint32_t)(i * kBigSlice + kk * 2 * 2048);
-            const uint64_t dPL = umma_desc(aPL + ka, 2048, 128);
-            const uint64_t dQ = umma_desc(aQ + ka, 2048, 128);
-            const uint64_t dQU = umma_desc(aQU + ka, 2048, 128);
-            const uint32_t kb = (uint32_t)(kk * 2 * 1024);
-            const uint64_t dA1 = umma_desc(bS + 0 * kSmallVar + kb, 1024, 128);
-            const uint64_t dNl = umma_desc(bS + 1 * kSmallVar + kb, 1024, 128);
-            const uint64_t dNg = umma_desc(bS + 2 * kSmallVar + kb, 1024, 128);
-            umma_bf16(dl + i * kNS, dPL, dA1, idesc, 1);
-            umma_bf16(dg + i * kNS, dQ, dA1, idesc, 1);
-            if (cls != 0) {
-              umma_bf16(dl + i * kNS, dQU, dNl, idesc, 1);
-              umma_bf16(dg + i * kNS, dQU, dNg, idesc, 1);
-            }
-          }
-        }
-        umma_commit(&sm.accfull[b]);
-        umma_commit(&sm.empty[s]);
-        last = u;
-      }
-      // wait for the MMAs still in flight before the accumulators are freed
-      if (last >= 0) {
-        const int it = (int)(last - u0);
-        long long spins = 0;
-        while (!mbar_try(&sm.empty[it % kStages], (it / kStages) & 1) && ++spins < kSpinLimit) __nanosleep(64);
-        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);  // copies or MMAs may still be in flight
-      }
-    }
-    __syncwarp();
-  } else {
-    // --------------------------------------------------------- epilogue --
-    const int j = tid;  // TMEM lane = output row (c_l, b)
-    const int cl = j / M, bb = j - cl * M;
-    const bool live_row = cl < CT;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    // both accumulator buffers start at zero; every drain zeroes its buffer again
-    for (int col = 0; col < 2 * kAccCols; col += 16) tmem_zero16(lane_addr + col);
-    tmem_wait_st();
-    tc_fence_before();
-    mbar_arrive(&sm.accempty[0]);
-    mbar_arrive(&sm.accempty[1]);
-    float run[2][kNS][2];
-#pragma unroll
-    for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-      for (int q = 0; q < kNS; ++q) { run[s2][q][0] = 0.f; run[s2][q][1] = 0.f; }
-    int local_seg = 0;
-    for (long long u = u0; u < u1; ++u) {
-      const int it = (int)(u - u0);
-      const int b = it & 1;
-      if (!__all_sync(0xffffffffu, wait_bar(sm, &sm.accfull[b], (it >> 1) & 1, a.status))) break;
-      tc_fence_after();
-      const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
-      const int part = tile % g.parts;
-      const int ec = live_row ? sm.accmeta[b][cl] : 0;
-      const float sc = pow2f(scale_from_field(ec) + a.e_small[kc * g.parts + part] - 14);
-      const uint32_t buf = lane_addr + b * kAccCols;
-#pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
-#pragma unroll
-        for (int q4 = 0; q4 < kNS; q4 += 4) {
-          float v[kLevels][4];
-          tmem_ld4xL(buf + grp * kGroupCols + q4, kNS, v);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            // sum_d v_d 2^(-8d) in double-float; every v_d is an exact integer
-            float hi = v[0][q], lo = 0.f, f = 1.f;
-#pragma unroll
-            for (int d = 1; d < kLevels; ++d) {
-              f *= 0.00390625f;  // 2^-8
-              df_add(hi, lo, v[d][q] * f);
-            }
-            float& rh = run[grp][q4 + q][0];
-            float& rl = run[grp][q4 + q][1];
-            df_add(rh, rl, hi * sc);
-            rl += lo * sc;
-          }
-        }
-      }
-      for (int col = 0; col < kAccCols; col += 16) tmem_zero16(buf + col);
-      tmem_wait_st();
-      tc_fence_before();
-      mbar_arrive(&sm.accempty[b]);
-      // segment end: the next unit is in another tile, or the range ends
-      if ((u + 1 == u1) || ((u + 1) / g.cpt != tile)) {
-        const int c = (tile / g.parts) * CT + cl;
-        if (live_row && c <= n) {
-          double2* out = reinterpret_cast<double2*>(a.part) + ((size_t)blockIdx.x * g.S + local_seg) * (2 * 128 * kNA);
-          // slot layout [s][c_l][a_l][b], a_l < 8; small-operand column = 2 a_l + (re, im)
-#pragma unroll
-          for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-            for (int al = 0; al < kNA; ++al) {
-              const double re = (double)run[s2][2 * al][0] + (double)run[s2][2 * al][1];
-              const double im = (double)run[s2][2 * al + 1][0] + (double)run[s2][2 * al + 1][1];
-              out[((size_t)s2 * CT + cl) * kNA * M + al * M + bb] = make_double2(re, im);
-            }
-        }
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-          for (int q = 0; q < kNS; ++q) { run[s2][q][0] = 0.f; run[s2][q][1] = 0.f; }
-        ++local_seg;
-      }
-    }
-  }
-  // ------------------------------------------------------------ teardown --
-  tc_fence_before();
-  __syncthreads();
-  if (warp == kEpiWarps) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
-  }
 }
 
 // ============================================================ planes path ==
@@ -824,23 +539,457 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
   }
 }
 
+// ============================================================ fused path ==
+// The same contraction with the conversion inside the contraction kernel,
+// over the units of one or many systems: no digit-plane buffer (a batch of
+// systems cannot hold one next to its histories).  Work list: the units
+// (column tile, chunk) of every system in order, split into contiguous
+// ranges of about equal cost, one range per persistent CTA.  For each unit
+// eight converter warps read the FP64 history entries of the unit's 128
+// output rows (both triangles) and write the PL, Q (and masked QU) digit
+// planes into a shared-memory stage, once; the two MMA threads then run the
+// unit's MMAs once per 8-orbital part (the small operands of each part
+// arrive by bulk copy in a ring of their own), and eight epilogue warps
+// (4 lane quadrants x 2 accumulator groups) fold each part's levels and
+// scale into double-float running sums kept in tensor memory, one per part,
+// written out as FP64 partials when the range leaves a column tile.
+// Tensor memory: two accumulator buffers of 160 columns and up to three
+// parts' running sums of 64 columns (512 columns), so M <= 24.
+constexpr int kFEpiWarps = 8;
+constexpr int kFConvWarps = kConvThreads / 32;
+constexpr int kFThreads = (kFEpiWarps + kFConvWarps + 3) * 32;  // + producer, two MMA warps: 608
+constexpr int kFStageBytes = 3 * kBigTile + 512;                 // PL | Q | QU | column exponents
+constexpr int kFSlots = 2;                                      // small-operand ring
+constexpr int kFMaxParts = 3;
+constexpr int kFRunCol = 2 * kAccCols;                          // running sums from column 320
+constexpr int kFRunPart = 2 * 2 * kNS;                          // per part: 2 groups x (16 hi, 16 lo)
+
+struct FusedSys {
+  const double* L;
+  const double* R;
+  const double* Sl;
+  const double* Sg;
+  WeightsView w;
+  double* out;
+  const uint8_t* small;   // [cpt][parts][kSmallBytes], written by fused_prep
+  int* e_small;           // [cpt][parts]
+  int M, n, CT, cpt, col_tiles;
+  int parts;                   // 8-orbital parts this entry contracts (<= 3): part0 .. part0 + parts - 1
+  int part0, parts_total;      // first part, and all parts of the system (small-operand layout)
+  long long unit_base, units;  // global units [unit_base, unit_base + units)
+  long long tile_base;         // global index of the first column tile
+  long long chunk_base;        // global index of the first chunk (prep grid)
+  long long col_base;          // global index of the first output column (reduce grid)
+};
+
+struct FusedArgs {
+  const FusedSys* sys;
+  int n_sys, G;
+  const long long* cta_lo;     // [G + 1]: CTA i takes the units [cta_lo[i], cta_lo[i+1])
+  const long long* cta_tile0;  // [G]: global column tile of CTA i's first unit
+  const long long* seg_base;   // [G]: CTA i's first segment (one per column tile it touches)
+  const long long* seg_slot;   // [segments]: first partial slot of the segment (one slot per part)
+  double* part;                // [slots][kSlotComplex] complex
+  int* status;
+  long long withhold;          // failure-path test: no small operand is issued from this unit on
+  long long spin;              // polls of a work wait before it gives up
+};
+
+struct SmemF {
+  uint8_t stage[kStages][kFStageBytes];
+  uint8_t small[kFSlots][kSmallBytes];
+  uint64_t full[kStages], empty[kStages], sfull[kFSlots], sempty[kFSlots];
+  uint64_t accfull[2], accempty[2], mmadone[2];
+  int accmeta[2][128];   // column exponents of the unit whose part is in accumulator buffer b
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ bool wait_f(SmemF& sm, void* bar, uint32_t parity, int* status, long long limit) {
+  long long it = 0;
+  while (!mbar_try(bar, parity)) {
+    if (++it > limit || *(volatile int*)&sm.abort) {
+      if (it > limit) { atomicOr(status, kStatusTimeout); sm.abort = 1; }
+      return false;
+    }
+    if (it > 64) __nanosleep(64);
+  }
+  return true;
+}
+
+// The system that holds global unit u, from the cursor si on (units increase).
+__device__ __forceinline__ const FusedSys& sys_at(const FusedArgs& a, int& si, long long u) {
+  while (si + 1 < a.n_sys && u >= a.sys[si].unit_base + a.sys[si].units) ++si;
+  return a.sys[si];
+}
+
+__device__ __forceinline__ int first_sys(const FusedArgs& a, long long u) {
+  int lo = 0, hi = a.n_sys;  // sys[lo].unit_base <= u
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.sys[mid].unit_base <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane from registers.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+// Small operands of every system's chunks (grid: global chunk x part).
+__global__ void __launch_bounds__(256) fused_prep(const FusedSys* __restrict__ sys, int n_sys) {
+  __shared__ int s_ef;
+  const long long g = blockIdx.x;
+  int lo = 0, hi = n_sys;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (sys[mid].chunk_base <= g) lo = mid; else hi = mid;
+  }
+  const FusedSys& S = sys[lo];
+  if ((int)blockIdx.y >= S.parts) return;
+  prep_chunk(S.M, S.n, S.parts_total, S.Sl, S.Sg, S.w, const_cast<uint8_t*>(S.small), S.e_small,
+             (int)(g - S.chunk_base), S.part0 + (int)blockIdx.y, &s_ef);
+}
+
+__global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  SmemF& sm = *reinterpret_cast<SmemF*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long ua = a.cta_lo[blockIdx.x], ub = a.cta_lo[blockIdx.x + 1];
+  constexpr int kProdWarp = kFEpiWarps + kFConvWarps, kMmaWarp = kProdWarp + 1;
+
+  // rows beyond a unit's CT M are never written by the converters: zero the stages once
+  for (int i = tid; i < kStages * kFStageBytes / 16; i += kFThreads)
+    reinterpret_cast<uint4*>(sm.stage)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    // full: every converter thread; empty, sempty: one commit from each MMA
+    // thread; sfull: the producer's transaction count; accfull: the first MMA
+    // thread's arrival (exponents copied) and both commits; accempty: every
+    // epilogue thread
+    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], kConvThreads); mbar_init(&sm.empty[s], 2); }
+    for (int s = 0; s < kFSlots; ++s) { mbar_init(&sm.sfull[s], 1); mbar_init(&sm.sempty[s], 2); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 3); mbar_init(&sm.accempty[b], kFEpiWarps * 32); }
+    mbar_init(&sm.mmadone[0], 1);
+    mbar_init(&sm.mmadone[1], 1);
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kProdWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+  int si = ua < ub ? first_sys(a, ua) : 0;
+
+  if (warp >= kFEpiWarps && warp < kProdWarp) {
+    // ------------------------------------------------------ converters --
+    // Thread ct owns one row j = (c_l, b) of one big operand (arr 0: the
+    // G^< plane from L, arr 1: the Q plane from R) and the chunk's 16 K
+    // entries: 16 loads in flight, then one 16-byte store per K-group.
+    const int ct = tid - kFEpiWarps * 32;
+    const int arr = ct >> 7, jrow = ct & 127;
+    for (long long u = ua; u < ub; ++u) {
+      const int it = (int)(u - ua);
+      const int s = it & 1;
+      const FusedSys& S = sys_at(a, si, u);
+      const int M = S.M, MM = M * M, n = S.n, CT = S.CT, bw = S.w.band_w;
+      const long long lu = u - S.unit_base;
+      const int ctile = (int)(lu / S.cpt), kc = (int)(lu % S.cpt);
+      const bool row_live = jrow < CT * M;
+      const int cl = row_live ? jrow / M : 0, bb = jrow - cl * M;
+      if (!conv_all(wait_f(sm, &sm.empty[s], ((it >> 1) & 1) ^ 1, a.status, a.spin))) break;
+      uint8_t* st = sm.stage[s];
+      int* ecol = reinterpret_cast<int*>(st + 3 * kBigTile);
+      const int c0 = ctile * CT;
+      const int kap0 = kc * kKC;
+      const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, bw);
+      if (ct < 128) ecol[ct] = 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(kConvThreads) : "memory");
+      const double2* base = reinterpret_cast<const double2*>(arr == 0 ? S.L : S.R);
+      const int c = c0 + cl;
+      const bool col_live = row_live && c <= n;
+      double er[kKC], ei[kKC];
+      unsigned keep = 0;  // bit k: K entry k lies in the tensor-core part of term 2 (m <= c - band_w)
+      int ef = 0;
+      {
+        int m = kap0 / M, x = kap0 - m * M;
+#pragma unroll
+        for (int k = 0; k < kKC; ++k) {
+          double2 z = make_double2(0.0, 0.0);
+          if (col_live && m <= n) {
+            if (m >= c) {
+              z = __ldcs(base + tri(m, c) * MM + x * M + bb);
+            } else {
+              z = __ldcs(base + tri(c, m) * MM + bb * M + x);
+              z.x = -z.x;  // -conj
+            }
+          }
+          er[k] = z.x;
+          ei[k] = z.y;
+          keep |= (unsigned)(m <= c - bw) << k;
+          if (++x == M) { x = 0; ++m; }
+        }
+#pragma unroll
+        for (int k = 0; k < kKC; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
+      }
+      if (row_live && ef > 0) atomicMax(&ecol[cl], ef);
+      asm volatile("bar.sync 1, %0;" ::"r"(kConvThreads) : "memory");
+      if (row_live) {
+        const int e = scale_from_field(ecol[cl]);
+        uint8_t* dst = st + arr * kBigTile;  // PL or Q
+        uint8_t* QU = st + 2 * kBigTile;
+        const bool qu = arr == 1 && cls == 2;
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg) {
+          uint32_t w[kSlices][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint32_t dr[kSlices], di[kSlices];
+            digits_bf16(fixed31(er[4 * kg + q], e), dr);
+            digits_bf16(fixed31(ei[4 * kg + q], e), di);
+#pragma unroll
+            for (int sl = 0; sl < kSlices; ++sl) w[sl][q] = __byte_perm(dr[sl], di[sl], 0x5410);
+          }
+          const int off = (kg * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
+#pragma unroll
+          for (int sl = 0; sl < kSlices; ++sl) {
+            *reinterpret_cast<uint4*>(dst + sl * kBigSlice + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+            if (qu) {
+              const unsigned kb = keep >> (4 * kg);
+              *reinterpret_cast<uint4*>(QU + sl * kBigSlice + off) =
+                  make_uint4(kb & 1u ? w[sl][0] : 0u, kb & 2u ? w[sl][1] : 0u, kb & 4u ? w[sl][2] : 0u,
+                             kb & 8u ? w[sl][3] : 0u);
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(&sm.full[s]);
+    }
+  } else if (warp == kProdWarp) {
+    // -------------------------------------------------------- producer --
+    // Small operands of each (unit, part), in the order the MMAs use them.
+    if (lane == 0) {
+      long long it2 = 0, issued = 0;
+      bool stop = false;
+      for (long long u = ua; u < ub && !stop; ++u) {
+        const FusedSys& S = sys_at(a, si, u);
+        const int kc = (int)((u - S.unit_base) % S.cpt);
+        for (int p = 0; p < S.parts; ++p, ++it2) {
+          const int ss = (int)(it2 & 1);
+          if (!wait_f(sm, &sm.sempty[ss], (uint32_t)(((it2 >> 1) & 1) ^ 1), a.status, a.spin) || u == a.withhold) {
+            stop = true;  // (withhold: test of the failure path, nothing issued from this unit on)
+            break;
+          }
+          mbar_arrive_expect_tx(&sm.sfull[ss], kSmallBytes);
+          bulk_g2s(sm.small[ss], S.small + ((size_t)kc * S.parts_total + S.part0 + p) * kSmallBytes, kSmallBytes,
+                   &sm.sfull[ss]);
+          issued = it2 + 1;
+        }
+      }
+      // the copies already issued must land before the CTA can exit
+      for (long long k = issued - 1; k >= 0 && k >= issued - kFSlots; --k) {
+        long long spins = 0;
+        while (!mbar_try(&sm.sfull[k & 1], (uint32_t)((k >> 1) & 1)) && ++spins < kSpinLimit) __nanosleep(64);
+        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);
+      }
+    }
+    __syncwarp();
+  } else if (warp > kProdWarp) {
+    // -------------------------------------------------------- MMA warps --
+    // group 0: I^< += PL A1 + QU NB^<;  group 1: D += Q A1 + QU NBD
+    const int mgrp = warp - kMmaWarp;
+    if (lane == 0) {
+      const uint64_t big0 = umma_desc(smem_u32(sm.stage[0]), 2048, 128);
+      const uint64_t small0 = umma_desc(smem_u32(sm.small[0]), 1024, 128);
+      long long it2 = 0;
+      bool any = false, stop = false;
+      for (long long u = ua; u < ub && !stop; ++u) {
+        const int it = (int)(u - ua);
+        const int s = it & 1;
+        const FusedSys& S = sys_at(a, si, u);
+        const int M = S.M, CT = S.CT, bw = S.w.band_w;
+        const long long lu = u - S.unit_base;
+        const int ctile = (int)(lu / S.cpt), kc = (int)(lu % S.cpt);
+        const int c0 = ctile * CT, kap0 = kc * kKC;
+        const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, bw);
+        if (!wait_f(sm, &sm.full[s], (uint32_t)((it >> 1) & 1), a.status, a.spin)) break;
+        const uint64_t so = (uint64_t)(s * kFStageBytes) >> 4;
+        const uint64_t dPL0 = big0 + so, dQ0 = dPL0 + (kBigTile >> 4);
+        const uint64_t dQU0 = cls == 1 ? dQ0 : dPL0 + ((2 * kBigTile) >> 4);
+        const uint64_t dA = mgrp == 0 ? dPL0 : dQ0;
+        for (int p = 0; p < S.parts; ++p, ++it2) {
+          const int b = (int)(it2 & 1);
+          const uint32_t par = (uint32_t)((it2 >> 1) & 1);
+          if (!wait_f(sm, &sm.sfull[b], par, a.status, a.spin) || !wait_f(sm, &sm.accempty[b], par, a.status, a.spin)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          if (mgrp == 0) {
+            const int* ecol = reinterpret_cast<const int*>(sm.stage[s] + 3 * kBigTile);
+            for (int q = 0; q < CT; ++q) sm.accmeta[b][q] = ecol[q];
+            mbar_arrive(&sm.accfull[b]);
+          }
+          const uint64_t dS0 = small0 + ((uint64_t)(b * kSmallBytes) >> 4);
+          const uint64_t dSU = dS0 + (uint64_t)(((1 + mgrp) * kSmallVar) >> 4);
+          const uint32_t dacc = tmem + b * kAccCols + mgrp * kGroupCols;
+#pragma unroll
+          for (int i = 0; i < kSlices; ++i) {
+            const uint32_t idesc = umma_idesc_bf16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t oa = (uint64_t)((i * kBigSlice + kk * 2 * 2048) >> 4);
+              const uint64_t ob = (uint64_t)((kk * 2 * 1024) >> 4);
+              umma_bf16(dacc + i * kNS, dA + oa, dS0 + ob, idesc, 1);
+              if (cls != 0) umma_bf16(dacc + i * kNS, dQU0 + oa, dSU + ob, idesc, 1);
+            }
+          }
+          umma_commit(&sm.accfull[b]);
+          umma_commit(&sm.sempty[b]);
+          any = true;
+        }
+        if (stop) break;
+        umma_commit(&sm.empty[s]);
+      }
+      // every MMA this thread issued must complete before tensor memory is freed
+      if (any) {
+        umma_commit(&sm.mmadone[mgrp]);
+        long long spins = 0;
+        while (!mbar_try(&sm.mmadone[mgrp], 0) && ++spins < kSpinLimit) __nanosleep(64);
+        if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);
+      }
+    }
+    __syncwarp();
+  } else {
+    // --------------------------------------------------------- epilogue --
+    // warp = 4 grp + quadrant: accumulator group grp (0: I^<, 1: D = I^> -
+    // I^<), all 16 small-operand columns, the 32 TMEM lanes (output rows) of
+    // its quadrant.
+    const int quad = warp & 3, grp = warp >> 2;
+    const int j = quad * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
+    for (int b = 0; b < 2; ++b)
+      for (int d = 0; d < kLevels; ++d) tmem_zero16(lane_addr + b * kAccCols + grp * kGroupCols + d * kNS);
+    for (int p = 0; p < kFMaxParts; ++p) {
+      tmem_zero16(lane_addr + kFRunCol + p * kFRunPart + grp * 2 * kNS);
+      tmem_zero16(lane_addr + kFRunCol + p * kFRunPart + grp * 2 * kNS + kNS);
+    }
+    tmem_wait_st();
+    tc_fence_before();
+    mbar_arrive(&sm.accempty[0]);
+    mbar_arrive(&sm.accempty[1]);
+    long long it2 = 0, seg = a.seg_base[blockIdx.x];
+    bool stop = false;
+    for (long long u = ua; u < ub && !stop; ++u) {
+      const FusedSys& S = sys_at(a, si, u);
+      const int M = S.M, n = S.n, CT = S.CT, parts = S.parts;
+      const long long lu = u - S.unit_base;
+      const int ctile = (int)(lu / S.cpt), kc = (int)(lu % S.cpt);
+      const int cl = j / M, bb = j - cl * M;
+      const bool live_row = cl < CT;
+      for (int p = 0; p < parts; ++p, ++it2) {
+        const int b = (int)(it2 & 1);
+        const int es = __ldg(S.e_small + kc * S.parts_total + S.part0 + p);
+        if (!__all_sync(0xffffffffu, wait_f(sm, &sm.accfull[b], (uint32_t)((it2 >> 1) & 1), a.status, a.spin))) {
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const int ec = live_row ? sm.accmeta[b][cl] : 0;
+        const float sc = pow2f(scale_from_field(ec) + es - 14);
+        const uint32_t buf = lane_addr + b * kAccCols + grp * kGroupCols;
+        const uint32_t run = lane_addr + kFRunCol + p * kFRunPart + grp * 2 * kNS;
+        float rh[kNS], rl[kNS];
+        tmem_ld16(run, rh);
+        tmem_ld16(run + kNS, rl);
+#pragma unroll
+        for (int q4 = 0; q4 < kNS; q4 += 4) {
+          float v[kLevels][4];
+          tmem_ld4xL(buf + q4, kNS, v);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float lv[kLevels] = {v[0][q], v[1][q], v[2][q], v[3][q], v[4][q]};
+            float hi, lo;
+            combine_levels(lv, hi, lo);
+            df_add(rh[q4 + q], rl[q4 + q], hi * sc);
+            rl[q4 + q] += lo * sc;
+          }
+        }
+        tmem_st16(run, rh);
+        tmem_st16(run + kNS, rl);
+#pragma unroll
+        for (int d = 0; d < kLevels; ++d) tmem_zero16(buf + d * kNS);
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&sm.accempty[b]);
+      }
+      if (stop) break;
+      // segment end: the next unit is in another column tile or system, or the range ends
+      const bool last = u + 1 == ub || u + 1 == S.unit_base + S.units || (lu + 1) / S.cpt != ctile;
+      if (last) {
+        const int c = ctile * CT + cl;
+        const long long slot0 = a.seg_slot[seg];
+        for (int p = 0; p < parts; ++p) {
+          const uint32_t run = lane_addr + kFRunCol + p * kFRunPart + grp * 2 * kNS;
+          float rh[kNS], rl[kNS];
+          tmem_ld16(run, rh);
+          tmem_ld16(run + kNS, rl);
+          if (live_row && c <= n) {
+            double2* out = reinterpret_cast<double2*>(a.part) + (slot0 + p) * kSlotComplex;
+#pragma unroll
+            for (int al = 0; al < kNA; ++al) {
+              const double re = (double)rh[2 * al] + (double)rl[2 * al];
+              const double im = (double)rh[2 * al + 1] + (double)rl[2 * al + 1];
+              out[((size_t)grp * CT + cl) * kNA * M + al * M + bb] = make_double2(re, im);
+            }
+          }
+          tmem_zero16(run);
+          tmem_zero16(run + kNS);
+        }
+        tmem_wait_st();
+        ++seg;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kProdWarp) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- reduce -
-// I_out[s][c][a][b] = sum of the partials of every CTA that covered the
-// tile of (c, a), in CTA order (I^< from group 0; I^> from groups 0 and 1),
-// plus the band of term 2 with the exact composite weights,
-//   sum_{m = c-K..c} w_{c,m} S^s(n,m)_ax conj(R(c,m)_bx).
-// Reduction of one output column c and one 8-orbital part (block (c, part)):
-// the per-CTA partials of the column's tile in CTA order (FP64), plus the
-// band of term 2, sum_{m in (c - band_w, c]} w_{c,m} Sigma^s(n,m) G^A(m,c),
-// with the exact weights.  The band runs in double-float on the FP32 pipe:
-// per band point m the block stages R(c,m) (transposed, [x][b]) and
-// w_{c,m} Sigma^s(n,m) for its rows a as double-float pairs in shared memory,
-// and each thread accumulates its outputs' products with Ogita-Rump-Oishi's
-// compensated dot product (TwoSum of the leading products, the product
-// errors and the TwoSum errors in a float tail), about 2^-47 of the
-// products' sizes, far below the slice's 1e-8 bound.  In FP64 the band's
-// band_w M^3 complex products per column and sign set this kernel's time
-// (the FP64 pipe issues 1/64 of the FP32 rate on this part).
+// Reduction of one output column c and one 8-orbital part: the per-CTA
+// partials of the column's tile (FP64, in CTA order; I^< from group 0,
+// I^> from groups 0 and 1), plus the band of term 2,
+//   sum_{m in (c - band_w, c]} w_{c,m} Sigma^s(n,m) G^A(m,c),
+// with the exact composite weights.  The band runs in double-float on the
+// FP32 pipe: the band points' R(c,m) (transposed, [x][b]) and
+// w_{c,m} Sigma^s(n,m) for the part's rows a are staged as double-float
+// pairs in shared memory, and each thread accumulates its outputs' products
+// with Ogita-Rump-Oishi's compensated dot product (TwoSum of the leading
+// products, the product errors and the TwoSum errors in a float tail),
+// about 2^-47 of the products' sizes, far below the slice's 1e-8 bound.  In
+// FP64 the band's band_w M^3 complex products per column and sign set this
+// kernel's time (the FP64 pipe issues 1/64 of the FP32 rate on this part).
 constexpr int kRedThreads = 128;
 constexpr int kRedOut = 2 * kNA * 32 / kRedThreads;  // outputs per thread at M = 32
 constexpr int kRedStage = 1792;  // float4 of staged operands: one point at M = 32 (1024 + 512)
@@ -865,81 +1014,63 @@ __device__ __forceinline__ float4 c2_of(double2 v) {
   return make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
-// Seven CTAs per SM (at most 73 registers, 29 KB of shared memory each):
-// one wave for the 1024 (c, part) blocks of an 8-orbital slice of row 1023.
-__global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, const double* __restrict__ part,
-                                                             const double* __restrict__ Sl,
-                                                             const double* __restrict__ Sg,
-                                                             const double* __restrict__ R, WeightsView w,
-                                                             double* __restrict__ out, int* status) {
-  const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
-  const int c = blockIdx.x, pt = blockIdx.y;
-  const int ctile = c / CT, cl = c - ctile * CT;
-  const int tile = ctile * g.parts + pt;
+struct RedShared {
+  int cnt, mnext, nslot;
+  float4 stage[kRedStage];   // the group's R(c,m) (transposed, [x][b]), then its w_{c,m} Sigma^s(n,m) ([s][al][x])
+  int m[kRedGroup];
+  double dw[kRedGroup], wt[kRedGroup];
+  long long slot[kMaxSplitCtas];  // partial slots of the column's tile, in CTA order
+};
+
+// Called by every thread of the block after slot[0..nslot) is set (and a
+// __syncthreads).  As many band points as the shared arrays hold are
+// staged together (all of them at M <= 8), so that their loads are in
+// flight at once; the sums take the points in the same order either way.
+__device__ __forceinline__ void reduce_column(RedShared& sh, int M, int n, int CT, int c, int pt,
+                                              const double* __restrict__ part, const double* __restrict__ Sl,
+                                              const double* __restrict__ Sg, const double* __restrict__ R,
+                                              const WeightsView& w, double* __restrict__ out, int* status) {
+  const int MM = M * M;
+  const int cl = c % CT;
   const int na = min(kNA, M - pt * kNA);
   const int nout = 2 * na * M;
-  __shared__ int s_i0, s_k, s_cnt, s_mnext;
-  __shared__ int s_seg[kMaxSplitCtas];
-  __shared__ float4 s_stage[kRedStage];        // the group's R(c,m) (transposed, [x][b]), then its
-                                               // w_{c,m} Sigma^s(n,m) ([s][al][x]), per point
-  __shared__ int s_m[kRedGroup];
-  __shared__ double s_dw[kRedGroup], s_wt[kRedGroup];
-  if (threadIdx.x == 0) {
-    const long long ulo = (long long)tile * g.cpt, uhi = ulo + g.cpt;
-    int i = (int)((ulo * g.G) / g.U);
-    while (i > 0 && g.U * i / g.G > ulo) --i;
-    while (i + 1 < g.G && g.U * (i + 1) / g.G <= ulo) ++i;
-    const int i0 = i;
-    int k = 0;
-    for (; i < g.G && k < kMaxSplitCtas; ++i) {
-      const long long b0 = g.U * i / g.G, b1 = g.U * (i + 1) / g.G;
-      if (b0 >= uhi) break;
-      s_seg[k++] = b1 <= b0 ? -1 : (int)(tile - b0 / g.cpt);
-    }
-    s_i0 = i0;
-    s_k = k;
-  }
   DotAcc acc[kRedOut][2];
 #pragma unroll
   for (int q = 0; q < kRedOut; ++q) acc[q][0] = acc[q][1] = DotAcc{0.f, 0.f};
-  // band of term 2: the points m = c - band_w + 1 .. c with w_{c,m} != 0,
-  // in increasing m.  As many points as the shared arrays hold are staged
-  // together (all of them at M <= 8), so that their loads are in flight at
-  // once; the sums take the points in the same order either way.
   const int per = min(kRedGroup, kRedStage / (MM + nout));
-  float4* s_r = s_stage;
-  float4* s_s = s_stage + per * MM;
+  float4* s_r = sh.stage;
+  float4* s_s = sh.stage + per * MM;
   for (int m_next = max(0, c - w.band_w + 1); m_next <= c;) {
     __syncthreads();  // the previous group's operands are consumed
     if (threadIdx.x < kRedGroup) {  // the next candidates' weights, loaded in parallel
       const int m = m_next + (int)threadIdx.x;
-      s_wt[threadIdx.x] = m <= c ? w.at(c, m) : 0.0;
+      sh.wt[threadIdx.x] = m <= c ? w.at(c, m) : 0.0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       int cnt = 0, k = 0;
       for (; k < kRedGroup && m_next + k <= c && cnt < per; ++k) {
-        const double dw = s_wt[k];
-        if (dw != 0.0) { s_m[cnt] = m_next + k; s_dw[cnt] = dw; ++cnt; }
+        const double dw = sh.wt[k];
+        if (dw != 0.0) { sh.m[cnt] = m_next + k; sh.dw[cnt] = dw; ++cnt; }
       }
-      s_cnt = cnt;
-      s_mnext = m_next + k;
+      sh.cnt = cnt;
+      sh.mnext = m_next + k;
     }
     __syncthreads();
-    const int cnt = s_cnt;
-    m_next = s_mnext;
+    const int cnt = sh.cnt;
+    m_next = sh.mnext;
 #pragma unroll 4
     for (int f = threadIdx.x; f < cnt * MM; f += kRedThreads) {
       const int j = f / MM, i = f - j * MM;
       const int b = i / M, x = i - b * M;
-      s_r[j * MM + x * M + b] = c2_of(reinterpret_cast<const double2*>(R)[tri(c, s_m[j]) * MM + i]);
+      s_r[j * MM + x * M + b] = c2_of(reinterpret_cast<const double2*>(R)[tri(c, sh.m[j]) * MM + i]);
     }
 #pragma unroll 4
     for (int f = threadIdx.x; f < cnt * nout; f += kRedThreads) {
       const int j = f / nout, i = f - j * nout;
       const int s = i / (na * M), r = i - s * (na * M);
-      const double2 v = reinterpret_cast<const double2*>(s ? Sg : Sl)[(size_t)s_m[j] * MM + pt * kNA * M + r];
-      const double dw = s_dw[j];
+      const double2 v = reinterpret_cast<const double2*>(s ? Sg : Sl)[(size_t)sh.m[j] * MM + pt * kNA * M + r];
+      const double dw = sh.dw[j];
       s_s[f] = c2_of(make_double2(dw * v.x, dw * v.y));
     }
     __syncthreads();
@@ -962,7 +1093,7 @@ __global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, con
     }
   }
   __syncthreads();
-  const int i0 = s_i0, nk = s_k;
+  const int nslot = sh.nslot;
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < kRedOut; ++q) {
@@ -970,17 +1101,15 @@ __global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, con
     if (o >= nout || c > n) break;
     const int s = o / (na * M), r = o - s * (na * M);
     const int al = r / M, bb = r - al * M;
-    // group 0 holds I^<, group 1 holds D = I^> - I^<
     // a non-finite float word is reported (to_double needs finite words)
     bad |= !(df::finite_bits(acc[q][0].s) && df::finite_bits(acc[q][0].c) && df::finite_bits(acc[q][1].s) &&
              df::finite_bits(acc[q][1].c));
     double re = df::to_double(df::F2{acc[q][0].s, acc[q][0].c});
     double im = df::to_double(df::F2{acc[q][1].s, acc[q][1].c});
+    // group 0 holds I^<, group 1 holds D = I^> - I^<
     for (int grp = 0; grp <= s; ++grp)
-      for (int k = 0; k < nk; ++k) {
-        const int seg = s_seg[k];
-        if (seg < 0) continue;
-        const double2 v = reinterpret_cast<const double2*>(part)[((size_t)(i0 + k) * g.S + seg) * (2 * 128 * kNA) +
+      for (int k = 0; k < nslot; ++k) {
+        const double2 v = reinterpret_cast<const double2*>(part)[sh.slot[k] * kSlotComplex +
                                                                   ((size_t)grp * CT + cl) * kNA * M + al * M + bb];
         re += v.x;
         im += v.y;
@@ -989,6 +1118,74 @@ __global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, con
     reinterpret_cast<double2*>(out)[((size_t)s * (n + 1) + c) * MM + (pt * kNA + al) * M + bb] = make_double2(re, im);
   }
   if (bad) atomicOr(status, kStatusNumeric);
+}
+
+// Planes path: the CTAs of the uniform partition of the units that cover the
+// column's tile, with their segment of that tile.  Seven CTAs per SM (at
+// most 73 registers, 29 KB of shared memory each): one wave for the 1024
+// (c, part) blocks of an 8-orbital slice of row 1023.
+__global__ void __launch_bounds__(kRedThreads, 7) split_reduce2(SplitGeom g, const double* __restrict__ part,
+                                                             const double* __restrict__ Sl,
+                                                             const double* __restrict__ Sg,
+                                                             const double* __restrict__ R, WeightsView w,
+                                                             double* __restrict__ out, int* status) {
+  __shared__ RedShared sh;
+  const int c = blockIdx.x, pt = blockIdx.y;
+  const int tile = (c / g.CT) * g.parts + pt;
+  if (threadIdx.x == 0) {
+    const long long ulo = (long long)tile * g.cpt, uhi = ulo + g.cpt;
+    int i = (int)((ulo * g.G) / g.U);
+    while (i > 0 && g.U * i / g.G > ulo) --i;
+    while (i + 1 < g.G && g.U * (i + 1) / g.G <= ulo) ++i;
+    int k = 0;
+    for (; i < g.G && k < kMaxSplitCtas; ++i) {
+      const long long b0 = g.U * i / g.G, b1 = g.U * (i + 1) / g.G;
+      if (b0 >= uhi) break;
+      if (b1 > b0) sh.slot[k++] = (long long)i * g.S + (tile - b0 / g.cpt);
+    }
+    sh.nslot = k;
+  }
+  reduce_column(sh, g.M, g.n, g.CT, c, pt, part, Sl, Sg, R, w, out, status);
+}
+
+// Fused path: the CTAs of the work list whose unit ranges meet the column's
+// tile, each with the segment it wrote for that tile (grid: global column x
+// part of the entry).
+__global__ void __launch_bounds__(kRedThreads, 7) fused_reduce(FusedArgs a) {
+  __shared__ RedShared sh;
+  const long long gcol = blockIdx.x;
+  int lo = 0, hi = a.n_sys;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.sys[mid].col_base <= gcol) lo = mid; else hi = mid;
+  }
+  // entries of one system with different part ranges share its columns: take the one holding this part
+  while (lo > 0 && a.sys[lo - 1].col_base == a.sys[lo].col_base) --lo;
+  int pt = blockIdx.y;
+  while (lo + 1 < a.n_sys && a.sys[lo + 1].col_base == a.sys[lo].col_base && pt >= a.sys[lo].parts) {
+    pt -= a.sys[lo].parts;
+    ++lo;
+  }
+  const FusedSys& S = a.sys[lo];
+  if (pt >= S.parts) return;
+  const int c = (int)(gcol - S.col_base);
+  if (threadIdx.x == 0) {
+    const int ct = c / S.CT;
+    const long long T = S.tile_base + ct;
+    const long long ulo = S.unit_base + (long long)ct * S.cpt, uhi = ulo + S.cpt;
+    int l = 0, h = a.G - 1;  // first CTA whose range ends beyond ulo
+    while (l < h) {
+      const int mid = (l + h) >> 1;
+      if (a.cta_lo[mid + 1] > ulo) h = mid; else l = mid + 1;
+    }
+    int k = 0;
+    for (int i = l; i < a.G && a.cta_lo[i] < uhi && k < kMaxSplitCtas; ++i) {
+      if (a.cta_lo[i + 1] <= a.cta_lo[i]) continue;
+      sh.slot[k++] = a.seg_slot[a.seg_base[i] + (T - a.cta_tile0[i])] + pt;
+    }
+    sh.nslot = k;
+  }
+  reduce_column(sh, S.M, S.n, S.CT, c, S.part0 + pt, a.part, S.Sl, S.Sg, S.R, S.w, S.out, a.status);
 }
 
 inline dim3 reduce2_grid(const SplitGeomHost& h) { return dim3((unsigned)(h.n + 1), (unsigned)h.parts); }
@@ -1014,12 +1211,25 @@ bool split_geometry(int M, int n, SplitGeomHost* h) {
   return true;
 }
 
+// Upper bounds of a fused launch over one system of n_max rows (its slice of
+// row n_max - 1 is the largest): partial slots and the plan image.
+static size_t fused_single_part_bytes(const SplitGeomHost& h) {
+  const int ctas = std::min(sm_count(), kMaxSplitCtas);
+  const long long col_tiles = (h.n + 1 + h.CT - 1) / h.CT;
+  return (size_t)(col_tiles + 2 * ctas) * h.parts * kSlotComplex * 16;
+}
+static size_t fused_single_plan_bytes(const SplitGeomHost& h) {
+  const int ctas = std::min(sm_count(), kMaxSplitCtas);
+  const long long col_tiles = (h.n + 1 + h.CT - 1) / h.CT;
+  return 4 * sizeof(FusedSys) + 8 * (size_t)(3 * ctas + 1) + 8 * (size_t)(2 * (col_tiles + ctas)) + 5 * 256;
+}
+
 size_t split_workspace_bytes(int M, int n_max) {
   SplitGeomHost h;
   if (!split_geometry(M, n_max - 1, &h)) return 0;
   const size_t small = (size_t)h.cpt * h.parts * kSmallBytes + (size_t)h.cpt * h.parts * sizeof(int) + 256;
-  const size_t part = (size_t)h.G * h.S * 2 * 128 * kNA * 16;
-  return small + part + 1024;
+  const size_t part = std::max((size_t)h.G * h.S * 2 * 128 * kNA * 16, fused_single_part_bytes(h));
+  return small + part + fused_single_plan_bytes(h) + 1024;
 }
 
 // The main kernel's dynamic shared memory exceeds the default limit; the
@@ -1032,7 +1242,7 @@ cudaError_t split_prepare() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done_mask.load() & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(split_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  e = cudaFuncSetAttribute(split_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemF));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(split_main2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem2));
   if (e == cudaSuccess) done_mask.fetch_or(bit);
@@ -1110,34 +1320,161 @@ cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& pl_la
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ fused host --
+bool fused_build(const FusedSystem* in, int n_sys, FusedPlanHost* p) {
+  p->image.clear();
+  p->max_parts = 0;
+  p->total_chunks = p->total_cols = 0;
+  p->G = std::min(sm_count(), kMaxSplitCtas);
+  if (n_sys < 1) return false;
+  std::vector<FusedSys> ent;
+  long long units = 0, tiles = 0, chunks = 0, cols = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    SplitGeomHost h;
+    if (!split_geometry(in[i].M, in[i].n, &h)) return false;
+    const int col_tiles = (h.n + 1 + h.CT - 1) / h.CT;
+    // systems of more than three 8-orbital parts run as entries of at most three parts each
+    const int n_ent = (h.parts + kFMaxParts - 1) / kFMaxParts;
+    const int per = (h.parts + n_ent - 1) / n_ent;
+    for (int q = 0, part0 = 0; q < n_ent; ++q, part0 += per) {
+      FusedSys f{};
+      f.L = in[i].L; f.R = in[i].R; f.Sl = in[i].Sl; f.Sg = in[i].Sg; f.w = in[i].w; f.out = in[i].out;
+      f.small = reinterpret_cast<const uint8_t*>(in[i].small);
+      f.e_small = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(in[i].small) +
+                                         (size_t)h.cpt * h.parts * kSmallBytes);
+      f.M = h.M; f.n = h.n; f.CT = h.CT; f.cpt = h.cpt; f.col_tiles = col_tiles;
+      f.part0 = part0;
+      f.parts = std::min(per, h.parts - part0);
+      f.parts_total = h.parts;
+      f.unit_base = units;
+      f.units = (long long)col_tiles * h.cpt;
+      f.tile_base = tiles;
+      f.chunk_base = chunks;
+      f.col_base = cols;
+      units += f.units;
+      tiles += col_tiles;
+      chunks += h.cpt;
+      ent.push_back(f);
+    }
+    cols += h.n + 1;
+    p->max_parts = std::max(p->max_parts, h.parts);
+  }
+  // contiguous unit ranges of about equal cost: a unit costs its conversion
+  // plus one MMA-and-epilogue pass per part (weights 2 + parts)
+  const int G = p->G;
+  long long W = 0;
+  for (const FusedSys& f : ent) W += f.units * (2 + f.parts);
+  std::vector<long long> lo(G + 1), tile0(G, -1), segb(G);
+  size_t e = 0;
+  long long cw = 0;  // weight of the units before entry e
+  for (int i = 0; i <= G; ++i) {
+    const long long target = (long long)((__int128)W * i / G);
+    while (e + 1 < ent.size() && cw + ent[e].units * (2 + ent[e].parts) <= target) {
+      cw += ent[e].units * (2 + ent[e].parts);
+      ++e;
+    }
+    const long long w = 2 + ent[e].parts;
+    long long k = (target - cw + w - 1) / w;
+    if (k > ent[e].units) k = ent[e].units;
+    lo[i] = i == G ? units : ent[e].unit_base + k;
+  }
+  for (int i = 1; i <= G; ++i) lo[i] = std::max(lo[i], lo[i - 1]);
+  std::vector<long long> slot;
+  long long seg = 0, slots = 0;
+  size_t k = 0;
+  for (int i = 0; i < G; ++i) {
+    segb[i] = seg;
+    if (lo[i + 1] <= lo[i]) continue;
+    while (k + 1 < ent.size() && lo[i] >= ent[k].unit_base + ent[k].units) ++k;
+    size_t kk = k;
+    long long prev_tile = -1;
+    for (long long u = lo[i]; u < lo[i + 1];) {
+      while (u >= ent[kk].unit_base + ent[kk].units) ++kk;
+      const FusedSys& f = ent[kk];
+      const long long t = f.tile_base + (u - f.unit_base) / f.cpt;
+      if (prev_tile < 0) tile0[i] = t;
+      prev_tile = t;
+      slot.push_back(slots);
+      slots += f.parts;
+      ++seg;
+      // next unit of another tile: the end of this tile in the entry
+      u = f.unit_base + ((u - f.unit_base) / f.cpt + 1) * f.cpt;
+    }
+  }
+  p->n_ent = (int)ent.size();
+  p->total_chunks = chunks;
+  p->total_cols = cols;
+  p->slots = slots;
+  p->segments = seg;
+  // device image: entries | cta_lo | cta_tile0 | seg_base | seg_slot
+  auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+  p->off_sys = 0;
+  p->off_lo = align(ent.size() * sizeof(FusedSys));
+  p->off_tile0 = align(p->off_lo + (G + 1) * 8);
+  p->off_segb = align(p->off_tile0 + G * 8);
+  p->off_slot = align(p->off_segb + G * 8);
+  p->image.assign(align(p->off_slot + std::max<size_t>(1, slot.size()) * 8), 0);
+  memcpy(p->image.data() + p->off_sys, ent.data(), ent.size() * sizeof(FusedSys));
+  memcpy(p->image.data() + p->off_lo, lo.data(), (G + 1) * 8);
+  memcpy(p->image.data() + p->off_tile0, tile0.data(), G * 8);
+  memcpy(p->image.data() + p->off_segb, segb.data(), G * 8);
+  if (!slot.empty()) memcpy(p->image.data() + p->off_slot, slot.data(), slot.size() * 8);
+  return true;
+}
+
+size_t fused_part_bytes(const FusedPlanHost& p) { return (size_t)std::max<long long>(1, p.slots) * kSlotComplex * 16; }
+
+cudaError_t launch_history_fused(const FusedPlanHost& p, const void* plan_dev, double* part, int* status,
+                                 cudaStream_t s, int* launches, cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                                 long long withhold, long long spin) {
+  *launches = 0;
+  cudaError_t e = split_prepare();
+  if (e != cudaSuccess) return e;
+  const uint8_t* b = reinterpret_cast<const uint8_t*>(plan_dev);
+  FusedArgs a{};
+  a.sys = reinterpret_cast<const FusedSys*>(b + p.off_sys);
+  a.n_sys = p.n_ent;
+  a.G = p.G;
+  a.cta_lo = reinterpret_cast<const long long*>(b + p.off_lo);
+  a.cta_tile0 = reinterpret_cast<const long long*>(b + p.off_tile0);
+  a.seg_base = reinterpret_cast<const long long*>(b + p.off_segb);
+  a.seg_slot = reinterpret_cast<const long long*>(b + p.off_slot);
+  a.part = part;
+  a.status = status;
+  a.withhold = withhold < 0 ? (1ll << 62) : withhold;
+  a.spin = spin > 0 ? spin : kSpinLimit;
+  fused_prep<<<dim3((unsigned)p.total_chunks, (unsigned)kFMaxParts), 256, 0, s>>>(a.sys, a.n_sys);
+  ++*launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev_begin) cudaEventRecord(ev_begin, s);
+  split_fused<<<p.G, kFThreads, sizeof(SmemF), s>>>(a);
+  if (ev_end) cudaEventRecord(ev_end, s);
+  ++*launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  fused_reduce<<<dim3((unsigned)p.total_cols, (unsigned)p.max_parts), kRedThreads, 0, s>>>(a);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// Single system without a plane buffer: the fused contraction, its plan
+// image uploaded from host memory into the tail of the workspace.
 cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* launches) {
   SplitGeomHost h;
   *launches = 0;
   if (!split_geometry(l.M, l.n, &h)) return cudaErrorInvalidValue;
-  SplitGeom g{h.M, h.M * h.M, h.n, h.CT, h.parts, h.cpt, h.tiles, h.U, h.G, h.S, l.w.band_w};
+  FusedSystem in{l.M, l.n, l.L, l.R, l.Sl, l.Sg, l.w, l.out, l.work};
+  FusedPlanHost p;
+  if (!fused_build(&in, 1, &p)) return cudaErrorInvalidValue;
   uint8_t* ws = reinterpret_cast<uint8_t*>(l.work);
-  uint8_t* small = ws;
-  int* e_small = reinterpret_cast<int*>(small + (size_t)h.cpt * h.parts * kSmallBytes);
-  size_t off = ((size_t)h.cpt * h.parts * kSmallBytes + (size_t)h.cpt * h.parts * sizeof(int) + 255) / 256 * 256;
+  const size_t off = ((size_t)h.cpt * h.parts * kSmallBytes + (size_t)h.cpt * h.parts * sizeof(int) + 255) / 256 * 256;
+  const size_t pb = (fused_part_bytes(p) + 255) / 256 * 256;
+  if (off + pb + p.image.size() > l.work_bytes) return cudaErrorInvalidValue;
   double* part = reinterpret_cast<double*>(ws + off);
-  const size_t need = off + (size_t)h.G * h.S * 2 * 128 * kNA * 16;
-  if (need > l.work_bytes) return cudaErrorInvalidValue;
-
-  cudaError_t e = split_prepare();
+  void* plan = ws + off + pb;
+  // pageable source: staged before the call returns, so the host image may go
+  cudaError_t e = cudaMemcpyAsync(plan, p.image.data(), p.image.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  split_prep<<<dim3(h.cpt, h.parts), 256, 0, s>>>(l.M, l.n, h.parts, l.Sl, l.Sg, l.w, small, e_small);
-  ++*launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int smem = (int)sizeof(Smem);
-  SplitArgs args{g, l.L, l.R, small, e_small, part, l.status};
-  if (l.ev_begin) cudaEventRecord(l.ev_begin, s);
-  split_main<<<h.G, kThreads, smem, s>>>(args);
-  if (l.ev_end) cudaEventRecord(l.ev_end, s);
-  ++*launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  split_reduce2<<<reduce2_grid(h), kRedThreads, 0, s>>>(g, part, l.Sl, l.Sg, l.R, l.w, l.out, l.status);
-  ++*launches;
-  return cudaGetLastError();
+  return launch_history_fused(p, plan, part, l.status, s, launches, l.ev_begin, l.ev_end, l.withhold, l.spin_limit);
 }
 
 }  // namespace kbe

@@ -106,6 +106,7 @@ struct kbe_ctx {
   void* d_planes = nullptr;   // digit planes of the history (split path), allocated by the first split slice
   kbe::SplitPlanes planes_layout;
   bool planes_failed = false; // allocation failed once: the in-kernel conversion path is used
+  bool split_planes = true;   // keep the digit-plane cache (kbe_set_split_planes)
   // Cache of the planes across KBE steps: rows < planes_rows of the arrays
   // planes_L / planes_R are encoded with their final values.
   const void* planes_L = nullptr;
@@ -228,6 +229,31 @@ struct SplitLaunch {
   long long spin_limit = 0;  // polls of a work wait before it gives up (0: the default)
 };
 bool split_geometry(int M, int n, SplitGeomHost* h);
+
+// Fused split path: one persistent contraction over the work units of one or
+// many systems, converting the FP64 history into digit planes inside the
+// kernel (no plane buffer), then a reduction over all systems' columns.
+struct FusedSystem {
+  int M, n;
+  const double* L;
+  const double* R;
+  const double* Sl;
+  const double* Sg;
+  WeightsView w;
+  double* out;   // [2][n+1][M][M]
+  void* small;   // the system's split workspace: small-operand digit planes, then their exponents
+};
+struct FusedPlanHost {
+  std::vector<unsigned char> image;  // device image of the work list (upload before launching)
+  int G = 0, n_ent = 0, max_parts = 0;
+  long long total_chunks = 0, total_cols = 0, slots = 0, segments = 0;
+  size_t off_sys = 0, off_lo = 0, off_tile0 = 0, off_segb = 0, off_slot = 0;
+};
+bool fused_build(const FusedSystem* in, int n_sys, FusedPlanHost* p);
+size_t fused_part_bytes(const FusedPlanHost& p);  // partial slots the launch writes
+cudaError_t launch_history_fused(const FusedPlanHost& p, const void* plan_dev, double* part, int* status,
+                                 cudaStream_t s, int* launches, cudaEvent_t ev_begin = nullptr,
+                                 cudaEvent_t ev_end = nullptr, long long withhold = -1, long long spin = 0);
 size_t split_workspace_bytes(int M, int n_max);
 cudaError_t launch_history_split(const SplitLaunch& l, cudaStream_t s, int* launches);
 cudaError_t split_prepare();  // one-time kernel attributes of the current device

@@ -68,11 +68,12 @@ def _magnitude_slice(t, order, n, L, R, Sl, Sg):
     return best
 
 
-def _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg):
+def _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, path="planes"):
     import torch
     ctx = kbe.Context(M, n_t)
     ctx.set_grid(t, order)
     ctx.set_model(h, np.ones(M), W.site_potential(M), None)
+    ctx.set_split_planes(path == "planes")
     out = torch.full((2, n + 1, M, M), float("nan"), dtype=torch.complex128, device="cuda")
     ctx.history_slice(n, Ld, Rd, _dev(Sl), _dev(Sg), out, precision="split")
     ctx.sync_status()
@@ -81,9 +82,10 @@ def _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg):
     return res
 
 
+@pytest.mark.parametrize("path", ["planes", "fused"])
 @pytest.mark.parametrize("M", [1, 2, 3, 4, 5, 8, 12, 16, 24, 32])
 @pytest.mark.parametrize("kind", ["free", "random"])
-def test_split_slice_matches_oracle(kbe, M, kind):
+def test_split_slice_matches_oracle(kbe, M, kind, path):
     n_t = 37 if M <= 16 else 21
     t, order, h, L, R = _case(M, n_t, 3 * M + (kind == "free"), kind)
     Ld, Rd = _dev(L), _dev(R)
@@ -93,7 +95,7 @@ def test_split_slice_matches_oracle(kbe, M, kind):
             Sl, Sg = oracle.sigma_row(oracle.local_U4(U), n, L, R)
         else:
             Sl, Sg = W.random_rows(M, n, 5 * n + M)
-        I = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg)
+        I = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, path)
         ref = oracle.history_slice(t, order, n, L, R, Sl, Sg, nthreads=8)
         if kind == "free":
             err = _rel(I, ref)
@@ -104,19 +106,37 @@ def test_split_slice_matches_oracle(kbe, M, kind):
             assert err < TOL_SPLIT, (M, kind, n, err, _rel(I, ref))
 
 
-def test_split_is_deterministic(kbe):
+@pytest.mark.parametrize("path", ["planes", "fused"])
+def test_split_is_deterministic(kbe, path):
     M, n_t = 8, 60
     t, order, h, L, R = _case(M, n_t, 1, "random")
     Ld, Rd = _dev(L), _dev(R)
     n = n_t - 1
     Sl, Sg = W.random_rows(M, n, 2)
-    a = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg)
-    b = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg)
+    a = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, path)
+    b = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, path)
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("M,n_t", [(3, 150), (8, 300), (16, 130), (24, 90), (32, 70)])
+def test_split_paths_agree(kbe, M, n_t):
+    """The fused contraction (digits formed inside the kernel, one pass of
+    all 8-orbital parts per unit) and the planes path (encoder, one pass per
+    part) form the same digits and level sums; only the grouping of the
+    double-float partial sums differs (the two partitions of the work), so
+    the slices agree far inside the split path's bound."""
+    t, order, h, L, R = _case(M, n_t, 40 + M, "free")
+    Ld, Rd = _dev(L), _dev(R)
+    n = n_t - 1
+    Sl, Sg = oracle.sigma_row(oracle.local_U4(np.linspace(0.5, 1.5, M)), n, L, R)
+    a = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, "planes")
+    b = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, "fused")
+    assert _rel(b, a) < 1e-12, (M, _rel(b, a))
+
+
+@pytest.mark.parametrize("path", ["planes", "fused"])
 @pytest.mark.parametrize("name", ["chain_m8_n1024", "goe_m32_n1024"])
-def test_split_full_size_sampled(kbe, name):
+def test_split_full_size_sampled(kbe, name, path):
     """Full-size slice n = N_t - 1 of the chain and GOE workloads; the oracle
     evaluates sampled output columns."""
     import torch
@@ -129,6 +149,7 @@ def test_split_full_size_sampled(kbe, name):
     ctx = kbe.Context(M, n_t)
     ctx.set_grid(t, order)
     ctx.set_model(h, U, v, pulse)
+    ctx.set_split_planes(path == "planes")
     n = n_t - 1
     Sl = torch.zeros((n + 1, M, M), dtype=torch.complex128, device="cuda")
     Sg = torch.zeros_like(Sl)
@@ -212,7 +233,8 @@ def test_split_plane_cache_is_exact(kbe, name, n_t):
         r.ctx.close()
 
 
-def test_split_wait_timeout_is_reported_and_the_context_recovers(kbe):
+@pytest.mark.parametrize("path", ["planes", "fused"])
+def test_split_wait_timeout_is_reported_and_the_context_recovers(kbe, path):
     """The device-side failure path of the contraction's pipeline, with no
     fault: one work unit's copies are withheld (kbe_debug_withhold_split)
     and the waits give up after 4096 polls.  The launch returns, the
@@ -227,6 +249,7 @@ def test_split_wait_timeout_is_reported_and_the_context_recovers(kbe):
     ctx = kbe.Context(M, n_t)
     ctx.set_grid(t, order)
     ctx.set_model(h, np.ones(M), W.site_potential(M), None)
+    ctx.set_split_planes(path == "planes")
     Ld, Rd, Sld, Sgd = _dev(L), _dev(R), _dev(Sl), _dev(Sg)
     out = torch.zeros((2, n + 1, M, M), dtype=torch.complex128, device="cuda")
     ctx.history_slice(n, Ld, Rd, Sld, Sgd, out, precision="split")  # planes allocated, kernels loaded
