@@ -157,12 +157,13 @@ __device__ __forceinline__ long long unit_begin(const SplitGeom& g, int cta) { r
 
 // AND of a predicate over the converter warps (named barrier 1); every
 // converter thread must call it at the same point.
+template <int NT = kConvThreads>
 __device__ __forceinline__ bool conv_all(bool ok) {
   uint32_t r;
   asm volatile(
       "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
       : "=r"(r)
-      : "r"((uint32_t)ok), "r"(kConvThreads)
+      : "r"((uint32_t)ok), "r"(NT)
       : "memory");
   return r != 0;
 }
@@ -273,11 +274,11 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
     uint32_t w[kSlices][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      uint32_t dr[kSlices], di[kSlices];
-      digits_bf16(fixed31(er[4 * kg + q], e), dr);
-      digits_bf16(fixed31(ei[4 * kg + q], e), di);
-#pragma unroll
-      for (int sl = 0; sl < kSlices; ++sl) w[sl][q] = __byte_perm(dr[sl], di[sl], 0x5410);
+      const int Vr = fixed31_fast(er[4 * kg + q], e), Vi = fixed31_fast(ei[4 * kg + q], e);
+      w[0][q] = digit_pair_bf16<0>(Vr, Vi);
+      w[1][q] = digit_pair_bf16<1>(Vr, Vi);
+      w[2][q] = digit_pair_bf16<2>(Vr, Vi);
+      w[3][q] = digit_pair_bf16<3>(Vr, Vi);
     }
     const int off = (kg * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
 #pragma unroll
@@ -556,8 +557,9 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
 // Tensor memory: two accumulator buffers of 160 columns and up to three
 // parts' running sums of 64 columns (512 columns), so M <= 24.
 constexpr int kFEpiWarps = 8;
-constexpr int kFConvWarps = kConvThreads / 32;
-constexpr int kFThreads = (kFEpiWarps + kFConvWarps + 3) * 32;  // + producer, two MMA warps: 608
+constexpr int kFConvWarps = 16;                                 // two threads per row and array: 8 K entries each
+constexpr int kFConvThreads = kFConvWarps * 32;
+constexpr int kFThreads = (kFEpiWarps + kFConvWarps + 3) * 32;  // + producer, two MMA warps: 864
 constexpr int kFStageBytes = 3 * kBigTile + 512;                 // PL | Q | QU | column exponents
 constexpr int kFSlots = 2;                                      // small-operand ring
 constexpr int kFMaxParts = 3;
@@ -676,7 +678,7 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
     // thread; sfull: the producer's transaction count; accfull: the first MMA
     // thread's arrival (exponents copied) and both commits; accempty: every
     // epilogue thread
-    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], kConvThreads); mbar_init(&sm.empty[s], 2); }
+    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], kFConvThreads); mbar_init(&sm.empty[s], 2); }
     for (int s = 0; s < kFSlots; ++s) { mbar_init(&sm.sfull[s], 1); mbar_init(&sm.sempty[s], 2); }
     for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 3); mbar_init(&sm.accempty[b], kFEpiWarps * 32); }
     mbar_init(&sm.mmadone[0], 1);
@@ -700,10 +702,12 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
   if (warp >= kFEpiWarps && warp < kProdWarp) {
     // ------------------------------------------------------ converters --
     // Thread ct owns one row j = (c_l, b) of one big operand (arr 0: the
-    // G^< plane from L, arr 1: the Q plane from R) and the chunk's 16 K
-    // entries: 16 loads in flight, then one 16-byte store per K-group.
+    // G^< plane from L, arr 1: the Q plane from R) and half of the chunk's
+    // K entries (8: two K-groups): 8 loads in flight, then one 16-byte store
+    // per K-group and digit (the encoder's balanced digits, fixed31_fast).
     const int ct = tid - kFEpiWarps * 32;
-    const int arr = ct >> 7, jrow = ct & 127;
+    const int arr = ct >> 8, half = (ct >> 7) & 1, jrow = ct & 127;
+    constexpr int kH = kKC / 2;
     for (long long u = ua; u < ub; ++u) {
       const int it = (int)(u - ua);
       const int s = it & 1;
@@ -713,31 +717,32 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
       const int ctile = (int)(lu / S.cpt), kc = (int)(lu % S.cpt);
       const bool row_live = jrow < CT * M;
       const int cl = row_live ? jrow / M : 0, bb = jrow - cl * M;
-      if (!conv_all(wait_f(sm, &sm.empty[s], ((it >> 1) & 1) ^ 1, a.status, a.spin))) break;
+      if (!conv_all<kFConvThreads>(wait_f(sm, &sm.empty[s], ((it >> 1) & 1) ^ 1, a.status, a.spin))) break;
       uint8_t* st = sm.stage[s];
       int* ecol = reinterpret_cast<int*>(st + 3 * kBigTile);
       const int c0 = ctile * CT;
       const int kap0 = kc * kKC;
       const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, bw);
       if (ct < 128) ecol[ct] = 0;
-      asm volatile("bar.sync 1, %0;" ::"r"(kConvThreads) : "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(kFConvThreads) : "memory");
       const double2* base = reinterpret_cast<const double2*>(arr == 0 ? S.L : S.R);
       const int c = c0 + cl;
       const bool col_live = row_live && c <= n;
-      double er[kKC], ei[kKC];
-      unsigned keep = 0;  // bit k: K entry k lies in the tensor-core part of term 2 (m <= c - band_w)
+      double er[kH], ei[kH];
+      unsigned keep = 0;  // bit k: K entry k of this half lies in the tensor-core part of term 2 (m <= c - band_w)
       int ef = 0;
       {
-        int m = kap0 / M, x = kap0 - m * M;
+        const int kap = kap0 + half * kH;
+        int m = kap / M, x = kap - m * M;
 #pragma unroll
-        for (int k = 0; k < kKC; ++k) {
+        for (int k = 0; k < kH; ++k) {
           double2 z = make_double2(0.0, 0.0);
           if (col_live && m <= n) {
             if (m >= c) {
               z = __ldcs(base + tri(m, c) * MM + x * M + bb);
             } else {
               z = __ldcs(base + tri(c, m) * MM + bb * M + x);
-              z.x = -z.x;  // -conj
+              z.x = __hiloint2double(__double2hiint(z.x) ^ (int)0x80000000, __double2loint(z.x));  // -conj
             }
           }
           er[k] = z.x;
@@ -746,32 +751,33 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
           if (++x == M) { x = 0; ++m; }
         }
 #pragma unroll
-        for (int k = 0; k < kKC; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
+        for (int k = 0; k < kH; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
       }
       if (row_live && ef > 0) atomicMax(&ecol[cl], ef);
-      asm volatile("bar.sync 1, %0;" ::"r"(kConvThreads) : "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(kFConvThreads) : "memory");
       if (row_live) {
         const int e = scale_from_field(ecol[cl]);
         uint8_t* dst = st + arr * kBigTile;  // PL or Q
         uint8_t* QU = st + 2 * kBigTile;
         const bool qu = arr == 1 && cls == 2;
 #pragma unroll
-        for (int kg = 0; kg < 4; ++kg) {
+        for (int g2 = 0; g2 < 2; ++g2) {
+          const int kg = 2 * half + g2;
           uint32_t w[kSlices][4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            uint32_t dr[kSlices], di[kSlices];
-            digits_bf16(fixed31(er[4 * kg + q], e), dr);
-            digits_bf16(fixed31(ei[4 * kg + q], e), di);
-#pragma unroll
-            for (int sl = 0; sl < kSlices; ++sl) w[sl][q] = __byte_perm(dr[sl], di[sl], 0x5410);
+            const int Vr = fixed31_fast(er[4 * g2 + q], e), Vi = fixed31_fast(ei[4 * g2 + q], e);
+            w[0][q] = digit_pair_bf16<0>(Vr, Vi);
+            w[1][q] = digit_pair_bf16<1>(Vr, Vi);
+            w[2][q] = digit_pair_bf16<2>(Vr, Vi);
+            w[3][q] = digit_pair_bf16<3>(Vr, Vi);
           }
           const int off = (kg * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
 #pragma unroll
           for (int sl = 0; sl < kSlices; ++sl) {
             *reinterpret_cast<uint4*>(dst + sl * kBigSlice + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
             if (qu) {
-              const unsigned kb = keep >> (4 * kg);
+              const unsigned kb = keep >> (4 * g2);
               *reinterpret_cast<uint4*>(QU + sl * kBigSlice + off) =
                   make_uint4(kb & 1u ? w[sl][0] : 0u, kb & 2u ? w[sl][1] : 0u, kb & 4u ? w[sl][2] : 0u,
                              kb & 8u ? w[sl][3] : 0u);

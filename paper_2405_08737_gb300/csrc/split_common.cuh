@@ -66,6 +66,37 @@ __device__ __forceinline__ void digits_bf16(int V, uint32_t out[kSlices]) {
   out[3] = __float_as_uint(__int_as_float(0x4B000000 | (w & 0xFFu)) - 8388736.0f) >> 16;
 }
 
+// round(v * 2^(31-e)) for |v| < 2^e with one 64-bit shift of the significand
+// (branch-free; the same integer as fixed31).
+__device__ __forceinline__ int fixed31_fast(double v, int e) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const int ef = (int)((hi >> 20) & 0x7FFu);
+  const int s = 1044 + e - ef;  // >= 22 when e bounds the value's exponent
+  const unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  unsigned long long V = (ef == 0 || s > 63) ? 0ull : (m + (1ull << (s - 1))) >> s;
+  V = V > 0x7FFFFFFFull ? 0x7FFFFFFFull : V;
+  return (int)hi < 0 ? -(int)V : (int)V;
+}
+
+// Balanced digit K (0: the top one, in [-128, 128]; 1..3 in [-128, 127]) of
+// Vr and Vi, as a packed bf16 pair (re in the low half): the same digits as
+// digits_bf16, each from one byte permute and one float add (0x4B0000uu is
+// the float 2^23 + u; subtracting 2^23 + 128 leaves u - 128 exactly).
+template <int K>
+__device__ __forceinline__ uint32_t digit_pair_bf16(int Vr, int Vi) {
+  float fr, fi;
+  if (K == 0) {
+    const int dr = (int)(((long long)Vr + 0x808080) >> 24), di = (int)(((long long)Vi + 0x808080) >> 24);
+    fr = __int_as_float(0x4B400000 + dr) - 12582912.0f;
+    fi = __int_as_float(0x4B400000 + di) - 12582912.0f;
+  } else {
+    const unsigned wr = (unsigned)Vr + 0x808080u, wi = (unsigned)Vi + 0x808080u;
+    fr = __int_as_float((int)__byte_perm(wr, 0x4B000000u, 0x7540u | (3 - K))) - 8388736.0f;
+    fi = __int_as_float((int)__byte_perm(wi, 0x4B000000u, 0x7540u | (3 - K))) - 8388736.0f;
+  }
+  return __byte_perm(__float_as_uint(fr), __float_as_uint(fi), 0x7632u);
+}
+
 // Digits as integers (used where the negated digits are needed too).
 __device__ __forceinline__ void digits(double v, int e, int d[kSlices]) {
   const int V = fixed31(v, e);
