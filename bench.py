@@ -386,6 +386,30 @@ def batch_bench(kbe, seed, P, stream, rank=0, world=1):
                                   "unit": "TFLOP/s (history slices, FP64-equivalent)",
                                   "graph_launches_per_step": 1, "kernels_per_step": batch.last_launch_count,
                                   "max_rel_dev_from_plain_fp64": err}
+    out["batched_split"]["contraction"] = ("one persistent tensor-core launch per sweep over every system's "
+                                           "(column tile, history chunk) units, digits formed in the kernel")
+    # the same split steps, one system at a time, with the same contraction (no plane buffer):
+    # what batching itself gains
+    for r in runs:
+        r.ctx.set_split_planes(False)
+    for r, n in zip(runs, rows):  # warm-up
+        r.step(n, P=P, precision="split", stream=stream)
+    torch.cuda.synchronize()
+    seq_launches = 0
+    e0.record(stream)
+    for r, n in zip(runs, rows):
+        r.step(n, P=P, precision="split", stream=stream)
+        seq_launches += r.ctx.last_launch_count
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = parallel.max_over_ranks(e0.elapsed_time(e1))
+    got = new_rows()
+    err = parallel.max_over_ranks(max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(got, ref)))
+    out["split_one_system_at_a_time"] = {
+        "ms_per_step": round(seq_ms, 2), "kernels_per_step": seq_launches,
+        "batched_split_speedup": round(seq_ms / out["batched_split"]["ms_per_step"], 3),
+        "note": "64 kbe_step calls with KBE_SPLIT_BF16 and the same fused contraction (kbe_set_split_planes(0))",
+        "max_rel_dev_from_plain_fp64": err}
     out["batched_fp64"]["roofline_frac_of_fp64_peak"] = round(out["batched_fp64"]["value"] / FP64_PEAK_TFLOPS, 4)
     batch.close()
     for r in runs:

@@ -281,6 +281,7 @@ struct kbe_batch {
   // split precision: the work list of the fused contraction over every
   // active system (host plan, its device image) and the partial sums
   FusedPlanHost fplan;
+  std::vector<int> fplan_rows;           // the rows the work list was built for
   std::vector<unsigned char> fplan_up;   // the image on the device
   void* d_fplan = nullptr;
   size_t fplan_bytes = 0;
@@ -341,7 +342,7 @@ cudaError_t enqueue_step(kbe_batch* b, int P, int precision, const int* rows_hos
         e = launch_history_df(a, s, &k);
         nl += k;
       }
-    } else {  // one persistent tensor-core contraction over every active system's units
+    } else if (b->fplan.n_ent > 0) {  // one persistent tensor-core contraction over every active system's units
       int k = 0;
       e = launch_history_fused(b->fplan, b->d_fplan, b->d_fpart, d.status, s, &k);
       nl += k;
@@ -509,7 +510,7 @@ kbe_status kbe_batch_bind(kbe_batch* b, int i, void* L, void* R, void* S_less, v
   b->bound[i] = 1;
   b->dirty = true;
   drop_graph(b);  // split graphs hold the pointers
-  b->g_rows.clear();  // and so does the split work list: rebuild it
+  b->fplan_rows.clear();  // and so does the split work list: rebuild it
   return KBE_OK;
 }
 
@@ -556,7 +557,10 @@ kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, v
   const bool same_rows = precision == KBE_FP64 ||
                          ((int)b->g_rows.size() == b->n_sys && std::equal(b->g_rows.begin(), b->g_rows.end(), rows));
   if (precision == KBE_SPLIT_BF16 && (e = split_prepare()) != cudaSuccess) return bcuda(b, e, "kbe_batch_step: split setup");
-  if (precision == KBE_SPLIT_BF16 && !same_rows) {  // the work list of these rows, before any capture
+  if (precision == KBE_SPLIT_BF16 &&
+      !((int)b->fplan_rows.size() == b->n_sys && std::equal(b->fplan_rows.begin(), b->fplan_rows.end(), rows))) {
+    // the work list of these rows, before any capture
+    b->fplan_rows.clear();
     std::vector<FusedSystem> fs;
     for (int i = 0; i < b->n_sys; ++i) {
       if (rows[i] < 1) continue;
@@ -601,6 +605,7 @@ kbe_status kbe_batch_step(kbe_batch* b, const int* rows, int P, int precision, v
         b->fplan_up = b->fplan.image;
       }
     }
+    b->fplan_rows.assign(rows, rows + b->n_sys);
   }
   if (!b->graph || b->g_P != P || b->g_prec != precision || b->g_block != b->dev.block ||
       b->g_work != b->dev.item_work_log2 || !same_rows) {

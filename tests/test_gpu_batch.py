@@ -189,3 +189,28 @@ def test_batch_autotune_and_errors(kbe):
     assert e.value.status == kbe.KBE_EINVAL
     del rows
     batch.close()
+
+
+def test_batch_precisions_alternate_on_the_same_rows(kbe):
+    """A split step right after an FP64 step of the same rows (and the FP64
+    step again after it) rebuilds the split work list for those rows: each
+    step matches the single-system stepper in its precision."""
+    runs = _runs(kbe)
+    batch = kbe.Batch(runs)
+    _advance(batch, SYSTEMS, upto=10)
+    rows = [min(10, s[1] - 1) for s in SYSTEMS]
+    single = _runs(kbe)
+    for run, s in zip(single, SYSTEMS):
+        for n in range(1, 10):
+            run.step(n, P=2)
+    for prec, tol in (("fp64", 1e-13), ("split", 1e-12), ("fp64", 1e-13)):
+        batch.step(rows, P=2, precision=prec)
+        batch.sync_status()
+        for a, b, n in zip(runs, single, rows):
+            b.ctx.set_split_planes(False)
+            b.step(n, P=2, precision=prec)
+            b.ctx.sync_status()
+            p = W.tri_size(n)
+            err = _rel(a.L[p:p + n + 1].cpu().numpy(), b.L[p:p + n + 1].cpu().numpy())
+            assert err < tol, (prec, n, err)
+    batch.close()
