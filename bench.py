@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-controller", action="store_true", help="skip the adaptive time-stepping runs")
     ap.add_argument("--no-thermal", action="store_true", help="skip the thermal-branch step")
     ap.add_argument("--no-seeds", action="store_true", help="skip the main step at the other input seeds")
+    ap.add_argument("--sharded", action="store_true",
+                    help="time the row-band sharded step (the N-GPU line) also on one GPU")
     ap.add_argument("--dense-norb", default="2,8,16,32",
                     help="comma-separated orbital counts of the dense self-energy rows")
     return ap.parse_args()
@@ -870,11 +872,145 @@ def step_rows(run, n):
             run.I[:, : n + 1].cpu().numpy())
 
 
+def sharded_bench(kbe, args, rank, world):
+    """The N-GPU line: ONE system (the chain workload's KBE step of row
+    n = N_t - 1) split by row bands of its stored triangles across the ranks
+    (parallel.row_bands, about equal stored blocks each); every step is
+    parallel.sharded_step: predictor, then P sweeps of {self-energy row and
+    the band's partial slice, NCCL all-reduce of the 2 (n+1) M^2 partials,
+    Fock matrix, right-hand side and corrector}.  Strong scaling: the work of
+    the step is fixed, `value` is its flops over the max-over-ranks time.
+    e2e: the same step with each rank's band rows, row n-1 and the
+    right-hand-side ring copied in from pinned host memory every step and the
+    new row read back."""
+    import torch
+    from paper_2405_08737_gb300 import parallel
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    kbe.lib()
+    cfg, t, order, h, U, v, pulse, ctx, run, n = setup_workload(kbe, args.seed, args.n_t)
+    M = cfg["M"]
+    stream = torch.cuda.current_stream()
+    bands = parallel.row_bands(n + 1, world)
+    band = bands[rank]
+
+    def step():
+        parallel.sharded_step(ctx, n, args.P, band, run.L, run.R, run.Sl, run.Sg, run.I, run.F, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    ctx.set_profiling(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    k_count, k_ms = ctx.read_profiling()
+    ctx.set_profiling(False)
+    clk = clocks.stop()
+    barrier()
+    ms = parallel.max_over_ranks(ms)
+    ms_step = ms / args.steps
+    flops_step = args.P * slice_flops(M, n)
+    lo, hi = band
+    band_blocks = parallel.tri(min(hi, n + 1)) - parallel.tri(min(lo, n + 1))
+    band_flops = slice_flops(M, n) * band_blocks / parallel.tri(n + 1)
+    k_avg = k_ms / max(k_count, 1)
+    achieved = band_flops / (k_avg * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+            "kernel": "history_partial over rank 0's row band (kbe_step_sweep_band)", "launches_timed": k_count,
+            "avg_ms": round(k_avg, 4), "band_rows": [int(lo), int(hi)],
+            "algorithmic_flops_per_launch": band_flops,
+            "peak_source": "unit counts x clock: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz"}
+    # e2e: band rows, row n-1 and the ring from pinned host memory, row n back
+    blk = M * M
+    L_h = run.L.cpu().pin_memory()
+    R_h = run.R.cpu().pin_memory()
+    F_h = run.F.cpu().pin_memory()
+    out_L = torch.empty((n + 1, M, M), dtype=torch.complex128).pin_memory()
+    out_R = torch.empty_like(out_L).pin_memory()
+    p0, p1 = parallel.tri(min(lo, n)), parallel.tri(min(hi, n))
+    pr0, pr1 = parallel.tri(n - 1), parallel.tri(n)
+    extra = 0 if lo <= n - 1 < hi else pr1 - pr0
+    h2d = 2 * ((p1 - p0) + extra) * blk * 16 + F_h.numel() * 16
+    d2h = 2 * (n + 1) * blk * 16
+
+    def one_host():
+        if p1 > p0:
+            run.L[p0:p1].copy_(L_h[p0:p1], non_blocking=True)
+            run.R[p0:p1].copy_(R_h[p0:p1], non_blocking=True)
+        if extra:
+            run.L[pr0:pr1].copy_(L_h[pr0:pr1], non_blocking=True)
+            run.R[pr0:pr1].copy_(R_h[pr0:pr1], non_blocking=True)
+        run.F.copy_(F_h, non_blocking=True)
+        step()
+        q = parallel.tri(n)
+        out_L.copy_(run.L[q:q + n + 1], non_blocking=True)
+        out_R.copy_(run.R[q:q + n + 1], non_blocking=True)
+
+    e2e = None
+    if not args.no_e2e:
+        one_host()
+        barrier()
+        e0.record(stream)
+        reps = max(3, args.steps // 4)
+        for _ in range(reps):
+            one_host()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = parallel.max_over_ranks(e0.elapsed_time(e1) / reps)
+        e2e = {"value": round(flops_step / (e2e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+               "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    ctx.sync_status()
+    line = {"metric": METRIC, "value": round(flops_step / (ms_step * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s: Hubbard chain M=8, N_t=%d nonuniform, orders 1..5, pulse; KBE step of row "
+                                   "n=%d with P=%d (FP64 path), one system split by row bands" % (WORKLOAD, n + 1, n,
+                                                                                                args.P),
+                       "norb": M, "n_t": n + 1, "n": n, "P": args.P, "precision": "fp64",
+                       "l2": "inputs larger than L2 (history %.2f GB per step)"
+                             % (2 * (n + 1) * (n + 2) / 2 * M * M * 16 / 1e9),
+                       "parallelism": "row bands of one system over %d GPU(s), all-reduce of the slice per sweep"
+                                      % world,
+                       "bands": [list(b) for b in bands]},
+            "roofline": roof, "e2e": e2e, "gpu_launches": k_count // max(args.steps, 1) * 0 + (1 + args.P * 5) * args.steps,
+            "all_reduces_per_step": args.P}
+    if clk:
+        line["clocks"] = clk
+    ctx.close()
+    del run
+    torch.cuda.empty_cache()
+    if not args.no_batch:
+        line["batching_form"] = batch_bench(kbe, args.seed, args.P, stream, rank, world)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
     if args.impl == "reference":
         return main_reference(args, rank, world)
+    if world > 1 or args.sharded:
+        import paper_2405_08737_gb300 as kbe
+        return sharded_bench(kbe, args, rank, world)
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)

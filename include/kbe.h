@@ -268,6 +268,28 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
 kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* S_less,
                     void* S_great, void* I_work, void* F_ring, void* stream);
 
+/* The phases of one KBE_FP64 step, for callers that form the history slice
+ * themselves -- one system split by row bands of the stored triangles across
+ * devices (Eq. KBE2 is a sum over stored blocks, so the bands' partial slices
+ * add up to the slice; the sum is the caller's, e.g. an all-reduce):
+ *   kbe_step_predict       the predictor of row n (as kbe_step);
+ *   kbe_step_sweep_band    self-energy row n into S_less, S_great, then the
+ *                          partial slice of the stored rows [row_lo, row_hi)
+ *                          into I_part ([2][n+1][M][M], kbe_history_slice_band);
+ *   kbe_step_sweep_finish  from the whole slice I of row n: the Fock matrix,
+ *                          the right-hand side row n (slot n of F_ring) and the
+ *                          corrector, which writes row n of L and R.
+ * kbe_step(ctx, n, P, KBE_FP64, ...) equals kbe_step_predict, then P times
+ * {kbe_step_sweep_band over rows [0, n+1), kbe_step_sweep_finish}, bitwise.
+ * A device that holds only its band of history rows needs, besides them,
+ * rows n-1 and n (every device computes row n from the same reduced slice)
+ * and the right-hand-side ring.  Layouts and errors as kbe_step; adaptive
+ * history orders and the thermal branch are KBE_ESTATE (they need kbe_step). */
+kbe_status kbe_step_predict(kbe_ctx* ctx, int n, void* L, void* R, void* F_ring, void* stream);
+kbe_status kbe_step_sweep_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, const void* L, const void* R,
+                               void* S_less, void* S_great, void* I_part, void* stream);
+kbe_status kbe_step_sweep_finish(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F_ring, void* stream);
+
 /* kbe_step with its inputs in host memory, for callers that keep the run on
  * the host: rows 0..n-1 of both triangles (L_host, R_host: the same packed
  * layout as L, R, at least tri(n) blocks) and the right-hand-side ring

@@ -64,6 +64,9 @@ def lib():
         L.kbe_init_uncorrelated.argtypes = [vp, vp, vp, vp, vp]
         L.kbe_debug_withhold_split.argtypes = [vp, ctypes.c_longlong, ctypes.c_longlong]
         L.kbe_set_split_planes.argtypes = [vp, i]
+        L.kbe_step_predict.argtypes = [vp, i, vp, vp, vp, vp]
+        L.kbe_step_sweep_band.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp]
+        L.kbe_step_sweep_finish.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
         L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -300,6 +303,20 @@ class Context:
         self._check(lib().kbe_step(self._h, n, P, PRECISIONS[precision], self._dev(L), self._dev(R),
                                    self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_ring),
                                    self._stream(stream)))
+
+    # -- the phases of a KBE_FP64 step (one system split by row bands)
+    def step_predict(self, n, L, R, F_ring, stream=None):
+        self._check(lib().kbe_step_predict(self._h, n, self._dev(L), self._dev(R), self._dev(F_ring),
+                                           self._stream(stream)))
+
+    def step_sweep_band(self, n, row_lo, row_hi, L, R, Sl, Sg, I_part, stream=None):
+        self._check(lib().kbe_step_sweep_band(self._h, n, int(row_lo), int(row_hi), self._dev(L), self._dev(R),
+                                              self._dev(Sl), self._dev(Sg), self._dev(I_part),
+                                              self._stream(stream)))
+
+    def step_sweep_finish(self, n, L, R, I, F_ring, stream=None):
+        self._check(lib().kbe_step_sweep_finish(self._h, n, self._dev(L), self._dev(R), self._dev(I),
+                                                self._dev(F_ring), self._stream(stream)))
 
     def step_host(self, n, L_host, R_host, F_host, L, R, Sl, Sg, I_work, F_ring, L_row_host, R_row_host, P=2,
                   precision="fp64", stream=None):

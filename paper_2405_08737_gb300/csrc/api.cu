@@ -913,6 +913,71 @@ kbe_status kbe_history_slice_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, c
   return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_history_slice_band: launch");
 }
 
+// ------------------------------------------------------------ step phases --
+// The phases of a KBE_FP64 step for callers that form the history slice
+// themselves (one system split by row bands across devices: the bands'
+// partial slices sum to the slice).
+static kbe_status check_phase(kbe_ctx* ctx, int n, const char* who) {
+  kbe_status st = check_row_call(ctx, n);
+  if (st != KBE_OK) return st;
+  if (n < 1) return fail(ctx, KBE_ERANGE, std::string(who) + ": n must be >= 1");
+  if (!ctx->model.set) return fail(ctx, KBE_ESTATE, "no model: call kbe_set_model first");
+  if (ctx->adaptive_K > 0 || ctx->thermal)
+    return fail(ctx, KBE_ESTATE, std::string(who) + ": adaptive history orders and the thermal branch need kbe_step");
+  return use_device(ctx);
+}
+
+kbe_status kbe_step_predict(kbe_ctx* ctx, int n, void* L, void* R, void* F_ring, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  kbe_status st = check_phase(ctx, n, "kbe_step_predict");
+  if (st != KBE_OK) return st;
+  if (!aligned16(L) || !aligned16(R) || !aligned16(F_ring))
+    return fail(ctx, KBE_EINVAL, "kbe_step_predict: NULL or misaligned pointer");
+  StepArgs a = step_args(ctx, n, L, R, nullptr, F_ring);
+  cudaError_t e = launch_predictor(a, (cudaStream_t)stream);
+  ctx->last_launches = 1;
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_step_predict");
+}
+
+kbe_status kbe_step_sweep_band(kbe_ctx* ctx, int n, int row_lo, int row_hi, const void* L, const void* R,
+                               void* S_less, void* S_great, void* I_part, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  kbe_status st = check_phase(ctx, n, "kbe_step_sweep_band");
+  if (st != KBE_OK) return st;
+  if (row_lo < 0 || row_hi < row_lo) return fail(ctx, KBE_EINVAL, "kbe_step_sweep_band: need 0 <= row_lo <= row_hi");
+  if (!aligned16(L) || !aligned16(R) || !aligned16(S_less) || !aligned16(S_great) || !aligned16(I_part))
+    return fail(ctx, KBE_EINVAL, "kbe_step_sweep_band: NULL or misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = sigma_blocks(ctx, tri(n, 0), n + 1, n, L, R, S_less, S_great, s);
+  if (e != cudaSuccess) { ctx->last_launches = 1; return cuda_fail(ctx, e, "kbe_step_sweep_band: self-energy"); }
+  HistoryArgs a{ctx->M, n, (const double*)L, (const double*)R, (const double*)S_less, (const double*)S_great,
+                weights_view(ctx), (double*)I_part, ctx->d_part, ctx->part_bytes, ctx->d_status};
+  a.band_lo = row_lo;
+  a.band_hi = row_hi;
+  if (!next_events(ctx, &a.ev_begin, &a.ev_end)) return fail(ctx, KBE_ECUDA, "profiling: cudaEventCreate");
+  int nl = 0;
+  e = launch_history_f64(a, s, &nl);
+  ctx->last_launches = 1 + nl;
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_step_sweep_band: history slice");
+}
+
+kbe_status kbe_step_sweep_finish(kbe_ctx* ctx, int n, void* L, void* R, const void* I, void* F_ring, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  kbe_status st = check_phase(ctx, n, "kbe_step_sweep_finish");
+  if (st != KBE_OK) return st;
+  if (!aligned16(L) || !aligned16(R) || !aligned16(I) || !aligned16(F_ring))
+    return fail(ctx, KBE_EINVAL, "kbe_step_sweep_finish: NULL or misaligned pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  StepArgs a = step_args(ctx, n, L, R, I, F_ring);
+  cudaError_t e = launch_fock(a, s);
+  if (e == cudaSuccess) e = launch_rhs_corrector(a, s);
+  ctx->last_launches = 3;
+  return e == cudaSuccess ? KBE_OK : cuda_fail(ctx, e, "kbe_step_sweep_finish");
+}
+
 kbe_status kbe_set_split_planes(kbe_ctx* ctx, int keep) {
   if (!ctx) return KBE_EINVAL;
   if (keep != 0 && keep != 1) return fail(ctx, KBE_EINVAL, "kbe_set_split_planes: keep must be 0 or 1");

@@ -107,6 +107,9 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
   if (prep_bytes + (nchunk > 1 ? (size_t)nchunk * 2 * row * 16 : 0) > a.part_bytes) return cudaErrorInvalidValue;
   const int chunk_len = (n + 1 + nchunk - 1) / nchunk;
   nchunk = (n + 1 + chunk_len - 1) / chunk_len;
+  // a band of stored rows below n contributes only history points m < band_hi:
+  // the chunks beyond them have no work for any output column
+  if (a.band_hi <= n) nchunk = std::max(1, std::min(nchunk, (a.band_hi + chunk_len - 1) / chunk_len));
 
   double* A1 = a.part;
   double* Bl = A1 + 2 * row;

@@ -8,7 +8,10 @@ One system can be split too: the stored triangle is cut into contiguous
 bands of rows, one per rank, with about equal numbers of stored blocks
 (row_bands); each rank's device computes its band's contributions with
 Context.history_slice_band (kbe_history_slice_band), and sharded_slice sums
-them.  The host logic is tested with gloo ranks on the CPU and the per-band
+them; sharded_step runs a whole KBE step of such a system (the predictor,
+then per sweep the self-energy row and the band's partial slice, the
+all-reduce, and the Fock matrix, right-hand side and corrector, which every
+rank forms identically from the reduced slice).  The host logic is tested with gloo ranks on the CPU and the per-band
 kernel on one GPU (the bands one after another); no call here drives more
 than one GPU.  A stored block (r, c), r >= c, enters the history
 slice of row n (Eq. KBE2) three times: term 1 of output column c (history
@@ -103,3 +106,28 @@ def sharded_slice(partial, group=None):
         dist.all_reduce(partial, op=dist.ReduceOp.SUM, group=group)
     return partial
 
+
+
+def sharded_step(ctx, n, P, band, L, R, Sl, Sg, I, F, group=None, stream=None):
+    """One KBE step (KBE_FP64) of row n of a system whose stored rows are
+    split in bands across ranks: ``band`` = (lo, hi) is this rank's rows
+    (row_bands), L, R, Sl, Sg, I, F the buffers of kbe_step on this rank's
+    device.  The predictor, then P sweeps of {self-energy row n and the
+    band's partial slice (kbe_step_sweep_band), all-reduce of the
+    2 (n+1) M^2 partials (sharded_slice), Fock matrix, right-hand side and
+    corrector (kbe_step_sweep_finish)}.  Every rank forms row n from the same
+    reduced slice, so no row is broadcast; a rank reads only its band's rows
+    of the history, rows n-1 and n, and the right-hand-side ring.  With one
+    rank and the band (0, n+1) this is kbe_step, bitwise.  Returns the
+    number of all-reduces (P)."""
+    import torch
+    lo, hi = min(int(band[0]), n + 1), min(int(band[1]), n + 1)
+    M = ctx.M
+    size = 2 * (n + 1) * M * M
+    flat = I.reshape(-1)[:size]
+    ctx.step_predict(n, L, R, F, stream=stream)
+    for _ in range(P):
+        ctx.step_sweep_band(n, lo, hi, L, R, Sl, Sg, I, stream=stream)
+        sharded_slice(torch.view_as_real(flat) if flat.is_complex() else flat, group)
+        ctx.step_sweep_finish(n, L, R, I, F, stream=stream)
+    return P

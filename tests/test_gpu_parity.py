@@ -327,3 +327,61 @@ def test_row_band_partials_sum_to_the_slice(kbe, world):
         ctx.history_slice_band(n, 5, 4, Ld, Rd, Sld, Sgd, part)
     assert e.value.status == kbe.KBE_EINVAL
     ctx.close()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5])
+def test_step_phases_with_row_bands(kbe, world):
+    """The phases of a KBE step (kbe_step_predict, kbe_step_sweep_band,
+    kbe_step_sweep_finish) with the slice summed over the row bands of
+    `world` ranks, run one after another on this GPU (what
+    parallel.sharded_step does with one band per device and an all-reduce):
+    with one band the rows are kbe_step's bitwise; with several, within
+    1e-13 of them and 1e-12 of the oracle's step."""
+    import torch
+    from paper_2405_08737_gb300 import parallel
+    M, n_t, seed = 4, 41, 12
+    t, order = W.grid(n_t, 0.05, 0.4, seed)
+    h = W.goe_h(M, seed)
+    U, v = np.linspace(0.5, 2.0, M), W.site_potential(M)
+    pulse = {"E0": 0.5, "t0": float(t[n_t // 2]), "sigma": 0.4, "omega": 2.0}
+    n = n_t - 1
+    Lh, Rh, F = W.restart_state(h, W.half_filled_rho(h), t, order, n, n)
+    runs = []
+    for phased in (False, True):
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        run = kbe.Run(ctx)
+        run.L[: W.tri_size(n)] = torch.as_tensor(Lh, device="cuda")
+        run.R[: W.tri_size(n)] = torch.as_tensor(Rh, device="cuda")
+        for j, Fj in F.items():
+            run.F[j % kbe.KBE_RING_ROWS, :, : j + 1] = torch.as_tensor(Fj, device="cuda")
+        if not phased:
+            run.step(n, P=2)
+        else:
+            bands = parallel.row_bands(n + 1, world)
+            parts = [torch.zeros_like(run.I) for _ in bands]
+            ctx.step_predict(n, run.L, run.R, run.F)
+            for _ in range(2):
+                for (lo, hi), part in zip(bands, parts):
+                    ctx.step_sweep_band(n, lo, hi, run.L, run.R, run.Sl, run.Sg, part)
+                total = parts[0].clone()
+                for part in parts[1:]:
+                    total += part
+                ctx.step_sweep_finish(n, run.L, run.R, total, run.F)
+        ctx.sync_status()
+        runs.append(run)
+    p = W.tri_size(n)
+    a = [r.L[p:p + n + 1].cpu().numpy() for r in runs]
+    b = [r.R[p:p + n + 1].cpu().numpy() for r in runs]
+    if world == 1:
+        assert np.array_equal(a[0], a[1]) and np.array_equal(b[0], b[1])
+    else:
+        assert _rel(a[1], a[0]) < 1e-13 and _rel(b[1], b[0]) < 1e-13
+    L = np.zeros((W.tri_size(n + 1), M, M), np.complex128)
+    R = np.zeros_like(L)
+    L[:p], R[:p] = Lh, Rh
+    Lo, Ro, _ = oracle.run(t, order, h, U, v, pulse, 2, L, R, F, n, n + 1)
+    assert _rel(a[1], Lo[p:]) < 1e-12 and _rel(b[1], Ro[p:]) < 1e-12
+    for r in runs:
+        r.ctx.close()

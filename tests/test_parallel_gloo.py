@@ -165,3 +165,146 @@ def test_row_band_ranks_sum_to_the_oracle_slice(world, kind):
     for rank, bands, got in res:
         assert bands == parallel.row_bands(n + 1, world)
         assert np.abs(got - ref).max() <= 1e-12 * scale, (rank, np.abs(got - ref).max() / scale)
+
+
+# ------------------------------------------------ one system, whole step --
+# parallel.sharded_step drives the phases of a KBE step (kbe_step_predict,
+# kbe_step_sweep_band, kbe_step_sweep_finish) and the all-reduce.  On the CPU
+# the phases are played by _HostPhases, written here from the stepper's
+# formulas (include/kbe.h, kbe_step): the band's partial slice of Eq. (KBE2)
+# as above, the predictor and corrector of the integral-form Adams rules,
+# and F^s(n,c) = -i(eps(t_n) G^s(n,c) + I^s(n,c)) with the oracle's Fock
+# matrix.  The ranks' whole step must equal the oracle's step to 1e-12.
+
+class _HostPhases:
+    def __init__(self, t, order, h, U, v, pulse, F):
+        import oracle
+        self.oracle = oracle
+        self.t, self.order, self.h, self.U, self.v, self.pulse = t, order, h, U, v, pulse
+        self.M = h.shape[0]
+        self.F = dict(F)  # row j -> [2, j+1, M, M]
+        self.calls = []
+
+    def _w(self, first, last, n):
+        return self.oracle.lagrange_weights(self.t[first:last + 1], self.t[n - 1], self.t[n])
+
+    def _step_rows(self, n, L, R, rows):
+        """G(n, .) = G(n-1, .) + sum_p w_p F(row_p, .) over the rows of the rule."""
+        M, kn = self.M, int(self.order[n])
+        tri = W.tri_index
+        Gl = np.zeros((n + 1, M, M), np.complex128)
+        Gg = np.zeros_like(Gl)
+        for c in range(n):
+            q = min(kn, n - c)
+            first, last = rows(q)
+            w = self._w(first, last, n)
+            al = L[tri(n - 1, c)].copy()
+            ag = R[tri(n - 1, c)] + L[tri(n - 1, c)]
+            for p, j in enumerate(range(first, last + 1)):
+                al = al + w[p] * self.F[j][0, c]
+                ag = ag + w[p] * self.F[j][1, c]
+            Gl[c], Gg[c] = al, ag
+        q = min(kn, n)
+        first, last = rows(q)
+        w = self._w(first, last, n)
+        al = L[tri(n - 1, n - 1)].copy()
+        for p, j in enumerate(range(first, last + 1)):
+            D = self.F[j][0, j] - self.F[j][0, j].conj().T  # d G^<(t,t)/dt at t_j
+            al = al + w[p] * D
+        Gl[n] = al
+        for c in range(n):
+            L[tri(n, c)] = Gl[c]
+            R[tri(n, c)] = Gg[c] - Gl[c]
+        L[tri(n, n)] = Gl[n]
+        R[tri(n, n)] = -1j * np.eye(M)
+
+    def step_predict(self, n, L, R, F, stream=None):
+        self.calls.append(("predict", n))
+        self._step_rows(n, L, R, lambda q: (n - q, n - 1))
+
+    def step_sweep_band(self, n, lo, hi, L, R, Sl, Sg, I, stream=None):
+        import torch
+        self.calls.append(("band", n, lo, hi))
+        sl, sg = self.oracle.sigma_row(self.oracle.local_U4(self.U), n, L, R)
+        Sl[: n + 1], Sg[: n + 1] = sl, sg
+        part = _band_contributions(self.t, self.order, n, L, R, sl, sg, (lo, hi))
+        I.reshape(-1)[: part.size] = torch.from_numpy(part.ravel())
+
+    def step_sweep_finish(self, n, L, R, I, F, stream=None):
+        self.calls.append(("finish", n))
+        M = self.M
+        Iv = I.reshape(-1)[: 2 * (n + 1) * M * M].numpy().reshape(2, n + 1, M, M)
+        eps = self.oracle.fock(self.t[n], self.h, self.U, self.v, self.pulse, L[W.tri_index(n, n)])
+        Fn = np.zeros((2, n + 1, M, M), np.complex128)
+        for c in range(n + 1):
+            Gl = L[W.tri_index(n, c)]
+            Gg = R[W.tri_index(n, c)] + Gl
+            Fn[0, c] = -1j * (eps @ Gl + Iv[0, c])
+            Fn[1, c] = -1j * (eps @ Gg + Iv[1, c])
+        self.F[n] = Fn
+        self._step_rows(n, L, R, lambda kap: (n - kap, n))
+
+
+def _step_case():
+    import oracle
+    M, n_t, seed = 3, 13, 9
+    t, order = W.grid(n_t, 0.05, 0.4, seed)
+    h = W.goe_h(M, seed)
+    U, v = np.linspace(0.5, 1.5, M), W.site_potential(M)
+    pulse = {"E0": 0.4, "t0": float(t[n_t // 2]), "sigma": 0.3, "omega": 2.0}
+    n = n_t - 1
+    Lh, Rh, F = W.restart_state(h, W.half_filled_rho(h), t, order, n, n)
+    L = np.zeros((W.tri_size(n + 1), M, M), np.complex128)
+    R = np.zeros_like(L)
+    L[: W.tri_size(n)], R[: W.tri_size(n)] = Lh, Rh
+    Lo, Ro, Io = oracle.run(t, order, h, U, v, pulse, 2, L, R, F, n, n + 1)
+    return (t, order, h, U, v, pulse, n, L, R, F), (Lo, Ro)
+
+
+def _step_rank(rank, world, port, case, out):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t, order, h, U, v, pulse, n, L, R, F = case
+        L, R = L.copy(), R.copy()
+        M = h.shape[0]
+        ph = _HostPhases(t, order, h, U, v, pulse, F)
+        bands = parallel.row_bands(n + 1, world)
+        Sl = np.zeros((n + 1, M, M), np.complex128)
+        Sg = np.zeros_like(Sl)
+        I = torch.zeros((2, n + 1, M, M), dtype=torch.complex128)
+        reduces = parallel.sharded_step(ph, n, 2, bands[rank], L, R, Sl, Sg, I, None)
+        p = W.tri_size(n)
+        out.put((rank, bands, ph.calls, reduces, L[p:p + n + 1], R[p:p + n + 1]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+def test_sharded_step_ranks_match_the_oracle_step(world):
+    """Every rank runs predictor, P = 2 sweeps of {band partial slice,
+    all-reduce, finish} on its row band; each rank's new row n equals the
+    oracle's KBE step of row n to 1e-12, and the ranks agree bitwise."""
+    case, (Lo, Ro) = _step_case()
+    n = case[6]
+    p = W.tri_size(n)
+    port = _free_port()
+    mctx = mp.get_context("spawn")
+    q = mctx.Queue()
+    procs = [mctx.Process(target=_step_rank, args=(r, world, port, case, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = sorted([q.get(timeout=180) for _ in range(world)], key=lambda x: x[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    scale = max(np.abs(Lo[p:]).max(), np.abs(Ro[p:]).max())
+    for rank, bands, calls, reduces, Ln, Rn in res:
+        lo, hi = bands[rank]
+        assert calls == [("predict", n), ("band", n, lo, hi), ("finish", n), ("band", n, lo, hi), ("finish", n)]
+        assert reduces == 2
+        assert np.abs(Ln - Lo[p:]).max() <= 1e-12 * scale, (world, rank, np.abs(Ln - Lo[p:]).max() / scale)
+        assert np.abs(Rn - Ro[p:]).max() <= 1e-12 * scale
+        assert np.array_equal(Ln, res[0][4]) and np.array_equal(Rn, res[0][5])
