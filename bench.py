@@ -894,8 +894,11 @@ def sharded_bench(kbe, args, rank, world):
     bands = parallel.row_bands(n + 1, world)
     band = bands[rank]
 
+    launches = [0]
+
     def step():
-        parallel.sharded_step(ctx, n, args.P, band, run.L, run.R, run.Sl, run.Sg, run.I, run.F, stream=stream)
+        launches[0] = parallel.sharded_step(ctx, n, args.P, band, run.L, run.R, run.Sl, run.Sg, run.I, run.F,
+                                            stream=stream)["kernels"]
 
     def barrier():
         torch.cuda.synchronize()
@@ -987,7 +990,7 @@ def sharded_bench(kbe, args, rank, world):
                        "parallelism": "row bands of one system over %d GPU(s), all-reduce of the slice per sweep"
                                       % world,
                        "bands": [list(b) for b in bands]},
-            "roofline": roof, "e2e": e2e, "gpu_launches": k_count // max(args.steps, 1) * 0 + (1 + args.P * 5) * args.steps,
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches[0] * args.steps,
             "all_reduces_per_step": args.P}
     if clk:
         line["clocks"] = clk
