@@ -119,15 +119,19 @@ def sharded_step(ctx, n, P, band, L, R, Sl, Sg, I, F, group=None, stream=None):
     reduced slice, so no row is broadcast; a rank reads only its band's rows
     of the history, rows n-1 and n, and the right-hand-side ring.  With one
     rank and the band (0, n+1) this is kbe_step, bitwise.  Returns the
-    number of all-reduces (P)."""
+    numbers of all-reduces (P) and of the kernels the phases launched."""
     import torch
     lo, hi = min(int(band[0]), n + 1), min(int(band[1]), n + 1)
     M = ctx.M
     size = 2 * (n + 1) * M * M
     flat = I.reshape(-1)[:size]
+    kernels = 0
     ctx.step_predict(n, L, R, F, stream=stream)
+    kernels += getattr(ctx, "last_launch_count", 0)
     for _ in range(P):
         ctx.step_sweep_band(n, lo, hi, L, R, Sl, Sg, I, stream=stream)
+        kernels += getattr(ctx, "last_launch_count", 0)
         sharded_slice(torch.view_as_real(flat) if flat.is_complex() else flat, group)
         ctx.step_sweep_finish(n, L, R, I, F, stream=stream)
-    return P
+        kernels += getattr(ctx, "last_launch_count", 0)
+    return {"all_reduces": P, "kernels": kernels}

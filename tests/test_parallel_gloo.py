@@ -304,7 +304,7 @@ def test_sharded_step_ranks_match_the_oracle_step(world):
     for rank, bands, calls, reduces, Ln, Rn in res:
         lo, hi = bands[rank]
         assert calls == [("predict", n), ("band", n, lo, hi), ("finish", n), ("band", n, lo, hi), ("finish", n)]
-        assert reduces == 2
+        assert reduces["all_reduces"] == 2
         assert np.abs(Ln - Lo[p:]).max() <= 1e-12 * scale, (world, rank, np.abs(Ln - Lo[p:]).max() / scale)
         assert np.abs(Rn - Ro[p:]).max() <= 1e-12 * scale
         assert np.array_equal(Ln, res[0][4]) and np.array_equal(Rn, res[0][5])
