@@ -81,6 +81,7 @@ def parse():
     ap.add_argument("--no-controller", action="store_true", help="skip the adaptive time-stepping runs")
     ap.add_argument("--no-thermal", action="store_true", help="skip the thermal-branch step")
     ap.add_argument("--no-seeds", action="store_true", help="skip the main step at the other input seeds")
+    ap.add_argument("--no-runs", action="store_true", help="skip the whole-run measurements")
     ap.add_argument("--sharded", action="store_true",
                     help="time the row-band sharded step (the N-GPU line) also on one GPU")
     ap.add_argument("--dense-norb", default="2,8,16,32",
@@ -846,6 +847,76 @@ def precision_m32_bench(kbe, seed, stream, steps):
             "gpu_launches": {"fp64": launches, "split": launches_s}}
 
 
+def whole_runs(kbe, seed, P, stream, oracle_rows=64):
+    """Whole second-Born runs from the uncorrelated state: every KBE step of
+    the dimer (N_t = 64) and of the 8-orbital chain (N_t = 1024, with its
+    pulse), in FP64, split and double-float precision.  Per run: the time of
+    all steps (CUDA events around the step loop, host launches included),
+    the final site densities n_a(T_f) = Im G^<_aa(T_f, T_f) and their
+    deviation from the FP64 run's, and the FP64 and split runs' first rows
+    against the oracle's run of the same grid."""
+    import torch
+    import oracle
+    import workloads as W
+    out = {}
+    for name in ("dimer_m2_n64", "chain_m8_n1024"):
+        cfg = W.CONFIGS[name]
+        M, n_t = cfg["M"], cfg["n_t"]
+        t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], seed)
+        h, U, v, pulse = W.build_model(cfg, seed)
+        rho0 = W.half_filled_rho(h)
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        res = {"workload": "%s: all %d KBE steps from the uncorrelated state, P=%d" % (name, n_t - 1, P),
+               "slice_flops_total": sum(P * slice_flops(M, n) for n in range(1, n_t))}
+        dens = {}
+        head = {}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for prec in ("fp64", "split", "df64"):
+            run = kbe.Run(ctx)
+            ctx.reset_cache()
+            run.init_uncorrelated(rho0, stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0.record(stream)
+            for n in range(1, n_t):
+                run.step(n, P=P, precision=prec, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            ctx.sync_status()
+            ms = e0.elapsed_time(e1)
+            last = run.L[W.tri_index(n_t - 1, n_t - 1)].cpu().numpy()
+            dens[prec] = np.imag(np.diag(last))
+            head[prec] = run.L[: W.tri_size(min(oracle_rows, n_t))].cpu().numpy()
+            res[prec] = {"ms_total": round(ms, 2), "host_wall_s": round(wall, 3),
+                         "tflops": round(res["slice_flops_total"] / (ms * 1e-3) / 1e12, 4)}
+            del run
+            torch.cuda.empty_cache()
+        for prec in ("split", "df64"):
+            d = dens[prec] - dens["fp64"]
+            res[prec]["final_density_max_abs_dev_from_fp64"] = float(np.abs(d).max())
+            res[prec]["final_density_rel_dev_from_fp64"] = float(np.abs(d).max() / np.abs(dens["fp64"]).max())
+            res[prec]["speedup_vs_fp64_run"] = round(res["fp64"]["ms_total"] / res[prec]["ms_total"], 3)
+        res["fp64"]["final_density"] = [round(float(x), 12) for x in dens["fp64"]]
+        # the oracle's run of the first rows of the same grid
+        k = min(oracle_rows, n_t)
+        L0, R0, F0 = oracle.initial_rhs(t, order, h, U, v, pulse, rho0)
+        Lo = np.zeros((W.tri_size(k), M, M), np.complex128)
+        Ro = np.zeros_like(Lo)
+        Lo[0], Ro[0] = L0[0], R0[0]
+        Lo, _, _ = oracle.run(t[:k], order[:k], h, U, v, pulse, P, Lo, Ro, {0: F0}, 1, k,
+                              nthreads=oracle.threads_available())
+        for prec in ("fp64", "split", "df64"):
+            res[prec]["rows_0_%d_rel_dev_from_oracle" % (k - 1)] = float(
+                np.abs(head[prec] - Lo).max() / np.abs(Lo).max())
+        out[name] = res
+        ctx.close()
+    return out
+
+
 def seed_spread(kbe, seeds, n_t, P, stream):
     """The main KBE step (FP64 and split) on the inputs of each seed (grid
     and pulse drawn from it): ms per step per seed and their medians."""
@@ -1138,6 +1209,8 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_seeds:
         line["seed_spread"] = seed_spread(kbe, sorted({args.seed, 1, 2} | {0}), args.n_t, args.P, stream)
+    if rank == 0 and not args.no_runs:
+        line["whole_runs"] = whole_runs(kbe, args.seed, args.P, stream)
     if rank == 0 and not args.no_m32:
         line["precision_form_goe_m32"] = precision_m32_bench(kbe, args.seed, stream, 3)
     if not args.no_batch:
