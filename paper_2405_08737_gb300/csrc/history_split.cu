@@ -168,6 +168,16 @@ __device__ __forceinline__ bool conv_all(bool ok) {
   return r != 0;
 }
 
+// ecol[col] = max(ecol[col], ef) for every lane of the warp, with one shared
+// atomic per distinct column of the warp (lanes of one column reduce first;
+// a per-lane atomic serializes on the lanes that share an address).  Every
+// lane of the warp must call it; lanes with live == false contribute nothing.
+__device__ __forceinline__ void column_max(int* ecol, int col, int ef, bool live) {
+  const unsigned grp = __match_any_sync(0xffffffffu, live ? col : -1);
+  const int m = __reduce_max_sync(grp, live ? ef : 0);
+  if (live && m > 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicMax(&ecol[col], m);
+}
+
 // Chunk class relative to the tile's column range [c0, c1]: term 2 of the
 // tensor-core part covers m <= c - band_w (QU = Q there, 0 elsewhere).
 // 0: QU = 0 for every (m, c) of the chunk; 1: QU = Q for all; 2: mixed.
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
 #pragma unroll
     for (int k = 0; k < kKC; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
   }
-  if (enc && ef > 0) atomicMax(&ecol[cl], ef);
+  column_max(ecol, cl, ef, enc);
   __syncthreads();
   uint8_t* unit = a.planes + ((size_t)ctile * a.cpt_stride + kc) * kUnitBytes;
   uint8_t* dst = unit + arr * kBigTile;
@@ -543,25 +553,48 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
 // ============================================================ fused path ==
 // The same contraction with the conversion inside the contraction kernel,
 // over the units of one or many systems: no digit-plane buffer (a batch of
-// systems cannot hold one next to its histories).  Work list: the units
-// (column tile, chunk) of every system in order, split into contiguous
-// ranges of about equal cost, one range per persistent CTA.  For each unit
-// eight converter warps read the FP64 history entries of the unit's 128
-// output rows (both triangles) and write the PL, Q (and masked QU) digit
-// planes into a shared-memory stage, once; the two MMA threads then run the
-// unit's MMAs once per 8-orbital part (the small operands of each part
-// arrive by bulk copy in a ring of their own), and eight epilogue warps
-// (4 lane quadrants x 2 accumulator groups) fold each part's levels and
-// scale into double-float running sums kept in tensor memory, one per part,
-// written out as FP64 partials when the range leaves a column tile.
+// systems cannot hold one next to its histories).  A unit here is half a
+// chunk: one column tile (128 output rows) times 8 complex history entries,
+// one MMA K-step per digit slice.  Work list: the units of every system in
+// order, split into contiguous ranges of about equal cost, one range per
+// persistent CTA.
+//
+// Roles in one CTA (one per SM):
+//  * 16 converter warps stream the FP64 history entries of the units three
+//    ahead into a ring of five shared-memory stages with per-thread
+//    asynchronous copies (cp.async, zero-filled outside the triangle), so
+//    HBM latency hides behind the conversion of the units before.  For the
+//    current unit each thread reads its own 4 entries back, the column
+//    exponents are reduced in shared memory, and the digit planes PL and Q
+//    overwrite the FP64 data of the same stage (after a barrier: the two take
+//    the same 32 KB); the rare units that straddle the weight band also
+//    write the masked QU plane into one separate buffer.
+//  * one producer thread copies the small operands of each (unit, 8-orbital
+//    part) into a ring of three 6 KB slots (the unit's half of the chunk's
+//    12 KB of digit planes);
+//  * two MMA-issuing threads, one per accumulator group (I^< and
+//    D = I^> - I^<), run the unit's MMAs once per part into two TMEM
+//    accumulator buffers;
+//  * eight epilogue warps (4 lane quadrants x 2 groups) fold each part's
+//    levels and scales into double-float running sums kept in tensor
+//    memory, one per part, written out as FP64 partials when the range
+//    leaves a column tile.
 // Tensor memory: two accumulator buffers of 160 columns and up to three
-// parts' running sums of 64 columns (512 columns), so M <= 24.
+// parts' running sums of 64 columns (512 columns), so an entry has at most
+// three parts; larger systems run as entries of part ranges.
 constexpr int kFEpiWarps = 8;
-constexpr int kFConvWarps = 16;                                 // two threads per row and array: 8 K entries each
+constexpr int kFConvWarps = 16;                                 // 512 threads: 4 entries of one row and array each
 constexpr int kFConvThreads = kFConvWarps * 32;
 constexpr int kFThreads = (kFEpiWarps + kFConvWarps + 3) * 32;  // + producer, two MMA warps: 864
-constexpr int kFStageBytes = 3 * kBigTile + 512;                 // PL | Q | QU | column exponents
-constexpr int kFSlots = 2;                                      // small-operand ring
+constexpr int kHK = kKC / 2;                                    // complex history entries per unit
+constexpr int kHSlice = 128 * 2 * kHK * 2;                      // one digit slice of one plane: 4 KB
+constexpr int kHPlane = kSlices * kHSlice;                      // 16 KB
+constexpr int kFStageBytes = 2 * kHPlane + 512;                 // PL | Q (FP64 staging in place) | exponents
+constexpr int kFStages = 5;
+constexpr int kFAhead = 3;                                      // units whose copies are in flight
+constexpr int kFSmallHalf = kSmallVar / 2;                      // one variant's half of a chunk: 2 KB
+constexpr int kFSmallSlot = 3 * kFSmallHalf;                    // 6 KB
+constexpr int kFSlots = 3;
 constexpr int kFMaxParts = 3;
 constexpr int kFRunCol = 2 * kAccCols;                          // running sums from column 320
 constexpr int kFRunPart = 2 * 2 * kNS;                          // per part: 2 groups x (16 hi, 16 lo)
@@ -573,9 +606,10 @@ struct FusedSys {
   const double* Sg;
   WeightsView w;
   double* out;
-  const uint8_t* small;   // [cpt][parts][kSmallBytes], written by fused_prep
-  int* e_small;           // [cpt][parts]
+  const uint8_t* small;   // [cpt][parts_total][kSmallBytes], written by fused_prep
+  int* e_small;           // [cpt][parts_total]
   int M, n, CT, cpt, col_tiles;
+  int upt;                     // units per column tile: 2 cpt
   int parts;                   // 8-orbital parts this entry contracts (<= 3): part0 .. part0 + parts - 1
   int part0, parts_total;      // first part, and all parts of the system (small-operand layout)
   long long unit_base, units;  // global units [unit_base, unit_base + units)
@@ -598,9 +632,10 @@ struct FusedArgs {
 };
 
 struct SmemF {
-  uint8_t stage[kStages][kFStageBytes];
-  uint8_t small[kFSlots][kSmallBytes];
-  uint64_t full[kStages], empty[kStages], sfull[kFSlots], sempty[kFSlots];
+  uint8_t stage[kFStages][kFStageBytes];
+  uint8_t qu[kHPlane];
+  uint8_t small[kFSlots][kFSmallSlot];
+  uint64_t full[kFStages], empty[kFStages], qufull, quempty, sfull[kFSlots], sempty[kFSlots];
   uint64_t accfull[2], accempty[2], mmadone[2];
   int accmeta[2][128];   // column exponents of the unit whose part is in accumulator buffer b
   uint32_t tmem;
@@ -617,12 +652,6 @@ __device__ __forceinline__ bool wait_f(SmemF& sm, void* bar, uint32_t parity, in
     if (it > 64) __nanosleep(64);
   }
   return true;
-}
-
-// The system that holds global unit u, from the cursor si on (units increase).
-__device__ __forceinline__ const FusedSys& sys_at(const FusedArgs& a, int& si, long long u) {
-  while (si + 1 < a.n_sys && u >= a.sys[si].unit_base + a.sys[si].units) ++si;
-  return a.sys[si];
 }
 
 __device__ __forceinline__ int first_sys(const FusedArgs& a, long long u) {
@@ -648,6 +677,51 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
       : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared of this thread (zero-filled
+// when `bytes` is 0), tracked by the thread's commit groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Where the units of a CTA's range sit, advanced one unit at a time (no
+// division per unit): entry si, column tile, half-chunk hk of the tile.
+struct UnitPos {
+  int ctile, kc, half, kap0;
+};
+struct Cursor {
+  int si, ctile, hk;
+};
+__device__ __forceinline__ Cursor cursor_at(const FusedArgs& a, long long u) {
+  Cursor c;
+  c.si = first_sys(a, u);
+  const FusedSys& S = a.sys[c.si];
+  const long long lu = u - S.unit_base;
+  c.ctile = (int)(lu / S.upt);
+  c.hk = (int)(lu - (long long)c.ctile * S.upt);
+  return c;
+}
+__device__ __forceinline__ void cursor_next(const FusedArgs& a, Cursor& c) {
+  const FusedSys& S = a.sys[c.si];
+  if (++c.hk == S.upt) {
+    c.hk = 0;
+    if (++c.ctile == S.col_tiles) {
+      c.ctile = 0;
+      ++c.si;
+    }
+  }
+}
+__device__ __forceinline__ UnitPos unit_pos(const Cursor& c) {
+  UnitPos p;
+  p.ctile = c.ctile;
+  p.kc = c.hk >> 1;
+  p.half = c.hk & 1;
+  p.kap0 = c.hk * kHK;
+  return p;
+}
+
 // Small operands of every system's chunks (grid: global chunk x part).
 __global__ void __launch_bounds__(256) fused_prep(const FusedSys* __restrict__ sys, int n_sys) {
   __shared__ int s_ef;
@@ -671,14 +745,16 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
   constexpr int kProdWarp = kFEpiWarps + kFConvWarps, kMmaWarp = kProdWarp + 1;
 
   // rows beyond a unit's CT M are never written by the converters: zero the stages once
-  for (int i = tid; i < kStages * kFStageBytes / 16; i += kFThreads)
+  for (int i = tid; i < (kFStages * kFStageBytes + kHPlane) / 16; i += kFThreads)
     reinterpret_cast<uint4*>(sm.stage)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    // full: every converter thread; empty, sempty: one commit from each MMA
-    // thread; sfull: the producer's transaction count; accfull: the first MMA
-    // thread's arrival (exponents copied) and both commits; accempty: every
-    // epilogue thread
-    for (int s = 0; s < kStages; ++s) { mbar_init(&sm.full[s], kFConvThreads); mbar_init(&sm.empty[s], 2); }
+    // full, qufull: every converter thread; empty, quempty, sempty: one commit
+    // from each MMA thread; sfull: the producer's transaction count;
+    // accfull: the first MMA thread's arrival (exponents copied) and both
+    // commits; accempty: every epilogue thread
+    for (int s = 0; s < kFStages; ++s) { mbar_init(&sm.full[s], kFConvThreads); mbar_init(&sm.empty[s], 2); }
+    mbar_init(&sm.qufull, kFConvThreads);
+    mbar_init(&sm.quempty, 2);
     for (int s = 0; s < kFSlots; ++s) { mbar_init(&sm.sfull[s], 1); mbar_init(&sm.sempty[s], 2); }
     for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 3); mbar_init(&sm.accempty[b], kFEpiWarps * 32); }
     mbar_init(&sm.mmadone[0], 1);
@@ -697,122 +773,160 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm.tmem;
-  int si = ua < ub ? first_sys(a, ua) : 0;
 
   if (warp >= kFEpiWarps && warp < kProdWarp) {
     // ------------------------------------------------------ converters --
-    // Thread ct owns one row j = (c_l, b) of one big operand (arr 0: the
-    // G^< plane from L, arr 1: the Q plane from R) and half of the chunk's
-    // K entries (8: two K-groups): 8 loads in flight, then one 16-byte store
-    // per K-group and digit (the encoder's balanced digits, fixed31_fast).
+    // Thread ct: array arr (0: L -> the G^< plane PL, 1: R -> the Q plane),
+    // output row jrow = (c_l, b), K entries 4 q .. 4 q + 3 of the unit (K-group
+    // q of the plane).  Its staged entry k sits at (k * 512 + ct) * 16 bytes
+    // of the stage (each warp reads 32 consecutive 16-byte words).
     const int ct = tid - kFEpiWarps * 32;
-    const int arr = ct >> 8, half = (ct >> 7) & 1, jrow = ct & 127;
-    constexpr int kH = kKC / 2;
-    for (long long u = ua; u < ub; ++u) {
-      const int it = (int)(u - ua);
-      const int s = it & 1;
-      const FusedSys& S = sys_at(a, si, u);
-      const int M = S.M, MM = M * M, n = S.n, CT = S.CT, bw = S.w.band_w;
-      const long long lu = u - S.unit_base;
-      const int ctile = (int)(lu / S.cpt), kc = (int)(lu % S.cpt);
+    const int arr = ct >> 8, jrow = (ct >> 1) & 127, q = ct & 1;
+    Cursor ci = cursor_at(a, ua);  // issue cursor (runs kFAhead units ahead)
+    auto issue = [&](long long v) {  // asynchronous copies of unit v (at cursor ci) into its stage
+      const FusedSys& S = a.sys[ci.si];
+      const int M = S.M, MM = M * M, n = S.n, CT = S.CT;
+      const UnitPos P = unit_pos(ci);
       const bool row_live = jrow < CT * M;
       const int cl = row_live ? jrow / M : 0, bb = jrow - cl * M;
-      if (!conv_all<kFConvThreads>(wait_f(sm, &sm.empty[s], ((it >> 1) & 1) ^ 1, a.status, a.spin))) break;
-      uint8_t* st = sm.stage[s];
-      int* ecol = reinterpret_cast<int*>(st + 3 * kBigTile);
-      const int c0 = ctile * CT;
-      const int kap0 = kc * kKC;
-      const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, bw);
-      if (ct < 128) ecol[ct] = 0;
-      asm volatile("bar.sync 1, %0;" ::"r"(kFConvThreads) : "memory");
-      const double2* base = reinterpret_cast<const double2*>(arr == 0 ? S.L : S.R);
-      const int c = c0 + cl;
+      const int c = P.ctile * CT + cl;
       const bool col_live = row_live && c <= n;
-      double er[kH], ei[kH];
-      unsigned keep = 0;  // bit k: K entry k of this half lies in the tensor-core part of term 2 (m <= c - band_w)
+      uint8_t* st = sm.stage[(int)((v - ua) % kFStages)];
+      if (ct < 128) reinterpret_cast<int*>(st + 2 * kHPlane)[ct] = 0;
+      const double2* base = reinterpret_cast<const double2*>(arr == 0 ? S.L : S.R);
+      const int kap = P.kap0 + 4 * q;
+      int m = kap / M, x = kap - m * M;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = col_live && m <= n;
+        const double2* src = base;
+        if (ok) src = m >= c ? base + tri(m, c) * MM + x * M + bb : base + tri(c, m) * MM + bb * M + x;
+        cp_async16(st + ((size_t)k * kFConvThreads + ct) * 16, src, ok ? 16u : 0u);
+        if (++x == M) { x = 0; ++m; }
+      }
+    };
+    // the first kFAhead units' copies
+    for (int d = 0; d < kFAhead; ++d) {
+      const long long v = ua + d;
+      if (v < ub && conv_all<kFConvThreads>(wait_f(sm, &sm.empty[d % kFStages], 1, a.status, a.spin))) {
+        issue(v);
+        cursor_next(a, ci);
+      }
+      cp_async_commit();
+    }
+    long long ncls2 = 0;
+    Cursor cu = cursor_at(a, ua);
+    for (long long u = ua; u < ub; ++u, cursor_next(a, cu)) {
+      const int it = (int)(u - ua);
+      const int s = it % kFStages;
+      const FusedSys& S = a.sys[cu.si];
+      const int M = S.M, CT = S.CT, bw = S.w.band_w;
+      const UnitPos P = unit_pos(cu);
+      const bool row_live = jrow < CT * M;
+      const int cl = row_live ? jrow / M : 0;
+      const int c0 = P.ctile * CT, c = c0 + cl;
+      const int cls = chunk_class(P.kap0 / M, (P.kap0 + kHK - 1) / M, c0, c0 + CT - 1, bw);
+      uint8_t* st = sm.stage[s];
+      int* ecol = reinterpret_cast<int*>(st + 2 * kHPlane);
+      cp_async_wait<kFAhead - 1>();  // this thread's copies of unit u have landed
+      double er[4], ei[4];
+      unsigned keep = 0;  // bit k: entry k lies in the tensor-core part of term 2 (m <= c - band_w)
       int ef = 0;
       {
-        const int kap = kap0 + half * kH;
+        const int kap = P.kap0 + 4 * q;
         int m = kap / M, x = kap - m * M;
 #pragma unroll
-        for (int k = 0; k < kH; ++k) {
-          double2 z = make_double2(0.0, 0.0);
-          if (col_live && m <= n) {
-            if (m >= c) {
-              z = __ldcs(base + tri(m, c) * MM + x * M + bb);
-            } else {
-              z = __ldcs(base + tri(c, m) * MM + bb * M + x);
-              z.x = __hiloint2double(__double2hiint(z.x) ^ (int)0x80000000, __double2loint(z.x));  // -conj
-            }
-          }
+        for (int k = 0; k < 4; ++k) {
+          double2 z = *reinterpret_cast<const double2*>(st + ((size_t)k * kFConvThreads + ct) * 16);
+          if (m < c) z.x = __hiloint2double(__double2hiint(z.x) ^ (int)0x80000000, __double2loint(z.x));  // -conj
           er[k] = z.x;
           ei[k] = z.y;
+          ef = max(ef, max(exp_field(z.x), exp_field(z.y)));
           keep |= (unsigned)(m <= c - bw) << k;
           if (++x == M) { x = 0; ++m; }
         }
-#pragma unroll
-        for (int k = 0; k < kH; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
       }
-      if (row_live && ef > 0) atomicMax(&ecol[cl], ef);
+      column_max(ecol, cl, ef, row_live);
+      // every exponent is in and every staged entry of the stage has been read
       asm volatile("bar.sync 1, %0;" ::"r"(kFConvThreads) : "memory");
+      const bool qu = cls == 2;
+      if (qu) {  // the masked plane's buffer must be free (its last unit's MMAs done)
+        if (!conv_all<kFConvThreads>(wait_f(sm, &sm.quempty, (uint32_t)((ncls2 & 1) ^ 1), a.status, a.spin))) break;
+      }
       if (row_live) {
         const int e = scale_from_field(ecol[cl]);
-        uint8_t* dst = st + arr * kBigTile;  // PL or Q
-        uint8_t* QU = st + 2 * kBigTile;
-        const bool qu = arr == 1 && cls == 2;
+        uint32_t w[kSlices][4];
 #pragma unroll
-        for (int g2 = 0; g2 < 2; ++g2) {
-          const int kg = 2 * half + g2;
-          uint32_t w[kSlices][4];
+        for (int k = 0; k < 4; ++k) {
+          const int Vr = fixed31_fast(er[k], e), Vi = fixed31_fast(ei[k], e);
+          w[0][k] = digit_pair_bf16<0>(Vr, Vi);
+          w[1][k] = digit_pair_bf16<1>(Vr, Vi);
+          w[2][k] = digit_pair_bf16<2>(Vr, Vi);
+          w[3][k] = digit_pair_bf16<3>(Vr, Vi);
+        }
+        const int off = (q * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
+        uint8_t* dst = st + arr * kHPlane;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int Vr = fixed31_fast(er[4 * g2 + q], e), Vi = fixed31_fast(ei[4 * g2 + q], e);
-            w[0][q] = digit_pair_bf16<0>(Vr, Vi);
-            w[1][q] = digit_pair_bf16<1>(Vr, Vi);
-            w[2][q] = digit_pair_bf16<2>(Vr, Vi);
-            w[3][q] = digit_pair_bf16<3>(Vr, Vi);
-          }
-          const int off = (kg * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
-#pragma unroll
-          for (int sl = 0; sl < kSlices; ++sl) {
-            *reinterpret_cast<uint4*>(dst + sl * kBigSlice + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
-            if (qu) {
-              const unsigned kb = keep >> (4 * g2);
-              *reinterpret_cast<uint4*>(QU + sl * kBigSlice + off) =
-                  make_uint4(kb & 1u ? w[sl][0] : 0u, kb & 2u ? w[sl][1] : 0u, kb & 4u ? w[sl][2] : 0u,
-                             kb & 8u ? w[sl][3] : 0u);
-            }
-          }
+        for (int sl = 0; sl < kSlices; ++sl) {
+          *reinterpret_cast<uint4*>(dst + sl * kHSlice + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+          if (qu && arr == 1)
+            *reinterpret_cast<uint4*>(sm.qu + sl * kHSlice + off) =
+                make_uint4(keep & 1u ? w[sl][0] : 0u, keep & 2u ? w[sl][1] : 0u, keep & 4u ? w[sl][2] : 0u,
+                           keep & 8u ? w[sl][3] : 0u);
         }
       }
       fence_async_smem();
       mbar_arrive(&sm.full[s]);
+      if (qu) {
+        mbar_arrive(&sm.qufull);
+        ++ncls2;
+      }
+      // the copies of unit u + kFAhead, once its stage is free
+      const long long v = u + kFAhead;
+      if (v < ub) {
+        const int sv = (int)((v - ua) % kFStages);
+        if (!conv_all<kFConvThreads>(
+                wait_f(sm, &sm.empty[sv], (uint32_t)((((v - ua) / kFStages) & 1) ^ 1), a.status, a.spin))) {
+          cp_async_wait<0>();
+          break;
+        }
+        issue(v);
+        cursor_next(a, ci);
+      }
+      cp_async_commit();
     }
+    cp_async_wait<0>();  // no copy may be in flight when the CTA exits
   } else if (warp == kProdWarp) {
     // -------------------------------------------------------- producer --
-    // Small operands of each (unit, part), in the order the MMAs use them.
+    // Small operands of each (unit, part), in the order the MMAs use them:
+    // the unit's half of each variant (2 KB) of the chunk's digit planes.
     if (lane == 0) {
       long long it2 = 0, issued = 0;
       bool stop = false;
-      for (long long u = ua; u < ub && !stop; ++u) {
-        const FusedSys& S = sys_at(a, si, u);
-        const int kc = (int)((u - S.unit_base) % S.cpt);
+      Cursor cu = cursor_at(a, ua);
+      for (long long u = ua; u < ub && !stop; ++u, cursor_next(a, cu)) {
+        const FusedSys& S = a.sys[cu.si];
+        const UnitPos P = unit_pos(cu);
         for (int p = 0; p < S.parts; ++p, ++it2) {
-          const int ss = (int)(it2 & 1);
-          if (!wait_f(sm, &sm.sempty[ss], (uint32_t)(((it2 >> 1) & 1) ^ 1), a.status, a.spin) || u == a.withhold) {
+          const int ss = (int)(it2 % kFSlots);
+          if (!wait_f(sm, &sm.sempty[ss], (uint32_t)(((it2 / kFSlots) & 1) ^ 1), a.status, a.spin) ||
+              u == a.withhold) {
             stop = true;  // (withhold: test of the failure path, nothing issued from this unit on)
             break;
           }
-          mbar_arrive_expect_tx(&sm.sfull[ss], kSmallBytes);
-          bulk_g2s(sm.small[ss], S.small + ((size_t)kc * S.parts_total + S.part0 + p) * kSmallBytes, kSmallBytes,
-                   &sm.sfull[ss]);
+          const uint8_t* src = S.small + ((size_t)P.kc * S.parts_total + S.part0 + p) * kSmallBytes + P.half * kFSmallHalf;
+          mbar_arrive_expect_tx(&sm.sfull[ss], kFSmallSlot);
+#pragma unroll
+          for (int var = 0; var < 3; ++var)
+            bulk_g2s(sm.small[ss] + var * kFSmallHalf, src + var * kSmallVar, kFSmallHalf, &sm.sfull[ss]);
           issued = it2 + 1;
         }
       }
       // the copies already issued must land before the CTA can exit
       for (long long k = issued - 1; k >= 0 && k >= issued - kFSlots; --k) {
         long long spins = 0;
-        while (!mbar_try(&sm.sfull[k & 1], (uint32_t)((k >> 1) & 1)) && ++spins < kSpinLimit) __nanosleep(64);
+        while (!mbar_try(&sm.sfull[k % kFSlots], (uint32_t)((k / kFSlots) & 1)) && ++spins < kSpinLimit)
+          __nanosleep(64);
         if (spins >= kSpinLimit) atomicOr(a.status, kStatusTimeout);
       }
     }
@@ -822,57 +936,60 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
     // group 0: I^< += PL A1 + QU NB^<;  group 1: D += Q A1 + QU NBD
     const int mgrp = warp - kMmaWarp;
     if (lane == 0) {
+      // A: [slice 4][K-group 2][row group 16][8 rows][16 B]; B: [K-group 2][slice 4][col group 2][8][16 B]
       const uint64_t big0 = umma_desc(smem_u32(sm.stage[0]), 2048, 128);
+      const uint64_t qu0 = umma_desc(smem_u32(sm.qu), 2048, 128);
       const uint64_t small0 = umma_desc(smem_u32(sm.small[0]), 1024, 128);
-      long long it2 = 0;
+      long long it2 = 0, ncls2 = 0;
       bool any = false, stop = false;
-      for (long long u = ua; u < ub && !stop; ++u) {
+      Cursor cu = cursor_at(a, ua);
+      for (long long u = ua; u < ub && !stop; ++u, cursor_next(a, cu)) {
         const int it = (int)(u - ua);
-        const int s = it & 1;
-        const FusedSys& S = sys_at(a, si, u);
+        const int s = it % kFStages;
+        const FusedSys& S = a.sys[cu.si];
         const int M = S.M, CT = S.CT, bw = S.w.band_w;
-        const long long lu = u - S.unit_base;
-        const int ctile = (int)(lu / S.cpt), kc = (int)(lu % S.cpt);
-        const int c0 = ctile * CT, kap0 = kc * kKC;
-        const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, bw);
-        if (!wait_f(sm, &sm.full[s], (uint32_t)((it >> 1) & 1), a.status, a.spin)) break;
+        const UnitPos P = unit_pos(cu);
+        const int c0 = P.ctile * CT;
+        const int cls = chunk_class(P.kap0 / M, (P.kap0 + kHK - 1) / M, c0, c0 + CT - 1, bw);
+        if (!wait_f(sm, &sm.full[s], (uint32_t)((it / kFStages) & 1), a.status, a.spin)) break;
+        if (cls == 2 && !wait_f(sm, &sm.qufull, (uint32_t)(ncls2 & 1), a.status, a.spin)) break;
         const uint64_t so = (uint64_t)(s * kFStageBytes) >> 4;
-        const uint64_t dPL0 = big0 + so, dQ0 = dPL0 + (kBigTile >> 4);
-        const uint64_t dQU0 = cls == 1 ? dQ0 : dPL0 + ((2 * kBigTile) >> 4);
+        const uint64_t dPL0 = big0 + so, dQ0 = dPL0 + (kHPlane >> 4);
+        const uint64_t dQU0 = cls == 1 ? dQ0 : qu0;
         const uint64_t dA = mgrp == 0 ? dPL0 : dQ0;
         for (int p = 0; p < S.parts; ++p, ++it2) {
-          const int b = (int)(it2 & 1);
-          const uint32_t par = (uint32_t)((it2 >> 1) & 1);
-          if (!wait_f(sm, &sm.sfull[b], par, a.status, a.spin) || !wait_f(sm, &sm.accempty[b], par, a.status, a.spin)) {
+          const int b = (int)(it2 & 1), ss = (int)(it2 % kFSlots);
+          if (!wait_f(sm, &sm.sfull[ss], (uint32_t)((it2 / kFSlots) & 1), a.status, a.spin) ||
+              !wait_f(sm, &sm.accempty[b], (uint32_t)((it2 >> 1) & 1), a.status, a.spin)) {
             stop = true;
             break;
           }
           tc_fence_after();
           if (mgrp == 0) {
-            const int* ecol = reinterpret_cast<const int*>(sm.stage[s] + 3 * kBigTile);
-            for (int q = 0; q < CT; ++q) sm.accmeta[b][q] = ecol[q];
+            const int* ecol = reinterpret_cast<const int*>(sm.stage[s] + 2 * kHPlane);
+            for (int k = 0; k < CT; ++k) sm.accmeta[b][k] = ecol[k];
             mbar_arrive(&sm.accfull[b]);
           }
-          const uint64_t dS0 = small0 + ((uint64_t)(b * kSmallBytes) >> 4);
-          const uint64_t dSU = dS0 + (uint64_t)(((1 + mgrp) * kSmallVar) >> 4);
+          const uint64_t dS0 = small0 + ((uint64_t)(ss * kFSmallSlot) >> 4);
+          const uint64_t dSU = dS0 + (uint64_t)(((1 + mgrp) * kFSmallHalf) >> 4);
           const uint32_t dacc = tmem + b * kAccCols + mgrp * kGroupCols;
 #pragma unroll
           for (int i = 0; i < kSlices; ++i) {
             const uint32_t idesc = umma_idesc_bf16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t oa = (uint64_t)((i * kBigSlice + kk * 2 * 2048) >> 4);
-              const uint64_t ob = (uint64_t)((kk * 2 * 1024) >> 4);
-              umma_bf16(dacc + i * kNS, dA + oa, dS0 + ob, idesc, 1);
-              if (cls != 0) umma_bf16(dacc + i * kNS, dQU0 + oa, dSU + ob, idesc, 1);
-            }
+            const uint64_t oa = (uint64_t)((i * kHSlice) >> 4);
+            umma_bf16(dacc + i * kNS, dA + oa, dS0, idesc, 1);
+            if (cls != 0) umma_bf16(dacc + i * kNS, dQU0 + oa, dSU, idesc, 1);
           }
           umma_commit(&sm.accfull[b]);
-          umma_commit(&sm.sempty[b]);
+          umma_commit(&sm.sempty[ss]);
           any = true;
         }
         if (stop) break;
         umma_commit(&sm.empty[s]);
+        if (cls == 2) {
+          umma_commit(&sm.quempty);
+          ++ncls2;
+        }
       }
       // every MMA this thread issued must complete before tensor memory is freed
       if (any) {
@@ -903,16 +1020,16 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
     mbar_arrive(&sm.accempty[1]);
     long long it2 = 0, seg = a.seg_base[blockIdx.x];
     bool stop = false;
-    for (long long u = ua; u < ub && !stop; ++u) {
-      const FusedSys& S = sys_at(a, si, u);
+    Cursor cu = cursor_at(a, ua);
+    for (long long u = ua; u < ub && !stop; ++u, cursor_next(a, cu)) {
+      const FusedSys& S = a.sys[cu.si];
       const int M = S.M, n = S.n, CT = S.CT, parts = S.parts;
-      const long long lu = u - S.unit_base;
-      const int ctile = (int)(lu / S.cpt), kc = (int)(lu % S.cpt);
+      const UnitPos P = unit_pos(cu);
       const int cl = j / M, bb = j - cl * M;
       const bool live_row = cl < CT;
       for (int p = 0; p < parts; ++p, ++it2) {
         const int b = (int)(it2 & 1);
-        const int es = __ldg(S.e_small + kc * S.parts_total + S.part0 + p);
+        const int es = __ldg(S.e_small + P.kc * S.parts_total + S.part0 + p);
         if (!__all_sync(0xffffffffu, wait_f(sm, &sm.accfull[b], (uint32_t)((it2 >> 1) & 1), a.status, a.spin))) {
           stop = true;
           break;
@@ -930,12 +1047,12 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
           float v[kLevels][4];
           tmem_ld4xL(buf + q4, kNS, v);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float lv[kLevels] = {v[0][q], v[1][q], v[2][q], v[3][q], v[4][q]};
+          for (int qq = 0; qq < 4; ++qq) {
+            const float lv[kLevels] = {v[0][qq], v[1][qq], v[2][qq], v[3][qq], v[4][qq]};
             float hi, lo;
             combine_levels(lv, hi, lo);
-            df_add(rh[q4 + q], rl[q4 + q], hi * sc);
-            rl[q4 + q] += lo * sc;
+            df_add(rh[q4 + qq], rl[q4 + qq], hi * sc);
+            rl[q4 + qq] += lo * sc;
           }
         }
         tmem_st16(run, rh);
@@ -948,9 +1065,9 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
       }
       if (stop) break;
       // segment end: the next unit is in another column tile or system, or the range ends
-      const bool last = u + 1 == ub || u + 1 == S.unit_base + S.units || (lu + 1) / S.cpt != ctile;
+      const bool last = u + 1 == ub || cu.hk + 1 == S.upt;
       if (last) {
-        const int c = ctile * CT + cl;
+        const int c = P.ctile * CT + cl;
         const long long slot0 = a.seg_slot[seg];
         for (int p = 0; p < parts; ++p) {
           const uint32_t run = lane_addr + kFRunCol + p * kFRunPart + grp * 2 * kNS;
@@ -1178,7 +1295,7 @@ __global__ void __launch_bounds__(kRedThreads, 7) fused_reduce(FusedArgs a) {
   if (threadIdx.x == 0) {
     const int ct = c / S.CT;
     const long long T = S.tile_base + ct;
-    const long long ulo = S.unit_base + (long long)ct * S.cpt, uhi = ulo + S.cpt;
+    const long long ulo = S.unit_base + (long long)ct * S.upt, uhi = ulo + S.upt;
     int l = 0, h = a.G - 1;  // first CTA whose range ends beyond ulo
     while (l < h) {
       const int mid = (l + h) >> 1;
@@ -1349,11 +1466,12 @@ bool fused_build(const FusedSystem* in, int n_sys, FusedPlanHost* p) {
       f.e_small = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(in[i].small) +
                                          (size_t)h.cpt * h.parts * kSmallBytes);
       f.M = h.M; f.n = h.n; f.CT = h.CT; f.cpt = h.cpt; f.col_tiles = col_tiles;
+      f.upt = 2 * h.cpt;
       f.part0 = part0;
       f.parts = std::min(per, h.parts - part0);
       f.parts_total = h.parts;
       f.unit_base = units;
-      f.units = (long long)col_tiles * h.cpt;
+      f.units = (long long)col_tiles * f.upt;
       f.tile_base = tiles;
       f.chunk_base = chunks;
       f.col_base = cols;
@@ -1397,14 +1515,14 @@ bool fused_build(const FusedSystem* in, int n_sys, FusedPlanHost* p) {
     for (long long u = lo[i]; u < lo[i + 1];) {
       while (u >= ent[kk].unit_base + ent[kk].units) ++kk;
       const FusedSys& f = ent[kk];
-      const long long t = f.tile_base + (u - f.unit_base) / f.cpt;
+      const long long t = f.tile_base + (u - f.unit_base) / f.upt;
       if (prev_tile < 0) tile0[i] = t;
       prev_tile = t;
       slot.push_back(slots);
       slots += f.parts;
       ++seg;
       // next unit of another tile: the end of this tile in the entry
-      u = f.unit_base + ((u - f.unit_base) / f.cpt + 1) * f.cpt;
+      u = f.unit_base + ((u - f.unit_base) / f.upt + 1) * f.upt;
     }
   }
   p->n_ent = (int)ent.size();

@@ -66,16 +66,23 @@ __device__ __forceinline__ void digits_bf16(int V, uint32_t out[kSlices]) {
   out[3] = __float_as_uint(__int_as_float(0x4B000000 | (w & 0xFFu)) - 8388736.0f) >> 16;
 }
 
-// round(v * 2^(31-e)) for |v| < 2^e with one 64-bit shift of the significand
-// (branch-free; the same integer as fixed31).
+// round(v * 2^(31-e)) for |v| < 2^e, branch-free in 32-bit operations (the
+// same integer as fixed31).  The significand m (53 bits) is shifted right by
+// s = 1044 + e - ef >= 22: with x = the top 32 bits of m (m >> 21) and
+// t = s - 22, q = x >> t (0 for t > 31) and the rounded quotient is
+// (q >> 1) + (q & 1), written so that q = 2^32 - 1 (a value within 2^-32 of
+// 2^e, shift 0) gives 2^31 and clamps to 2^31 - 1 instead of wrapping to 0.
 __device__ __forceinline__ int fixed31_fast(double v, int e) {
   const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
   const int ef = (int)((hi >> 20) & 0x7FFu);
-  const int s = 1044 + e - ef;  // >= 22 when e bounds the value's exponent
-  const unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
-  unsigned long long V = (ef == 0 || s > 63) ? 0ull : (m + (1ull << (s - 1))) >> s;
-  V = V > 0x7FFFFFFFull ? 0x7FFFFFFFull : V;
-  return (int)hi < 0 ? -(int)V : (int)V;
+  const unsigned mh = (hi & 0xFFFFFu) | 0x100000u;
+  const unsigned x = __funnelshift_l(lo, mh, 11);           // (mh:lo) >> 21, 32 bits
+  const unsigned t = (unsigned)(1022 + e - ef);             // s - 22
+  const unsigned q = __funnelshift_rc(x, 0u, t);             // shifts of 32 or more give 0
+  unsigned V = (q >> 1) + (q & 1u);
+  V = ef == 0 ? 0u : min(V, 0x7FFFFFFFu);
+  const unsigned sg = (unsigned)((int)hi >> 31);            // 0 or all ones
+  return (int)((V ^ sg) - sg);
 }
 
 // Balanced digit K (0: the top one, in [-128, 128]; 1..3 in [-128, 127]) of
@@ -85,8 +92,8 @@ __device__ __forceinline__ int fixed31_fast(double v, int e) {
 template <int K>
 __device__ __forceinline__ uint32_t digit_pair_bf16(int Vr, int Vi) {
   float fr, fi;
-  if (K == 0) {
-    const int dr = (int)(((long long)Vr + 0x808080) >> 24), di = (int)(((long long)Vi + 0x808080) >> 24);
+  if (K == 0) {  // floor((V + 0x808080) / 2^24) = floor(((V >> 1) + 0x404040) / 2^23), without overflow
+    const int dr = ((Vr >> 1) + 0x404040) >> 23, di = ((Vi >> 1) + 0x404040) >> 23;
     fr = __int_as_float(0x4B400000 + dr) - 12582912.0f;
     fi = __int_as_float(0x4B400000 + di) - 12582912.0f;
   } else {

@@ -106,6 +106,37 @@ def test_split_slice_matches_oracle(kbe, M, kind, path):
             assert err < TOL_SPLIT, (M, kind, n, err, _rel(I, ref))
 
 
+def _just_below_powers_of_two(x):
+    """Each real and imaginary part moved to just below the next power of two
+    of its magnitude (same sign): 2^k (1 - 2^-40), whose significand's top 32
+    bits are all ones, so the entry that sets a column's exponent rounds up
+    to the fixed-point maximum."""
+    def f(a):
+        k = np.ceil(np.log2(np.maximum(np.abs(a), 1e-300)))
+        return np.where(a == 0, 0.0, np.sign(a) * np.exp2(k) * (1.0 - 2.0 ** -40))
+    return f(x.real) + 1j * f(x.imag)
+
+
+@pytest.mark.parametrize("path", ["planes", "fused"])
+@pytest.mark.parametrize("M", [2, 8])
+def test_split_entries_just_below_a_power_of_two(kbe, M, path):
+    """Entries within 2^-40 of a power of two (as a half-filled occupation
+    1 - 1e-12 is) take the largest fixed-point value, never 0: the slice
+    stays within the bound of the oracle's."""
+    n_t = 37
+    t, order, h, L, R = _case(M, n_t, 70 + M, "random")
+    L, R = _just_below_powers_of_two(L), _just_below_powers_of_two(R)
+    Ld, Rd = _dev(L), _dev(R)
+    for n in (1, 9, n_t - 1):
+        Sl, Sg = W.random_rows(M, n, 3 * n + M)
+        Sl, Sg = _just_below_powers_of_two(Sl), _just_below_powers_of_two(Sg)
+        I = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, path)
+        ref = oracle.history_slice(t, order, n, L, R, Sl, Sg, nthreads=8)
+        mag = _magnitude_slice(t, order, n, L, R, Sl, Sg)
+        err = np.abs(I - ref).max() / max(mag, 1e-300)
+        assert err < TOL_SPLIT, (M, n, path, err)
+
+
 @pytest.mark.parametrize("path", ["planes", "fused"])
 def test_split_is_deterministic(kbe, path):
     M, n_t = 8, 60
@@ -120,18 +151,18 @@ def test_split_is_deterministic(kbe, path):
 
 @pytest.mark.parametrize("M,n_t", [(3, 150), (8, 300), (16, 130), (24, 90), (32, 70)])
 def test_split_paths_agree(kbe, M, n_t):
-    """The fused contraction (digits formed inside the kernel, one pass of
-    all 8-orbital parts per unit) and the planes path (encoder, one pass per
-    part) form the same digits and level sums; only the grouping of the
-    double-float partial sums differs (the two partitions of the work), so
-    the slices agree far inside the split path's bound."""
+    """The fused contraction (digits formed inside the kernel, column
+    exponents per 8 history entries) and the planes path (encoder, exponents
+    per 16 entries) round the same values to different fixed-point grids,
+    each within the split path's bound of the exact slice (tested against
+    the oracle above), so they agree within that bound."""
     t, order, h, L, R = _case(M, n_t, 40 + M, "free")
     Ld, Rd = _dev(L), _dev(R)
     n = n_t - 1
     Sl, Sg = oracle.sigma_row(oracle.local_U4(np.linspace(0.5, 1.5, M)), n, L, R)
     a = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, "planes")
     b = _split_slice(kbe, M, n_t, t, order, h, n, Ld, Rd, Sl, Sg, "fused")
-    assert _rel(b, a) < 1e-12, (M, _rel(b, a))
+    assert _rel(b, a) < TOL_SPLIT, (M, _rel(b, a))
 
 
 @pytest.mark.parametrize("path", ["planes", "fused"])
