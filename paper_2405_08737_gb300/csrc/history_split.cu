@@ -342,12 +342,61 @@ __device__ __forceinline__ bool wait_bar2(Smem2& sm, void* bar, uint32_t parity,
   return true;
 }
 
+// Where unit u = tile * cpt + kc sits (tile = column tile * parts + part),
+// advanced one unit at a time so that no role divides per unit: the chunk's
+// first and last history points m_lo = 16 kc / M, m_hi = (16 kc + 15) / M
+// with their remainders, and the first QU slot of the column tile.
+struct UnitCur {
+  int kc, ctile, part, c0, qfirst;
+  int m_lo, r_lo, m_hi, r_hi;
+};
+__device__ __forceinline__ int qu_first(int c0, int M, int band_w) { return -qu_slot(0, c0, M, band_w); }
+__device__ __forceinline__ UnitCur unit_cur(const SplitGeom& g, long long u) {
+  UnitCur c;
+  const int tile = (int)(u / g.cpt);
+  c.kc = (int)(u - (long long)tile * g.cpt);
+  c.ctile = tile / g.parts;
+  c.part = tile - c.ctile * g.parts;
+  c.c0 = c.ctile * g.CT;
+  c.qfirst = qu_first(c.c0, g.M, g.band_w);
+  const int k0 = c.kc * kKC, k1 = k0 + kKC - 1;
+  c.m_lo = k0 / g.M;
+  c.r_lo = k0 - c.m_lo * g.M;
+  c.m_hi = k1 / g.M;
+  c.r_hi = k1 - c.m_hi * g.M;
+  return c;
+}
+// q16 = 16 / M and r16 = 16 % M of the launch
+__device__ __forceinline__ void unit_next(const SplitGeom& g, UnitCur& c, int q16, int r16) {
+  if (++c.kc == g.cpt) {
+    c.kc = 0;
+    c.m_lo = 0;
+    c.r_lo = 0;
+    c.m_hi = (kKC - 1) / g.M;
+    c.r_hi = (kKC - 1) - c.m_hi * g.M;
+    if (++c.part == g.parts) {
+      c.part = 0;
+      ++c.ctile;
+      c.c0 += g.CT;
+      c.qfirst = qu_first(c.c0, g.M, g.band_w);
+    }
+    return;
+  }
+  c.m_lo += q16;
+  c.r_lo += r16;
+  if (c.r_lo >= g.M) { c.r_lo -= g.M; ++c.m_lo; }
+  c.m_hi += q16;
+  c.r_hi += r16;
+  if (c.r_hi >= g.M) { c.r_hi -= g.M; ++c.m_hi; }
+}
+
 __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem2& sm = *reinterpret_cast<Smem2*>(smem_raw);
   const SplitGeom& g = a.g;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = g.M, n = g.n, CT = g.CT;
+  const int q16 = kKC / M, r16 = kKC - q16 * M;
   const long long u0 = unit_begin(g, blockIdx.x), u1 = unit_begin(g, blockIdx.x + 1);
 
   if (tid == 0) {
@@ -376,25 +425,23 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
     // -------------------------------------------------------- producer --
     if (lane == 0) {
       long long issued = u0;
-      for (long long u = u0; u < u1; ++u) {
+      UnitCur cu = unit_cur(g, u0);
+      for (long long u = u0; u < u1; ++u, unit_next(g, cu, q16, r16)) {
         const int it = (int)(u - u0);
         const int s = it % kStages;
         if (!wait_bar2(sm, &sm.empty[s], ((it / kStages) & 1) ^ 1, a.status, a.spin)) break;
         if (u == a.withhold) break;  // test of the failure path: nothing issued for this stage
-        const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
-        const int ctile = tile / g.parts, part = tile % g.parts;
-        const int c0 = ctile * CT;
-        const int kap0 = kc * kKC;
-        const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
-        const int slot = cls == 2 ? qu_slot(kc, c0, M, g.band_w) : 0;
+        const int cls = chunk_class(cu.m_lo, cu.m_hi, cu.c0, cu.c0 + CT - 1, g.band_w);
+        const int slot = cls == 2 ? cu.kc - cu.qfirst : 0;
         const bool with_qu = cls == 2 && slot >= 0 && slot < a.qu_slots;
         uint8_t* st = sm.stage[s];
         mbar_arrive_expect_tx(&sm.full[s], kUnitBytes + kSmallBytes + (with_qu ? kBigTile : 0));
-        bulk_g2s(st, a.planes + ((size_t)ctile * a.cpt_stride + kc) * kUnitBytes, kUnitBytes, &sm.full[s]);
-        bulk_g2s(st + kUnitBytes + kBigTile, a.small + ((size_t)kc * g.parts + part) * kSmallBytes, kSmallBytes,
-                 &sm.full[s]);
+        bulk_g2s(st, a.planes + ((size_t)cu.ctile * a.cpt_stride + cu.kc) * kUnitBytes, kUnitBytes, &sm.full[s]);
+        bulk_g2s(st + kUnitBytes + kBigTile, a.small + ((size_t)cu.kc * g.parts + cu.part) * kSmallBytes,
+                 kSmallBytes, &sm.full[s]);
         if (with_qu)
-          bulk_g2s(st + kUnitBytes, a.qu + ((size_t)ctile * a.qu_slots + slot) * kBigTile, kBigTile, &sm.full[s]);
+          bulk_g2s(st + kUnitBytes, a.qu + ((size_t)cu.ctile * a.qu_slots + slot) * kBigTile, kBigTile,
+                   &sm.full[s]);
         issued = u + 1;
       }
       // before the CTA can exit, the copies of the last units must have landed
@@ -419,20 +466,19 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
       const uint64_t big0 = umma_desc(smem_u32(sm.stage[0]), 2048, 128);
       const uint64_t small0 = umma_desc(smem_u32(sm.stage[0] + kUnitBytes + kBigTile), 1024, 128);
       long long last = -1;
-      for (long long u = u0; u < u1; ++u) {
+      UnitCur cu = unit_cur(g, u0);
+      for (long long u = u0; u < u1; ++u, unit_next(g, cu, q16, r16)) {
         const int it = (int)(u - u0);
         const int s = it % kStages, b = it & 1;
+        // the unit's class before the waits (it depends on the position only)
+        int cls = chunk_class(cu.m_lo, cu.m_hi, cu.c0, cu.c0 + CT - 1, g.band_w);
+        if (cls == 2) {
+          const int slot = cu.kc - cu.qfirst;
+          if (slot < 0 || slot >= a.qu_slots) cls = 0;  // reported by the encoder (status word)
+        }
         if (!wait_bar2(sm, &sm.full[s], (it / kStages) & 1, a.status, a.spin)) break;
         if (!wait_bar2(sm, &sm.accempty[b], (it >> 1) & 1, a.status, a.spin)) break;
         tc_fence_after();
-        const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
-        const int c0 = (tile / g.parts) * CT;
-        const int kap0 = kc * kKC;
-        int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
-        if (cls == 2) {
-          const int slot = qu_slot(kc, c0, M, g.band_w);
-          if (slot < 0 || slot >= a.qu_slots) cls = 0;  // reported by the encoder (status word)
-        }
         const uint64_t so = (uint64_t)(s * kStage2Bytes) >> 4;
         const uint64_t dPL0 = big0 + so, dQ0 = dPL0 + (kBigTile >> 4);
         const uint64_t dQU0 = cls == 1 ? dQ0 : dPL0 + (kUnitBytes >> 4);
@@ -489,17 +535,17 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
 #pragma unroll
     for (int q = 0; q < kQ; ++q) { run[q][0] = 0.f; run[q][1] = 0.f; }
     int local_seg = 0;
-    for (long long u = u0; u < u1; ++u) {
+    UnitCur cu = unit_cur(g, u0);
+    for (long long u = u0; u < u1; ++u, unit_next(g, cu, q16, r16)) {
       const int it = (int)(u - u0);
       const int b = it & 1;
-      const int tile = (int)(u / g.cpt), kc = (int)(u % g.cpt);
       // the unit's column exponent (stored with its planes) and small-operand
       // exponent, fetched before waiting for the accumulators
       const int ec = live_row ? __ldg(reinterpret_cast<const int*>(
-                                      a.planes + ((size_t)(tile / g.parts) * a.cpt_stride + kc) * kUnitBytes +
+                                      a.planes + ((size_t)cu.ctile * a.cpt_stride + cu.kc) * kUnitBytes +
                                       2 * kBigTile) + cl)
                               : 0;
-      const int es = __ldg(a.e_small + kc * g.parts + tile % g.parts);
+      const int es = __ldg(a.e_small + cu.kc * g.parts + cu.part);
       if (!__all_sync(0xffffffffu, wait_bar2(sm, &sm.accfull[b], (it >> 1) & 1, a.status, a.spin))) break;
       tc_fence_after();
       const float sc = pow2f(scale_from_field(ec) + es - 14);
@@ -524,8 +570,8 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&sm.accempty[b]);
-      if ((u + 1 == u1) || ((u + 1) / g.cpt != tile)) {
-        const int c = (tile / g.parts) * CT + cl;
+      if (u + 1 == u1 || cu.kc + 1 == g.cpt) {
+        const int c = cu.c0 + cl;
         if (live_row && c <= n) {
           double2* out = reinterpret_cast<double2*>(a.part) + ((size_t)blockIdx.x * g.S + local_seg) * (2 * 128 * kNA);
 #pragma unroll
@@ -596,6 +642,7 @@ constexpr int kFSmallHalf = kSmallVar / 2;                      // one variant's
 constexpr int kFSmallSlot = 3 * kFSmallHalf;                    // 6 KB
 constexpr int kFSlots = 3;
 constexpr int kFMaxParts = 3;
+constexpr int kFConvWeight = 7;                                 // a unit's conversion, in MMA-and-epilogue passes
 constexpr int kFRunCol = 2 * kAccCols;                          // running sums from column 320
 constexpr int kFRunPart = 2 * 2 * kNS;                          // per part: 2 groups x (16 hi, 16 lo)
 
@@ -1484,20 +1531,22 @@ bool fused_build(const FusedSystem* in, int n_sys, FusedPlanHost* p) {
     p->max_parts = std::max(p->max_parts, h.parts);
   }
   // contiguous unit ranges of about equal cost: a unit costs its conversion
-  // plus one MMA-and-epilogue pass per part (weights 2 + parts)
+  // plus one MMA-and-epilogue pass per part, weights kFConvWeight + parts
+  // (measured per-system times at M = 4..24 put a unit's conversion at
+  // about seven passes)
   const int G = p->G;
   long long W = 0;
-  for (const FusedSys& f : ent) W += f.units * (2 + f.parts);
+  for (const FusedSys& f : ent) W += f.units * (kFConvWeight + f.parts);
   std::vector<long long> lo(G + 1), tile0(G, -1), segb(G);
   size_t e = 0;
   long long cw = 0;  // weight of the units before entry e
   for (int i = 0; i <= G; ++i) {
     const long long target = (long long)((__int128)W * i / G);
-    while (e + 1 < ent.size() && cw + ent[e].units * (2 + ent[e].parts) <= target) {
-      cw += ent[e].units * (2 + ent[e].parts);
+    while (e + 1 < ent.size() && cw + ent[e].units * (kFConvWeight + ent[e].parts) <= target) {
+      cw += ent[e].units * (kFConvWeight + ent[e].parts);
       ++e;
     }
-    const long long w = 2 + ent[e].parts;
+    const long long w = kFConvWeight + ent[e].parts;
     long long k = (target - cw + w - 1) / w;
     if (k > ent[e].units) k = ent[e].units;
     lo[i] = i == G ? units : ent[e].unit_base + k;
