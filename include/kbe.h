@@ -66,14 +66,18 @@ typedef int kbe_status;
 
 /* precision argument of kbe_history_slice / kbe_step */
 #define KBE_FP64 0        /* plain FP64 arithmetic, deterministic            */
-#define KBE_SPLIT_BF16 1  /* the contraction on the bf16 tensor cores with   */
-                          /* error-free 4-digit fixed-point splitting: every  */
-                          /* value becomes round(v 2^(31-e)) in balanced      */
-                          /* base-256 digits (e: exponent of its 16-entry     */
-                          /* chunk), all 16 digit products are summed exactly */
-                          /* in FP32 and combined in double-float; about 1e-9 */
-                          /* relative to the slice maximum.  norb <= 32.      */
-                          /* Deterministic.  Requires R(r,r) = -i*1 exactly. */
+#define KBE_SPLIT_BF16 1  /* the contraction on the 16-bit-float tensor cores */
+                          /* with error-free 4-digit fixed-point splitting:   */
+                          /* every value becomes round(v 2^(31-e)) in base-256 */
+                          /* digits (e: exponent of its column over 16 (the   */
+                          /* planes path) or 8 (the fused path) history       */
+                          /* entries), each digit exact in fp16 (bf16 would   */
+                          /* hold them too; fp16 takes three instructions per */
+                          /* digit pair to form), the 13 digit products of    */
+                          /* levels 0..4 summed exactly in FP32 and combined  */
+                          /* in double-float; about 1e-9 relative to the      */
+                          /* slice maximum.  norb <= 32.  Deterministic.      */
+                          /* Requires R(r,r) = -i*1 exactly.                  */
 #define KBE_DF64 2        /* the contraction in double-float arithmetic on    */
                           /* the FP32 pipe (hi + lo floats, about 2^-47 per   */
                           /* product, compensated sums): about 1e-14 of the   */
@@ -459,9 +463,9 @@ kbe_status kbe_run_controlled(kbe_ctx* ctx, const double* opts, const int* iopts
  * buffer (an existing one is freed, after a device synchronisation); every
  * split slice runs one persistent contraction that converts the FP64
  * history entries into digit planes inside the kernel, the form the batched
- * steps use.  Both give the same results to rounding (the same digits and
- * sums; partial sums are grouped differently).  KBE_EINVAL unless keep is 0
- * or 1. */
+ * steps use.  The two round to different fixed-point grids (column
+ * exponents over 16 resp. 8 history entries), each within the split
+ * path's bound of the exact slice.  KBE_EINVAL unless keep is 0 or 1. */
 kbe_status kbe_set_split_planes(kbe_ctx* ctx, int keep);
 
 /* Forget per-history state kept between steps (the split path's digit

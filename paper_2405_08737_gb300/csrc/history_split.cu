@@ -2,7 +2,7 @@
 //
 // The same contraction as history_f64.cu,
 //   I^s(n,c) = sum_m w_{n,m} Sigma^R(n,m) G^s(m,c) + sum_{m<=c} w_{c,m} Sigma^s(n,m) G^A(m,c),
-// evaluated on the bf16 tensor cores with error-free fixed-point slicing
+// evaluated on the fp16 tensor cores with error-free fixed-point slicing
 // (split_common.cuh): every operand becomes four 8-bit digits, each
 // tensor-core sum is exact in FP32, and the per-chunk scales are applied in
 // double-float arithmetic on the FP32 pipe.  No FP64 instruction touches the
@@ -26,13 +26,14 @@
 // where w_{c,m} still differs from wbar_m, is left out of QU and added with
 // the exact weights in double-float by the reduction kernel.
 //
-// Roles in one CTA (1 CTA per SM, persistent over a contiguous range of
-// (tile, chunk) units): 8 converter warps load the FP64 blocks, find the
-// chunk exponent of each column, and write the bf16 digit planes into shared
-// memory (two stages); one MMA warp issues tcgen05.mma into two TMEM buffers;
-// 4 epilogue warps drain TMEM into double-float running sums and write one
-// FP64 partial per (CTA, tile).  All mbarrier waits are bounded; a wait that
-// runs out sets the status word and every role leaves its loop.
+// Two forms of the contraction share the prep and reduction kernels.  The
+// planes path (one system, with a buffer that keeps every unit's digit
+// planes between slices) streams the encoded units into the tensor-core
+// kernel; the fused path (batches, or no buffer) converts the FP64 history
+// inside the tensor-core kernel.  Both are persistent (one CTA per SM) over
+// contiguous ranges of (column tile, chunk) units, with the roles and
+// buffers described at each kernel.  All mbarrier waits are bounded; a wait
+// that runs out sets the status word and every role leaves its loop.
 
 #include <atomic>
 #include <cstdio>
@@ -50,7 +51,7 @@ constexpr int kConvThreads = 256;        // threads that convert FP64 history ro
 constexpr int kKC = 16;                     // complex K entries per chunk (32 real)
 constexpr int kNS = 16;                     // small-operand columns per slice: 8 a x (re, im)
 constexpr int kNA = 8;                      // a values per part
-constexpr int kBigSlice = 128 * 2 * kKC * 2;          // bytes of one digit plane: 128 rows x 32 bf16
+constexpr int kBigSlice = 128 * 2 * kKC * 2;          // bytes of one digit plane: 128 rows x 32 fp16
 constexpr int kBigTile = kSlices * kBigSlice;         // 32 KB
 constexpr int kSmallVar = 4 * kSlices * 2 * 128;      // 4 kgroups x 4 slices x 2 colgroups x 128 B = 4 KB
 constexpr int kSmallBytes = 3 * kSmallVar;            // 12 KB
@@ -75,7 +76,7 @@ struct SplitGeom {
 };
 
 // ---------------------------------------------------------------- prep ---
-// Small operands of chunk kc, part p: A1, NB^<, NBD as bf16 digit planes in
+// Small operands of chunk kc, part p: A1, NB^<, NBD as fp16 digit planes in
 // the shared-memory layout [variant][kgroup 4][slice 4][colgroup 2][8][8],
 // entries B[(a, q_out)][(kappa, q_in)] of the real form of P z:
 //   (re,re) = P.re, (re,im) = -P.im, (im,re) = P.im, (im,im) = P.re.
@@ -132,7 +133,7 @@ __device__ __forceinline__ void prep_chunk(int M, int n, int parts, const double
     const int kg = k >> 3, kin = k & 7;
 #pragma unroll
     for (int sl = 0; sl < kSlices; ++sl) {
-      const uint32_t pr = bf16_of_int(dr[sl]), pi = bf16_of_int(di[sl]), npi = bf16_of_int(-di[sl]);
+      const uint32_t pr = f16_of_int(dr[sl]), pi = f16_of_int(di[sl]), npi = f16_of_int(-di[sl]);
       // column (al, re): (P.re, -P.im); column (al, im): (P.im, P.re)
       const int col_re = 2 * al, col_im = 2 * al + 1;
       uint8_t* base = out + v * kSmallVar + ((kg * kSlices + sl) * 2) * 128;
@@ -285,10 +286,10 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int Vr = fixed31_fast(er[4 * kg + q], e), Vi = fixed31_fast(ei[4 * kg + q], e);
-      w[0][q] = digit_pair_bf16<0>(Vr, Vi);
-      w[1][q] = digit_pair_bf16<1>(Vr, Vi);
-      w[2][q] = digit_pair_bf16<2>(Vr, Vi);
-      w[3][q] = digit_pair_bf16<3>(Vr, Vi);
+      w[0][q] = digit_pair_f16<0>(Vr, Vi);
+      w[1][q] = digit_pair_f16<1>(Vr, Vi);
+      w[2][q] = digit_pair_f16<2>(Vr, Vi);
+      w[3][q] = digit_pair_f16<3>(Vr, Vi);
     }
     const int off = (kg * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
 #pragma unroll
@@ -489,13 +490,13 @@ __global__ void __launch_bounds__(kThreads2, 1) split_main2(Split2Args a) {
         const uint64_t dSU = dS0 + (uint64_t)(((1 + mgrp) * kSmallVar) >> 4);
 #pragma unroll
         for (int i = 0; i < kSlices; ++i) {
-          const uint32_t idesc = umma_idesc_bf16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
+          const uint32_t idesc = umma_idesc_f16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             const uint64_t oa = (uint64_t)((i * kBigSlice + kk * 2 * 2048) >> 4);
             const uint64_t ob = (uint64_t)((kk * 2 * 1024) >> 4);
-            umma_bf16(dacc + i * kNS, dA + oa, dS0 + ob, idesc, 1);
-            if (cls != 0) umma_bf16(dacc + i * kNS, dQU0 + oa, dSU + ob, idesc, 1);
+            umma_f16(dacc + i * kNS, dA + oa, dS0 + ob, idesc, 1);
+            if (cls != 0) umma_f16(dacc + i * kNS, dQU0 + oa, dSU + ob, idesc, 1);
           }
         }
         umma_commit(&sm.accfull[b]);
@@ -906,10 +907,10 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int Vr = fixed31_fast(er[k], e), Vi = fixed31_fast(ei[k], e);
-          w[0][k] = digit_pair_bf16<0>(Vr, Vi);
-          w[1][k] = digit_pair_bf16<1>(Vr, Vi);
-          w[2][k] = digit_pair_bf16<2>(Vr, Vi);
-          w[3][k] = digit_pair_bf16<3>(Vr, Vi);
+          w[0][k] = digit_pair_f16<0>(Vr, Vi);
+          w[1][k] = digit_pair_f16<1>(Vr, Vi);
+          w[2][k] = digit_pair_f16<2>(Vr, Vi);
+          w[3][k] = digit_pair_f16<3>(Vr, Vi);
         }
         const int off = (q * 16 + (jrow >> 3)) * 128 + (jrow & 7) * 16;
         uint8_t* dst = st + arr * kHPlane;
@@ -1022,10 +1023,10 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
           const uint32_t dacc = tmem + b * kAccCols + mgrp * kGroupCols;
 #pragma unroll
           for (int i = 0; i < kSlices; ++i) {
-            const uint32_t idesc = umma_idesc_bf16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
+            const uint32_t idesc = umma_idesc_f16(kNS * (kLevels - i < kSlices ? kLevels - i : kSlices));
             const uint64_t oa = (uint64_t)((i * kHSlice) >> 4);
-            umma_bf16(dacc + i * kNS, dA + oa, dS0, idesc, 1);
-            if (cls != 0) umma_bf16(dacc + i * kNS, dQU0 + oa, dSU, idesc, 1);
+            umma_f16(dacc + i * kNS, dA + oa, dS0, idesc, 1);
+            if (cls != 0) umma_f16(dacc + i * kNS, dQU0 + oa, dSU, idesc, 1);
           }
           umma_commit(&sm.accfull[b]);
           umma_commit(&sm.sempty[ss]);

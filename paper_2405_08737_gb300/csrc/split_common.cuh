@@ -1,18 +1,23 @@
-// split_common.cuh -- fixed-point bf16 slicing and tcgen05 helpers of the
+// split_common.cuh -- fixed-point digit slicing and tcgen05 helpers of the
 // split-precision history slice.
 //
 // A double v with |v| < 2^e is represented as V = round(v * 2^(31-e)), an
-// integer with |V| < 2^31, written in balanced base-256 digits
-//   V = d0 2^24 + d1 2^16 + d2 2^8 + d3,   d0 in [-128, 128], d1..d3 in [-128, 127],
-// so v ~= 2^(e-7) (d0 + d1 2^-8 + d2 2^-16 + d3 2^-24).  Every digit is an
-// integer of at most 8 significant bits and is exact in bf16; a product of
-// two digits is at most 2^14 in magnitude and exact in FP32, and FP32 sums
-// of such products stay exact while they stay below 2^24.  The split path
-// keeps every tensor-core accumulation under that bound, forms the digit
-// products of levels d = i + j = 0..4 (the dropped levels 5 and 6 weigh
-// below 2^-40 of the product), and folds the per-chunk scales in afterwards
-// (Ozaki-style error-free splitting; Ozaki, Ogita, Oishi & Rump, Numer.
-// Algorithms 59 (2012)).
+// integer with |V| < 2^31, written in base-256 digits
+//   V = d0 2^24 + d1 2^16 + d2 2^8 + d3,
+// so v ~= 2^(e-7) (d0 + d1 2^-8 + d2 2^-16 + d3 2^-24).  The history
+// operands take the two's-complement bytes of V (d0 = V >> 24 in
+// [-128, 127], d1..d3 unsigned in [0, 255]); the small operands take
+// balanced digits (d0 in [-128, 128], d1..d3 in [-128, 127]).  Every digit
+// is an integer below 2^8 in magnitude, exact in the 16-bit float formats
+// of the tensor cores (fp16 here: a byte placed in the mantissa of 1024
+// becomes its digit with one packed subtraction); a product of a history
+// digit and a small-operand digit is below 2^15 in magnitude and exact in
+// FP32, and FP32 sums of such products stay exact while they stay below
+// 2^24.  The split path keeps every tensor-core accumulation under that
+// bound, forms the digit products of levels d = i + j = 0..4 (the dropped
+// levels 5 and 6 weigh below 2^-39 of the product), and folds the
+// per-chunk scales in afterwards (Ozaki-style error-free splitting; Ozaki,
+// Ogita, Oishi & Rump, Numer. Algorithms 59 (2012)).
 //
 // Conversions use integer operations on the IEEE-754 bit pattern only (no
 // FP64 instructions, which are slow on this part).
@@ -56,16 +61,6 @@ __device__ __forceinline__ int fixed31(double v, int e) {
   return hi < 0 ? -(int)V : (int)V;
 }
 
-// The four balanced digits of V as bf16 bit patterns (low 16 bits).
-__device__ __forceinline__ void digits_bf16(int V, uint32_t out[kSlices]) {
-  const int d0 = (int)(((long long)V + 0x808080) >> 24);  // [-128, 128]
-  const unsigned w = (unsigned)V + 0x808080u;
-  out[0] = __float_as_uint(__int_as_float(0x4B400000 + d0) - 12582912.0f) >> 16;
-  out[1] = __float_as_uint(__int_as_float(0x4B000000 | ((w >> 16) & 0xFFu)) - 8388736.0f) >> 16;
-  out[2] = __float_as_uint(__int_as_float(0x4B000000 | ((w >> 8) & 0xFFu)) - 8388736.0f) >> 16;
-  out[3] = __float_as_uint(__int_as_float(0x4B000000 | (w & 0xFFu)) - 8388736.0f) >> 16;
-}
-
 // round(v * 2^(31-e)) for |v| < 2^e, branch-free in 32-bit operations (the
 // same integer as fixed31).  The significand m (53 bits) is shifted right by
 // s = 1044 + e - ef >= 22: with x = the top 32 bits of m (m >> 21) and
@@ -85,23 +80,22 @@ __device__ __forceinline__ int fixed31_fast(double v, int e) {
   return (int)((V ^ sg) - sg);
 }
 
-// Balanced digit K (0: the top one, in [-128, 128]; 1..3 in [-128, 127]) of
-// Vr and Vi, as a packed bf16 pair (re in the low half): the same digits as
-// digits_bf16, each from one byte permute and one float add (0x4B0000uu is
-// the float 2^23 + u; subtracting 2^23 + 128 leaves u - 128 exactly).
+// Digit K of Vr and Vi in the history operands' form (K = 0: the signed
+// top byte V >> 24; K = 1..3: the unsigned byte (V >> (24 - 8 K)) & 255) as
+// a packed fp16 pair, re in the low half.  One byte permute gathers the two
+// bytes, one logic operation puts each into the low mantissa bits of the
+// fp16 1024 + b (the top byte with its sign bit flipped: 1152 + d), and one
+// packed subtraction of (1024, 1024), resp. (1152, 1152), leaves the digits,
+// exactly (fp16 holds every integer of [1024, 2048)).
 template <int K>
-__device__ __forceinline__ uint32_t digit_pair_bf16(int Vr, int Vi) {
-  float fr, fi;
-  if (K == 0) {  // floor((V + 0x808080) / 2^24) = floor(((V >> 1) + 0x404040) / 2^23), without overflow
-    const int dr = ((Vr >> 1) + 0x404040) >> 23, di = ((Vi >> 1) + 0x404040) >> 23;
-    fr = __int_as_float(0x4B400000 + dr) - 12582912.0f;
-    fi = __int_as_float(0x4B400000 + di) - 12582912.0f;
-  } else {
-    const unsigned wr = (unsigned)Vr + 0x808080u, wi = (unsigned)Vi + 0x808080u;
-    fr = __int_as_float((int)__byte_perm(wr, 0x4B000000u, 0x7540u | (3 - K))) - 8388736.0f;
-    fi = __int_as_float((int)__byte_perm(wi, 0x4B000000u, 0x7540u | (3 - K))) - 8388736.0f;
-  }
-  return __byte_perm(__float_as_uint(fr), __float_as_uint(fi), 0x7632u);
+__device__ __forceinline__ uint32_t digit_pair_f16(int Vr, int Vi) {
+  constexpr unsigned kByte = 3 - K;
+  const unsigned x = __byte_perm((unsigned)Vr, (unsigned)Vi, kByte | ((kByte + 4) << 8));
+  const unsigned bias = K == 0 ? 0x64806480u : 0x64006400u;
+  const unsigned w = K == 0 ? ((x & 0x00FF00FFu) ^ 0x64806480u) : ((x & 0x00FF00FFu) | 0x64006400u);
+  unsigned r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(bias));
+  return r;
 }
 
 // Digits as integers (used where the negated digits are needed too).
@@ -114,13 +108,15 @@ __device__ __forceinline__ void digits(double v, int e, int d[kSlices]) {
   d[3] = (int)(w & 0xFFu) - 128;
 }
 
-// bf16 bit pattern of a small integer (|d| <= 2^8, exactly representable).
-__device__ __forceinline__ uint32_t bf16_of_int(int d) {
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;  // exact float(d)
-  return __float_as_uint(f) >> 16;
+// fp16 bit pattern of a small integer (|d| <= 2^8, exactly representable):
+// d in the low mantissa bits of the fp16 1280 (1280 + d), minus 1280.
+__device__ __forceinline__ uint32_t f16_of_int(int d) {
+  unsigned r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(0x6500u + (unsigned)d), "r"(0x6500u));
+  return r & 0xFFFFu;
 }
 
-// Pack (lo, hi) bf16 patterns into one 32-bit word (lo at the lower address).
+// Pack (lo, hi) fp16 patterns into one 32-bit word (lo at the lower address).
 __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return (hi << 16) | (lo & 0xFFFFu); }
 
 // ---------------------------------------------------------------- tcgen05 --
@@ -138,12 +134,12 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
-// Instruction descriptor: bf16 x bf16 -> f32, K-major A and B, M = 128.
-__host__ __device__ __forceinline__ uint32_t umma_idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptor: fp16 x fp16 -> f32, K-major A and B, M = 128.
+__host__ __device__ __forceinline__ uint32_t umma_idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
