@@ -37,11 +37,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # profiles/history_partial_fp64_chain_m8_n1024.md)
 FP64_SLICE_TRAFFIC = 2.056e9
 # DRAM bytes of one split contraction launch (split_main2) of the bench slice
-# (ncu capture, profiles/split_main_chain_m8_n1024.md)
-SPLIT_SLICE_TRAFFIC = 2.262e9
+# (ncu capture, profiles/split_main2_chain_m8_n1024.md)
+SPLIT_SLICE_TRAFFIC = 2.263e9
 SPLIT_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of the launch at n=767 (18432 units), scaled by units to "
                         "n=1023 (32768 units)")
-SPLIT_KERNEL = "split_main2 (tcgen05 contraction fed by bulk copies of bf16 digit planes)"
+SPLIT_KERNEL = "split_main2 (tcgen05 contraction fed by bulk copies of fp16 digit planes)"
 
 
 def split_stream_bytes(M, n):
@@ -84,6 +84,11 @@ def parse():
     ap.add_argument("--no-runs", action="store_true", help="skip the whole-run measurements")
     ap.add_argument("--sharded", action="store_true",
                     help="time the row-band sharded step (the N-GPU line) also on one GPU")
+    ap.add_argument("--profile-slice", default=None, choices=["fp64", "split", "split-fused", "df64"],
+                    help="only run three history slices of row n_t - 1 with this contraction (a small case "
+                         "for ncu with --n-t; split-fused: the split path without its plane buffer) and exit")
+    ap.add_argument("--workload", default=None, choices=["chain_m8_n1024", "goe_m32_n1024"],
+                    help="workload of --profile-slice (default: the main one)")
     ap.add_argument("--dense-norb", default="2,8,16,32",
                     help="comma-separated orbital counts of the dense self-energy rows")
     return ap.parse_args()
@@ -427,7 +432,8 @@ def split_roofline(M, n, k_avg_ms):
     the HBM time of the algorithmic bytes (the FP64 L and R triangles read
     once, 16 M^2 (n+1)(n+2) B) and the tensor time of the digit products
     (13 digit pairs x 4 real products x 2 flops per complex multiply-add,
-    (n+1)(3n+2) M^3 of them) at the sustained bf16 peak.  achieved/frac are
+    (n+1)(3n+2) M^3 of them) at the sustained fp16 peak (the measured bf16
+    figure: fp16 and bf16 share the nominal dense rate).  achieved/frac are
     on the binding one; the bytes the kernel actually streams are reported
     beside it."""
     hbm = hbm_peak_gbs()
@@ -447,7 +453,8 @@ def split_roofline(M, n, k_avg_ms):
     else:
         out.update({"bound": "tensor", "achieved": round(digit_flops / sec / 1e12, 2), "peak": tc,
                     "unit": "TFLOP/s", "frac": out["tensor_frac_on_digit_flops"],
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"})
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 1 (fp16 digits; fp16 and bf16 "
+                                   "share the nominal dense tensor rate)"})
     return out
 
 
@@ -1077,11 +1084,38 @@ def sharded_bench(kbe, args, rank, world):
         dist.destroy_process_group()
 
 
+def profile_slice(kbe, args):
+    """Three history slices of row n_t - 1 with one contraction (the launch
+    a profiler captures), then one JSON line with their mean duration."""
+    import torch
+    cfg, t, order, h, U, v, pulse, ctx, run, n = setup_workload(kbe, args.seed, args.n_t, args.workload)
+    stream = torch.cuda.current_stream()
+    prec = "split" if args.profile_slice.startswith("split") else args.profile_slice
+    if args.profile_slice == "split-fused":
+        ctx.set_split_planes(False)
+    ctx.selfenergy_slice(n, run.L, run.R, run.Sl, run.Sg, stream=stream)
+    I = torch.empty_like(run.I)
+    ctx.set_profiling(True)
+    for _ in range(3):
+        ctx.history_slice(n, run.L, run.R, run.Sl, run.Sg, I, precision=prec, stream=stream)
+    torch.cuda.synchronize()
+    k, ms = ctx.read_profiling()
+    ctx.set_profiling(False)
+    ctx.sync_status()
+    print(json.dumps({"profile_slice": args.profile_slice, "workload": args.workload or WORKLOAD, "n": n,
+                      "contraction_ms": round(ms / max(k, 1), 4)}))
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
     if args.impl == "reference":
         return main_reference(args, rank, world)
+    if args.profile_slice:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import paper_2405_08737_gb300 as kbe
+        return profile_slice(kbe, args)
     if world > 1 or args.sharded:
         import paper_2405_08737_gb300 as kbe
         return sharded_bench(kbe, args, rank, world)
@@ -1130,7 +1164,7 @@ def main():
     split_roof = split_roofline(M, n, k_avg_s)
     split_roof["traffic"] = SPLIT_SLICE_TRAFFIC if (M, n) == (8, 1023) else None
     split_roof["traffic_source"] = SPLIT_TRAFFIC_SOURCE
-    split = {"precision": "split: 4-digit bf16 fixed-point slices on tcgen05, exact FP32 chunk sums, "
+    split = {"precision": "split: 4-digit fixed-point slices (fp16 digits) on tcgen05, exact FP32 chunk sums, "
                           "double-float accumulation (KBE_SPLIT_BF16)", "roofline": split_roof,
              "ms_per_step": round(ms_step_s, 4),
              "value": round(world * flops_step / (ms_step_s * 1e-3) / 1e12, 4), "unit": "TFLOP/s (FP64-equivalent)",
