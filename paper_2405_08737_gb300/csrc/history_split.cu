@@ -657,6 +657,7 @@ struct FusedSys {
   const uint8_t* small;   // [cpt][parts_total][kSmallBytes], written by fused_prep
   int* e_small;           // [cpt][parts_total]
   int M, n, CT, cpt, col_tiles;
+  uint32_t magic;              // ceil(2^32 / M) (0 for M = 1): x / M without a division (fused_div)
   int upt;                     // units per column tile: 2 cpt
   int parts;                   // 8-orbital parts this entry contracts (<= 3): part0 .. part0 + parts - 1
   int part0, parts_total;      // first part, and all parts of the system (small-operand layout)
@@ -665,6 +666,12 @@ struct FusedSys {
   long long chunk_base;        // global index of the first chunk (prep grid)
   long long col_base;          // global index of the first output column (reduce grid)
 };
+
+// x / M for 0 <= x < 2^32 / M: floor(x ceil(2^32/M) / 2^32) equals floor(x / M)
+// there (the product's excess over x 2^32 / M is below x / 2^32 < 1 / M).
+__device__ __forceinline__ int fused_div(int x, int M, uint32_t magic) {
+  return M == 1 ? x : (int)__umulhi((uint32_t)x, magic);
+}
 
 struct FusedArgs {
   const FusedSys* sys;
@@ -834,16 +841,17 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
     auto issue = [&](long long v) {  // asynchronous copies of unit v (at cursor ci) into its stage
       const FusedSys& S = a.sys[ci.si];
       const int M = S.M, MM = M * M, n = S.n, CT = S.CT;
+      const uint32_t mg = S.magic;
       const UnitPos P = unit_pos(ci);
       const bool row_live = jrow < CT * M;
-      const int cl = row_live ? jrow / M : 0, bb = jrow - cl * M;
+      const int cl = row_live ? fused_div(jrow, M, mg) : 0, bb = jrow - cl * M;
       const int c = P.ctile * CT + cl;
       const bool col_live = row_live && c <= n;
       uint8_t* st = sm.stage[(int)((v - ua) % kFStages)];
       if (ct < 128) reinterpret_cast<int*>(st + 2 * kHPlane)[ct] = 0;
       const double2* base = reinterpret_cast<const double2*>(arr == 0 ? S.L : S.R);
       const int kap = P.kap0 + 4 * q;
-      int m = kap / M, x = kap - m * M;
+      int m = fused_div(kap, M, mg), x = kap - m * M;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const bool ok = col_live && m <= n;
@@ -869,11 +877,12 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
       const int s = it % kFStages;
       const FusedSys& S = a.sys[cu.si];
       const int M = S.M, CT = S.CT, bw = S.w.band_w;
+      const uint32_t mg = S.magic;
       const UnitPos P = unit_pos(cu);
       const bool row_live = jrow < CT * M;
-      const int cl = row_live ? jrow / M : 0;
+      const int cl = row_live ? fused_div(jrow, M, mg) : 0;
       const int c0 = P.ctile * CT, c = c0 + cl;
-      const int cls = chunk_class(P.kap0 / M, (P.kap0 + kHK - 1) / M, c0, c0 + CT - 1, bw);
+      const int cls = chunk_class(fused_div(P.kap0, M, mg), fused_div(P.kap0 + kHK - 1, M, mg), c0, c0 + CT - 1, bw);
       uint8_t* st = sm.stage[s];
       int* ecol = reinterpret_cast<int*>(st + 2 * kHPlane);
       cp_async_wait<kFAhead - 1>();  // this thread's copies of unit u have landed
@@ -882,7 +891,7 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
       int ef = 0;
       {
         const int kap = P.kap0 + 4 * q;
-        int m = kap / M, x = kap - m * M;
+        int m = fused_div(kap, M, mg), x = kap - m * M;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           double2 z = *reinterpret_cast<const double2*>(st + ((size_t)k * kFConvThreads + ct) * 16);
@@ -998,7 +1007,8 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
         const int M = S.M, CT = S.CT, bw = S.w.band_w;
         const UnitPos P = unit_pos(cu);
         const int c0 = P.ctile * CT;
-        const int cls = chunk_class(P.kap0 / M, (P.kap0 + kHK - 1) / M, c0, c0 + CT - 1, bw);
+        const int cls =
+            chunk_class(fused_div(P.kap0, M, S.magic), fused_div(P.kap0 + kHK - 1, M, S.magic), c0, c0 + CT - 1, bw);
         if (!wait_f(sm, &sm.full[s], (uint32_t)((it / kFStages) & 1), a.status, a.spin)) break;
         if (cls == 2 && !wait_f(sm, &sm.qufull, (uint32_t)(ncls2 & 1), a.status, a.spin)) break;
         const uint64_t so = (uint64_t)(s * kFStageBytes) >> 4;
@@ -1073,7 +1083,7 @@ __global__ void __launch_bounds__(kFThreads, 1) split_fused(FusedArgs a) {
       const FusedSys& S = a.sys[cu.si];
       const int M = S.M, n = S.n, CT = S.CT, parts = S.parts;
       const UnitPos P = unit_pos(cu);
-      const int cl = j / M, bb = j - cl * M;
+      const int cl = fused_div(j, M, S.magic), bb = j - cl * M;
       const bool live_row = cl < CT;
       for (int p = 0; p < parts; ++p, ++it2) {
         const int b = (int)(it2 & 1);
@@ -1514,6 +1524,7 @@ bool fused_build(const FusedSystem* in, int n_sys, FusedPlanHost* p) {
       f.e_small = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(in[i].small) +
                                          (size_t)h.cpt * h.parts * kSmallBytes);
       f.M = h.M; f.n = h.n; f.CT = h.CT; f.cpt = h.cpt; f.col_tiles = col_tiles;
+      f.magic = h.M == 1 ? 0u : (uint32_t)((0x100000000ull + (unsigned long long)h.M - 1) / (unsigned long long)h.M);
       f.upt = 2 * h.cpt;
       f.part0 = part0;
       f.parts = std::min(per, h.parts - part0);
