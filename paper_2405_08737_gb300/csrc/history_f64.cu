@@ -49,8 +49,12 @@ __global__ void __launch_bounds__(256) history_prep(int MM, int n, const double*
 }
 
 // Output entries lin in [lin0, lin_end) (whole columns: lin = c M^2 + a M + b).
+// Blocks take the columns from the last one down: within a chunk of the
+// history index, the columns past the chunk carry both terms of Eq. (KBE2)
+// and the ones before it term 1 only, so the launch order (x fastest) puts
+// the heavier blocks of each chunk first and the last wave holds light ones.
 __global__ void __launch_bounds__(256) history_partial(PartialArgs p, int64_t lin0, int64_t lin_end) {
-  const int64_t lin = lin0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t lin = lin0 + (int64_t)(gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
   if (lin >= lin_end) return;
   rk::history_partial_entry(p, lin, blockIdx.y);
 }
