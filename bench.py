@@ -35,7 +35,7 @@ WORKLOAD = "chain_m8_n1024"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes of one FP64 contraction launch of the bench slice (ncu capture,
 # profiles/history_partial_fp64_chain_m8_n1024.md)
-FP64_SLICE_TRAFFIC = 2.056e9
+FP64_SLICE_TRAFFIC = 1.989e9
 # DRAM bytes of one split contraction launch (split_main2) of the bench slice
 # (ncu capture, profiles/split_main2_chain_m8_n1024.md)
 SPLIT_SLICE_TRAFFIC = 2.263e9
@@ -1155,7 +1155,7 @@ def main():
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
             "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
             "traffic": FP64_SLICE_TRAFFIC if (M, n) == (8, 1023) else None,
-            "traffic_source": "ncu dram__bytes_read+write of the launch at n=1022, scaled to n=1023",
+            "traffic_source": "ncu dram__bytes_read+write of the launch at n=767, scaled by stored blocks to n=1023",
             "kernel": "history_partial (FP64 DFMA contraction)", "launches_timed": k_count,
             "avg_ms": round(k_avg, 4), "peak_source": "unit counts x clock: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz "
                               "(FP64 is not in MEASURED_PEAKS.json)"}
