@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(256) history_df_prep(int MM, int n, const doub
 
 __global__ void __launch_bounds__(kDfBlock) history_df_partial(DfArgs p) {
   const int M = p.M, MM = p.MM, n = p.n, AG = p.AG;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // column blocks from the last column down: the heavier blocks of each
+  // chunk (columns past it carry both terms) start first
+  const int64_t t = (int64_t)(gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= (int64_t)(n + 1) * AG * M) return;
   const int c = (int)(t / ((int64_t)AG * M));
   const int r = (int)(t - (int64_t)c * AG * M);
@@ -183,7 +185,9 @@ __global__ void __launch_bounds__(kDfBlock) history_df_tiled(DfArgs p, TileGeom 
   const int CB = tg.CB, AGB = tg.AGB, TM = tg.TM, NAB = AGB * kNA;
   float4* sG = sm;                                  // [TM][CB][3][MM]: G^<, G^>, G^A as [x][b]
   float4* sS = sm + (size_t)TM * CB * 3 * MM;       // [TM][3][NAB][M]: A1, B^<, B^> rows
-  const int ct = blockIdx.x / tg.ag_tiles, at = blockIdx.x - ct * tg.ag_tiles;
+  // column tiles from the last one down (heavier tiles of each chunk first)
+  const int bx = (int)(gridDim.x - 1 - blockIdx.x);
+  const int ct = bx / tg.ag_tiles, at = bx - ct * tg.ag_tiles;
   const int c_base = ct * CB, ag_base = at * AGB;
   const int a_base = ag_base * kNA;
   const int tid = threadIdx.x;
