@@ -221,25 +221,43 @@ struct EncodeArgs {
   int ct_base, kc_base, kc_count;  // units: ct_base + i / kc_count, kc_base + i % kc_count
   int c_min;                       // only the columns c >= c_min are encoded
   int* status;
+  // rows [row_lo, row_lo + rows) of each unit, upc units per CTA, units in
+  // all (whole units: 0, 128, 1)
+  int row_lo, rows, upc;
+  unsigned units;
 };
+constexpr int kEncMaxUpc = 16;  // units per CTA of the encoder, at most
 
-// One CTA per (column tile, chunk): thread (arr, jrow) encodes row jrow of
-// plane arr (0: G^< from L, 1: Q from R) for the chunk's 16 K entries.
-// Every column has its own exponent, so the rows of the columns below c_min
-// are left as they are.
-__global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
+// Thread (arr, k, jrow) encodes row jrow of plane arr (0: G^< from L, 1: Q
+// from R) for the 16 K entries of the CTA's k-th unit (column tile, chunk).
+// Whole units take one CTA each (256 threads: rows 0..127 of both planes);
+// a KBE step's new column takes its few rows of 16 units per CTA.  Every
+// column has its own exponent, so the rows of the columns below c_min are
+// left as they are.  Threads past the mapped ones (the block is a whole
+// number of warps) only join the collective steps.  kNarrow: the general
+// mapping (several units per CTA, a band of rows), at one CTA per SM's
+// worth of registers; otherwise whole units at three CTAs per SM.
+template <bool kNarrow>
+__global__ void __launch_bounds__(256, kNarrow ? 1 : 3) split_encode(EncodeArgs a) {
   const SplitGeom& g = a.g;
   const int M = g.M, MM = g.MM, n = g.n, CT = g.CT;
-  const int ctile = a.ct_base + (int)(blockIdx.x / (unsigned)a.kc_count);
-  const int kc = a.kc_base + (int)(blockIdx.x % (unsigned)a.kc_count);
-  __shared__ int ecol[128];
-  const int ct = threadIdx.x, arr = ct >> 7, jrow = ct & 127;
-  const bool row_live = jrow < CT * M;
+  constexpr int kUpcMax = kNarrow ? kEncMaxUpc : 1;
+  __shared__ int ecol[kUpcMax * 128];
+  const int upc = kNarrow ? a.upc : 1, rows = kNarrow ? a.rows : 128;
+  const int t = threadIdx.x, per = upc * rows;
+  const int arr = kNarrow ? t / per : t >> 7;
+  const int rem = t - arr * per, k = kNarrow ? rem / rows : 0;
+  const int jrow = kNarrow ? a.row_lo + (rem - k * rows) : (t & 127);
+  const unsigned ui = blockIdx.x * (unsigned)upc + (unsigned)k;
+  const bool mapped = kNarrow ? (arr < 2 && ui < a.units) : true;
+  const int ctile = a.ct_base + (int)(mapped ? ui / (unsigned)a.kc_count : 0u);
+  const int kc = a.kc_base + (int)(mapped ? ui % (unsigned)a.kc_count : 0u);
+  const bool row_live = mapped && jrow < CT * M;
   const int cl = row_live ? jrow / M : 0, bb = jrow - cl * M;
   const int c0 = ctile * CT;
   const int kap0 = kc * kKC;
   const int cls = chunk_class(kap0 / M, (kap0 + kKC - 1) / M, c0, c0 + CT - 1, g.band_w);
-  if (ct < 128) ecol[ct] = 0;
+  for (int e = t; e < upc * 128; e += blockDim.x) ecol[e] = 0;
   __syncthreads();
   const double2* base = reinterpret_cast<const double2*>(arr == 0 ? a.L : a.R);
   const int c = c0 + cl;
@@ -269,17 +287,17 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
 #pragma unroll
     for (int k = 0; k < kKC; ++k) ef = max(ef, max(exp_field(er[k]), exp_field(ei[k])));
   }
-  column_max(ecol, cl, ef, enc);
+  column_max(ecol, k * 128 + cl, ef, enc);
   __syncthreads();
   uint8_t* unit = a.planes + ((size_t)ctile * a.cpt_stride + kc) * kUnitBytes;
-  uint8_t* dst = unit + arr * kBigTile;
+  uint8_t* dst = unit + (arr & 1) * kBigTile;
   uint8_t* QU = nullptr;
-  if (arr == 1 && cls == 2) {
+  if (mapped && arr == 1 && cls == 2) {
     const int slot = qu_slot(kc, c0, M, g.band_w);
     if (slot >= 0 && slot < a.qu_slots) QU = a.qu + ((size_t)ctile * a.qu_slots + slot) * kBigTile;
-    else if (ct == 128) atomicOr(a.status, kStatusInternal);  // geometry error: reported, never written
+    else if (jrow == a.row_lo) atomicOr(a.status, kStatusInternal);  // geometry error: reported, never written
   }
-  const int e = scale_from_field(ecol[cl]);
+  const int e = scale_from_field(ecol[k * 128 + cl]);
 #pragma unroll
   for (int kg = 0; kg < 4 && enc; ++kg) {
     uint32_t w[kSlices][4];
@@ -304,7 +322,15 @@ __global__ void __launch_bounds__(256, 3) split_encode(EncodeArgs a) {
     }
   }
   // exponents of the encoded columns (and the padding beyond the tile's CT)
-  if (ct < 128 && c0 + ct >= a.c_min) reinterpret_cast<int*>(unit + 2 * kBigTile)[ct] = ecol[ct];
+  for (int e2 = t; e2 < upc * 128; e2 += blockDim.x) {
+    const int k2 = e2 >> 7, col = e2 & 127;
+    const unsigned u2 = blockIdx.x * (unsigned)upc + (unsigned)k2;
+    if (u2 >= a.units) break;
+    const int ct2 = a.ct_base + (int)(u2 / (unsigned)a.kc_count), kc2 = a.kc_base + (int)(u2 % (unsigned)a.kc_count);
+    if (ct2 * CT + col >= a.c_min)
+      reinterpret_cast<int*>(a.planes + ((size_t)ct2 * a.cpt_stride + kc2) * kUnitBytes + 2 * kBigTile)[col] =
+          ecol[e2];
+  }
 }
 
 struct Smem2 {
@@ -1479,13 +1505,31 @@ cudaError_t launch_history_split2(const SplitLaunch& l, const SplitPlanes& pl_la
   const int kc_lo = (int)(((long long)r0 * h.M) / kKC);
   if (ct_lo < col_tiles) {
     EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, ct_lo, 0, h.cpt, r0, l.status};
-    split_encode<<<(unsigned)((size_t)(col_tiles - ct_lo) * h.cpt), 256, 0, s>>>(ea);
+    ea.units = (unsigned)(col_tiles - ct_lo) * (unsigned)h.cpt;
+    ea.row_lo = 0;
+    ea.rows = 128;
+    ea.upc = 1;
+    unsigned threads = 256;
+    if (col_tiles - ct_lo == 1) {  // one tile: only its rows from column r0 on, several chunks per CTA
+      ea.row_lo = (r0 - ct_lo * h.CT) * h.M;
+      ea.rows = h.CT * h.M - ea.row_lo;
+      ea.upc = std::max(1, std::min(kEncMaxUpc, 128 / ea.rows));
+      threads = (unsigned)((2 * ea.upc * ea.rows + 31) / 32 * 32);
+    }
+    if (ea.upc > 1 || ea.row_lo > 0)
+      split_encode<true><<<(ea.units + ea.upc - 1) / ea.upc, threads, 0, s>>>(ea);
+    else
+      split_encode<false><<<ea.units, 256, 0, s>>>(ea);
     ++*launches;
   }
   const int ct_hi = std::min(col_tiles, ct_lo + 1);
   if (r0 > 0 && kc_lo < h.cpt) {
     EncodeArgs ea{g, l.L, l.R, pl, qu, pl_layout.cpt_stride, qs, 0, kc_lo, h.cpt - kc_lo, 0, l.status};
-    split_encode<<<(unsigned)((size_t)ct_hi * (h.cpt - kc_lo)), 256, 0, s>>>(ea);
+    ea.units = (unsigned)ct_hi * (unsigned)(h.cpt - kc_lo);
+    ea.row_lo = 0;
+    ea.rows = 128;
+    ea.upc = 1;
+    split_encode<false><<<ea.units, 256, 0, s>>>(ea);
     ++*launches;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
