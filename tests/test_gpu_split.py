@@ -264,6 +264,45 @@ def test_split_plane_cache_is_exact(kbe, name, n_t):
         r.ctx.close()
 
 
+@pytest.mark.parametrize("M,n_t,kind", [(3, 50, "goe"), (5, 40, "chain"), (12, 28, "goe"), (24, 16, "chain")])
+def test_split_steps_other_orbital_counts(kbe, M, n_t, kind):
+    """Split KBE steps at orbital counts whose tiles hold 42, 25, 10 and 5
+    columns (the new row's columns are encoded by the encoder's narrow form,
+    a block padded to whole warps): cached planes give bitwise the rows of
+    steps that encode everything again, and the run stays within the
+    compounded split bound (5e-8) of the oracle's FP64 run."""
+    import torch
+    t, order = W.grid(n_t, 0.05, 0.4, 60 + M)
+    h = W.chain_h(M, 1.0) if kind == "chain" else W.goe_h(M, 60 + M)
+    U = np.linspace(0.5, 2.0, M)
+    v = W.site_potential(M)
+    rho0 = W.half_filled_rho(h)
+    runs = []
+    for fresh in (False, True):
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, None)
+        run = kbe.Run(ctx)
+        run.init_uncorrelated(rho0)
+        for n in range(1, n_t):
+            if fresh:
+                ctx.reset_cache()
+            run.step(n, P=2, precision="split")
+        ctx.sync_status()
+        runs.append(run)
+    assert torch.equal(runs[0].L, runs[1].L) and torch.equal(runs[0].R, runs[1].R)
+    L0, R0, F0 = oracle.initial_rhs(t, order, h, U, v, None, rho0)
+    Lo = np.zeros((W.tri_size(n_t), M, M), np.complex128)
+    Ro = np.zeros_like(Lo)
+    Lo[0], Ro[0] = L0[0], R0[0]
+    Lo, Ro, _ = oracle.run(t, order, h, U, v, None, 2, Lo, Ro, {0: F0}, 1, n_t,
+                           nthreads=oracle.threads_available())
+    err = _rel(runs[0].L[: W.tri_size(n_t)].cpu().numpy(), Lo)
+    assert err < 5e-8, (M, err)
+    for r in runs:
+        r.ctx.close()
+
+
 @pytest.mark.parametrize("path", ["planes", "fused"])
 def test_split_wait_timeout_is_reported_and_the_context_recovers(kbe, path):
     """The device-side failure path of the contraction's pipeline, with no
