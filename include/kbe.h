@@ -272,6 +272,16 @@ kbe_status kbe_rhs_row(kbe_ctx* ctx, int j, int precision, const void* L, const 
 kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R, void* S_less,
                     void* S_great, void* I_work, void* F_ring, void* stream);
 
+/* The KBE steps of rows n_first..n_last in order (1 <= n_first <= n_last <
+ * n_max), each exactly kbe_step's (the same kernels, rows and ring slots;
+ * rows 0..n_first-1 and the right-hand-side rows before n_first present as
+ * kbe_step requires for row n_first): a whole run on the given grid (Sec. 3.1
+ * with the grid's steps and orders) in one call, all on `stream` with no
+ * host synchronisation and no call per step.  Errors as kbe_step; on an
+ * error the rows before the failing one are stepped. */
+kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int precision, void* L, void* R,
+                         void* S_less, void* S_great, void* I_work, void* F_ring, void* stream);
+
 /* The phases of one KBE_FP64 step, for callers that form the history slice
  * themselves -- one system split by row bands of the stored triangles across
  * devices (Eq. KBE2 is a sum over stored blocks, so the bands' partial slices

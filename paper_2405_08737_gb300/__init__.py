@@ -68,6 +68,7 @@ def lib():
         L.kbe_step_sweep_band.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp]
         L.kbe_step_sweep_finish.argtypes = [vp, i, vp, vp, vp, vp, vp]
         L.kbe_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp]
+        L.kbe_run_steps.argtypes = [vp, i, i, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_step_rows.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, i, i, vp]
         L.kbe_step_host.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_history_slice_band.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp]
@@ -304,6 +305,12 @@ class Context:
                                    self._dev(Sl), self._dev(Sg), self._dev(I_work), self._dev(F_ring),
                                    self._stream(stream)))
 
+    def run_steps(self, n_first, n_last, L, R, Sl, Sg, I_work, F_ring, P=2, precision="fp64", stream=None):
+        """kbe_run_steps: the steps of rows n_first..n_last in one call."""
+        self._check(lib().kbe_run_steps(self._h, int(n_first), int(n_last), P, PRECISIONS[precision],
+                                        self._dev(L), self._dev(R), self._dev(Sl), self._dev(Sg),
+                                        self._dev(I_work), self._dev(F_ring), self._stream(stream)))
+
     # -- the phases of a KBE_FP64 step (one system split by row bands)
     def step_predict(self, n, L, R, F_ring, stream=None):
         self._check(lib().kbe_step_predict(self._h, n, self._dev(L), self._dev(R), self._dev(F_ring),
@@ -465,6 +472,10 @@ class Run:
     def step(self, n, P=2, precision="fp64", stream=None):
         self.ctx.step(n, self.L, self.R, self.Sl, self.Sg, self.I, self.F, P=P, precision=precision,
                       stream=stream)
+
+    def run_steps(self, n_first, n_last, P=2, precision="fp64", stream=None):
+        self.ctx.run_steps(n_first, n_last, self.L, self.R, self.Sl, self.Sg, self.I, self.F, P=P,
+                           precision=precision, stream=stream)
 
     def step_host(self, n, L_host, R_host, F_host, L_row_host, R_row_host, P=2, precision="fp64", stream=None):
         """One step with the history and ring uploaded from host tensors and

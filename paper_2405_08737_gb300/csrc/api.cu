@@ -1072,6 +1072,28 @@ kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R,
   return st;
 }
 
+// The steps of rows n_first..n_last, one after another on the stream.
+// (Capturing them into one CUDA graph was measured on the 63-step dimer run:
+// 5.77 ms against 5.61 ms launched one by one; its steps are bound on the
+// device, at about 6 microseconds per small kernel, not by the launches.)
+kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int precision, void* L, void* R, void* Sl,
+                         void* Sg, void* I_work, void* F_ring, void* stream) {
+  if (!ctx) return KBE_EINVAL;
+  ctx->last_launches = 0;
+  if (n_first < 1 || n_last < n_first) return fail(ctx, KBE_EINVAL, "kbe_run_steps: need 1 <= n_first <= n_last");
+  kbe_status st = check_step_call(ctx, n_last, P, precision, L, R, Sl, Sg, I_work, F_ring);
+  if (st != KBE_OK) return st;
+  int total = 0;
+  for (int n = n_first; n <= n_last && st == KBE_OK; ++n) {
+    int count = 0;
+    st = step_impl(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_ring, 0, kRing, (cudaStream_t)stream, nullptr,
+                   &count);
+    total += count;
+  }
+  ctx->last_launches = total;
+  return st;
+}
+
 kbe_status kbe_step_host(kbe_ctx* ctx, int n, int P, int precision, const void* L_host, const void* R_host,
                          const void* F_host, void* L, void* R, void* Sl, void* Sg, void* I_work, void* F_ring,
                          void* L_row_host, void* R_row_host, void* stream) {

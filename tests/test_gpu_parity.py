@@ -385,3 +385,43 @@ def test_step_phases_with_row_bands(kbe, world):
     assert _rel(a[1], Lo[p:]) < 1e-12 and _rel(b[1], Ro[p:]) < 1e-12
     for r in runs:
         r.ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split", "df64"])
+def test_run_steps_is_the_step_loop(kbe, precision):
+    """kbe_run_steps (the steps of rows n_first..n_last in one call) gives
+    bitwise the rows, slices and ring of one kbe_step call per row, also when
+    a run continues from a later row; bad row ranges are rejected."""
+    import torch
+    M, n_t, seed = 3, 37, 14
+    t, order = W.grid(n_t, 0.05, 0.4, seed)
+    h = W.goe_h(M, seed)
+    U, v = np.linspace(0.5, 2.0, M), W.site_potential(M)
+    pulse = dict(W.PULSE_CHAIN, t0=float(t[n_t // 2]), sigma=0.3)
+    runs = []
+    for mode in ("loop", "one call", "two calls"):
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        run = kbe.Run(ctx)
+        run.init_uncorrelated(W.half_filled_rho(h))
+        if mode == "loop":
+            for n in range(1, n_t):
+                run.step(n, P=2, precision=precision)
+        elif mode == "one call":
+            run.run_steps(1, n_t - 1, P=2, precision=precision)
+        else:
+            run.run_steps(1, 20, P=2, precision=precision)
+            run.run_steps(21, n_t - 1, P=2, precision=precision)
+        ctx.sync_status()
+        runs.append(run)
+    for other in runs[1:]:
+        for a, b in ((runs[0].L, other.L), (runs[0].R, other.R), (runs[0].F, other.F), (runs[0].I, other.I)):
+            assert torch.equal(a, b)
+    ctx = runs[0].ctx
+    for lo, hi in ((0, 5), (5, 4), (1, n_t)):
+        with pytest.raises(kbe.KBEError) as e:
+            runs[0].run_steps(lo, hi, P=2, precision=precision)
+        assert e.value.status in (kbe.KBE_EINVAL, kbe.KBE_ERANGE)
+    for r in runs:
+        r.ctx.close()
