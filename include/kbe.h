@@ -277,8 +277,14 @@ kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R,
  * rows 0..n_first-1 and the right-hand-side rows before n_first present as
  * kbe_step requires for row n_first): a whole run on the given grid (Sec. 3.1
  * with the grid's steps and orders) in one call, all on `stream` with no
- * host synchronisation and no call per step.  Errors as kbe_step; on an
- * error the rows before the failing one are stepped. */
+ * host synchronisation and no call per step.  With KBE_FP64, the local
+ * interaction, fixed history orders, no thermal branch and profiling off,
+ * rows of at most 4096 complex entries per component ((n+1) M^2 <= 4096)
+ * run up to 64 at a time in one cooperative launch (one block per SM, a
+ * device-wide barrier with a bounded wait between the phases of a step; a
+ * wait that runs out is reported as KBE_ETIMEOUT by kbe_sync_status); the
+ * rows, slices and ring are bitwise kbe_step's.  Errors as kbe_step; on a
+ * launch error the rows before the failing launch are stepped. */
 kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int precision, void* L, void* R,
                          void* S_less, void* S_great, void* I_work, void* F_ring, void* stream);
 

@@ -48,6 +48,8 @@ void release(kbe_ctx* ctx) {
   cudaFree(ctx->d_wbar); cudaFree(ctx->d_band); cudaFree(ctx->d_corr); cudaFree(ctx->d_pred);
   cudaFree(ctx->d_h0); cudaFree(ctx->d_U); cudaFree(ctx->d_v); cudaFree(ctx->d_eps);
   cudaFree(ctx->d_part); cudaFree(ctx->d_status); cudaFree(ctx->d_split); cudaFree(ctx->d_adj);
+  cudaFree(ctx->d_runbar);
+  ctx->d_runbar = nullptr;
   cudaFree(ctx->d_planes);
   cudaFree(ctx->d_hist);
   cudaFree(ctx->d_korder);
@@ -626,7 +628,7 @@ kbe_status kbe_create(int norb, int n_max, kbe_ctx** out) {
       (e = dev_alloc(&ctx->d_U, (size_t)norb)) != cudaSuccess ||
       (e = dev_alloc(&ctx->d_v, (size_t)norb)) != cudaSuccess ||
       (e = dev_alloc(&ctx->d_eps, 2 * MM)) != cudaSuccess ||
-      (e = dev_alloc(&ctx->d_status, 1)) != cudaSuccess) {
+      (e = dev_alloc(&ctx->d_status, 1)) != cudaSuccess || (e = dev_alloc(&ctx->d_runbar, 1)) != cudaSuccess) {
     release(ctx);
     delete ctx;
     cudaGetLastError();
@@ -1084,11 +1086,47 @@ kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int preci
   kbe_status st = check_step_call(ctx, n_last, P, precision, L, R, Sl, Sg, I_work, F_ring);
   if (st != KBE_OK) return st;
   int total = 0;
-  for (int n = n_first; n <= n_last && st == KBE_OK; ++n) {
+  // Plain FP64 steps with the local interaction and fixed orders: runs of
+  // small rows go to the cooperative kernel, up to kRunMaxSteps rows per launch.
+  const bool coop = precision == KBE_FP64 && !ctx->dense && ctx->adaptive_K == 0 && !ctx->thermal &&
+                    !ctx->profiling;
+  const int64_t MM = (int64_t)ctx->M * ctx->M;
+  int n = n_first;
+  while (n <= n_last && st == KBE_OK) {
+    if (coop && (int64_t)(n + 1) * MM <= kRunMaxRow) {
+      RunSmallHost h{};
+      h.base = step_args(ctx, n, L, R, I_work, F_ring);
+      h.Sl = (double*)Sl;
+      h.Sg = (double*)Sg;
+      h.I = (double*)I_work;
+      h.w = weights_view(ctx);
+      h.part = ctx->d_part;
+      h.corr0 = ctx->d_corr;
+      h.pred0 = ctx->d_pred;
+      h.bar = ctx->d_runbar;
+      h.spin = 1ll << 24;  // polls (at least 64 ns each after the first 256): about a second or more
+      h.P = P;
+      while (h.nsteps < kRunMaxSteps && n <= n_last && (int64_t)(n + 1) * MM <= kRunMaxRow) {
+        const int i = h.nsteps;
+        if (!history_f64_split(ctx->M, n, ctx->part_bytes, 0x7fffffff, &h.nchunk[i], &h.chunk_len[i]))
+          return fail(ctx, KBE_ENOMEM, "kbe_run_steps: history workspace too small");
+        h.n[i] = n;
+        h.kn[i] = ctx->grid.order[n];
+        h.field[i] = ctx->model.field(ctx->grid.t[n]);
+        ++h.nsteps;
+        ++n;
+      }
+      int count = 0;
+      const cudaError_t e = launch_run_small(h, (cudaStream_t)stream, &count);
+      total += count;
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "kbe_run_steps: cooperative run launch");
+      continue;
+    }
     int count = 0;
     st = step_impl(ctx, n, P, precision, L, R, Sl, Sg, I_work, F_ring, 0, kRing, (cudaStream_t)stream, nullptr,
                    &count);
     total += count;
+    ++n;
   }
   ctx->last_launches = total;
   return st;

@@ -85,6 +85,31 @@ inline unsigned grid_for(int64_t n, int64_t cap) {
 
 }  // namespace
 
+// Split of the history index m of the FP64 slice of row n: at least enough
+// threads for full occupancy (every SM x 2048 threads), and chunks short
+// enough that one 128-thread block does about 2^16 complex multiply-adds
+// (3M per point and output), which keeps the tail of the launch short; the
+// partials must fit the workspace.  A band of stored rows below n
+// contributes only history points m < band_hi: the chunks beyond them have
+// no work.  False when even one chunk does not fit.
+bool history_f64_split(int M, int n, size_t part_bytes, int band_hi, int* nchunk_out, int* chunk_len_out) {
+  const int64_t row = (int64_t)(n + 1) * M * M;
+  int64_t want = ((int64_t)sm_count() * 2048 + row - 1) / row;
+  const int64_t len_target = std::max<int64_t>(1, (1 << 16) / (kHistBlock * 3 * M));
+  want = std::max<int64_t>(want, (n + 1 + len_target - 1) / len_target);
+  int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
+  if (nchunk > n + 1) nchunk = n + 1;
+  const size_t prep_bytes = (size_t)3 * row * 16;
+  while (nchunk > 1 && prep_bytes + (size_t)nchunk * 2 * row * 16 > part_bytes) --nchunk;
+  if (prep_bytes + (nchunk > 1 ? (size_t)nchunk * 2 * row * 16 : 0) > part_bytes) return false;
+  const int chunk_len = (n + 1 + nchunk - 1) / nchunk;
+  nchunk = (n + 1 + chunk_len - 1) / chunk_len;
+  if (band_hi <= n) nchunk = std::max(1, std::min(nchunk, (band_hi + chunk_len - 1) / chunk_len));
+  *nchunk_out = nchunk;
+  *chunk_len_out = chunk_len;
+  return true;
+}
+
 // Workspace layout (doubles): A1, Bl, Bg: 3 x (n+1) MM complex; then the
 // split partials nchunk x 2 x (n+1) MM complex.  The output columns may be
 // contracted in several launches (column ranges, each after an optional
@@ -95,25 +120,8 @@ cudaError_t launch_history_f64_ranges(const HistoryArgs& a, int nranges, const i
                                       const cudaEvent_t* wait, cudaStream_t s, int* launches) {
   const int M = a.M, MM = M * M, n = a.n;
   const int64_t row = (int64_t)(n + 1) * MM;       // complex entries per s
-  const int64_t outputs = row;                     // threads of one chunk
-  // Split of the history index m: at least enough threads for full
-  // occupancy (every SM x 2048 threads), and chunks short enough that one
-  // 128-thread block does about 2^16 complex multiply-adds (3M per point and
-  // output), which keeps the tail of the launch short.
-  int64_t want = ((int64_t)sm_count() * 2048 + outputs - 1) / outputs;
-  const int64_t len_target = std::max<int64_t>(1, (1 << 16) / (kHistBlock * 3 * M));
-  want = std::max<int64_t>(want, (n + 1 + len_target - 1) / len_target);
-  int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
-  if (nchunk > n + 1) nchunk = n + 1;
-  // the partials must fit the workspace
-  const size_t prep_bytes = (size_t)3 * row * 16;
-  while (nchunk > 1 && prep_bytes + (size_t)nchunk * 2 * row * 16 > a.part_bytes) --nchunk;
-  if (prep_bytes + (nchunk > 1 ? (size_t)nchunk * 2 * row * 16 : 0) > a.part_bytes) return cudaErrorInvalidValue;
-  const int chunk_len = (n + 1 + nchunk - 1) / nchunk;
-  nchunk = (n + 1 + chunk_len - 1) / chunk_len;
-  // a band of stored rows below n contributes only history points m < band_hi:
-  // the chunks beyond them have no work for any output column
-  if (a.band_hi <= n) nchunk = std::max(1, std::min(nchunk, (a.band_hi + chunk_len - 1) / chunk_len));
+  int nchunk = 0, chunk_len = 0;
+  if (!history_f64_split(M, n, a.part_bytes, a.band_hi, &nchunk, &chunk_len)) return cudaErrorInvalidValue;
 
   double* A1 = a.part;
   double* Bl = A1 + 2 * row;

@@ -116,6 +116,7 @@ struct kbe_ctx {
   long long dbg_withhold = -1;
   long long dbg_spin = 0;
   int* d_status = nullptr;
+  unsigned* d_runbar = nullptr;  // barrier counter of the cooperative small-row run kernel
   size_t part_bytes = 0;
   // reverse-mode workspace, allocated by the first adjoint call that needs it
   double* d_adj = nullptr;
@@ -285,6 +286,33 @@ struct StepArgs {
   int* status;
 };
 cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s);
+// Split of the history index of the FP64 slice of row n (chunks and their
+// length), as every FP64 slice launch takes it; false when the workspace
+// holds no split.
+bool history_f64_split(int M, int n, size_t part_bytes, int band_hi, int* nchunk, int* chunk_len);
+
+// Consecutive FP64 KBE steps of a small system in one cooperative launch
+// (run_small.cu): the rows n[0..nsteps), each with its interval's order,
+// field and history split; the rest as in kbe_step's launches.
+constexpr int kRunMaxSteps = 64;
+constexpr int kRunThreads = 256;
+constexpr int kRunMaxRow = 4096;  // rows of at most this many entries ((n+1) M^2) run in the cooperative kernel
+struct RunSmallHost {
+  StepArgs base;                 // n, kn, field, corr, pred are set per row
+  double* Sl;
+  double* Sg;
+  double* I;
+  WeightsView w;
+  double* part;
+  const double* corr0;
+  const double* pred0;
+  unsigned* bar;                 // one counter of device memory
+  long long spin;
+  int P, nsteps;
+  int n[kRunMaxSteps], kn[kRunMaxSteps], chunk_len[kRunMaxSteps], nchunk[kRunMaxSteps];
+  double field[kRunMaxSteps];
+};
+cudaError_t launch_run_small(const RunSmallHost& h, cudaStream_t s, int* launches);
 // L(0,0) = i rho, R(0,0) = -i 1 from the device matrix rho (complex MxM).
 cudaError_t launch_init_row0(int M, const double* rho, double* L, double* R, cudaStream_t s);
 cudaError_t launch_fock(const StepArgs& a, cudaStream_t s);

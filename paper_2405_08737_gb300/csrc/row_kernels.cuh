@@ -13,8 +13,12 @@ namespace rk {
 struct Cd {
   double re, im;
 };
+// kReadOnly: through the read-only cache (data nobody writes during the
+// launch); otherwise a plain load, which sees what other blocks of the same
+// launch wrote before a device-wide barrier (release/acquire) that it follows.
+template <bool kReadOnly = true>
 __device__ __forceinline__ Cd ld(const double* p) {
-  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 v = kReadOnly ? __ldg(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
   return Cd{v.x, v.y};
 }
 // acc += a * b
@@ -133,8 +137,11 @@ struct PartialArgs {
 };
 
 // Output entry lin = (c, a, b) of the history slice over history points
-// m in chunk `chunk`; writes I^< and I^> partials of that chunk.
+// m in chunk `chunk`; writes I^< and I^> partials of that chunk.  The
+// operand loads take the path of ld<kReadOnly>; the arithmetic is the same.
+template <bool kReadOnly = true>
 __device__ __forceinline__ void history_partial_entry(const PartialArgs& p, int64_t lin, int chunk) {
+  const auto ld = [](const double* q) { return rk::ld<kReadOnly>(q); };
   const int M = p.M, MM = p.MM, n = p.n;
   const int c = (int)(lin / MM);
   const int ab = (int)(lin - (int64_t)c * MM);

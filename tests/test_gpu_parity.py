@@ -425,3 +425,40 @@ def test_run_steps_is_the_step_loop(kbe, precision):
         assert e.value.status in (kbe.KBE_EINVAL, kbe.KBE_ERANGE)
     for r in runs:
         r.ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("M,n_t,launches", [(2, 100, 2), (8, 80, None)])
+def test_run_steps_cooperative_rows(kbe, M, n_t, launches):
+    """FP64 rows of at most 4096 entries run in one cooperative launch per
+    64 rows with device-wide barriers between the phases of a step: the
+    dimer's 99 steps take two launches, and a run of an 8-orbital chain
+    crosses from those rows (n <= 63) to the per-kernel step; both give
+    bitwise the rows, slice and ring of one kbe_step call per row."""
+    import torch
+    seed = 21
+    t, order = W.grid(n_t, 0.05, 0.4, seed)
+    h = W.goe_h(M, seed)
+    U, v = np.linspace(0.5, 2.0, M), W.site_potential(M)
+    pulse = dict(W.PULSE_CHAIN, t0=float(t[n_t // 3]), sigma=0.3)
+    runs = []
+    for one_call in (False, True):
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        run = kbe.Run(ctx)
+        run.init_uncorrelated(W.half_filled_rho(h))
+        if one_call:
+            run.run_steps(1, n_t - 1, P=2)
+            if launches is not None:
+                assert ctx.last_launch_count == launches
+        else:
+            for n in range(1, n_t):
+                run.step(n, P=2)
+        ctx.sync_status()
+        runs.append(run)
+    for a, b in ((runs[0].L, runs[1].L), (runs[0].R, runs[1].R), (runs[0].F, runs[1].F), (runs[0].I, runs[1].I)):
+        assert torch.equal(a, b)
+    assert bool(torch.isfinite(runs[1].L).all())
+    for r in runs:
+        r.ctx.close()
