@@ -507,6 +507,18 @@ kbe_status kbe_sync_status(kbe_ctx* ctx, void* stream);
  * nothing.  KBE_EINVAL for unit < 0 or spin_limit < 1. */
 kbe_status kbe_debug_withhold_split(kbe_ctx* ctx, long long unit, long long spin_limit);
 
+/* Test support for the failure path of kbe_run_steps' cooperative launch
+ * (no fault is involved): in the next such launch on this context, block 0
+ * leaves the kernel at device-wide barrier number `barrier` (0 = the one
+ * after the launch's first predictor, then four per sweep) without arriving,
+ * and every barrier wait gives up after spin_limit polls (instead of about
+ * 2^24).  The other blocks' waits run out and they return; kbe_sync_status
+ * reports KBE_ETIMEOUT and the rows of that launch are undefined.  Later
+ * launches are unaffected (the setting clears itself).  A barrier beyond the
+ * launch's last withholds nothing.  KBE_EINVAL for barrier < 0 or
+ * spin_limit < 1. */
+kbe_status kbe_debug_withhold_run(kbe_ctx* ctx, int barrier, long long spin_limit);
+
 /* Number of kernels the last kbe_* call on this context enqueued. */
 int kbe_last_launch_count(const kbe_ctx* ctx);
 

@@ -63,6 +63,7 @@ def lib():
         L.kbe_rhs_row.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp]
         L.kbe_init_uncorrelated.argtypes = [vp, vp, vp, vp, vp]
         L.kbe_debug_withhold_split.argtypes = [vp, ctypes.c_longlong, ctypes.c_longlong]
+        L.kbe_debug_withhold_run.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
         L.kbe_set_split_planes.argtypes = [vp, i]
         L.kbe_step_predict.argtypes = [vp, i, vp, vp, vp, vp]
         L.kbe_step_sweep_band.argtypes = [vp, i, i, i, vp, vp, vp, vp, vp, vp]
@@ -429,6 +430,10 @@ class Context:
     def set_split_planes(self, keep):
         """kbe_set_split_planes: keep (True) or drop (False) the digit-plane cache of the split path."""
         self._check(lib().kbe_set_split_planes(self._h, 1 if keep else 0))
+
+    def debug_withhold_run(self, barrier, spin_limit):
+        """Failure-path test of the next cooperative run launch (kbe_debug_withhold_run)."""
+        self._check(lib().kbe_debug_withhold_run(self._h, int(barrier), int(spin_limit)))
 
     def debug_withhold_split(self, unit, spin_limit):
         """Failure-path test of the next split contraction (kbe_debug_withhold_split)."""

@@ -997,6 +997,14 @@ kbe_status kbe_set_split_planes(kbe_ctx* ctx, int keep) {
   return KBE_OK;
 }
 
+kbe_status kbe_debug_withhold_run(kbe_ctx* ctx, int barrier, long long spin_limit) {
+  if (!ctx) return KBE_EINVAL;
+  if (barrier < 0 || spin_limit < 1) return fail(ctx, KBE_EINVAL, "kbe_debug_withhold_run: barrier < 0 or spin_limit < 1");
+  ctx->dbg_run_withhold = barrier;
+  ctx->dbg_run_spin = spin_limit;
+  return KBE_OK;
+}
+
 kbe_status kbe_debug_withhold_split(kbe_ctx* ctx, long long unit, long long spin_limit) {
   if (!ctx) return KBE_EINVAL;
   if (unit < 0 || spin_limit < 1) return fail(ctx, KBE_EINVAL, "kbe_debug_withhold_split: unit < 0 or spin_limit < 1");
@@ -1104,7 +1112,10 @@ kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int preci
       h.corr0 = ctx->d_corr;
       h.pred0 = ctx->d_pred;
       h.bar = ctx->d_runbar;
-      h.spin = 1ll << 24;  // polls (at least 64 ns each after the first 256): about a second or more
+      h.spin = ctx->dbg_run_spin > 0 ? ctx->dbg_run_spin : 1ll << 24;  // polls: about a second or more
+      h.withhold = ctx->dbg_run_withhold;
+      ctx->dbg_run_spin = 0;  // one launch only
+      ctx->dbg_run_withhold = -1;
       h.P = P;
       while (h.nsteps < kRunMaxSteps && n <= n_last && (int64_t)(n + 1) * MM <= kRunMaxRow) {
         const int i = h.nsteps;

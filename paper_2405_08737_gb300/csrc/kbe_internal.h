@@ -115,6 +115,8 @@ struct kbe_ctx {
   // failure-path test of the next split contraction (kbe_debug_withhold_split)
   long long dbg_withhold = -1;
   long long dbg_spin = 0;
+  int dbg_run_withhold = -1;     // kbe_debug_withhold_run: next cooperative run launch only
+  long long dbg_run_spin = 0;
   int* d_status = nullptr;
   unsigned* d_runbar = nullptr;  // barrier counter of the cooperative small-row run kernel
   size_t part_bytes = 0;
@@ -308,6 +310,7 @@ struct RunSmallHost {
   const double* pred0;
   unsigned* bar;                 // one counter of device memory
   long long spin;
+  int withhold = -1;             // barrier at which block 0 leaves without arriving (failure-path test)
   int P, nsteps;
   int n[kRunMaxSteps], kn[kRunMaxSteps], chunk_len[kRunMaxSteps], nchunk[kRunMaxSteps];
   double field[kRunMaxSteps];

@@ -51,6 +51,7 @@ struct RunSmallArgs {
   const double* pred0;
   unsigned* bar;         // barrier counter, zero at launch
   long long spin;        // polls of a barrier wait before it gives up
+  int withhold;          // barrier at which block 0 leaves without arriving (failure-path test), or -1
   int P, nsteps;
   RunStep step[kRunMaxSteps];
 };
@@ -60,7 +61,9 @@ struct RunSmallArgs {
 // ordered before it by the block barrier, become visible with it) and polls
 // with acquire loads until every block has arrived.  Returns false when the
 // wait ran out (status bit set); the caller then leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned k, int* status, long long limit) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned k, int* status, long long limit,
+                                             int withhold) {
+  if ((int)k == withhold && blockIdx.x == 0) return false;  // the whole block leaves; the others' waits run out
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
       const StepArgs sa = row_args(a, st);
       const Span sp = span(row);
       for (int64_t lin = sp.lo; lin < sp.hi; lin += bs) rk::adams_entry(sa, lin, false);
-      if (!grid_barrier(a.bar, k++, status, a.spin)) return;
+      if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
     }
     const int64_t off = (int64_t)tri(n, 0) * MM;
     const double2* Lr = reinterpret_cast<const double2*>(a.base.L) + off;
@@ -163,14 +166,14 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
         const StepArgs sa = row_args(a, st);
         for (int ab = threadIdx.x; ab < MM; ab += blockDim.x) rk::fock_entry(sa, ab);
       }
-      if (!grid_barrier(a.bar, k++, status, a.spin)) return;
+      if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
       // B: history slice of row n (Eq. KBE2), chunk by chunk of the history index
       const Span sq = span(row * r.nchunk);
       for (int64_t q = sq.lo; q < sq.hi; q += bs) {
         const int chunk = (int)(q / row);
         rk::history_partial_entry<false>(p, q - (int64_t)chunk * row, chunk);
       }
-      if (!grid_barrier(a.bar, k++, status, a.spin)) return;
+      if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
       // C: I^<(lin) and I^>(lin), then F(lin)
       for (int64_t lin = sr.lo; lin < sr.hi; lin += bs) {
         const StepArgs sa = row_args(a, st);
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
         }
         ok &= rk::rhs_entry(sa, lin);
       }
-      if (!grid_barrier(a.bar, k++, status, a.spin)) return;
+      if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
       // D: corrector (and the next row's predictor)
       const bool pred_next = next && it == a.P - 1;
       for (int64_t lin = sr.lo; lin < sr.hi; lin += bs) {
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
           if (lin >= row - MM) rk::adams_entry(sn, lin + MM, false);
         }
       }
-      if (!grid_barrier(a.bar, k++, status, a.spin)) return;
+      if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
     }
   }
   if (!ok) atomicOr(status, kStatusNumeric);
@@ -226,6 +229,7 @@ cudaError_t launch_run_small(const RunSmallHost& h, cudaStream_t s, int* launche
   a.pred0 = h.pred0;
   a.bar = h.bar;
   a.spin = h.spin;
+  a.withhold = h.withhold;
   a.P = h.P;
   a.nsteps = h.nsteps;
   for (int i = 0; i < h.nsteps; ++i)

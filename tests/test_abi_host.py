@@ -98,4 +98,6 @@ def test_create_rejects_bad_sizes_without_touching_the_gpu(kbe):
     assert b"norb" in lib.kbe_last_error(None) or b"NULL" in lib.kbe_last_error(None)
     # calls on a NULL context are rejected
     assert lib.kbe_history_slice(None, 0, 0, None, None, None, None, None, None) == kbe.KBE_EINVAL
+    assert lib.kbe_debug_withhold_run(None, 0, 1) == kbe.KBE_EINVAL
+    assert lib.kbe_run_steps(None, 1, 1, 2, 0, None, None, None, None, None, None, None) == kbe.KBE_EINVAL
     assert lib.kbe_destroy(None) == kbe.KBE_OK

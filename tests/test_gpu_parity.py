@@ -462,3 +462,44 @@ def test_run_steps_cooperative_rows(kbe, M, n_t, launches):
     assert bool(torch.isfinite(runs[1].L).all())
     for r in runs:
         r.ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("barrier", [0, 6, 311, 10**6])
+def test_run_barrier_timeout_is_reported_and_the_context_recovers(kbe, barrier):
+    """The failure path of the cooperative run launch, with no fault: block
+    0 leaves at one device-wide barrier without arriving
+    (kbe_debug_withhold_run) and the waits give up after 4096 polls.  The
+    launch returns, the status reads KBE_ETIMEOUT, and the next run on the
+    same context is bitwise the step loop again; a barrier beyond the launch's
+    last (39 steps: 313 barriers) withholds nothing."""
+    import torch
+    M, n_t, seed = 2, 40, 5
+    t, order = W.grid(n_t, 0.05, 0.4, seed)
+    h = W.goe_h(M, seed)
+    U, v = np.linspace(0.5, 2.0, M), W.site_potential(M)
+    rho0 = W.half_filled_rho(h)
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, U, v, None)
+    ref = kbe.Run(ctx)
+    ref.init_uncorrelated(rho0)
+    for n in range(1, n_t):
+        ref.step(n, P=2)
+    ctx.sync_status()
+    run = kbe.Run(ctx)
+    run.init_uncorrelated(rho0)
+    ctx.debug_withhold_run(barrier, 4096)
+    run.run_steps(1, n_t - 1, P=2)
+    if barrier < 313:
+        with pytest.raises(kbe.KBEError) as e:
+            ctx.sync_status()
+        assert e.value.status == kbe.KBE_ETIMEOUT
+        run.init_uncorrelated(rho0)
+        run.run_steps(1, n_t - 1, P=2)
+    ctx.sync_status()
+    for a, b in ((ref.L, run.L), (ref.R, run.R), (ref.F, run.F), (ref.I, run.I)):
+        assert torch.equal(a, b)
+    with pytest.raises(kbe.KBEError):
+        ctx.debug_withhold_run(-1, 4096)
+    ctx.close()
