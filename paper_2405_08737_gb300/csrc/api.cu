@@ -618,7 +618,9 @@ kbe_status kbe_create(int norb, int n_max, kbe_ctx** out) {
   if (e != cudaSuccess) { delete ctx; return fail(nullptr, KBE_ECUDA, std::string("kbe_create: ") + cudaGetErrorString(e)); }
   const size_t MM = (size_t)norb * norb;
   const size_t row = (size_t)n_max * MM;  // complex entries of one s-row
-  ctx->part_bytes = (3 + 2 * (size_t)kMaxSplit) * row * 16;
+  // prep rows and chunk partials of the FP64 slice (history_f64_split): small
+  // rows take up to kMaxSplitSmall chunks
+  ctx->part_bytes = (3 + 2 * (size_t)(row <= (size_t)kRunMaxRow ? kMaxSplitSmall : kMaxSplit)) * row * 16;
   if ((e = dev_alloc(&ctx->d_part, ctx->part_bytes / sizeof(double))) != cudaSuccess ||
       (e = dev_alloc(&ctx->d_wbar, (size_t)n_max)) != cudaSuccess ||
       (e = dev_alloc(&ctx->d_band, (size_t)n_max * (kMaxOrder + 1))) != cudaSuccess ||

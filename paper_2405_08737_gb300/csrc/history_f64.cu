@@ -28,6 +28,7 @@
 // times from L1 (once per a), the self-energy row stays L2-resident.
 
 #include <algorithm>
+#include <cmath>
 
 #include "row_kernels.cuh"
 
@@ -92,12 +93,26 @@ inline unsigned grid_for(int64_t n, int64_t cap) {
 // partials must fit the workspace.  A band of stored rows below n
 // contributes only history points m < band_hi: the chunks beyond them have
 // no work.  False when even one chunk does not fit.
+//
+// Rows of at most kRunMaxRow entries are latency-bound: every thread runs a
+// short chain of FP64 instructions (this part retires about 2 FP64 FMAs per
+// clock per SM), about 16 M per history point in the contraction and two
+// per chunk and component in the chunk sum, so the chunk length that
+// minimises the chain, sqrt((n+1) / (8M)) points, is taken, with up to
+// kMaxSplitSmall chunks while the items stay within one per thread of one
+// 256-thread block per SM (kbe_step and the cooperative run kernel of
+// kbe_run_steps take the same split).
 bool history_f64_split(int M, int n, size_t part_bytes, int band_hi, int* nchunk_out, int* chunk_len_out) {
   const int64_t row = (int64_t)(n + 1) * M * M;
   int64_t want = ((int64_t)sm_count() * 2048 + row - 1) / row;
   const int64_t len_target = std::max<int64_t>(1, (1 << 16) / (kHistBlock * 3 * M));
   want = std::max<int64_t>(want, (n + 1 + len_target - 1) / len_target);
   int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
+  if (row <= kRunMaxRow) {
+    const int len = std::max(1, (int)std::lround(std::sqrt((n + 1) / (8.0 * M))));
+    const int64_t cap = std::max<int64_t>(kMaxSplit, (int64_t)sm_count() * 256 / row);
+    nchunk = (int)std::min<int64_t>(std::min<int64_t>((n + 1 + len - 1) / len, cap), kMaxSplitSmall);
+  }
   if (nchunk > n + 1) nchunk = n + 1;
   const size_t prep_bytes = (size_t)3 * row * 16;
   while (nchunk > 1 && prep_bytes + (size_t)nchunk * 2 * row * 16 > part_bytes) --nchunk;

@@ -15,6 +15,7 @@ constexpr int kMaxOrder = KBE_MAX_ORDER;
 constexpr int kRing = KBE_RING_ROWS;
 constexpr int kMaxNorb = 64;
 constexpr int kMaxSplit = 16;      // largest split of the history index m
+constexpr int kMaxSplitSmall = 64; // ... for rows of at most kRunMaxRow entries (history_f64_split)
 constexpr int kWTab = kMaxOrder + 1;  // row stride of the stepper weight tables
 constexpr int kDenseMaxM = KBE_DENSE_MAX_NORB;  // largest norb of the dense-interaction self-energy
 
@@ -100,7 +101,7 @@ struct kbe_ctx {
   double* d_U = nullptr;      // M
   double* d_v = nullptr;      // M
   double* d_eps = nullptr;    // complex MxM (Fock matrix of the current row)
-  double* d_part = nullptr;   // split partials [kMaxSplit][2][n_max][M][M] complex
+  double* d_part = nullptr;   // FP64 slice workspace: prep rows, chunk partials [chunks][2][n_max][M][M] complex
   void* d_split = nullptr;    // split-precision workspace (digit planes of the small operands, partials)
   size_t split_bytes = 0;
   void* d_planes = nullptr;   // digit planes of the history (split path), allocated by the first split slice

@@ -340,5 +340,32 @@ __device__ __forceinline__ bool rhs_entry(const StepArgs& a, int64_t lin) {
   return isfinite(fl.x) && isfinite(fl.y) && isfinite(fg.x) && isfinite(fg.y);
 }
 
+// The same for one component s (0: F^<, 1: F^>) of entry lin: the same
+// operations in the same order as that component's in rhs_entry, so the
+// value is bitwise rhs_entry's; returns false on a non-finite value.
+__device__ __forceinline__ bool rhs_entry_s(const StepArgs& a, int64_t lin, int s) {
+  const int M = a.M, MM = M * M, n = a.n;
+  const int c = (int)(lin / MM), ab = (int)(lin - (int64_t)c * MM);
+  const int ia = ab / M, ib = ab - ia * M;
+  const double* Lb = a.L + tri(n, c) * MM * 2;
+  const double* Rb = a.R + tri(n, c) * MM * 2;
+  double2 acc = ldd(a.I + (((int64_t)s * (n + 1) + c) * MM + ab) * 2);
+  for (int x = 0; x < M; ++x) {
+    const double2 e = ldd(a.eps + 2 * (ia * M + x));
+    const double2 l = ldd(Lb + 2 * (x * M + ib));
+    double gr = l.x, gi = l.y;
+    if (s) {
+      const double2 r = ldd(Rb + 2 * (x * M + ib));
+      gr = r.x + l.x;
+      gi = r.y + l.y;
+    }
+    acc.x = fma(e.x, gr, acc.x); acc.x = fma(-e.y, gi, acc.x);
+    acc.y = fma(e.x, gi, acc.y); acc.y = fma(e.y, gr, acc.y);
+  }
+  const double2 f = make_double2(acc.y, -acc.x);
+  std2(const_cast<double*>(ring_at(a, n, s, c, ab)), f);
+  return isfinite(f.x) && isfinite(f.y);
+}
+
 }  // namespace rk
 }  // namespace kbe

@@ -101,8 +101,8 @@ __device__ __forceinline__ StepArgs row_args(const RunSmallArgs& a, int st) {
 //      has just written) and the Fock matrix (reads only the diagonal block
 //      of row n, final since the last barrier);
 //   B  history partials, chunk by chunk of the history index;
-//   C  chunk sums of I^< and I^> of an entry, then that entry's right-hand
-//      side (which reads only those two sums of the slice);
+//   C  chunk sum of one component (I^< or I^>) of an entry, then that
+//      component of the entry's right-hand side (which reads only that sum);
 //   D  corrector; after the last sweep also the predictor of the next row of
 //      the launch: entry (c, ab) of row n+1 reads the entry (c, ab) of row n
 //      that the same thread has just corrected, and the new diagonal entry
@@ -174,20 +174,19 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
         rk::history_partial_entry<false>(p, q - (int64_t)chunk * row, chunk);
       }
       if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
-      // C: I^<(lin) and I^>(lin), then F(lin)
-      for (int64_t lin = sr.lo; lin < sr.hi; lin += bs) {
+      // C: chunk sum of one component of an entry, then that component's F
+      const Span sc = span(2 * row);
+      for (int64_t u = sc.lo; u < sc.hi; u += bs) {
         const StepArgs sa = row_args(a, st);
         if (r.nchunk > 1) {
-          const double2* part = reinterpret_cast<const double2*>(partials);
-          double2* out = reinterpret_cast<double2*>(a.I);
-          ok &= rk::history_reduce_entry(2 * row, r.nchunk, lin, part, out);
-          ok &= rk::history_reduce_entry(2 * row, r.nchunk, row + lin, part, out);
+          ok &= rk::history_reduce_entry(2 * row, r.nchunk, u, reinterpret_cast<const double2*>(partials),
+                                         reinterpret_cast<double2*>(a.I));
         } else {
-          const double2 x = reinterpret_cast<const double2*>(a.I)[lin];
-          const double2 y = reinterpret_cast<const double2*>(a.I)[row + lin];
-          ok &= isfinite(x.x) && isfinite(x.y) && isfinite(y.x) && isfinite(y.y);
+          const double2 x = reinterpret_cast<const double2*>(a.I)[u];
+          ok &= isfinite(x.x) && isfinite(x.y);
         }
-        ok &= rk::rhs_entry(sa, lin);
+        const int comp = u >= row ? 1 : 0;
+        ok &= rk::rhs_entry_s(sa, u - comp * row, comp);
       }
       if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
       // D: corrector (and the next row's predictor)
