@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--no-runs", action="store_true", help="skip the whole-run measurements")
     ap.add_argument("--sharded", action="store_true",
                     help="time the row-band sharded step (the N-GPU line) also on one GPU")
+    ap.add_argument("--profile-run", default=None, choices=["dimer_m2_n64"],
+                    help="only the FP64 whole run of this workload, twice, with one JSON line (the launches a "
+                         "profiler captures)")
     ap.add_argument("--profile-slice", default=None, choices=["fp64", "split", "split-fused", "df64"],
                     help="only run three history slices of row n_t - 1 with this contraction (a small case "
                          "for ncu with --n-t; split-fused: the split path without its plane buffer) and exit")
@@ -1119,11 +1122,43 @@ def profile_slice(kbe, args):
                       "contraction_ms": round(ms / max(k, 1), 4)}))
 
 
+def profile_run(kbe, args):
+    """The FP64 whole run of a small workload (every step in one
+    kbe_run_steps call, the cooperative run kernel), twice, then one JSON
+    line with the second run's duration."""
+    import torch
+    import workloads as W
+    cfg = W.CONFIGS[args.profile_run]
+    M, n_t = cfg["M"], cfg["n_t"]
+    t, order = W.grid(n_t, cfg["dt0"], cfg["sig"], args.seed)
+    h, U, v, pulse = W.build_model(cfg, args.seed)
+    ctx = kbe.Context(M, n_t)
+    ctx.set_grid(t, order)
+    ctx.set_model(h, U, v, pulse)
+    run = kbe.Run(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        run.init_uncorrelated(W.half_filled_rho(h))
+        e0.record()
+        run.run_steps(1, n_t - 1, P=args.P)
+        launches = ctx.last_launch_count
+        e1.record()
+        torch.cuda.synchronize()
+    ctx.sync_status()
+    print(json.dumps({"profile_run": args.profile_run, "steps": n_t - 1, "launches": launches,
+                      "ms": round(e0.elapsed_time(e1), 3)}))
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
     if args.impl == "reference":
         return main_reference(args, rank, world)
+    if args.profile_run:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import paper_2405_08737_gb300 as kbe
+        return profile_run(kbe, args)
     if args.profile_slice:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

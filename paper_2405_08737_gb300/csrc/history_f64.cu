@@ -94,11 +94,12 @@ inline unsigned grid_for(int64_t n, int64_t cap) {
 // contributes only history points m < band_hi: the chunks beyond them have
 // no work.  False when even one chunk does not fit.
 //
-// Rows of at most kRunMaxRow entries are latency-bound: every thread runs a
-// short chain of FP64 instructions (this part retires about 2 FP64 FMAs per
-// clock per SM), about 16 M per history point in the contraction and two
-// per chunk and component in the chunk sum, so the chunk length that
-// minimises the chain, sqrt((n+1) / (8M)) points, is taken, with up to
+// Rows of at most kRunMaxRow entries are latency-bound: a phase lasts as
+// long as its longest per-thread chain of dependent loads and FP64
+// operations (the FP64 pipe measured 6% busy over the small-row run kernel),
+// about 16 M operations per history point in the contraction and two per
+// chunk and component in the chunk sum, so the chunk length that minimises
+// the two chains together, sqrt((n+1) / (8M)) points, is taken, with up to
 // kMaxSplitSmall chunks while the items stay within one per thread of one
 // 256-thread block per SM (kbe_step and the cooperative run kernel of
 // kbe_run_steps take the same split).

@@ -111,12 +111,11 @@ __device__ __forceinline__ StepArgs row_args(const RunSmallArgs& a, int st) {
 // The first step of a launch starts with its own predictor phase.
 // Work items [0, total) of a phase: block b takes the contiguous span
 // [b per, (b+1) per), per = ceil(total / blocks), its threads consecutive
-// items of it.  On this part an SM retires about 2 FP64 FMAs per clock, and
-// a phase of a small row is a short chain of FP64 instructions per thread:
-// the rows' items are spread over every SM, packed into as few warps of each
-// as they fill (a warp-wide FP64 instruction costs about the same with few
-// active lanes as with all 32, measured: spreading a block's items over its
-// eight warps made the contraction phase 1.3x slower).
+// items of it, so a small row's items are spread over every SM and packed
+// into as few warps of each as they fill.  (A phase is bound by its longest
+// per-thread chain of dependent loads and FP64 operations; spreading a
+// block's items over all eight of its warps was measured 1.3x slower in the
+// contraction phase.)
 struct Span {
   int64_t lo, hi;
 };
