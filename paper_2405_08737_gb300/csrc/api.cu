@@ -1093,8 +1093,12 @@ kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int preci
   if (!ctx) return KBE_EINVAL;
   ctx->last_launches = 0;
   if (n_first < 1 || n_last < n_first) return fail(ctx, KBE_EINVAL, "kbe_run_steps: need 1 <= n_first <= n_last");
-  kbe_status st = check_step_call(ctx, n_last, P, precision, L, R, Sl, Sg, I_work, F_ring);
+  kbe_status st = check_row_call(ctx, n_last);  // the whole range on the grid
   if (st != KBE_OK) return st;
+  // the rest as kbe_step of the first row (with adaptive orders: the rows in order from the next one)
+  st = check_step_call(ctx, n_first, P, precision, L, R, Sl, Sg, I_work, F_ring);
+  if (st != KBE_OK) return st;
+  if (ctx->adaptive_K > 0) ctx->adaptive_rows = n_last + 1;  // the rows above n_first are stepped here
   int total = 0;
   // Plain FP64 steps with the local interaction and fixed orders: runs of
   // small rows go to the cooperative kernel, up to kRunMaxSteps rows per launch.

@@ -503,3 +503,48 @@ def test_run_barrier_timeout_is_reported_and_the_context_recovers(kbe, barrier):
     with pytest.raises(kbe.KBEError):
         ctx.debug_withhold_run(-1, 4096)
     ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["P1", "P3", "dense", "adaptive", "profiling"])
+def test_run_steps_other_settings(kbe, mode):
+    """kbe_run_steps is bitwise the step loop with one and three sweeps per
+    step (the cooperative kernel), and with the settings under which it keeps
+    the per-kernel step: a dense interaction, adaptive history orders (the
+    chosen orders equal too) and profiling."""
+    import torch
+    M, n_t, seed = 2, 30, 8
+    P = {"P1": 1, "P3": 3}.get(mode, 2)
+    t, order = W.grid(n_t, 0.05, 0.4, seed)
+    h = W.goe_h(M, seed)
+    U, v = np.linspace(0.5, 2.0, M), W.site_potential(M)
+    pulse = dict(W.PULSE_CHAIN, t0=float(t[n_t // 2]), sigma=0.3)
+    runs = []
+    for one_call in (False, True):
+        ctx = kbe.Context(M, n_t)
+        ctx.set_grid(t, order)
+        ctx.set_model(h, U, v, pulse)
+        if mode == "dense":
+            ctx.set_interaction(W.coulomb_tensor(M, 2, U=1.3))
+        elif mode == "adaptive":
+            ctx.set_adaptive_orders(4)
+        elif mode == "profiling":
+            ctx.set_profiling(True)
+        run = kbe.Run(ctx)
+        run.init_uncorrelated(W.half_filled_rho(h))
+        if one_call:
+            run.run_steps(1, n_t - 1, P=P)
+        else:
+            for n in range(1, n_t):
+                run.step(n, P=P)
+        ctx.sync_status()
+        runs.append(run)
+    for a, b in ((runs[0].L, runs[1].L), (runs[0].R, runs[1].R), (runs[0].F, runs[1].F), (runs[0].I, runs[1].I)):
+        assert torch.equal(a, b)
+    if mode == "adaptive":
+        assert np.array_equal(runs[0].ctx.history_orders(n_t), runs[1].ctx.history_orders(n_t))
+    if mode == "profiling":
+        k, ms = runs[1].ctx.read_profiling()
+        assert k >= (n_t - 1) * P and ms > 0  # one record per sweep's contraction (and the start row's)
+    for r in runs:
+        r.ctx.close()
