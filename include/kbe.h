@@ -283,7 +283,10 @@ kbe_status kbe_step(kbe_ctx* ctx, int n, int P, int precision, void* L, void* R,
  * run up to 64 at a time in one cooperative launch (one block per SM, a
  * device-wide barrier with a bounded wait between the phases of a step; a
  * wait that runs out is reported as KBE_ETIMEOUT by kbe_sync_status); the
- * rows, slices and ring are bitwise kbe_step's.  Errors as kbe_step; on a
+ * rows, slices and ring are bitwise kbe_step's.  Where the device refuses
+ * the cooperative launch (fewer SMs available to the process than the
+ * device has), those rows and all later ones on the context take
+ * kbe_step's kernels instead, with the same results.  Errors as kbe_step; on a
  * launch error the rows before the failing launch are stepped. */
 kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int precision, void* L, void* R,
                          void* S_less, void* S_great, void* I_work, void* F_ring, void* stream);

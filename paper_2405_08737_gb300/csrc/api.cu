@@ -1103,7 +1103,7 @@ kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int preci
   // Plain FP64 steps with the local interaction and fixed orders: runs of
   // small rows go to the cooperative kernel, up to kRunMaxSteps rows per launch.
   const bool coop = precision == KBE_FP64 && !ctx->dense && ctx->adaptive_K == 0 && !ctx->thermal &&
-                    !ctx->profiling;
+                    !ctx->profiling && !ctx->run_coop_refused;
   const int64_t MM = (int64_t)ctx->M * ctx->M;
   int n = n_first;
   while (n <= n_last && st == KBE_OK) {
@@ -1136,7 +1136,20 @@ kbe_status kbe_run_steps(kbe_ctx* ctx, int n_first, int n_last, int P, int preci
       int count = 0;
       const cudaError_t e = launch_run_small(h, (cudaStream_t)stream, &count);
       total += count;
-      if (e != cudaSuccess) st = cuda_fail(ctx, e, "kbe_run_steps: cooperative run launch");
+      if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+        // fewer SMs available than the device has (e.g. a partitioned GPU): these rows and all later ones
+        // take the per-kernel step (the launch error is not sticky)
+        cudaGetLastError();
+        ctx->run_coop_refused = true;
+        for (int i = 0; i < h.nsteps && st == KBE_OK; ++i) {
+          int c = 0;
+          st = step_impl(ctx, h.n[i], P, precision, L, R, Sl, Sg, I_work, F_ring, 0, kRing, (cudaStream_t)stream,
+                         nullptr, &c);
+          total += c;
+        }
+      } else if (e != cudaSuccess) {
+        st = cuda_fail(ctx, e, "kbe_run_steps: cooperative run launch");
+      }
       continue;
     }
     int count = 0;

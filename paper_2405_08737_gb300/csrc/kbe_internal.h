@@ -120,6 +120,7 @@ struct kbe_ctx {
   long long dbg_run_spin = 0;
   int* d_status = nullptr;
   unsigned* d_runbar = nullptr;  // barrier counter of the cooperative small-row run kernel
+  bool run_coop_refused = false; // the device refused the cooperative launch once: per-kernel steps only
   size_t part_bytes = 0;
   // reverse-mode workspace, allocated by the first adjoint call that needs it
   double* d_adj = nullptr;
