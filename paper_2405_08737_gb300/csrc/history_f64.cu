@@ -96,10 +96,12 @@ inline unsigned grid_for(int64_t n, int64_t cap) {
 //
 // Rows of at most kRunMaxRow entries are latency-bound: a phase lasts as
 // long as its longest per-thread chain of dependent loads and FP64
-// operations (the FP64 pipe measured 6% busy over the small-row run kernel),
-// about 16 M operations per history point in the contraction and two per
-// chunk and component in the chunk sum, so the chunk length that minimises
-// the two chains together, sqrt((n+1) / (8M)) points, is taken, with up to
+// operations (the FP64 pipe measured 6% busy over the small-row run kernel).
+// Measured on the dimer's rows: about 1.7 M us per history point of a chunk
+// in the contraction and 0.075 us per chunk in the chunk sum, so the chunk
+// length that minimises the two together, about sqrt((n+1) / (24M)) points,
+// is taken (chunks of 1, 2 and 4 points at n = 63, M = 2: whole run 2.43,
+// 2.50 and 2.65 ms), with up to
 // kMaxSplitSmall chunks while the items stay within one per thread of one
 // 256-thread block per SM (kbe_step and the cooperative run kernel of
 // kbe_run_steps take the same split).
@@ -110,7 +112,7 @@ bool history_f64_split(int M, int n, size_t part_bytes, int band_hi, int* nchunk
   want = std::max<int64_t>(want, (n + 1 + len_target - 1) / len_target);
   int nchunk = (int)(want < 1 ? 1 : (want > kMaxSplit ? kMaxSplit : want));
   if (row <= kRunMaxRow) {
-    const int len = std::max(1, (int)std::lround(std::sqrt((n + 1) / (8.0 * M))));
+    const int len = std::max(1, (int)std::lround(std::sqrt((n + 1) / (24.0 * M))));
     const int64_t cap = std::max<int64_t>(kMaxSplit, (int64_t)sm_count() * 256 / row);
     nchunk = (int)std::min<int64_t>(std::min<int64_t>((n + 1 + len - 1) / len, cap), kMaxSplitSmall);
   }

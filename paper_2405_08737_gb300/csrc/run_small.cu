@@ -9,7 +9,7 @@
 // -- for up to kRunMaxSteps consecutive rows, with device-wide barriers
 // instead of kernel boundaries, four per sweep: work that reads only what
 // the same thread wrote shares a phase (see the kernel).  Measured on the
-// 63-step dimer run: 2.7 ms against 5.4 ms for one kbe_step call per step;
+// 63-step dimer run: 2.55 ms against 5.46 ms for one kbe_step call per step;
 // a barrier costs about 1.2 us, and the phases are short chains of FP64
 // instructions per thread.  Every entry is computed by
 // the per-entry functions of the single-step kernels (row_kernels.cuh) with
