@@ -2,7 +2,7 @@
 
 Each translation unit is compiled in parallel, then linked into one shared
 library next to this file.  The CUDA runtime is linked statically, so the
-library only needs the driver at run time.
+library only needs the NVIDIA driver at run time.
 """
 import concurrent.futures
 import os

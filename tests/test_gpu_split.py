@@ -1,6 +1,6 @@
 """GPU parity of the split-precision history slice (KBE_SPLIT_BF16).
 
-Stated bound: 1e-8 relative in the max norm per slice (the benchmark spec's bound
+Stated bound: 1e-8 relative in the max norm per slice (the error bound set
 for the precision form) on physical histories; the scheme's own error is
 about 1e-9.  A fixed-point scheme's error is relative to the magnitude of
 the terms, not of their sum, so for random stress data (which cancel
