@@ -10,6 +10,13 @@
 namespace kbe {
 namespace rk {
 
+// floor(x / d) for 0 <= x, 0 < d: a 32-bit division where x fits (the
+// 64-bit one is a long instruction sequence on the latency path of small
+// rows); the same quotient either way.
+__device__ __forceinline__ int div_idx(int64_t x, int d) {
+  return x <= 0x7fffffff ? (int)((unsigned)x / (unsigned)d) : (int)(x / d);
+}
+
 struct Cd {
   double re, im;
 };
@@ -109,7 +116,7 @@ __device__ __forceinline__ void history_prep_entry(int MM, int n, int64_t e, con
                                                    const double* __restrict__ Sg, const WeightsView& w,
                                                    double* __restrict__ A1, double* __restrict__ Bl,
                                                    double* __restrict__ Bg) {
-  const int m = (int)(e / MM);
+  const int m = div_idx(e, MM);
   const double wn = w.at(n, m), wb = w.wbar[m];
   const double2 l = reinterpret_cast<const double2*>(Sl)[e];
   const double2 g = reinterpret_cast<const double2*>(Sg)[e];
@@ -143,7 +150,7 @@ template <bool kReadOnly = true>
 __device__ __forceinline__ void history_partial_entry(const PartialArgs& p, int64_t lin, int chunk) {
   const auto ld = [](const double* q) { return rk::ld<kReadOnly>(q); };
   const int M = p.M, MM = p.MM, n = p.n;
-  const int c = (int)(lin / MM);
+  const int c = kReadOnly ? (int)(lin / MM) : div_idx(lin, MM);  // the bulk kernels keep their code
   const int ab = (int)(lin - (int64_t)c * MM);
   const int a = ab / M, b = ab - a * M;
   const int m0 = chunk * p.chunk_len;
@@ -276,7 +283,7 @@ __device__ __forceinline__ void fock_entry(const StepArgs& a, int ab) {
 // lin = (c, a, b) of row n.
 __device__ __forceinline__ void adams_entry(const StepArgs& a, int64_t lin, bool corrector) {
   const int M = a.M, MM = M * M, n = a.n;
-  const int c = (int)(lin / MM), ab = (int)(lin - (int64_t)c * MM);
+  const int c = div_idx(lin, MM), ab = (int)(lin - (int64_t)c * MM);
   const int ia = ab / M, ib = ab - ia * M;
   const double* wt = corrector ? a.corr : a.pred;
   const int extra = corrector ? 1 : 0;  // the corrector also uses the node t_n
@@ -317,7 +324,7 @@ __device__ __forceinline__ void adams_entry(const StepArgs& a, int64_t lin, bool
 // returns false on a non-finite value.
 __device__ __forceinline__ bool rhs_entry(const StepArgs& a, int64_t lin) {
   const int M = a.M, MM = M * M, n = a.n;
-  const int c = (int)(lin / MM), ab = (int)(lin - (int64_t)c * MM);
+  const int c = div_idx(lin, MM), ab = (int)(lin - (int64_t)c * MM);
   const int ia = ab / M, ib = ab - ia * M;
   const double* Lb = a.L + tri(n, c) * MM * 2;
   const double* Rb = a.R + tri(n, c) * MM * 2;
@@ -345,7 +352,7 @@ __device__ __forceinline__ bool rhs_entry(const StepArgs& a, int64_t lin) {
 // value is bitwise rhs_entry's; returns false on a non-finite value.
 __device__ __forceinline__ bool rhs_entry_s(const StepArgs& a, int64_t lin, int s) {
   const int M = a.M, MM = M * M, n = a.n;
-  const int c = (int)(lin / MM), ab = (int)(lin - (int64_t)c * MM);
+  const int c = div_idx(lin, MM), ab = (int)(lin - (int64_t)c * MM);
   const int ia = ab / M, ib = ab - ia * M;
   const double* Lb = a.L + tri(n, c) * MM * 2;
   const double* Rb = a.R + tri(n, c) * MM * 2;

@@ -120,7 +120,7 @@ struct Span {
   int64_t lo, hi;
 };
 __device__ __forceinline__ Span span(int64_t total) {
-  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t per = rk::div_idx(total + gridDim.x - 1, (int)gridDim.x);
   const int64_t lo = (int64_t)blockIdx.x * per;
   return Span{lo + threadIdx.x, min(total, lo + per)};
 }
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
       // row), weight fold of the same entries, Fock matrix
       const Span sr = span(row);
       for (int64_t e = sr.lo; e < sr.hi; e += bs) {
-        const int blk = (int)(e / MM), ab = (int)(e - (int64_t)blk * MM);
+        const int blk = rk::div_idx(e, MM), ab = (int)(e - (int64_t)blk * MM);
         ok &= rk::sigma_entry(M, e, ab, blk == n, rk::sigma_uu(M, ab, a.base.U), Lr, Rr,
                               reinterpret_cast<double2*>(a.Sl_w), reinterpret_cast<double2*>(a.Sg_w));
         rk::history_prep_entry(MM, n, e, a.Sl, a.Sg, a.w, A1, Bl, Bg);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
       // B: history slice of row n (Eq. KBE2), chunk by chunk of the history index
       const Span sq = span(row * r.nchunk);
       for (int64_t q = sq.lo; q < sq.hi; q += bs) {
-        const int chunk = (int)(q / row);
+        const int chunk = rk::div_idx(q, (int)row);
         rk::history_partial_entry<false>(p, q - (int64_t)chunk * row, chunk);
       }
       if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
