@@ -416,7 +416,8 @@ def test_run_steps_is_the_step_loop(kbe, precision):
         ctx.sync_status()
         runs.append(run)
     for other in runs[1:]:
-        for a, b in ((runs[0].L, other.L), (runs[0].R, other.R), (runs[0].F, other.F), (runs[0].I, other.I)):
+        for a, b in ((runs[0].L, other.L), (runs[0].R, other.R), (runs[0].F, other.F), (runs[0].I, other.I),
+                     (runs[0].Sl, other.Sl), (runs[0].Sg, other.Sg)):
             assert torch.equal(a, b)
     ctx = runs[0].ctx
     for lo, hi in ((0, 5), (5, 4), (1, n_t)):
@@ -457,7 +458,8 @@ def test_run_steps_cooperative_rows(kbe, M, n_t, launches):
                 run.step(n, P=2)
         ctx.sync_status()
         runs.append(run)
-    for a, b in ((runs[0].L, runs[1].L), (runs[0].R, runs[1].R), (runs[0].F, runs[1].F), (runs[0].I, runs[1].I)):
+    for a, b in ((runs[0].L, runs[1].L), (runs[0].R, runs[1].R), (runs[0].F, runs[1].F), (runs[0].I, runs[1].I),
+                 (runs[0].Sl, runs[1].Sl), (runs[0].Sg, runs[1].Sg)):
         assert torch.equal(a, b)
     assert bool(torch.isfinite(runs[1].L).all())
     for r in runs:
@@ -498,7 +500,7 @@ def test_run_barrier_timeout_is_reported_and_the_context_recovers(kbe, barrier):
         run.init_uncorrelated(rho0)
         run.run_steps(1, n_t - 1, P=2)
     ctx.sync_status()
-    for a, b in ((ref.L, run.L), (ref.R, run.R), (ref.F, run.F), (ref.I, run.I)):
+    for a, b in ((ref.L, run.L), (ref.R, run.R), (ref.F, run.F), (ref.I, run.I), (ref.Sl, run.Sl), (ref.Sg, run.Sg)):
         assert torch.equal(a, b)
     with pytest.raises(kbe.KBEError):
         ctx.debug_withhold_run(-1, 4096)
@@ -539,7 +541,8 @@ def test_run_steps_other_settings(kbe, mode):
                 run.step(n, P=P)
         ctx.sync_status()
         runs.append(run)
-    for a, b in ((runs[0].L, runs[1].L), (runs[0].R, runs[1].R), (runs[0].F, runs[1].F), (runs[0].I, runs[1].I)):
+    for a, b in ((runs[0].L, runs[1].L), (runs[0].R, runs[1].R), (runs[0].F, runs[1].F), (runs[0].I, runs[1].I),
+                 (runs[0].Sl, runs[1].Sl), (runs[0].Sg, runs[1].Sg)):
         assert torch.equal(a, b)
     if mode == "adaptive":
         assert np.array_equal(runs[0].ctx.history_orders(n_t), runs[1].ctx.history_orders(n_t))
