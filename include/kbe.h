@@ -513,7 +513,8 @@ kbe_status kbe_debug_withhold_split(kbe_ctx* ctx, long long unit, long long spin
 /* Test support for the failure path of kbe_run_steps' cooperative launch
  * (no fault is involved): in the next such launch on this context, block 0
  * leaves the kernel at device-wide barrier number `barrier` (0 = the one
- * after the launch's first predictor, then four per sweep) without arriving,
+ * after the launch's first predictor, then four in the first sweep of each
+ * step and three in each later sweep) without arriving,
  * and every barrier wait gives up after spin_limit polls (instead of about
  * 2^24).  The other blocks' waits run out and they return; kbe_sync_status
  * reports KBE_ETIMEOUT and the rows of that launch are undefined.  Later

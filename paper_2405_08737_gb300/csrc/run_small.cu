@@ -7,8 +7,9 @@
 // same work -- predictor, then P sweeps of {self-energy row, weight fold,
 // history contraction, chunk sum, Fock matrix, right-hand side, corrector}
 // -- for up to kRunMaxSteps consecutive rows, with device-wide barriers
-// instead of kernel boundaries, four per sweep: work that reads only what
-// the same thread wrote shares a phase (see the kernel).  Measured on the
+// instead of kernel boundaries, seven per step of two sweeps: work that reads
+// only what the same thread, or the same CTA before a block barrier, wrote
+// shares a phase (see the kernel).  Measured on the
 // 63-step dimer run: 2.55 ms against 5.46 ms for one kbe_step call per step;
 // a barrier costs about 1.2 us, and the phases are short chains of FP64
 // instructions per thread.  Every entry is computed by
@@ -96,10 +97,16 @@ __device__ __forceinline__ StepArgs row_args(const RunSmallArgs& a, int st) {
   return sa;
 }
 
-// Phases of a step, separated by device-wide barriers (4 per sweep):
+// Phases of a step, separated by device-wide barriers (4 in the first sweep,
+// 3 in each later one):
 //   A  self-energy row n, its weight fold (a thread folds the entries it
 //      has just written) and the Fock matrix (reads only the diagonal block
-//      of row n, final since the last barrier);
+//      of row n); in the sweeps after the first, A shares a phase with the
+//      previous sweep's corrector D, separated by a block barrier: a block's
+//      span of row entries is a whole number of M x M blocks, so the entries
+//      that the self-energy and the Fock matrix read (an entry, the
+//      transposed entry of the diagonal block, the diagonal block itself)
+//      were corrected by the same CTA;
 //   B  history partials, chunk by chunk of the history index;
 //   C  chunk sum of one component (I^< or I^>) of an entry, then that
 //      component of the entry's right-hand side (which reads only that sum);
@@ -117,12 +124,19 @@ __device__ __forceinline__ StepArgs row_args(const RunSmallArgs& a, int st) {
 // block's items over all eight of its warps was measured 1.3x slower in the
 // contraction phase.)
 struct Span {
-  int64_t lo, hi;
+  int64_t lo, hi;  // this thread's first item, the end of the block's span
+  int64_t base;    // the block's first item
 };
 __device__ __forceinline__ Span span(int64_t total) {
   const int64_t per = rk::div_idx(total + gridDim.x - 1, (int)gridDim.x);
   const int64_t lo = (int64_t)blockIdx.x * per;
-  return Span{lo + threadIdx.x, min(total, lo + per)};
+  return Span{lo + threadIdx.x, min(total, lo + per), lo};
+}
+// ... with per rounded up to a multiple of `unit` (row entries: whole M x M blocks)
+__device__ __forceinline__ Span span_units(int64_t total, int unit) {
+  const int64_t per = (int64_t)rk::div_idx(rk::div_idx(total + gridDim.x - 1, (int)gridDim.x) + unit - 1, unit) * unit;
+  const int64_t lo = (int64_t)blockIdx.x * per;
+  return Span{lo + threadIdx.x, min(total, lo + per), lo};
 }
 
 __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_constant__ RunSmallArgs a) {
@@ -137,7 +151,7 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
     const int64_t row = (int64_t)(n + 1) * MM;  // complex entries of row n per component
     if (st == 0) {
       const StepArgs sa = row_args(a, st);
-      const Span sp = span(row);
+      const Span sp = span_units(row, MM);
       for (int64_t lin = sp.lo; lin < sp.hi; lin += bs) rk::adams_entry(sa, lin, false);
       if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
     }
@@ -151,21 +165,29 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
     rk::PartialArgs p{M, MM, n, r.chunk_len, a.base.L, a.base.R, a.Sl, a.Sg, A1, Bl, Bg, a.w,
                       r.nchunk == 1 ? a.I : partials};
     const bool next = st + 1 < a.nsteps;
-    for (int it = 0; it < a.P; ++it) {
-      // A: self-energy row n (Eq. SE; the diagonal block is block n of the
-      // row), weight fold of the same entries, Fock matrix
-      const Span sr = span(row);
+    const Span sr = span_units(row, MM);
+    // A: self-energy row n (Eq. SE; the diagonal block is block n of the
+    // row), weight fold of the same entries, Fock matrix (by the block whose
+    // span holds the diagonal block)
+    auto phase_a = [&]() {
       for (int64_t e = sr.lo; e < sr.hi; e += bs) {
         const int blk = rk::div_idx(e, MM), ab = (int)(e - (int64_t)blk * MM);
         ok &= rk::sigma_entry(M, e, ab, blk == n, rk::sigma_uu(M, ab, a.base.U), Lr, Rr,
                               reinterpret_cast<double2*>(a.Sl_w), reinterpret_cast<double2*>(a.Sg_w));
         rk::history_prep_entry(MM, n, e, a.Sl, a.Sg, a.w, A1, Bl, Bg);
       }
-      if (blockIdx.x == gridDim.x - 1) {  // the last block has the fewest row entries
+      if (sr.base <= row - MM && row - MM < sr.hi) {
+        // threads from the top of the block: those past the span's entries
+        // run it alongside the self-energy instead of after it
         const StepArgs sa = row_args(a, st);
-        for (int ab = threadIdx.x; ab < MM; ab += blockDim.x) rk::fock_entry(sa, ab);
+        for (int ab = (int)blockDim.x - 1 - (int)threadIdx.x; ab < MM; ab += blockDim.x) rk::fock_entry(sa, ab);
       }
-      if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
+    };
+    for (int it = 0; it < a.P; ++it) {
+      if (it == 0) {
+        phase_a();
+        if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
+      }
       // B: history slice of row n (Eq. KBE2), chunk by chunk of the history index
       const Span sq = span(row * r.nchunk);
       for (int64_t q = sq.lo; q < sq.hi; q += bs) {
@@ -188,7 +210,8 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
         ok &= rk::rhs_entry_s(sa, u - comp * row, comp);
       }
       if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
-      // D: corrector (and the next row's predictor)
+      // D: corrector, then the next sweep's A after a block barrier, or after
+      // the last sweep the next row's predictor
       const bool pred_next = next && it == a.P - 1;
       for (int64_t lin = sr.lo; lin < sr.hi; lin += bs) {
         rk::adams_entry(row_args(a, st), lin, true);
@@ -197,6 +220,10 @@ __global__ void __launch_bounds__(kRunThreads, 2) run_small_kernel(const __grid_
           rk::adams_entry(sn, lin, false);
           if (lin >= row - MM) rk::adams_entry(sn, lin + MM, false);
         }
+      }
+      if (it + 1 < a.P) {
+        __syncthreads();  // the CTA's corrected entries are visible to all of its threads
+        phase_a();
       }
       if (!grid_barrier(a.bar, k++, status, a.spin, a.withhold)) return;
     }

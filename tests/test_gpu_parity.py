@@ -467,14 +467,14 @@ def test_run_steps_cooperative_rows(kbe, M, n_t, launches):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("barrier", [0, 6, 311, 10**6])
+@pytest.mark.parametrize("barrier", [0, 6, 272, 10**6])
 def test_run_barrier_timeout_is_reported_and_the_context_recovers(kbe, barrier):
     """The failure path of the cooperative run launch, with no fault: block
     0 leaves at one device-wide barrier without arriving
     (kbe_debug_withhold_run) and the waits give up after 4096 polls.  The
     launch returns, the status reads KBE_ETIMEOUT, and the next run on the
     same context is bitwise the step loop again; a barrier beyond the launch's
-    last (39 steps: 313 barriers) withholds nothing."""
+    last (39 steps of two sweeps: 1 + 39 x 7 = 274 barriers) withholds nothing."""
     import torch
     M, n_t, seed = 2, 40, 5
     t, order = W.grid(n_t, 0.05, 0.4, seed)
@@ -493,7 +493,7 @@ def test_run_barrier_timeout_is_reported_and_the_context_recovers(kbe, barrier):
     run.init_uncorrelated(rho0)
     ctx.debug_withhold_run(barrier, 4096)
     run.run_steps(1, n_t - 1, P=2)
-    if barrier < 313:
+    if barrier < 274:
         with pytest.raises(kbe.KBEError) as e:
             ctx.sync_status()
         assert e.value.status == kbe.KBE_ETIMEOUT
