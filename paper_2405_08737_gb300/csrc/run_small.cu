@@ -9,11 +9,11 @@
 // -- for up to kRunMaxSteps consecutive rows, with device-wide barriers
 // instead of kernel boundaries, seven per step of two sweeps: work that reads
 // only what the same thread, or the same CTA before a block barrier, wrote
-// shares a phase (see the kernel).  Measured on the
-// 63-step dimer run: 2.55 ms against 5.46 ms for one kbe_step call per step;
-// a barrier costs about 1.2 us, and the phases are short chains of FP64
-// instructions per thread.  Every entry is computed by
-// the per-entry functions of the single-step kernels (row_kernels.cuh) with
+// shares a phase (see the kernel).  Measured on the 63-step dimer run:
+// 2.55 ms against 5.46 ms for one kbe_step call per step; a barrier costs
+// about 1.2 us, and each phase is a short per-thread chain of dependent
+// loads and FP64 operations.  Every entry is computed by the per-entry
+// functions of the single-step kernels (row_kernels.cuh) with
 // the same arguments and the same split of the history index, so the rows,
 // slices and ring are bitwise those of kbe_step.
 //
